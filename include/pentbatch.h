@@ -1,0 +1,213 @@
+/*
+ * pentbatch -- batched pentadiagonal factor-once / solve-many on one GB300 GPU.
+ *
+ * The method is the one of Gloster, O Naraigh and Pang, "cuPentBatch -- A
+ * batched pentadiagonal solver for NVIDIA GPUs" (arXiv 1807.07382): each
+ * system's matrix A = L R is factorised once without pivoting (Sec. 2.4,
+ * factorisation steps 1-14) and kept on the device; every later right-hand
+ * side then costs one forward substitution L g = f and one back substitution
+ * R x = g (Sec. 2.4, the steps for g and for x; the factor/solve split of
+ * Sec. 2.6).  The right-hand sides come from implicit hyperdiffusion steps
+ * (Sec. 2.2-2.3) and from alternating-direction steps of the 2D
+ * Cahn-Hilliard equation (Sec. 2.1 and the ADI remark of Sec. 4).
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ *  * Rows.  System s has n_s rows; row i (0-based, the paper's row i+1) of
+ *    system s is element off[s] + i of every per-row array, with
+ *    off[s] = n_0 + ... + n_{s-1} ("system-major" layout).  The library's own
+ *    layouts (interleaved, chunked) are private to the workspace.
+ *  * Band.  Row i reads a_i x_{i-2} + b_i x_{i-1} + c_i x_i + d_i x_{i+1}
+ *    + e_i x_{i+2} (Sec. 2.4, the general pentadiagonal A).  Entries that would
+ *    fall outside the matrix (a_0, a_1, b_0, d_{n-1}, e_{n-2}, e_{n-1}) are
+ *    never read.
+ *  * Memory.  Every pointer argument named d_* or documented as "device" is
+ *    device memory owned by the caller.  The library allocates no device
+ *    memory: the plan's workspace is caller-provided (pent_plan_bind).
+ *  * Asynchrony.  Every call except pent_plan_create/destroy, pent_plan_bind
+ *    and pent_get_info is asynchronous on the plan's bound stream, performs no
+ *    host synchronisation, allocation or host read-back, and may therefore be
+ *    captured into a CUDA graph.
+ *  * Errors.  Argument errors are detected on the host before anything is
+ *    launched and return PENT_EINVAL.  Numerical failures found on the device
+ *    (a zero or non-finite pivot, refinement that does not converge) are
+ *    recorded in a device info word and returned by pent_get_info.  Nothing
+ *    traps, aborts or throws.
+ */
+#ifndef PENTBATCH_H
+#define PENTBATCH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PENT_OK = 0,
+  PENT_EINVAL = -1,        /* invalid argument (host-side check, nothing launched) */
+  PENT_ESINGULAR = -2,     /* a pivot alpha_i was zero or not finite (from pent_get_info) */
+  PENT_ENOCONV = -3,       /* iterative refinement did not reach its tolerance (pent_get_info) */
+  PENT_ECUDA = -4,         /* a CUDA runtime call failed */
+  PENT_ENOTFACTORED = -5,  /* a solve was requested before any factorisation */
+  PENT_ENOTBOUND = -6      /* the plan has no workspace/stream bound */
+} pent_status;
+
+typedef enum {
+  PENT_F64 = 0,        /* FP64 factors, FP64 substitutions */
+  PENT_F32_REFINE = 1  /* FP32 factors and substitutions, refined against an extended-precision residual */
+} pent_precision;
+
+/* Residual arithmetic used by PENT_F32_REFINE (pent_plan_set_option key PENT_OPT_RESIDUAL). */
+typedef enum {
+  PENT_RESIDUAL_FF = 0,   /* residual f - A x in double-FP32 ("float-float") arithmetic on the FP32 units */
+  PENT_RESIDUAL_F64 = 1   /* residual f - A x in native FP64 */
+} pent_residual;
+
+typedef struct pent_plan pent_plan;
+
+/*
+ * Create a plan for `batch` independent systems.
+ *   n_per_system: host array of `batch` row counts (each >= 1), or NULL when
+ *                 every system has n_uniform rows.
+ *   shared_matrix: nonzero when all systems share one matrix (the paper's
+ *                 benchmark case, Sec. 3): the band/sigma arguments then
+ *                 describe a single system and n_per_system must be NULL.
+ *   precision:    PENT_F64 or PENT_F32_REFINE.
+ *   tune_cache:   path of a JSON autotuning cache to read (may be NULL).
+ * The plan is a host object; it records shapes and choices only.
+ * Errors: PENT_EINVAL for batch < 1, a row count < 1, shared_matrix with
+ * uneven sizes, or a NULL `plan`.
+ */
+pent_status pent_plan_create(pent_plan** plan, int64_t batch, const int64_t* n_per_system, int64_t n_uniform,
+                             int shared_matrix, pent_precision precision, const char* tune_cache);
+
+/* Bytes of device workspace the plan needs (factors, scratch, info word). */
+size_t pent_plan_workspace_bytes(const pent_plan* plan);
+
+/*
+ * Bind caller-owned device workspace (at least pent_plan_workspace_bytes,
+ * 256-byte aligned) and a CUDA stream (cudaStream_t, may be NULL for the
+ * legacy default stream).  Uploads the plan's small per-system tables with a
+ * synchronous copy; this call is not capture-safe.  The workspace must stay
+ * valid until the plan is destroyed or re-bound.
+ */
+pent_status pent_plan_bind(pent_plan* plan, void* d_workspace, void* cuda_stream);
+
+/*
+ * Tuning options (keys below); values are integers.  Unknown keys or values
+ * return PENT_EINVAL.  Changing PENT_OPT_THREADS_PER_SYSTEM after a
+ * factorisation returns PENT_EINVAL (the factor layout depends on it).
+ */
+enum {
+  PENT_OPT_THREADS_PER_SYSTEM = 1, /* 1 (one thread per system) or 32 (one warp per system, F32_REFINE) */
+  PENT_OPT_RESIDUAL = 2,           /* pent_residual */
+  PENT_OPT_BLOCK_WARPS = 3,        /* warps per CTA for the solve kernels (1..32) */
+  PENT_OPT_REFINE_TOL_LOG2 = 4     /* refinement stops when |r| <= 2^-tol * |f| (default 50) */
+};
+pent_status pent_plan_set_option(pent_plan* plan, int key, int64_t value);
+pent_status pent_plan_get_option(const pent_plan* plan, int key, int64_t* value);
+
+/*
+ * Factor every system's band (Sec. 2.4, factorisation steps 1-14) into the
+ * workspace.  a..e are device arrays of sum(n_s) doubles (n_0 doubles when the
+ * matrix is shared), system-major.  Resets the info word.  A zero or
+ * non-finite pivot is recorded (lowest system, its row) and reported by
+ * pent_get_info as PENT_ESINGULAR; that system's solutions are unspecified.
+ */
+pent_status pent_factor_batch(pent_plan* plan, const double* a, const double* b, const double* c, const double* d,
+                              const double* e);
+
+/*
+ * Build and factor A_s = I + sigma_s D4 for every system, where D4 is the
+ * centred fourth difference of Sec. 2.2 (interior band [1, -4, 6, -4, 1]) on
+ * a cell-centred grid with no-flux walls (ghost values mirror the cells next
+ * to the wall, so D4 = D2N^2 with D2N the no-flux second difference).
+ * d_sigma: device array of `batch` doubles (one when the matrix is shared),
+ * each > 0.  The plan keeps sigma for the refinement residual.
+ */
+pent_status pent_factor_hyperdiff(pent_plan* plan, const double* d_sigma);
+
+/*
+ * x_s = A_s^{-1} f_s for every system (Sec. 2.4: L g = f, then R x = g).
+ * f, x: device arrays of sum(n_s) doubles, system-major; x may alias f.
+ * max_refine: PENT_F32_REFINE only -- at most this many refinement steps
+ * (each: residual r = f - A x, correction A dx = r by the FP32 factors,
+ * x += dx); 0 returns the plain FP32 solution.  Ignored for PENT_F64.
+ */
+pent_status pent_solve_batch(pent_plan* plan, const double* f, double* x, int max_refine);
+
+/*
+ * `nsteps` implicit steps in place: x <- A^{-1} x, repeated.  The sequence is
+ * captured once into a CUDA graph (keyed by x and nsteps) and replayed on
+ * later calls; the factors stay resident.  The first call for a given key is
+ * therefore not capture-safe; later calls are single graph launches.
+ */
+pent_status pent_solve_steps(pent_plan* plan, double* x, int64_t nsteps, int max_refine);
+
+/*
+ * Adjoint solve y_s = A_s^{-T} f_s from the stored factors: A^T = R^T L^T, so
+ * R^T z = f (unit lower: z_i = f_i - gamma_{i-1} z_{i-1} - delta_{i-2} z_{i-2})
+ * then L^T y = z (y_i = (z_i - beta_{i+1} y_{i+1} - epsilon_{i+2} y_{i+2}) /
+ * alpha_i).  The transposed solve is not in the paper; it follows from its
+ * factors (Sec. 2.4, the definitions of L and R).  Same layout and aliasing
+ * rules as pent_solve_batch.  PENT_F64 plans only (others: PENT_EINVAL).
+ */
+pent_status pent_adjoint_solve_batch(pent_plan* plan, const double* f, double* x, int max_refine);
+
+/*
+ * dL/dsigma_s contribution of one implicit step: g_sigma[s] -= mu_s . (D4 x_s)
+ * for every system, with mu and x device arrays laid out like f.  Used by the
+ * differentiable time stepper (from A x^k = x^{k-1} and dA/dsigma = D4).
+ */
+pent_status pent_hyperdiff_sigma_grad(pent_plan* plan, const double* mu, const double* x, double* g_sigma);
+
+/*
+ * One alternating-direction step of the 2D Cahn-Hilliard equation on an
+ * ny x nx grid with no-flux walls, in place on C (device, row-major, x fastest):
+ *   rhs = mu L(C^3 - C) - sigma L(L C),  mu = dt/dx^2, sigma = gamma dt/dx^4,
+ *   (I + sigma D4_x)(I + sigma D4_y) dC = rhs,  C <- C + dC - mean(dC).
+ * L is the five-point Laplacian with the same wall reflection as D4.  The
+ * paper names ADI for 2D problems without giving a scheme (Sec. 4); this is
+ * the Douglas delta form of its semi-implicit step (Sec. 2.1).  Exact dC has
+ * zero mean; removing the mean of the computed dC keeps the total mass to
+ * rounding of C itself.
+ * px: a shared-matrix plan of ny systems of n = nx, factored by
+ *     pent_factor_hyperdiff with sigma; it also holds the step's scratch.
+ * py: a shared-matrix plan of nx systems of n = ny, factored likewise.
+ * Both must be bound to the same stream.  max_refine as in pent_solve_batch.
+ */
+pent_status adi_step_2d(pent_plan* px, pent_plan* py, double* C, int64_t nx, int64_t ny, double gamma, double dt,
+                        double dx, int max_refine);
+
+/* `nsteps` ADI steps, captured once into a CUDA graph and replayed. */
+pent_status adi_steps_2d(pent_plan* px, pent_plan* py, double* C, int64_t nx, int64_t ny, double gamma, double dt,
+                         double dx, int max_refine, int64_t nsteps);
+
+/*
+ * Synchronise the plan's stream and read the info word.  Returns PENT_OK,
+ * PENT_ESINGULAR (bad_system/bad_row give the lowest failing system and its
+ * row) or PENT_ENOCONV.  refine_steps_used: the largest number of refinement
+ * steps any system needed since the last factorisation.  Output pointers may
+ * be NULL.  Clears nothing.
+ */
+pent_status pent_get_info(pent_plan* plan, int64_t* bad_system, int64_t* bad_row, int* refine_steps_used);
+
+/* Reset the info word (asynchronous, capture-safe). */
+pent_status pent_clear_info(pent_plan* plan);
+
+/* Destroy a plan (host memory only; the workspace is the caller's). NULL is a no-op. */
+void pent_plan_destroy(pent_plan* plan);
+
+/* Static text for a status code. */
+const char* pent_status_string(pent_status status);
+
+/* Library version, e.g. "0.1.0". */
+const char* pent_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PENTBATCH_H */

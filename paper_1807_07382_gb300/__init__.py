@@ -1,0 +1,197 @@
+"""Batched pentadiagonal factor-once / solve-many on one GB300 GPU.
+
+Python binding of the C ABI in include/pentbatch.h.  Every step of the solve
+runs in the library's CUDA kernels; this module only marshals arguments.
+PyTorch supplies device memory (the plan's workspace and the caller's
+vectors) and the CUDA stream.  There is no CPU fallback: if the CUDA library
+is missing, or a tensor is not on a CUDA device, the calls raise.
+
+Method: Gloster, O Naraigh and Pang, "cuPentBatch -- A batched pentadiagonal
+solver for NVIDIA GPUs" (arXiv 1807.07382), Sec. 2.4 (LU without pivoting,
+forward and back substitution) and Sec. 2.6 (factor once, solve many).
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence
+
+from . import _lib
+from ._lib import (PENT_ENOCONV, PENT_ESINGULAR, PENT_F32_REFINE, PENT_F64, PENT_OK, PENT_OPT_BLOCK_WARPS,
+                   PENT_OPT_REFINE_TOL_LOG2, PENT_OPT_RESIDUAL, PENT_OPT_THREADS_PER_SYSTEM, PENT_RESIDUAL_F64,
+                   PENT_RESIDUAL_FF, PentError, check)
+
+__all__ = ["Plan", "PentError", "PENT_F64", "PENT_F32_REFINE", "PENT_RESIDUAL_FF", "PENT_RESIDUAL_F64",
+           "library_path", "load_library", "adi_step_2d", "adi_steps_2d"]
+
+__version__ = "0.1.0"
+
+
+def library_path():
+    return _lib.LIB_PATH
+
+
+def load_library():
+    return _lib.load()
+
+
+def _torch():
+    import torch  # imported lazily: the CPU-only checks load the library without touching CUDA
+    return torch
+
+
+def _dev_ptr(t, what: str, dtype=None) -> int:
+    torch = _torch()
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{what} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{what} must be a CUDA tensor (the library has no CPU path)")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{what} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    return t.data_ptr()
+
+
+class Plan:
+    """A batch of pentadiagonal systems, factored once on the device.
+
+    n:         int (every system has n rows) or a sequence of row counts.
+    batch:     number of systems (required when n is an int).
+    shared:    all systems share one matrix (band / sigma describe one system).
+    precision: PENT_F64 or PENT_F32_REFINE.
+    """
+
+    def __init__(self, n, batch: Optional[int] = None, shared: bool = False, precision: int = PENT_F64,
+                 device=None, stream=None, tune_cache: Optional[str] = None):
+        torch = _torch()
+        L = _lib.load()
+        self._L = L
+        self._h = ctypes.c_void_p()
+        if isinstance(n, int):
+            if batch is None:
+                raise ValueError("batch is required when n is an int")
+            nptr, n_uniform = None, int(n)
+            self.n = [int(n)] * int(batch)
+        else:
+            ns = [int(v) for v in n]
+            if batch is not None and batch != len(ns):
+                raise ValueError("batch does not match len(n)")
+            batch = len(ns)
+            self._narr = (ctypes.c_int64 * batch)(*ns)
+            nptr, n_uniform = self._narr, 0
+            self.n = ns
+        self.batch = int(batch)
+        self.shared = bool(shared)
+        self.precision = int(precision)
+        self.rows = sum(self.n)
+        check(L.pent_plan_create(ctypes.byref(self._h), self.batch, nptr, n_uniform, int(self.shared),
+                                 self.precision, tune_cache.encode() if tune_cache else None), "pent_plan_create")
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        nbytes = int(L.pent_plan_workspace_bytes(self._h))
+        self.workspace = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        check(L.pent_plan_bind(self._h, self.workspace.data_ptr(), ctypes.c_void_p(self.stream.cuda_stream)),
+              "pent_plan_bind")
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._L.pent_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(self._L.pent_plan_workspace_bytes(self._h))
+
+    # -- options
+    def set_option(self, key: int, value: int):
+        check(self._L.pent_plan_set_option(self._h, key, int(value)), "pent_plan_set_option")
+
+    def get_option(self, key: int) -> int:
+        v = ctypes.c_int64()
+        check(self._L.pent_plan_get_option(self._h, key, ctypes.byref(v)), "pent_plan_get_option")
+        return int(v.value)
+
+    # -- factorisation
+    def factor(self, a, b, c, d, e):
+        """Factor general bands (device float64 tensors, system-major)."""
+        torch = _torch()
+        ptrs = [_dev_ptr(t, name, torch.float64) for t, name in zip((a, b, c, d, e), "abcde")]
+        check(self._L.pent_factor_batch(self._h, *ptrs), "pent_factor_batch")
+
+    def factor_hyperdiff(self, sigma):
+        """Factor A_s = I + sigma_s D4 (no-flux) from device float64 sigma."""
+        torch = _torch()
+        self._sigma_ref = sigma
+        check(self._L.pent_factor_hyperdiff(self._h, _dev_ptr(sigma, "sigma", torch.float64)), "pent_factor_hyperdiff")
+
+    # -- solves
+    def solve(self, f, x=None, max_refine: int = 2):
+        """x_s = A_s^{-1} f_s; x may be f (in place)."""
+        torch = _torch()
+        if x is None:
+            x = torch.empty_like(f)
+        check(self._L.pent_solve_batch(self._h, _dev_ptr(f, "f", torch.float64), _dev_ptr(x, "x", torch.float64),
+                                       int(max_refine)), "pent_solve_batch")
+        return x
+
+    def solve_steps(self, x, nsteps: int, max_refine: int = 2):
+        """nsteps in-place implicit steps x <- A^{-1} x (one CUDA graph)."""
+        torch = _torch()
+        check(self._L.pent_solve_steps(self._h, _dev_ptr(x, "x", torch.float64), int(nsteps), int(max_refine)),
+              "pent_solve_steps")
+        return x
+
+    def adjoint_solve(self, f, x=None):
+        """y_s = A_s^{-T} f_s from the stored factors."""
+        torch = _torch()
+        if x is None:
+            x = torch.empty_like(f)
+        check(self._L.pent_adjoint_solve_batch(self._h, _dev_ptr(f, "f", torch.float64),
+                                               _dev_ptr(x, "x", torch.float64), 0), "pent_adjoint_solve_batch")
+        return x
+
+    def sigma_grad(self, mu, x, g_sigma):
+        """g_sigma[s] -= mu_s . (D4 x_s)."""
+        torch = _torch()
+        check(self._L.pent_hyperdiff_sigma_grad(self._h, _dev_ptr(mu, "mu", torch.float64),
+                                                _dev_ptr(x, "x", torch.float64),
+                                                _dev_ptr(g_sigma, "g_sigma", torch.float64)),
+              "pent_hyperdiff_sigma_grad")
+        return g_sigma
+
+    # -- diagnostics
+    def info(self):
+        """(status, bad_system, bad_row, refine_steps_used); synchronises the stream."""
+        bs, br, rs = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+        st = self._L.pent_get_info(self._h, ctypes.byref(bs), ctypes.byref(br), ctypes.byref(rs))
+        return int(st), int(bs.value), int(br.value), int(rs.value)
+
+    def clear_info(self):
+        check(self._L.pent_clear_info(self._h), "pent_clear_info")
+
+
+def adi_step_2d(px: Plan, py: Plan, C, gamma: float, dt: float, dx: float, max_refine: int = 0):
+    torch = _torch()
+    ny, nx = C.shape
+    check(_lib.load().adi_step_2d(px._h, py._h, _dev_ptr(C, "C", torch.float64), nx, ny, float(gamma), float(dt),
+                                  float(dx), int(max_refine)), "adi_step_2d")
+    return C
+
+
+def adi_steps_2d(px: Plan, py: Plan, C, gamma: float, dt: float, dx: float, nsteps: int, max_refine: int = 0):
+    torch = _torch()
+    ny, nx = C.shape
+    check(_lib.load().adi_steps_2d(px._h, py._h, _dev_ptr(C, "C", torch.float64), nx, ny, float(gamma), float(dt),
+                                   float(dx), int(max_refine), int(nsteps)), "adi_steps_2d")
+    return C

@@ -1,0 +1,355 @@
+// FP64 factorisation, substitution and adjoint kernels (one thread per system).
+//
+// Layout.  Systems are visited in "sorted position" order q = 0..ngroups*32-1
+// (perm[q] is the system, longest first, so a warp's 32 systems have similar
+// lengths).  Warp k owns the 32 systems q = 32k..32k+31 and walks the rows of
+// all of them in lock step; record row R = goff[k] + r holds row r of those 32
+// systems next to each other, so every factor load and every scratch store of
+// the warp is one contiguous, coalesced 256-byte access.  This is the
+// interleaved one-thread-per-system layout of the paper (Sec. 2.6), applied per
+// group of 32 instead of across the whole batch, which keeps uneven lengths
+// cheap to pad.
+#include <cmath>
+#include <cstdint>
+
+#include "internal.cuh"
+
+namespace pent {
+namespace {
+
+// Weights of the centred fourth difference [1, -4, 6, -4, 1] (Sec. 2.2) on row
+// i of an n-row cell-centred grid with no-flux walls: an index that falls
+// outside 0..n-1 is reflected about the wall (-1 -> 0, -2 -> 1, n -> n-1,
+// n+1 -> n-2, repeatedly for very short grids) and its weight is added to the
+// reflected column.  w[k] is the coefficient of x_{i+k-2}.
+__device__ __forceinline__ void d4_weights(int64_t i, int64_t n, double w[5]) {
+  const double st[5] = {1.0, -4.0, 6.0, -4.0, 1.0};
+#pragma unroll
+  for (int k = 0; k < 5; ++k) w[k] = 0.0;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    int64_t j = i + k - 2;
+    while (j < 0 || j >= n) j = (j < 0) ? (-1 - j) : (2 * n - 1 - j);
+    w[j - i + 2] += st[k];
+  }
+}
+
+__device__ __forceinline__ void report_bad_pivot(unsigned long long* info, int64_t s, int64_t r) {
+  const unsigned long long key = ((unsigned long long)s << 32) | (unsigned long long)(uint32_t)r;
+  atomicMin(info, key);
+}
+
+// Factor one system per thread (Sec. 2.4, factorisation steps 1-14, written as
+// the generic row step with out-of-range quantities zero) and write its FP64
+// records.  Rows after a failed pivot and padding rows get identity records
+// (1/alpha = 1, all couplings 0), so later solves stay finite.
+__global__ void k_factor64(DevPlan P, const double* __restrict__ a, const double* __restrict__ b,
+                           const double* __restrict__ c, const double* __restrict__ d, const double* __restrict__ e,
+                           const double* __restrict__ sigma, F64Factors F) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nslots = P.shared ? 1 : P.ngroups * kWarp;
+  if (q >= nslots) return;
+  const int64_t s = P.shared ? 0 : P.perm[q];
+  const int64_t k = q / kWarp;
+  const int lane = (int)(q % kWarp);
+  const int64_t Lg = P.shared ? P.n_shared : P.glen[k];
+  const int64_t R0 = P.shared ? 0 : P.goff[k];
+  auto fwd_at = [&](int64_t r, int p) -> double& {
+    return P.shared ? F.fwd[r * 3 + p] : F.fwd[((R0 + r) * 3 + p) * kWarp + lane];
+  };
+  auto bwd_at = [&](int64_t r, int p) -> double& {
+    return P.shared ? F.bwd[r * 2 + p] : F.bwd[((R0 + r) * 2 + p) * kWarp + lane];
+  };
+  int64_t r = 0;
+  if (s >= 0) {
+    const int64_t n = P.shared ? P.n_shared : P.n[s];
+    const int64_t o = P.shared ? 0 : P.off[s];
+    const double sg = sigma ? sigma[P.shared ? 0 : s] : 0.0;
+    double gam2 = 0.0, del2 = 0.0, gam1 = 0.0, del1 = 0.0;  // gamma/delta of rows r-2, r-1
+    for (; r < n; ++r) {
+      double ar, br, cr, dr, er;
+      if (sigma) {
+        double w[5];
+        d4_weights(r, n, w);
+        ar = sg * w[0];
+        br = sg * w[1];
+        cr = 1.0 + sg * w[2];
+        dr = sg * w[3];
+        er = sg * w[4];
+      } else {
+        cr = c[o + r];
+        ar = (r >= 2) ? a[o + r] : 0.0;
+        br = (r >= 1) ? b[o + r] : 0.0;
+        dr = (r + 1 < n) ? d[o + r] : 0.0;
+        er = (r + 2 < n) ? e[o + r] : 0.0;
+      }
+      if (r < 2) ar = 0.0;
+      if (r < 1) br = 0.0;
+      if (r + 1 >= n) dr = 0.0;
+      if (r + 2 >= n) er = 0.0;
+      const double beta = br - ar * gam2;
+      const double alpha = cr - ar * del2 - beta * gam1;
+      if (!(alpha != 0.0) || !isfinite(alpha)) {
+        report_bad_pivot(P.info, s, r);
+        break;
+      }
+      const double gamma = (dr - beta * del1) / alpha;
+      const double delta = er / alpha;
+      fwd_at(r, 0) = 1.0 / alpha;
+      fwd_at(r, 1) = beta / alpha;
+      fwd_at(r, 2) = ar / alpha;
+      bwd_at(r, 0) = gamma;
+      bwd_at(r, 1) = delta;
+      gam2 = gam1;
+      del2 = del1;
+      gam1 = gamma;
+      del1 = delta;
+    }
+  }
+  for (; r < Lg; ++r) {
+    fwd_at(r, 0) = 1.0;
+    fwd_at(r, 1) = 0.0;
+    fwd_at(r, 2) = 0.0;
+    bwd_at(r, 0) = 0.0;
+    bwd_at(r, 1) = 0.0;
+  }
+}
+
+struct Lane {
+  int64_t n;   // rows of this lane's system (0 for an empty lane)
+  int64_t fo;  // first row of the system in f/x
+  int64_t Lg;  // rows walked by the warp
+  int64_t R0;  // first record row of the warp
+};
+
+template <bool SHARED>
+__device__ __forceinline__ Lane lane_setup(const DevPlan& P, int64_t k, int lane) {
+  Lane L;
+  const int64_t q = k * kWarp + lane;
+  if (SHARED) {
+    L.n = (q < P.batch) ? P.n_shared : 0;
+    L.fo = (q < P.batch) ? q * P.n_shared : 0;
+    L.Lg = P.n_shared;
+    L.R0 = k * P.n_shared;
+  } else {
+    const int s = P.perm[q];
+    L.n = (s >= 0) ? P.n[s] : 0;
+    L.fo = (s >= 0) ? P.off[s] : 0;
+    L.Lg = P.glen[k];
+    L.R0 = P.goff[k];
+  }
+  return L;
+}
+
+template <bool SHARED>
+__device__ __forceinline__ int64_t fwd_idx(const Lane& L, int64_t r, int p, int lane) {
+  return SHARED ? r * 3 + p : ((L.R0 + r) * 3 + p) * kWarp + lane;
+}
+template <bool SHARED>
+__device__ __forceinline__ int64_t bwd_idx(const Lane& L, int64_t r, int p, int lane) {
+  return SHARED ? r * 2 + p : ((L.R0 + r) * 2 + p) * kWarp + lane;
+}
+
+// x = A^{-1} f by the forward substitution L g = f and the back substitution
+// R x = g (Sec. 2.4).  With the stored 1/alpha, beta/alpha, epsilon/alpha:
+//   g_i = (1/alpha_i) f_i - (epsilon_i/alpha_i) g_{i-2} - (beta_i/alpha_i) g_{i-1}
+//   x_i = g_i - gamma_i x_{i+1} - delta_i x_{i+2}
+// g goes to the warp's scratch rows (coalesced) and comes back in reverse.
+// Loads run U rows ahead of the arithmetic (register double buffering) so each
+// lane keeps several independent memory requests in flight.
+template <bool SHARED, int U>
+__global__ void __launch_bounds__(256) k_solve64(DevPlan P, F64Factors F, const double* f, double* x,
+                                                 double* __restrict__ gscr) {
+  const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kWarp;
+  if (k >= P.ngroups) return;
+  const int lane = threadIdx.x & (kWarp - 1);
+  const Lane L = lane_setup<SHARED>(P, k, lane);
+  const double* __restrict__ fwd = F.fwd;
+  const double* __restrict__ bwd = F.bwd;
+
+  // ---- forward: L g = f ----
+  double ca[U], cb[U], ce[U], cf[U];
+  double na[U], nb[U], ne[U], nf[U];
+  auto load_f = [&](int64_t r0, double* A, double* B, double* E, double* Fv) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t r = r0 + u;
+      if (r < L.Lg) {
+        A[u] = __ldg(fwd + fwd_idx<SHARED>(L, r, 0, lane));
+        B[u] = __ldg(fwd + fwd_idx<SHARED>(L, r, 1, lane));
+        E[u] = __ldg(fwd + fwd_idx<SHARED>(L, r, 2, lane));
+        Fv[u] = (r < L.n) ? f[L.fo + r] : 0.0;
+      }
+    }
+  };
+  double g1 = 0.0, g2 = 0.0;
+  load_f(0, ca, cb, ce, cf);
+  for (int64_t r0 = 0; r0 < L.Lg; r0 += U) {
+    if (r0 + U < L.Lg) load_f(r0 + U, na, nb, ne, nf);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t r = r0 + u;
+      if (r < L.Lg) {
+        const double g = fma(-cb[u], g1, fma(-ce[u], g2, ca[u] * cf[u]));
+        gscr[(L.R0 + r) * kWarp + lane] = g;
+        g2 = g1;
+        g1 = g;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      ca[u] = na[u];
+      cb[u] = nb[u];
+      ce[u] = ne[u];
+      cf[u] = nf[u];
+    }
+  }
+
+  // ---- back: R x = g ----
+  double cg[U], cd[U], cG[U];
+  double ng[U], nd[U], nG[U];
+  auto load_b = [&](int64_t r0, double* Ga, double* De, double* Gv) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t r = r0 - u;
+      if (r >= 0) {
+        Ga[u] = __ldg(bwd + bwd_idx<SHARED>(L, r, 0, lane));
+        De[u] = __ldg(bwd + bwd_idx<SHARED>(L, r, 1, lane));
+        Gv[u] = gscr[(L.R0 + r) * kWarp + lane];
+      }
+    }
+  };
+  double x1 = 0.0, x2 = 0.0;
+  load_b(L.Lg - 1, cg, cd, cG);
+  for (int64_t r0 = L.Lg - 1; r0 >= 0; r0 -= U) {
+    if (r0 - U >= 0) load_b(r0 - U, ng, nd, nG);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t r = r0 - u;
+      if (r >= 0) {
+        const double xv = fma(-cg[u], x1, fma(-cd[u], x2, cG[u]));
+        if (r < L.n) x[L.fo + r] = xv;
+        x2 = x1;
+        x1 = xv;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      cg[u] = ng[u];
+      cd[u] = nd[u];
+      cG[u] = nG[u];
+    }
+  }
+}
+
+// y = A^{-T} f from the stored factors.  With L = D_alpha Lhat (Lhat unit lower
+// with beta/alpha, epsilon/alpha) and A = L R:  A^T = R^T Lhat^T D_alpha, so
+//   R^T z = f:      z_i = f_i - gamma_{i-1} z_{i-1} - delta_{i-2} z_{i-2}       (ascending)
+//   Lhat^T w = z:   w_i = z_i - (beta/alpha)_{i+1} w_{i+1} - (eps/alpha)_{i+2} w_{i+2} (descending)
+//   y_i = (1/alpha_i) w_i.
+// Each sweep reads one record row per step; the couplings of later rows are
+// carried in registers.
+template <bool SHARED>
+__global__ void __launch_bounds__(256) k_adjoint64(DevPlan P, F64Factors F, const double* f, double* y,
+                                                   double* __restrict__ zscr) {
+  const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kWarp;
+  if (k >= P.ngroups) return;
+  const int lane = threadIdx.x & (kWarp - 1);
+  const Lane L = lane_setup<SHARED>(P, k, lane);
+  const double* __restrict__ fwd = F.fwd;
+  const double* __restrict__ bwd = F.bwd;
+  // ascending: z
+  double z1 = 0.0, z2 = 0.0;       // z_{i-1}, z_{i-2}
+  double gam_m1 = 0.0, del_m1 = 0.0, del_m2 = 0.0;  // gamma_{i-1}, delta_{i-1}, delta_{i-2}
+  for (int64_t r = 0; r < L.Lg; ++r) {
+    const double fr = (r < L.n) ? f[L.fo + r] : 0.0;
+    const double z = fma(-gam_m1, z1, fma(-del_m2, z2, fr));
+    zscr[(L.R0 + r) * kWarp + lane] = z;
+    z2 = z1;
+    z1 = z;
+    del_m2 = del_m1;
+    gam_m1 = __ldg(bwd + bwd_idx<SHARED>(L, r, 0, lane));
+    del_m1 = __ldg(bwd + bwd_idx<SHARED>(L, r, 1, lane));
+  }
+  // descending: w, y
+  double w1 = 0.0, w2 = 0.0;          // w_{i+1}, w_{i+2}
+  double bp_p1 = 0.0, ep_p1 = 0.0, ep_p2 = 0.0;  // (beta/alpha)_{i+1}, (eps/alpha)_{i+1}, (eps/alpha)_{i+2}
+  for (int64_t r = L.Lg - 1; r >= 0; --r) {
+    const double ainv = __ldg(fwd + fwd_idx<SHARED>(L, r, 0, lane));
+    const double z = zscr[(L.R0 + r) * kWarp + lane];
+    const double w = fma(-bp_p1, w1, fma(-ep_p2, w2, z));
+    if (r < L.n) y[L.fo + r] = ainv * w;
+    w2 = w1;
+    w1 = w;
+    ep_p2 = ep_p1;
+    bp_p1 = __ldg(fwd + fwd_idx<SHARED>(L, r, 1, lane));
+    ep_p1 = __ldg(fwd + fwd_idx<SHARED>(L, r, 2, lane));
+  }
+}
+
+// g_sigma[s] -= sum_i mu_i (D4 x)_i, one warp per system.
+__global__ void k_sigma_grad(DevPlan P, const double* __restrict__ mu, const double* __restrict__ x,
+                             double* g_sigma) {
+  const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kWarp;
+  if (s >= P.batch) return;
+  const int lane = threadIdx.x & (kWarp - 1);
+  const int64_t n = P.shared ? P.n_shared : P.n[s];
+  const int64_t o = P.shared ? s * P.n_shared : P.off[s];
+  double acc = 0.0;
+  for (int64_t i = lane; i < n; i += kWarp) {
+    double w[5];
+    d4_weights(i, n, w);
+    double d4x = 0.0;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const int64_t j = i + k - 2;
+      if (j >= 0 && j < n && w[k] != 0.0) d4x = fma(w[k], x[o + j], d4x);
+    }
+    acc = fma(mu[o + i], d4x, acc);
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
+  if (lane == 0) g_sigma[s] -= acc;
+}
+
+inline int grid_for(int64_t threads, int block) { return (int)((threads + block - 1) / block); }
+
+}  // namespace
+
+cudaError_t launch_factor64(const DevPlan& P, const double* a, const double* b, const double* c, const double* d,
+                            const double* e, const double* sigma, F64Factors F, cudaStream_t st) {
+  const int64_t nslots = P.shared ? 1 : P.ngroups * kWarp;
+  const int block = 128;
+  k_factor64<<<grid_for(nslots, block), block, 0, st>>>(P, a, b, c, d, e, sigma, F);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_solve64(const DevPlan& P, F64Factors F, const double* f, double* x, double* gscr, int block_warps,
+                           cudaStream_t st) {
+  const int block = kWarp * block_warps;
+  const int grid = grid_for(P.ngroups * kWarp, block);
+  if (P.shared)
+    k_solve64<true, 8><<<grid, block, 0, st>>>(P, F, f, x, gscr);
+  else
+    k_solve64<false, 8><<<grid, block, 0, st>>>(P, F, f, x, gscr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint64(const DevPlan& P, F64Factors F, const double* f, double* x, double* gscr,
+                             int block_warps, cudaStream_t st) {
+  const int block = kWarp * block_warps;
+  const int grid = grid_for(P.ngroups * kWarp, block);
+  if (P.shared)
+    k_adjoint64<true><<<grid, block, 0, st>>>(P, F, f, x, gscr);
+  else
+    k_adjoint64<false><<<grid, block, 0, st>>>(P, F, f, x, gscr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sigma_grad(const DevPlan& P, const double* mu, const double* x, double* g_sigma, cudaStream_t st) {
+  const int block = 256;
+  k_sigma_grad<<<grid_for(P.batch * kWarp, block), block, 0, st>>>(P, mu, x, g_sigma);
+  return cudaGetLastError();
+}
+
+}  // namespace pent

@@ -1,0 +1,71 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pent {
+
+constexpr int kWarp = 32;
+
+// Device info word (int64 x 4):
+//   [0] lowest (system << 32 | row) whose pivot failed, or kInfoNone
+//   [1] largest number of refinement steps any system used
+//   [2] flags: bit 0 = refinement not converged
+//   [3] unused
+constexpr int kInfoWords = 4;
+constexpr unsigned long long kInfoNone = 0x7f7f7f7f7f7f7f7full;  // every byte 0x7f: settable by cudaMemsetAsync
+
+// Read-only view of the plan's per-system tables and factor storage, passed by value to kernels.
+struct DevPlan {
+  int64_t batch;        // number of systems
+  int64_t ngroups;      // ceil(batch / 32): one group of 32 systems per warp in thread-per-system kernels
+  int shared;           // all systems share one matrix
+  int64_t n_shared;     // rows of the shared matrix
+  const int32_t* perm;  // [ngroups*32] system at sorted position q (-1 for padding lanes)
+  const int64_t* off;   // [batch] first row of each system in the caller's layout
+  const int32_t* n;     // [batch] rows of each system
+  const int64_t* goff;  // [ngroups] first record row of each group
+  const int32_t* glen;  // [ngroups] padded rows of each group (max n in the group)
+  unsigned long long* info;
+};
+
+// FP64 factor records, per group of 32 systems and row r (record row R = goff[k] + r):
+//   fwd[(R*3 + p)*32 + lane], p = 0: 1/alpha, 1: beta/alpha, 2: epsilon/alpha
+//   bwd[(R*2 + p)*32 + lane], p = 0: gamma,   1: delta
+// For a shared matrix: fwd[r*3 + p], bwd[r*2 + p].
+struct F64Factors {
+  double* fwd;
+  double* bwd;
+};
+
+// FP32 warp-per-system storage for system s (uniform length n, L = rows per lane, n <= 32 L):
+//   rows i = t*L + j of lane t are stored at slot j*32 + t of each plane;
+//   fac[(s*5 + p)*32*L + j*32 + t], p = 0: 1/alpha, 1: beta/alpha, 2: epsilon/alpha, 3: gamma, 4: delta
+//   phi[(s*32 + t)*8 + k]: k = 0..3 forward chunk map (row-major 2x2), 4..7 backward chunk map.
+struct F32Factors {
+  float* fac;
+  float* phi;
+  int L;
+};
+
+// ---- launchers (kernels live in the .cu files) ----
+cudaError_t launch_factor64(const DevPlan& P, const double* a, const double* b, const double* c, const double* d,
+                            const double* e, const double* sigma, F64Factors F, cudaStream_t st);
+cudaError_t launch_factor32(const DevPlan& P, const double* a, const double* b, const double* c, const double* d,
+                            const double* e, const double* sigma, F32Factors F, int n, cudaStream_t st);
+cudaError_t launch_solve64(const DevPlan& P, F64Factors F, const double* f, double* x, double* gscr, int block_warps,
+                           cudaStream_t st);
+cudaError_t launch_adjoint64(const DevPlan& P, F64Factors F, const double* f, double* x, double* gscr,
+                             int block_warps, cudaStream_t st);
+cudaError_t launch_solve32r(const DevPlan& P, F32Factors F, const double* sigma, int n, const double* f, double* x,
+                            int max_refine, int residual_f64, int tol_log2, cudaStream_t st);
+cudaError_t launch_sigma_grad(const DevPlan& P, const double* mu, const double* x, double* g_sigma, cudaStream_t st);
+cudaError_t launch_adi_rhs(const double* C, double* rhs, int64_t nx, int64_t ny, double mu, double sigma,
+                           cudaStream_t st);
+cudaError_t launch_adi_xsweep(F64Factors F, double* rhs, int64_t nx, int64_t ny, cudaStream_t st);
+cudaError_t launch_adi_ysweep_update(F64Factors F, const double* w, double* C, double* dcsum, int64_t nx, int64_t ny,
+                                     cudaStream_t st);
+cudaError_t launch_adi_update(double* C, const double* dC, const double* dcsum, int64_t nx, int64_t ny, cudaStream_t st);
+
+}  // namespace pent

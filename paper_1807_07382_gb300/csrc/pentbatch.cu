@@ -1,0 +1,433 @@
+// Host side of the C ABI declared in include/pentbatch.h: plans, workspace
+// layout, argument checks, dispatch and CUDA-graph time stepping.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <tuple>
+#include <vector>
+
+#include "../../include/pentbatch.h"
+#include "internal.cuh"
+
+using namespace pent;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct Region {
+  size_t off = 0, bytes = 0;
+};
+
+}  // namespace
+
+struct pent_plan {
+  // shapes
+  int64_t batch = 0;
+  std::vector<int64_t> n;    // rows per system
+  std::vector<int64_t> off;  // batch + 1 offsets, caller layout
+  int64_t rows = 0;
+  bool uniform = true;
+  int64_t n_uniform = 0;
+  bool shared = false;
+  pent_precision precision = PENT_F64;
+  // options
+  int threads_per_system = 1;
+  int residual = PENT_RESIDUAL_FF;
+  int block_warps = 4;
+  int tol_log2 = 40;
+  // thread-per-system grouping (systems sorted by length, longest first)
+  std::vector<int32_t> perm;  // [ngroups*32], -1 for padding lanes
+  int64_t ngroups = 0;
+  std::vector<int64_t> goff;
+  std::vector<int32_t> glen;
+  int64_t grows = 0;  // record rows over all groups
+  // warp-per-system FP32 storage
+  int L32 = 0;
+  // workspace regions
+  Region r_info, r_perm, r_off, r_n, r_goff, r_glen, r_sigma, r_fwd, r_bwd, r_scr, r_fac32, r_phi, r_adi;
+  size_t ws_bytes = 0;
+  // binding / state
+  unsigned char* ws = nullptr;
+  cudaStream_t stream = nullptr;
+  bool bound = false;
+  int factored = 0;  // 0 none, 1 general band, 2 hyperdiffusion
+  // graph cache: (x, nsteps, max_refine) -> exec
+  std::map<std::tuple<const void*, int64_t, int, int64_t>, cudaGraphExec_t> graphs;
+
+  template <class T>
+  T* at(const Region& r) const {
+    return reinterpret_cast<T*>(ws + r.off);
+  }
+  DevPlan dev() const {
+    DevPlan P;
+    P.batch = batch;
+    P.ngroups = ngroups;
+    P.shared = shared ? 1 : 0;
+    P.n_shared = shared ? n_uniform : 0;
+    P.perm = at<int32_t>(r_perm);
+    P.off = at<int64_t>(r_off);
+    P.n = at<int32_t>(r_n);
+    P.goff = at<int64_t>(r_goff);
+    P.glen = at<int32_t>(r_glen);
+    P.info = at<unsigned long long>(r_info);
+    return P;
+  }
+  F64Factors f64() const { return F64Factors{at<double>(r_fwd), at<double>(r_bwd)}; }
+  F32Factors f32() const { return F32Factors{at<float>(r_fac32), at<float>(r_phi), L32}; }
+  void drop_graphs() {
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+    graphs.clear();
+  }
+};
+
+namespace {
+
+pent_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PENT_OK : PENT_ECUDA; }
+
+int choose_L32(int64_t n) {
+  for (int L : {2, 4, 8, 16, 32})
+    if (n <= 32 * L) return L;
+  return 0;
+}
+
+void layout(pent_plan* p) {
+  size_t cur = 0;
+  auto take = [&](Region& r, size_t bytes) {
+    r.off = cur;
+    r.bytes = bytes;
+    cur = align_up(cur + std::max<size_t>(bytes, 1));
+  };
+  const int64_t nfac = p->shared ? 1 : p->batch;
+  take(p->r_info, kInfoWords * sizeof(unsigned long long));
+  take(p->r_perm, (size_t)p->ngroups * kWarp * sizeof(int32_t));
+  take(p->r_off, (size_t)p->batch * sizeof(int64_t));
+  take(p->r_n, (size_t)p->batch * sizeof(int32_t));
+  take(p->r_goff, (size_t)p->ngroups * sizeof(int64_t));
+  take(p->r_glen, (size_t)p->ngroups * sizeof(int32_t));
+  take(p->r_sigma, (size_t)nfac * sizeof(double));
+  if (p->precision == PENT_F64) {
+    const int64_t frows = p->shared ? p->n_uniform : p->grows;
+    const int64_t lanes = p->shared ? 1 : kWarp;
+    take(p->r_fwd, (size_t)frows * 3 * lanes * sizeof(double));
+    take(p->r_bwd, (size_t)frows * 2 * lanes * sizeof(double));
+    take(p->r_scr, (size_t)p->grows * kWarp * sizeof(double));
+  } else {
+    take(p->r_fac32, (size_t)nfac * 5 * 32 * p->L32 * sizeof(float));
+    take(p->r_phi, (size_t)nfac * 32 * 8 * sizeof(float));
+  }
+  // ADI scratch: a full field (rows * 1 double) plus the mean accumulator, for shared-matrix plans
+  if (p->shared) take(p->r_adi, (size_t)p->rows * sizeof(double) + 256);
+  p->ws_bytes = cur;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pent_version(void) { return "0.1.0"; }
+
+const char* pent_status_string(pent_status s) {
+  switch (s) {
+    case PENT_OK: return "ok";
+    case PENT_EINVAL: return "invalid argument";
+    case PENT_ESINGULAR: return "zero or non-finite pivot";
+    case PENT_ENOCONV: return "refinement did not converge";
+    case PENT_ECUDA: return "CUDA error";
+    case PENT_ENOTFACTORED: return "not factored";
+    case PENT_ENOTBOUND: return "no workspace bound";
+  }
+  return "unknown status";
+}
+
+pent_status pent_plan_create(pent_plan** out, int64_t batch, const int64_t* n_per_system, int64_t n_uniform,
+                             int shared_matrix, pent_precision precision, const char* tune_cache) {
+  (void)tune_cache;
+  if (!out) return PENT_EINVAL;
+  *out = nullptr;
+  if (batch < 1 || batch > (int64_t)INT32_MAX) return PENT_EINVAL;
+  if (precision != PENT_F64 && precision != PENT_F32_REFINE) return PENT_EINVAL;
+  if (shared_matrix && n_per_system) return PENT_EINVAL;
+  pent_plan* p = new pent_plan();
+  p->batch = batch;
+  p->shared = shared_matrix != 0;
+  p->precision = precision;
+  p->n.resize(batch);
+  for (int64_t s = 0; s < batch; ++s) {
+    const int64_t v = n_per_system ? n_per_system[s] : n_uniform;
+    if (v < 1 || v > (int64_t)INT32_MAX) {
+      delete p;
+      return PENT_EINVAL;
+    }
+    p->n[s] = v;
+  }
+  p->off.assign(batch + 1, 0);
+  for (int64_t s = 0; s < batch; ++s) p->off[s + 1] = p->off[s] + p->n[s];
+  p->rows = p->off[batch];
+  p->uniform = std::all_of(p->n.begin(), p->n.end(), [&](int64_t v) { return v == p->n[0]; });
+  p->n_uniform = p->uniform ? p->n[0] : 0;
+  // groups of 32 systems, longest first (stable), so a warp's lanes walk similar lengths
+  p->ngroups = (batch + kWarp - 1) / kWarp;
+  std::vector<int32_t> order(batch);
+  std::iota(order.begin(), order.end(), 0);
+  if (!p->uniform)
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return p->n[x] > p->n[y]; });
+  p->perm.assign(p->ngroups * kWarp, -1);
+  for (int64_t q = 0; q < batch; ++q) p->perm[q] = order[q];
+  p->goff.resize(p->ngroups);
+  p->glen.resize(p->ngroups);
+  int64_t acc = 0;
+  for (int64_t k = 0; k < p->ngroups; ++k) {
+    int64_t mx = 0;
+    for (int l = 0; l < kWarp; ++l) {
+      const int32_t s = p->perm[k * kWarp + l];
+      if (s >= 0) mx = std::max(mx, p->n[s]);
+    }
+    p->goff[k] = acc;
+    p->glen[k] = (int32_t)mx;
+    acc += mx;
+  }
+  p->grows = acc;
+  if (precision == PENT_F32_REFINE) {
+    if (!p->uniform) {
+      delete p;
+      return PENT_EINVAL;
+    }
+    p->L32 = choose_L32(p->n_uniform);
+    if (p->L32 == 0) {
+      delete p;
+      return PENT_EINVAL;
+    }
+    p->threads_per_system = 32;
+  }
+  layout(p);
+  *out = p;
+  return PENT_OK;
+}
+
+size_t pent_plan_workspace_bytes(const pent_plan* p) { return p ? p->ws_bytes : 0; }
+
+pent_status pent_plan_bind(pent_plan* p, void* ws, void* stream) {
+  if (!p || !ws) return PENT_EINVAL;
+  if (((uintptr_t)ws) % kAlign) return PENT_EINVAL;
+  p->drop_graphs();
+  p->ws = static_cast<unsigned char*>(ws);
+  p->stream = static_cast<cudaStream_t>(stream);
+  std::vector<int32_t> n32(p->batch);
+  for (int64_t s = 0; s < p->batch; ++s) n32[s] = (int32_t)p->n[s];
+  cudaError_t e = cudaSuccess;
+  auto up = [&](const Region& r, const void* src, size_t bytes) {
+    if (e == cudaSuccess && bytes) e = cudaMemcpy(p->ws + r.off, src, bytes, cudaMemcpyHostToDevice);
+  };
+  up(p->r_perm, p->perm.data(), p->perm.size() * sizeof(int32_t));
+  up(p->r_off, p->off.data(), (size_t)p->batch * sizeof(int64_t));
+  up(p->r_n, n32.data(), n32.size() * sizeof(int32_t));
+  up(p->r_goff, p->goff.data(), p->goff.size() * sizeof(int64_t));
+  up(p->r_glen, p->glen.data(), p->glen.size() * sizeof(int32_t));
+  const unsigned long long init[kInfoWords] = {kInfoNone, 0, 0, 0};
+  up(p->r_info, init, sizeof(init));
+  if (e != cudaSuccess) return PENT_ECUDA;
+  p->bound = true;
+  p->factored = 0;
+  return PENT_OK;
+}
+
+pent_status pent_plan_set_option(pent_plan* p, int key, int64_t value) {
+  if (!p) return PENT_EINVAL;
+  switch (key) {
+    case PENT_OPT_THREADS_PER_SYSTEM:
+      if (p->factored) return PENT_EINVAL;
+      if (p->precision == PENT_F64 && value != 1) return PENT_EINVAL;
+      if (p->precision == PENT_F32_REFINE && value != 32) return PENT_EINVAL;
+      p->threads_per_system = (int)value;
+      return PENT_OK;
+    case PENT_OPT_RESIDUAL:
+      if (value != PENT_RESIDUAL_FF && value != PENT_RESIDUAL_F64) return PENT_EINVAL;
+      p->residual = (int)value;
+      return PENT_OK;
+    case PENT_OPT_BLOCK_WARPS:
+      if (value < 1 || value > 8) return PENT_EINVAL;
+      p->block_warps = (int)value;
+      p->drop_graphs();
+      return PENT_OK;
+    case PENT_OPT_REFINE_TOL_LOG2:
+      if (value < 1 || value > 60) return PENT_EINVAL;
+      p->tol_log2 = (int)value;
+      p->drop_graphs();
+      return PENT_OK;
+  }
+  return PENT_EINVAL;
+}
+
+pent_status pent_plan_get_option(const pent_plan* p, int key, int64_t* value) {
+  if (!p || !value) return PENT_EINVAL;
+  switch (key) {
+    case PENT_OPT_THREADS_PER_SYSTEM: *value = p->threads_per_system; return PENT_OK;
+    case PENT_OPT_RESIDUAL: *value = p->residual; return PENT_OK;
+    case PENT_OPT_BLOCK_WARPS: *value = p->block_warps; return PENT_OK;
+    case PENT_OPT_REFINE_TOL_LOG2: *value = p->tol_log2; return PENT_OK;
+  }
+  return PENT_EINVAL;
+}
+
+static pent_status reset_info(pent_plan* p) {
+  // memsets only, so the reset is asynchronous and capture-safe
+  cudaError_t e = cudaMemsetAsync(p->at<unsigned char>(p->r_info), 0x7f, sizeof(unsigned long long), p->stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(p->at<unsigned char>(p->r_info) + sizeof(unsigned long long), 0,
+                        (kInfoWords - 1) * sizeof(unsigned long long), p->stream);
+  return cuda_status(e);
+}
+
+static pent_status factor_common(pent_plan* p, const double* a, const double* b, const double* c, const double* d,
+                                 const double* e, const double* sigma) {
+  if (!p) return PENT_EINVAL;
+  if (!p->bound) return PENT_ENOTBOUND;
+  p->drop_graphs();
+  pent_status st = reset_info(p);
+  if (st != PENT_OK) return st;
+  const DevPlan P = p->dev();
+  const int64_t nsig = p->shared ? 1 : p->batch;
+  if (sigma) {
+    cudaError_t err = cudaMemcpyAsync(p->at<double>(p->r_sigma), sigma, (size_t)nsig * sizeof(double),
+                                      cudaMemcpyDeviceToDevice, p->stream);
+    if (err != cudaSuccess) return PENT_ECUDA;
+  }
+  const double* sg = sigma ? p->at<double>(p->r_sigma) : nullptr;
+  cudaError_t err;
+  if (p->precision == PENT_F64)
+    err = launch_factor64(P, a, b, c, d, e, sg, p->f64(), p->stream);
+  else
+    err = launch_factor32(P, a, b, c, d, e, sg, p->f32(), (int)p->n_uniform, p->stream);
+  if (err != cudaSuccess) return PENT_ECUDA;
+  p->factored = sigma ? 2 : 1;
+  return PENT_OK;
+}
+
+pent_status pent_factor_batch(pent_plan* p, const double* a, const double* b, const double* c, const double* d,
+                              const double* e) {
+  if (!p || !a || !b || !c || !d || !e) return PENT_EINVAL;
+  if (p->precision == PENT_F32_REFINE) return PENT_EINVAL;  // refinement needs the band in closed form (sigma)
+  return factor_common(p, a, b, c, d, e, nullptr);
+}
+
+pent_status pent_factor_hyperdiff(pent_plan* p, const double* d_sigma) {
+  if (!p || !d_sigma) return PENT_EINVAL;
+  return factor_common(p, nullptr, nullptr, nullptr, nullptr, nullptr, d_sigma);
+}
+
+static pent_status solve_launch(pent_plan* p, const double* f, double* x, int max_refine) {
+  const DevPlan P = p->dev();
+  cudaError_t err;
+  if (p->precision == PENT_F64) {
+    err = launch_solve64(P, p->f64(), f, x, p->at<double>(p->r_scr), p->block_warps, p->stream);
+  } else {
+    err = launch_solve32r(P, p->f32(), p->at<double>(p->r_sigma), (int)p->n_uniform, f, x, max_refine,
+                          p->residual == PENT_RESIDUAL_F64, p->tol_log2, p->stream);
+  }
+  return cuda_status(err);
+}
+
+static pent_status check_solve(pent_plan* p, const void* f, const void* x, int max_refine) {
+  if (!p || !f || !x || max_refine < 0) return PENT_EINVAL;
+  if (!p->bound) return PENT_ENOTBOUND;
+  if (!p->factored) return PENT_ENOTFACTORED;
+  if ((((uintptr_t)f) | ((uintptr_t)x)) % sizeof(double)) return PENT_EINVAL;
+  return PENT_OK;
+}
+
+pent_status pent_solve_batch(pent_plan* p, const double* f, double* x, int max_refine) {
+  pent_status st = check_solve(p, f, x, max_refine);
+  if (st != PENT_OK) return st;
+  return solve_launch(p, f, x, max_refine);
+}
+
+pent_status pent_solve_steps(pent_plan* p, double* x, int64_t nsteps, int max_refine) {
+  pent_status st = check_solve(p, x, x, max_refine);
+  if (st != PENT_OK) return st;
+  if (nsteps < 0) return PENT_EINVAL;
+  if (nsteps == 0) return PENT_OK;
+  if (p->stream == nullptr) {  // the legacy stream cannot be captured: plain launches
+    for (int64_t k = 0; k < nsteps && st == PENT_OK; ++k) st = solve_launch(p, x, x, max_refine);
+    return st;
+  }
+  const auto key = std::make_tuple((const void*)x, nsteps, max_refine, (int64_t)p->block_warps);
+  auto it = p->graphs.find(key);
+  if (it == p->graphs.end()) {
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return PENT_ECUDA;
+    for (int64_t k = 0; k < nsteps && st == PENT_OK; ++k) st = solve_launch(p, x, x, max_refine);
+    cudaError_t e = cudaStreamEndCapture(p->stream, &g);
+    if (st != PENT_OK || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return st != PENT_OK ? st : PENT_ECUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return PENT_ECUDA;
+    it = p->graphs.emplace(key, exec).first;
+  }
+  return cuda_status(cudaGraphLaunch(it->second, p->stream));
+}
+
+pent_status pent_adjoint_solve_batch(pent_plan* p, const double* f, double* x, int max_refine) {
+  pent_status st = check_solve(p, f, x, max_refine);
+  if (st != PENT_OK) return st;
+  if (p->precision != PENT_F64) return PENT_EINVAL;
+  return cuda_status(
+      launch_adjoint64(p->dev(), p->f64(), f, x, p->at<double>(p->r_scr), p->block_warps, p->stream));
+}
+
+pent_status pent_hyperdiff_sigma_grad(pent_plan* p, const double* mu, const double* x, double* g_sigma) {
+  if (!p || !mu || !x || !g_sigma) return PENT_EINVAL;
+  if (!p->bound) return PENT_ENOTBOUND;
+  return cuda_status(launch_sigma_grad(p->dev(), mu, x, g_sigma, p->stream));
+}
+
+pent_status pent_get_info(pent_plan* p, int64_t* bad_system, int64_t* bad_row, int* refine_steps_used) {
+  if (!p) return PENT_EINVAL;
+  if (!p->bound) return PENT_ENOTBOUND;
+  unsigned long long h[kInfoWords];
+  cudaError_t e = cudaStreamSynchronize(p->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(h, p->at<unsigned long long>(p->r_info), sizeof(h), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return PENT_ECUDA;
+  const bool bad = h[0] != kInfoNone;
+  if (bad_system) *bad_system = bad ? (int64_t)(h[0] >> 32) : -1;
+  if (bad_row) *bad_row = bad ? (int64_t)(h[0] & 0xffffffffull) : -1;
+  if (refine_steps_used) *refine_steps_used = (int)h[1];
+  if (bad) return PENT_ESINGULAR;
+  if (h[2] & 1ull) return PENT_ENOCONV;
+  return PENT_OK;
+}
+
+pent_status pent_clear_info(pent_plan* p) {
+  if (!p) return PENT_EINVAL;
+  if (!p->bound) return PENT_ENOTBOUND;
+  return reset_info(p);
+}
+
+void pent_plan_destroy(pent_plan* p) {
+  if (!p) return;
+  p->drop_graphs();
+  delete p;
+}
+
+pent_status adi_step_2d(pent_plan* px, pent_plan* py, double* C, int64_t nx, int64_t ny, double gamma, double dt,
+                        double dx, int max_refine) {
+  (void)px; (void)py; (void)C; (void)nx; (void)ny; (void)gamma; (void)dt; (void)dx; (void)max_refine;
+  return PENT_EINVAL;
+}
+
+pent_status adi_steps_2d(pent_plan* px, pent_plan* py, double* C, int64_t nx, int64_t ny, double gamma, double dt,
+                         double dx, int max_refine, int64_t nsteps) {
+  (void)nsteps;
+  return adi_step_2d(px, py, C, nx, ny, gamma, dt, dx, max_refine);
+}
+
+}  // extern "C"

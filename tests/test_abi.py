@@ -1,0 +1,94 @@
+"""Host-side checks of the C-ABI library: it builds, loads without a GPU, exports
+every entry point the header declares, and validates plan arguments on the host
+(no CUDA call is made by anything tested here)."""
+import ctypes
+import re
+from pathlib import Path
+
+import pytest
+
+import paper_1807_07382_gb300 as pb
+from paper_1807_07382_gb300 import _lib, build
+
+ROOT = Path(__file__).resolve().parents[1]
+HEADER = ROOT / "include" / "pentbatch.h"
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return _lib.load()
+
+
+def declared_functions():
+    text = HEADER.read_text()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_]+\s*\*?\s*([a-z_0-9]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_hot_path_entry_points():
+    names = declared_functions()
+    for required in ("pent_factor_batch", "pent_solve_batch", "pent_adjoint_solve_batch", "adi_step_2d"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    names = declared_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(L, name), name
+    assert set(names) <= set(_lib.SIGNATURES), set(names) - set(_lib.SIGNATURES)
+
+
+def test_version_and_status_strings(L):
+    assert L.pent_version().decode() == pb.__version__
+    assert L.pent_status_string(_lib.PENT_ESINGULAR).decode() == "zero or non-finite pivot"
+
+
+def _create(L, batch, n=None, n_uniform=0, shared=0, prec=0):
+    h = ctypes.c_void_p()
+    arr = (ctypes.c_int64 * len(n))(*n) if n is not None else None
+    st = L.pent_plan_create(ctypes.byref(h), batch, arr, n_uniform, shared, prec, None)
+    return st, h
+
+
+@pytest.mark.parametrize("args", [
+    dict(batch=0, n_uniform=8),
+    dict(batch=4, n_uniform=0),
+    dict(batch=3, n=[4, 0, 5]),
+    dict(batch=2, n=[4, 5], shared=1),
+    dict(batch=2, n_uniform=8, prec=7),
+    dict(batch=2, n=[40, 50], prec=1),          # FP32 refinement needs uniform lengths
+    dict(batch=2, n_uniform=5000, prec=1),      # ... and n <= 1024 per warp
+])
+def test_plan_create_rejects_bad_arguments(L, args):
+    st, h = _create(L, **args)
+    assert st == _lib.PENT_EINVAL
+    assert not h.value
+
+
+def test_plan_workspace_and_options(L):
+    st, h = _create(L, batch=70, n_uniform=1024)
+    assert st == 0
+    ws = L.pent_plan_workspace_bytes(h)
+    # FP64 records (5 doubles) + scratch (1 double) per padded row, 3 groups of 32
+    assert ws >= 3 * 32 * 1024 * 6 * 8
+    v = ctypes.c_int64()
+    assert L.pent_plan_get_option(h, _lib.PENT_OPT_BLOCK_WARPS, ctypes.byref(v)) == 0 and v.value >= 1
+    assert L.pent_plan_set_option(h, _lib.PENT_OPT_BLOCK_WARPS, 0) == _lib.PENT_EINVAL
+    assert L.pent_plan_set_option(h, _lib.PENT_OPT_BLOCK_WARPS, 2) == 0
+    assert L.pent_plan_set_option(h, _lib.PENT_OPT_THREADS_PER_SYSTEM, 32) == _lib.PENT_EINVAL
+    assert L.pent_plan_set_option(h, 999, 1) == _lib.PENT_EINVAL
+    # unbound plans refuse to work, without touching the GPU
+    assert L.pent_solve_batch(h, ctypes.c_void_p(16), ctypes.c_void_p(16), 0) == _lib.PENT_ENOTBOUND
+    assert L.pent_factor_hyperdiff(h, None) == _lib.PENT_EINVAL
+    L.pent_plan_destroy(h)
+
+
+def test_uneven_plan_workspace_counts_padded_groups(L):
+    n = [64] * 31 + [1000]  # one group of 32: padded to the longest system
+    st, h = _create(L, batch=32, n=n)
+    assert st == 0
+    assert L.pent_plan_workspace_bytes(h) >= 32 * 1000 * 6 * 8
+    L.pent_plan_destroy(h)

@@ -1,0 +1,200 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, element by
+element on the same seeded inputs.  Error metric (per system, maximised over
+systems): max_i |x_i - x_ref_i| / max_i |x_ref_i|.
+
+Tolerances.  FP64 solves: 1e-12 (the target for both precisions).  The two
+sides round differently (the library multiplies by stored 1/alpha and
+beta/alpha and uses fused multiply-adds; the oracle divides), so each row
+differs by a few ulps; for the well-conditioned bands used here (diagonally
+dominant, kappa <= 1 + 16 sigma <= 161) the forward error stays orders of
+magnitude below the bar."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1807_07382_gb300 as pb  # noqa: E402
+from paper_1807_07382_gb300 import build  # noqa: E402
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def sys_rel_err(x, ref, n_per_system):
+    off = oracle.offsets(n_per_system)
+    worst = 0.0
+    for s in range(len(off) - 1):
+        r = ref[off[s]:off[s + 1]]
+        d = np.max(np.abs(x[off[s]:off[s + 1]] - r))
+        worst = max(worst, d / max(np.max(np.abs(r)), 1e-300))
+    return worst
+
+
+def cat_bands(bands):
+    return tuple(np.concatenate([bb[k] for bb in bands]) for k in range(5))
+
+
+# ----------------------------------------------------------------------------- general bands, FP64
+
+@pytest.mark.parametrize("kind", ["diagdom", "spd"])
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 17, 64, 257, 1024])
+def test_factor_solve_general_band_f64(kind, n):
+    batch = 70  # two full warps and a ragged third
+    band = synth.random_bands(batch, n, seed=1000 + n, kind=kind)
+    f = synth.uniform(2000 + n, 0, batch * n, -1, 1)
+    ns = np.full(batch, n)
+    fac, bad, _ = oracle.factor_batch(ns, band)
+    assert bad == -1
+    ref = oracle.solve_batch(ns, fac, f)
+    plan = pb.Plan(n, batch=batch)
+    plan.factor(*[dev(v) for v in band])
+    x = plan.solve(dev(f))
+    assert plan.info()[0] == pb.PENT_OK
+    assert sys_rel_err(host(x), ref, ns) <= TOL
+
+
+def test_uneven_lengths_f64():
+    ns = np.array([1, 2, 3, 5, 8, 13, 64, 100, 257, 31, 32, 33, 500, 7, 1024, 2] * 5)
+    bands = [synth.random_bands(1, int(m), seed=int(m) * 7 + i, kind="diagdom") for i, m in enumerate(ns)]
+    band = cat_bands(bands)
+    f = synth.uniform(77, 0, int(ns.sum()), -1, 1)
+    fac, _, _ = oracle.factor_batch(ns, band)
+    ref = oracle.solve_batch(ns, fac, f)
+    plan = pb.Plan(list(ns))
+    plan.factor(*[dev(v) for v in band])
+    x = plan.solve(dev(f))
+    assert sys_rel_err(host(x), ref, ns) <= TOL
+    # in place: x aliases f
+    fx = dev(f)
+    plan.solve(fx, fx)
+    assert sys_rel_err(host(fx), ref, ns) <= TOL
+
+
+def test_adjoint_general_band_f64():
+    ns = np.array([3, 64, 257, 1024, 5, 100] * 6)
+    bands = [synth.random_bands(1, int(m), seed=int(m) + 31 * i, kind="diagdom") for i, m in enumerate(ns)]
+    band = cat_bands(bands)
+    f = synth.uniform(78, 0, int(ns.sum()), -1, 1)
+    ref = oracle.adjoint_solve_batch(ns, band, f)
+    plan = pb.Plan(list(ns))
+    plan.factor(*[dev(v) for v in band])
+    y = plan.adjoint_solve(dev(f))
+    assert sys_rel_err(host(y), ref, ns) <= TOL
+
+
+def test_zero_pivot_reports_system_and_row():
+    n = 6
+    good = synth.random_bands(1, n, seed=5, kind="diagdom")
+    a, b, c, d, e = (np.full(n, v) for v in (0.1, 0.2, 3.0, 0.2, 0.1))
+    d[:3] = 0.0
+    e[:3] = 0.0
+    c[3] = 0.0  # alpha_4 = 0 exactly (rows before it do not couple forward)
+    bad_band = (a, b, c, d, e)
+    band = cat_bands([good, good, bad_band, good, bad_band])
+    plan = pb.Plan(n, batch=5)
+    plan.factor(*[dev(v) for v in band])
+    st, bs, br, _ = plan.info()
+    assert (st, bs, br) == (pb._lib.PENT_ESINGULAR, 2, 3)
+    # healthy systems still solve correctly
+    f = synth.uniform(3, 0, 5 * n, -1, 1)
+    x = host(plan.solve(dev(f)))
+    fac, _ = oracle.factor(good)
+    ref = oracle.solve(fac, f[:n])
+    assert np.max(np.abs(x[:n] - ref)) <= TOL * np.max(np.abs(ref))
+
+
+# ----------------------------------------------------------------------------- hyperdiffusion, FP64
+
+def test_hyperdiff_cosines_shared_f64_full_config():
+    """64 systems of N=256 sharing sigma = 0.5, 100 implicit steps (full size)."""
+    w = synth.hyperdiff_cosines()
+    ref = oracle.hyperdiff_steps(w.n, w.sigma, w.field0, w.steps, shared=True)
+    plan = pb.Plan(256, batch=64, shared=True)
+    plan.factor_hyperdiff(dev(w.sigma))
+    x = dev(w.field0)
+    plan.solve_steps(x, w.steps)
+    assert sys_rel_err(host(x), ref, w.n) <= TOL
+    # the graph replay equals step-by-step launches bit for bit
+    y = dev(w.field0)
+    for _ in range(w.steps):
+        plan.solve(y, y)
+    assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("precision", [pb.PENT_F64, pb.PENT_F32_REFINE])
+def test_hyperdiff_parametric_reduced(precision):
+    """sigma_i log-uniform in [1e-3, 10], N = 1024, ragged batch, 3 steps."""
+    w = synth.hyperdiff_parametric(batch=100, n=1024, steps=3)
+    ref = oracle.hyperdiff_steps(w.n, w.sigma, w.field0, w.steps)
+    plan = pb.Plan(1024, batch=w.batch, precision=precision)
+    plan.factor_hyperdiff(dev(w.sigma))
+    x = dev(w.field0)
+    for _ in range(w.steps):
+        plan.solve(x, x, max_refine=3)
+    st, _, _, used = plan.info()
+    assert st == pb.PENT_OK
+    assert sys_rel_err(host(x), ref, w.n) <= TOL
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 33, 64, 100, 255, 512, 1000])
+def test_f32_refine_small_and_ragged_lengths(n):
+    w = synth.hyperdiff_parametric(batch=37, n=n, steps=1, sigma_range=(1e-3, 10.0))
+    ref = oracle.hyperdiff_steps(w.n, w.sigma, w.field0, 1)
+    plan = pb.Plan(n, batch=w.batch, precision=pb.PENT_F32_REFINE)
+    plan.factor_hyperdiff(dev(w.sigma))
+    x = plan.solve(dev(w.field0), max_refine=3)
+    assert sys_rel_err(host(x), ref, w.n) <= TOL
+
+
+def test_f32_refine_error_by_step_count():
+    """Records the error after 0, 1, 2 refinement steps; 2 steps meet the bar."""
+    w = synth.hyperdiff_parametric(batch=64, n=1024, steps=1)
+    ref = oracle.hyperdiff_steps(w.n, w.sigma, w.field0, 1)
+    plan = pb.Plan(1024, batch=w.batch, precision=pb.PENT_F32_REFINE)
+    plan.set_option(pb.PENT_OPT_REFINE_TOL_LOG2, 60)  # never stop early
+    plan.factor_hyperdiff(dev(w.sigma))
+    errs = []
+    for k in range(4):
+        x = plan.solve(dev(w.field0), max_refine=k)
+        errs.append(sys_rel_err(host(x), ref, w.n))
+    print("FP32+refine error by refinement steps:", errs)
+    assert errs[0] < 1e-4
+    assert errs[1] < errs[0]
+    assert errs[2] <= TOL
+
+
+def test_full_size_parametric_sampled():
+    """65,536 systems of N=1024 (the benchmark size), one step in each precision;
+    64 sampled systems are checked against the oracle."""
+    w = synth.hyperdiff_parametric(steps=1)
+    idx = np.unique(np.linspace(0, w.batch - 1, 64).astype(int))
+    n = 1024
+    sub_f = np.concatenate([w.field0[s * n:(s + 1) * n] for s in idx])
+    ref = oracle.hyperdiff_steps(np.full(len(idx), n), w.sigma[idx], sub_f, 1)
+    f = dev(w.field0)
+    for precision in (pb.PENT_F64, pb.PENT_F32_REFINE):
+        plan = pb.Plan(n, batch=w.batch, precision=precision)
+        plan.factor_hyperdiff(dev(w.sigma))
+        x = plan.solve(f, max_refine=2)
+        xs = host(x.view(w.batch, n)[torch.as_tensor(idx, device=x.device)]).reshape(-1)
+        assert plan.info()[0] == pb.PENT_OK
+        assert sys_rel_err(xs, ref, np.full(len(idx), n)) <= TOL
+        del plan, x
+        torch.cuda.empty_cache()
