@@ -1,0 +1,397 @@
+#!/usr/bin/env python
+"""Benchmark of the batched pentadiagonal solve on the hyperdiffusion parametric batch.
+
+Workload: 65,536 independent systems A_s = I + sigma_s D4 of N = 1024 rows
+(sigma_s log-uniform in [1e-3, 10], initial fields uniform in [-1, 1]),
+factored once (untimed, as in the paper's benchmark, Sec. 3), then implicit
+time steps x <- A^{-1} x captured in one CUDA graph.  A bench step is one
+implicit step over the whole batch: forward and back substitution (and, for
+FP32+refine, the refinement residuals and corrections) for every row.
+
+Metric: row-solves/s = sum(N) * steps / time.  The headline precision is
+FP32 + float-float refinement; the FP64 solve is measured beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl own|reference]
+
+One JSON line is printed by rank 0.  Under torchrun each rank runs its own
+copy of the batch (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "row-solves/s and % of HBM peak; FP32+refine vs FP64 solve at rel err 1e-12"
+UNIT = "row-solves/s"
+BATCH, N = 65536, 1024
+WORKLOAD = ("hyperdiffusion parametric batch: 65,536 systems x N=1024, sigma_i log-uniform [1e-3,10], "
+            "C0 uniform [-1,1], implicit steps x <- (I + sigma D4)^-1 x in one CUDA graph, factors resident")
+# Algorithmic bytes per row and step (the paper's six-vector method, Sec. 2.4: read the
+# row's factors and f, write x).  FP64: 5 x 8 B factors + 8 B f + 8 B x.  FP32+refine:
+# 5 x 4 B factors + 8 B f + 8 B x (the refinement residual's band comes from sigma).
+ALG_BYTES = {"f64": 56, "f32_refine": 36}
+KERNEL = {"f64": "k_solve64", "f32_refine": "k_solve32r"}
+KERNEL_SRC = {"f64": "paper_1807_07382_gb300/csrc/core64.cu", "f32_refine": "paper_1807_07382_gb300/csrc/f32r.cu"}
+
+
+# ----------------------------------------------------------------------------- helpers
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def source_sha(path):
+    with open(os.path.join(ROOT, path), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def traffic_per_row(variant):
+    """DRAM bytes per row from a committed ncu summary, if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    e = d.get(variant)
+    if not e or e.get("source_sha") != source_sha(KERNEL_SRC[variant]):
+        return None
+    return float(e["dram_bytes_per_row"])
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(self.idx).uuid)
+            sel = uuid if uuid.startswith("GPU-") else f"GPU-{uuid}"
+        except Exception:  # noqa: BLE001
+            sel = str(self.idx)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", sel, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------------------------- CPU baseline (oracle)
+
+def cpu_baseline(w, budget_s=15.0, gpu_results=None):
+    """Time the oracle (plain serial FP64 per system, OpenMP over systems as in the paper's
+    Sec. 3.3) on a bounded sample of the same workload, and check the GPU's one-step results
+    for the sampled systems against it."""
+    import oracle
+    cores = oracle.max_threads()
+    n = N
+    sample = min(4096, w.batch)
+    idx = np.arange(sample) * (w.batch // sample)
+    band = oracle.band_hyperdiff_batch(np.full(sample, n), w.sigma[idx])
+    fac, bad, _ = oracle.factor_batch(np.full(sample, n), band)
+    f = np.concatenate([w.field0[s * n:(s + 1) * n] for s in idx])
+    t0 = time.perf_counter()
+    x1 = oracle.solve_batch(np.full(sample, n), fac, f)
+    t1 = time.perf_counter() - t0
+    steps = max(1, int(budget_s / max(t1, 1e-6)))
+    x = x1
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        x = oracle.solve_batch(np.full(sample, n), fac, x)
+    dt = time.perf_counter() - t0
+    out = {"value": sample * n * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{sample} of {w.batch} systems (every {w.batch // sample}th) x N={n}, {steps} implicit steps, "
+                     f"factored untimed; OpenMP over systems"}
+    errs = {}
+    if gpu_results:
+        ref = x1.reshape(sample, n)
+        for k, g in gpu_results.items():
+            got = g[idx]
+            errs[k] = float(np.max(np.max(np.abs(got - ref), axis=1) / np.max(np.abs(ref), axis=1)))
+    return out, errs
+
+
+# ----------------------------------------------------------------------------- own arm
+
+def run_own(args):
+    import torch
+    import paper_1807_07382_gb300 as pb
+    from paper_1807_07382_gb300 import build as pbuild
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    pbuild.build()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    BATCH = args.batch
+    w = synth.hyperdiff_parametric(batch=BATCH, n=N, steps=args.steps)
+    f0 = torch.from_numpy(w.field0).to(dev)
+    sigma = torch.from_numpy(w.sigma).to(dev)
+    rows = BATCH * N
+    peak, peak_kind = measured_peaks()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    variants = {}
+    one_step = {}
+    order = ["f64", "f32_refine"] if args.precision == "both" else [args.precision]
+    clocks = None
+    for name in order:
+        prec = pb.PENT_F64 if name == "f64" else pb.PENT_F32_REFINE
+        plan = pb.Plan(N, batch=BATCH, precision=prec, device=dev, stream=stream)
+        plan.factor_hyperdiff(sigma)
+        x = f0.clone()
+        # one step from C0 for the accuracy check against the oracle
+        one_step[name] = plan.solve(f0, max_refine=args.max_refine).view(BATCH, N).cpu().numpy()
+        # warm-up: W steps, then the K-step graph once (capture + instantiate + run)
+        plan.solve_steps(x, args.warmup, max_refine=args.max_refine)
+        plan.solve_steps(x, args.steps, max_refine=args.max_refine)
+        torch.cuda.synchronize(dev)
+        st = plan.info()[0]
+        if st != pb.PENT_OK:
+            raise RuntimeError(f"{name}: device status {st}")
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize(dev)
+        with ClockSampler(local) as cs:
+            ev0.record(stream)
+            plan.solve_steps(x, args.steps, max_refine=args.max_refine)
+            ev1.record(stream)
+            torch.cuda.synchronize(dev)
+        barrier()
+        ms = ev0.elapsed_time(ev1)
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        ms_step = ms / args.steps
+        value = world * rows * args.steps / (ms / 1e3)
+        achieved = ALG_BYTES[name] * rows / (ms_step / 1e3) / 1e9
+        tr = traffic_per_row(name)
+        variants[name] = {
+            "value": value, "ms_per_step": ms_step, "dtype": "f64" if name == "f64" else "f32",
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": (tr * rows) if tr is not None else None,
+                         "kernel": KERNEL[name], "alg_bytes_per_row": ALG_BYTES[name],
+                         "peak_kind": peak_kind},
+            "clocks": cs.summary(),
+        }
+        if name == "f32_refine":
+            variants[name]["max_refine"] = args.max_refine
+            variants[name]["refine_steps_used"] = plan.info()[3]
+        clocks = variants[name]["clocks"]
+        del plan
+        torch.cuda.empty_cache()
+
+    head = "f32_refine" if "f32_refine" in variants else order[0]
+    hv = variants[head]
+
+    # end to end through the public API: per step, H2D of the step's RHS from pinned
+    # host memory, the solve, D2H of the solution
+    e2e = None
+    if not args.no_e2e:
+        prec = pb.PENT_F64 if head == "f64" else pb.PENT_F32_REFINE
+        plan = pb.Plan(N, batch=BATCH, precision=prec, device=dev, stream=stream)
+        plan.factor_hyperdiff(sigma)
+        fh = torch.from_numpy(w.field0).pin_memory()
+        xh = torch.empty_like(fh).pin_memory()
+        fd = torch.empty_like(f0)
+        xd = torch.empty_like(f0)
+        e2e_steps = 10
+        for _ in range(2):
+            plan.solve_host(fh, xh, fd, xd, max_refine=args.max_refine)
+        torch.cuda.synchronize(dev)
+        barrier()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(e2e_steps):
+            plan.solve_host(fh, xh, fd, xd, max_refine=args.max_refine)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        ms = ev0.elapsed_time(ev1)
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        e2e = {"value": world * rows * e2e_steps / (ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(fh.numel() * 8), "d2h_bytes_per_step": int(xh.numel() * 8),
+               "steps": e2e_steps, "precision": head}
+        del plan
+        torch.cuda.empty_cache()
+
+    base, errs = (None, {})
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base, errs = cpu_baseline(w, budget_s=args.cpu_budget, gpu_results=one_step)
+    for k, v in errs.items():
+        variants[k]["max_rel_err_vs_oracle"] = v
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": hv["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": hv["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": hv["dtype"], "data": "synthetic",
+            "config": {"workload": WORKLOAD if BATCH == 65536 else WORKLOAD.replace("65,536", f"{BATCH:,}"),
+                       "batch": BATCH, "n": N, "precision": head,
+                       "max_refine": args.max_refine if head == "f32_refine" else 0,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "working set (factors + field) >= 1.9 GB, larger than L2; no flush"},
+            "roofline": hv["roofline"], "cpu_baseline": base, "e2e": e2e, "gpu_launches": args.steps,
+            "clocks": clocks, "variants": variants,
+        }
+        if errs:
+            line["max_rel_err_vs_oracle"] = errs.get(head)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    """The oracle as it stands on the host cores, same workload, metric and unit; each
+    step solves a bounded sample of the batch so the run ends in a few minutes."""
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return
+    import oracle
+    w = synth.hyperdiff_parametric(batch=BATCH, n=N, steps=1)
+    cores = oracle.max_threads()
+    n = N
+    budget = 120.0
+    probe = 256
+    idx = np.arange(probe)
+    band = oracle.band_hyperdiff_batch(np.full(probe, n), w.sigma[idx])
+    fac, _, _ = oracle.factor_batch(np.full(probe, n), band)
+    f = w.field0[:probe * n].copy()
+    t0 = time.perf_counter()
+    oracle.solve_batch(np.full(probe, n), fac, f)
+    per_row = (time.perf_counter() - t0) / (probe * n)
+    per_step_budget = budget / max(1, args.steps + args.warmup)
+    sample = int(min(BATCH, max(32, per_step_budget / max(per_row, 1e-12) / n)))
+    idx = np.arange(sample) * (BATCH // sample)
+    band = oracle.band_hyperdiff_batch(np.full(sample, n), w.sigma[idx])
+    fac, _, _ = oracle.factor_batch(np.full(sample, n), band)
+    x = np.concatenate([w.field0[s * n:(s + 1) * n] for s in idx])
+    ns = np.full(sample, n)
+    for _ in range(args.warmup):
+        x = oracle.solve_batch(ns, fac, x)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        x = oracle.solve_batch(ns, fac, x)
+    dt = time.perf_counter() - t0
+    value = sample * n * args.steps / dt
+    desc = (f"{sample} of {BATCH} systems (every {BATCH // sample}th) x N={n} per step, FP64 serial per system, "
+            f"OpenMP over systems, factored untimed")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "batch": BATCH, "n": N, "precision": "f64"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["own", "reference"], default="own")
+    ap.add_argument("--precision", choices=["both", "f64", "f32_refine"], default="both")
+    ap.add_argument("--max-refine", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--batch", type=int, default=BATCH, help="systems (default: the full workload; smaller for profiling)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_own(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -145,6 +145,21 @@ class Plan:
                                        int(max_refine)), "pent_solve_batch")
         return x
 
+    def solve_host(self, f_host, x_host, f_dev=None, x_dev=None, max_refine: int = 2):
+        """Solve for right-hand sides held in (pinned) host memory: copy f to the device,
+        solve, copy x back, all asynchronously on the plan's stream.  f_dev / x_dev are
+        optional device staging buffers."""
+        torch = _torch()
+        if f_host.is_cuda or x_host.is_cuda:
+            raise ValueError("solve_host takes host tensors")
+        with torch.cuda.stream(self.stream):
+            fd = f_dev if f_dev is not None else torch.empty(f_host.shape, dtype=torch.float64, device=self.device)
+            xd = x_dev if x_dev is not None else torch.empty_like(fd)
+            fd.copy_(f_host, non_blocking=True)
+            self.solve(fd, xd, max_refine=max_refine)
+            x_host.copy_(xd, non_blocking=True)
+        return x_host
+
     def solve_steps(self, x, nsteps: int, max_refine: int = 2):
         """nsteps in-place implicit steps x <- A^{-1} x (one CUDA graph)."""
         torch = _torch()
