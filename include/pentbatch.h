@@ -197,6 +197,29 @@ pent_status pent_get_info(pent_plan* plan, int64_t* bad_system, int64_t* bad_row
 /* Reset the info word (asynchronous, capture-safe). */
 pent_status pent_clear_info(pent_plan* plan);
 
+/*
+ * Factor and solve `batch` systems of n rows each without allocating anything
+ * (the paper has no counterpart to this entry point; it serves callers that
+ * may not allocate device memory -- code that runs under a framework whose
+ * allocator owns the GPU, plug-ins that are given buffers but no allocator, or
+ * work that is about to be captured into a CUDA graph).  a..e, f, x: device
+ * arrays of batch*n doubles, system-major as above; x may alias f.  d_info:
+ * optional device word (may be NULL) that receives the lowest failing
+ * (system << 32 | row) of a zero or non-finite pivot, or 0x7f7f7f7f7f7f7f7f.
+ * Scratch: a fixed 32 MiB array owned by the library in every device's
+ * memory, held from the moment a device loads the library until the process
+ * exits; ceil(batch/32) * 32 * n * 24 bytes must fit in it (for example 1,365
+ * systems of 1,024 rows), otherwise PENT_EINVAL and nothing is launched.  The
+ * first call on each device looks up the array's device address; make that
+ * first call before any stream capture.  Every call uses the same array, so
+ * calls whose kernels may overlap on the GPU (unordered streams) race; order
+ * them on one stream.  Asynchronous on cuda_stream; no cudaMalloc, cudaFree
+ * or other allocating call is made.
+ */
+pent_status pent_gbsv_batch_noalloc(int64_t batch, int64_t n, const double* a, const double* b, const double* c,
+                                    const double* d, const double* e, const double* f, double* x,
+                                    unsigned long long* d_info, void* cuda_stream);
+
 /* Destroy a plan (host memory only; the workspace is the caller's). NULL is a no-op. */
 void pent_plan_destroy(pent_plan* plan);
 
