@@ -97,14 +97,17 @@ pent_status pent_plan_bind(pent_plan* plan, void* d_workspace, void* cuda_stream
 
 /*
  * Tuning options (keys below); values are integers.  Unknown keys or values
- * return PENT_EINVAL.  Changing PENT_OPT_THREADS_PER_SYSTEM after a
- * factorisation returns PENT_EINVAL (the factor layout depends on it).
+ * return PENT_EINVAL.  PENT_OPT_THREADS_PER_SYSTEM changes the factor layout
+ * and the workspace size, so it is accepted only before pent_plan_bind (query
+ * pent_plan_workspace_bytes after setting it).
  */
 enum {
-  PENT_OPT_THREADS_PER_SYSTEM = 1, /* 1 (one thread per system) or 32 (one warp per system, F32_REFINE) */
+  PENT_OPT_THREADS_PER_SYSTEM = 1, /* PENT_F64: 1 (one thread per system).  PENT_F32_REFINE: 32..512, a power
+                                      of two (one CTA of that many threads per system; n <= 4096) */
   PENT_OPT_RESIDUAL = 2,           /* pent_residual */
-  PENT_OPT_BLOCK_WARPS = 3,        /* warps per CTA for the solve kernels (1..32) */
-  PENT_OPT_REFINE_TOL_LOG2 = 4     /* refinement stops when |r| <= 2^-tol * |f| (default 50) */
+  PENT_OPT_BLOCK_WARPS = 3,        /* PENT_F64: warps per CTA of the solve kernels (1..8) */
+  PENT_OPT_REFINE_TOL_LOG2 = 4,    /* refinement stops once a correction is <= 2^-tol * |x| (default 40) */
+  PENT_OPT_UNROLL = 5              /* PENT_F64: rows loaded ahead of the arithmetic: 2, 4 or 8 (default 4) */
 };
 pent_status pent_plan_set_option(pent_plan* plan, int key, int64_t value);
 pent_status pent_plan_get_option(const pent_plan* plan, int key, int64_t* value);

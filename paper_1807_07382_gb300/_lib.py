@@ -27,6 +27,7 @@ PENT_OPT_THREADS_PER_SYSTEM = 1
 PENT_OPT_RESIDUAL = 2
 PENT_OPT_BLOCK_WARPS = 3
 PENT_OPT_REFINE_TOL_LOG2 = 4
+PENT_OPT_UNROLL = 5
 
 # every symbol the header declares, with (restype, argtypes)
 _vp = ctypes.c_void_p

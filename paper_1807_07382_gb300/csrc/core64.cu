@@ -3,12 +3,14 @@
 // Layout.  Systems are visited in "sorted position" order q = 0..ngroups*32-1
 // (perm[q] is the system, longest first, so a warp's 32 systems have similar
 // lengths).  Warp k owns the 32 systems q = 32k..32k+31 and walks the rows of
-// all of them in lock step; record row R = goff[k] + r holds row r of those 32
-// systems next to each other, so every factor load and every scratch store of
-// the warp is one contiguous, coalesced 256-byte access.  This is the
-// interleaved one-thread-per-system layout of the paper (Sec. 2.6), applied per
-// group of 32 instead of across the whole batch, which keeps uneven lengths
-// cheap to pad.
+// all of them in lock step.  Record rows R = goff[k] + r (goff even, group
+// lengths padded to even) are stored in pairs: for factor plane p the pair
+// PR = R / 2 holds, for each lane, rows 2 PR and 2 PR + 1 side by side, so a
+// warp fetches two rows of one plane for its 32 systems with one coalesced
+// 512-byte access of 16 bytes per lane.  This is the interleaved
+// one-thread-per-system layout of the paper (Sec. 2.6), applied per group of
+// 32 systems (which keeps uneven lengths cheap to pad) and with row pairs (which
+// halves the number of memory instructions per row).
 #include <cmath>
 #include <cstdint>
 
@@ -55,10 +57,10 @@ __global__ void k_factor64(DevPlan P, const double* __restrict__ a, const double
   const int64_t Lg = P.shared ? P.n_shared : P.glen[k];
   const int64_t R0 = P.shared ? 0 : P.goff[k];
   auto fwd_at = [&](int64_t r, int p) -> double& {
-    return P.shared ? F.fwd[r * 3 + p] : F.fwd[((R0 + r) * 3 + p) * kWarp + lane];
+    return P.shared ? F.fwd[r * 3 + p] : F.fwd[(((R0 + r) >> 1) * 3 + p) * 2 * kWarp + lane * 2 + ((R0 + r) & 1)];
   };
   auto bwd_at = [&](int64_t r, int p) -> double& {
-    return P.shared ? F.bwd[r * 2 + p] : F.bwd[((R0 + r) * 2 + p) * kWarp + lane];
+    return P.shared ? F.bwd[r * 2 + p] : F.bwd[(((R0 + r) >> 1) * 2 + p) * 2 * kWarp + lane * 2 + ((R0 + r) & 1)];
   };
   int64_t r = 0;
   if (s >= 0) {
@@ -143,11 +145,16 @@ __device__ __forceinline__ Lane lane_setup(const DevPlan& P, int64_t k, int lane
 
 template <bool SHARED>
 __device__ __forceinline__ int64_t fwd_idx(const Lane& L, int64_t r, int p, int lane) {
-  return SHARED ? r * 3 + p : ((L.R0 + r) * 3 + p) * kWarp + lane;
+  return SHARED ? r * 3 + p : (((L.R0 + r) >> 1) * 3 + p) * 2 * kWarp + lane * 2 + ((L.R0 + r) & 1);
 }
 template <bool SHARED>
 __device__ __forceinline__ int64_t bwd_idx(const Lane& L, int64_t r, int p, int lane) {
-  return SHARED ? r * 2 + p : ((L.R0 + r) * 2 + p) * kWarp + lane;
+  return SHARED ? r * 2 + p : (((L.R0 + r) >> 1) * 2 + p) * 2 * kWarp + lane * 2 + ((L.R0 + r) & 1);
+}
+// Scratch row r of the lane (g of the forward sweep, z of the adjoint).
+template <bool SHARED>
+__device__ __forceinline__ int64_t scr_idx(const Lane& L, int64_t r, int lane) {
+  return SHARED ? (L.R0 + r) * kWarp + lane : (((L.R0 + r) >> 1) * kWarp + lane) * 2 + ((L.R0 + r) & 1);
 }
 
 // x = A^{-1} f by the forward substitution L g = f and the back substitution
@@ -191,7 +198,7 @@ __global__ void __launch_bounds__(256) k_solve64(DevPlan P, F64Factors F, const 
       const int64_t r = r0 + u;
       if (r < L.Lg) {
         const double g = fma(-cb[u], g1, fma(-ce[u], g2, ca[u] * cf[u]));
-        gscr[(L.R0 + r) * kWarp + lane] = g;
+        gscr[scr_idx<SHARED>(L, r, lane)] = g;
         g2 = g1;
         g1 = g;
       }
@@ -215,7 +222,7 @@ __global__ void __launch_bounds__(256) k_solve64(DevPlan P, F64Factors F, const 
       if (r >= 0) {
         Ga[u] = __ldg(bwd + bwd_idx<SHARED>(L, r, 0, lane));
         De[u] = __ldg(bwd + bwd_idx<SHARED>(L, r, 1, lane));
-        Gv[u] = gscr[(L.R0 + r) * kWarp + lane];
+        Gv[u] = gscr[scr_idx<SHARED>(L, r, lane)];
       }
     }
   };
@@ -235,6 +242,116 @@ __global__ void __launch_bounds__(256) k_solve64(DevPlan P, F64Factors F, const 
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
+      cg[u] = ng[u];
+      cd[u] = nd[u];
+      cG[u] = nG[u];
+    }
+  }
+}
+
+// The same substitutions for per-system factors, walking row pairs: every
+// factor plane, the scratch g and (when aligned) f and x move 16 bytes per lane
+// per access.  Loads run U2 pairs ahead of the arithmetic (register double
+// buffering).
+template <int U2>
+__global__ void __launch_bounds__(128) k_solve64_pair(DevPlan P, F64Factors F, const double* f, double* x,
+                                                      double* __restrict__ gscr) {
+  const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kWarp;
+  if (k >= P.ngroups) return;
+  const int lane = threadIdx.x & (kWarp - 1);
+  const Lane L = lane_setup<false>(P, k, lane);
+  const double2* __restrict__ fwd = reinterpret_cast<const double2*>(F.fwd);
+  const double2* __restrict__ bwd = reinterpret_cast<const double2*>(F.bwd);
+  double2* __restrict__ g2s = reinterpret_cast<double2*>(gscr);
+  const int64_t np = L.Lg >> 1;   // pairs walked by the warp (Lg is even)
+  const int64_t P0 = L.R0 >> 1;   // first record pair of the warp
+  const bool fvec = ((L.fo & 1) == 0) && ((((uintptr_t)f) & 15) == 0);
+  const bool xvec = ((L.fo & 1) == 0) && ((((uintptr_t)x) & 15) == 0);
+
+  // ---- forward: L g = f ----
+  double2 ca[U2], cb[U2], ce[U2], cf[U2];
+  double2 na[U2], nb[U2], ne[U2], nf[U2];
+  auto load_f = [&](int64_t q0, double2* A, double2* B, double2* E, double2* Fv) {
+#pragma unroll
+    for (int u = 0; u < U2; ++u) {
+      const int64_t q = q0 + u;
+      if (q < np) {
+        const double2* rec = fwd + ((P0 + q) * 3) * kWarp + lane;
+        A[u] = __ldg(rec);
+        B[u] = __ldg(rec + kWarp);
+        E[u] = __ldg(rec + 2 * kWarp);
+        const int64_t r = 2 * q;
+        if (fvec && r + 1 < L.n) {
+          Fv[u] = *reinterpret_cast<const double2*>(f + L.fo + r);
+        } else {
+          Fv[u].x = (r < L.n) ? f[L.fo + r] : 0.0;
+          Fv[u].y = (r + 1 < L.n) ? f[L.fo + r + 1] : 0.0;
+        }
+      }
+    }
+  };
+  double g1 = 0.0, g2 = 0.0;
+  load_f(0, ca, cb, ce, cf);
+  for (int64_t q0 = 0; q0 < np; q0 += U2) {
+    if (q0 + U2 < np) load_f(q0 + U2, na, nb, ne, nf);
+#pragma unroll
+    for (int u = 0; u < U2; ++u) {
+      const int64_t q = q0 + u;
+      if (q < np) {
+        const double ga = fma(-cb[u].x, g1, fma(-ce[u].x, g2, ca[u].x * cf[u].x));
+        const double gb = fma(-cb[u].y, ga, fma(-ce[u].y, g1, ca[u].y * cf[u].y));
+        g2s[(P0 + q) * kWarp + lane] = make_double2(ga, gb);
+        g2 = ga;
+        g1 = gb;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U2; ++u) {
+      ca[u] = na[u];
+      cb[u] = nb[u];
+      ce[u] = ne[u];
+      cf[u] = nf[u];
+    }
+  }
+
+  // ---- back: R x = g ----
+  double2 cg[U2], cd[U2], cG[U2];
+  double2 ng[U2], nd[U2], nG[U2];
+  auto load_b = [&](int64_t q0, double2* Ga, double2* De, double2* Gv) {
+#pragma unroll
+    for (int u = 0; u < U2; ++u) {
+      const int64_t q = q0 - u;
+      if (q >= 0) {
+        const double2* rec = bwd + ((P0 + q) * 2) * kWarp + lane;
+        Ga[u] = __ldg(rec);
+        De[u] = __ldg(rec + kWarp);
+        Gv[u] = g2s[(P0 + q) * kWarp + lane];
+      }
+    }
+  };
+  double x1 = 0.0, x2 = 0.0;
+  load_b(np - 1, cg, cd, cG);
+  for (int64_t q0 = np - 1; q0 >= 0; q0 -= U2) {
+    if (q0 - U2 >= 0) load_b(q0 - U2, ng, nd, nG);
+#pragma unroll
+    for (int u = 0; u < U2; ++u) {
+      const int64_t q = q0 - u;
+      if (q >= 0) {
+        const double xb = fma(-cg[u].y, x1, fma(-cd[u].y, x2, cG[u].y));
+        const double xa = fma(-cg[u].x, xb, fma(-cd[u].x, x1, cG[u].x));
+        const int64_t r = 2 * q;
+        if (xvec && r + 1 < L.n) {
+          *reinterpret_cast<double2*>(x + L.fo + r) = make_double2(xa, xb);
+        } else {
+          if (r < L.n) x[L.fo + r] = xa;
+          if (r + 1 < L.n) x[L.fo + r + 1] = xb;
+        }
+        x2 = xb;
+        x1 = xa;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U2; ++u) {
       cg[u] = ng[u];
       cd[u] = nd[u];
       cG[u] = nG[u];
@@ -264,7 +381,7 @@ __global__ void __launch_bounds__(256) k_adjoint64(DevPlan P, F64Factors F, cons
   for (int64_t r = 0; r < L.Lg; ++r) {
     const double fr = (r < L.n) ? f[L.fo + r] : 0.0;
     const double z = fma(-gam_m1, z1, fma(-del_m2, z2, fr));
-    zscr[(L.R0 + r) * kWarp + lane] = z;
+    zscr[scr_idx<SHARED>(L, r, lane)] = z;
     z2 = z1;
     z1 = z;
     del_m2 = del_m1;
@@ -276,7 +393,7 @@ __global__ void __launch_bounds__(256) k_adjoint64(DevPlan P, F64Factors F, cons
   double bp_p1 = 0.0, ep_p1 = 0.0, ep_p2 = 0.0;  // (beta/alpha)_{i+1}, (eps/alpha)_{i+1}, (eps/alpha)_{i+2}
   for (int64_t r = L.Lg - 1; r >= 0; --r) {
     const double ainv = __ldg(fwd + fwd_idx<SHARED>(L, r, 0, lane));
-    const double z = zscr[(L.R0 + r) * kWarp + lane];
+    const double z = zscr[scr_idx<SHARED>(L, r, lane)];
     const double w = fma(-bp_p1, w1, fma(-ep_p2, w2, z));
     if (r < L.n) y[L.fo + r] = ainv * w;
     w2 = w1;
@@ -325,13 +442,24 @@ cudaError_t launch_factor64(const DevPlan& P, const double* a, const double* b, 
 }
 
 cudaError_t launch_solve64(const DevPlan& P, F64Factors F, const double* f, double* x, double* gscr, int block_warps,
-                           cudaStream_t st) {
+                           int unroll, cudaStream_t st) {
   const int block = kWarp * block_warps;
   const int grid = grid_for(P.ngroups * kWarp, block);
-  if (P.shared)
-    k_solve64<true, 8><<<grid, block, 0, st>>>(P, F, f, x, gscr);
-  else
-    k_solve64<false, 8><<<grid, block, 0, st>>>(P, F, f, x, gscr);
+  if (P.shared) {
+#define PENT_U(U_)                                                   \
+  if (unroll == U_) {                                                \
+    k_solve64<true, U_><<<grid, block, 0, st>>>(P, F, f, x, gscr);   \
+    return cudaGetLastError();                                       \
+  }
+    PENT_U(2) PENT_U(4) PENT_U(8)
+#undef PENT_U
+    return cudaErrorInvalidValue;
+  }
+  // per-system factors: row pairs, unroll rows = 2 x pairs ahead
+  if (unroll == 2) k_solve64_pair<1><<<grid, block, 0, st>>>(P, F, f, x, gscr);
+  else if (unroll == 4) k_solve64_pair<2><<<grid, block, 0, st>>>(P, F, f, x, gscr);
+  else if (unroll == 8) k_solve64_pair<4><<<grid, block, 0, st>>>(P, F, f, x, gscr);
+  else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 

@@ -1,4 +1,4 @@
-// FP32 substitution with iterative refinement, one warp per system.
+// FP32 substitution with iterative refinement, one CTA per system.
 //
 // Why this shape.  On GB300 the FP64 pipe runs at 1/64 of the FP32 rate, and
 // conversions between FP64 and FP32 run on that same slow pipe.  The solve
@@ -9,16 +9,23 @@
 // inputs are split into float pairs and results reassembled with integer bit
 // operations instead of conversion instructions.
 //
-// One warp owns one system of n <= 32 L rows: lane t holds rows t L .. t L + L - 1
-// in registers.  Each substitution (Sec. 2.4: L g = f, then R x = g) is a
-// second-order linear recurrence, so a lane's chunk acts on the two carried
-// values as an affine map.  The lane runs its chunk from a zero state to get
-// the affine part, the warp composes the maps with a Kogge-Stone shuffle scan
-// (the 2x2 linear parts of the chunks are precomputed at factorisation time,
-// because they depend on the factors only), and every lane reruns its chunk
-// from the true entering state.  The system's factors (20 bytes per row) are
-// staged once in shared memory and reused by every substitution of every
-// refinement step, so a refined solve reads its factors from HBM once.
+// One CTA of P = 32 W threads owns one system of n <= P L rows: thread t holds
+// rows t L .. t L + L - 1, their factors and their right-hand side in registers
+// (all loaded with coalesced 16-byte accesses, since a thread's rows are
+// contiguous).  Each substitution (Sec. 2.4: L g = f, then R x = g) is a
+// second-order linear recurrence, so a thread's chunk acts on the two carried
+// values as an affine map.  The thread runs its chunk from a zero state to get
+// the affine part; the CTA composes the maps with a Kogge-Stone shuffle scan in
+// each warp and a short carry across warps; then every thread reruns its chunk
+// from the true entering state.  The factors are read from HBM once per call
+// and reused by every substitution of every refinement step.
+//
+// The hyperdiffusion matrices are symmetric, so A = L D^{-1} L^T with D the
+// diagonal alpha of L: R = D^{-1} L^T, gamma_i = beta_{i+1} / alpha_i and
+// delta_i = epsilon_{i+2} / alpha_i, and epsilon_i = a_i is sigma times a
+// stencil weight.  Only 1/alpha_i and beta_i are stored (8 bytes per row in
+// FP32); epsilon, gamma, delta and the chunks' 2x2 transfer maps are rebuilt in
+// registers, trading FP32 arithmetic for HBM bytes.
 #include <cmath>
 #include <cstdint>
 
@@ -26,18 +33,6 @@
 
 namespace pent {
 namespace {
-
-// ---------------------------------------------------------------- async copies (sm_80+ cp.async)
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // ---------------------------------------------------------------- error-free transformations (FP32)
 
@@ -90,6 +85,11 @@ __device__ __forceinline__ void split_scaled(double v, int k, float& hi, float& 
   lo = __uint_as_float(__float_as_uint(__fmul_rn(r, scale)) ^ sign);
 }
 
+// Rare path of f2d_shift (subnormal float or a result outside the normal double
+// range).  Kept out of line so that its FP64 arithmetic is never if-converted
+// into the common path.
+__device__ __noinline__ double f2d_shift_slow(float v, int k) { return ldexp((double)v, k); }
+
 // Exact v * 2^k as a double, by moving v's exponent and mantissa bit fields.
 __device__ __forceinline__ double f2d_shift(float v, int k) {
   const unsigned u = __float_as_uint(v);
@@ -97,7 +97,7 @@ __device__ __forceinline__ double f2d_shift(float v, int k) {
   if (a == 0u) return 0.0;
   const int e = (int)(a >> 23);
   const int de = e + 896 + k;
-  if (e == 0 || e == 255 || de < 1 || de > 2046) return ldexp((double)v, k);  // rare: subnormal / out of range
+  if (e == 0 || e == 255 || de < 1 || de > 2046) return f2d_shift_slow(v, k);
   const unsigned long long bits = ((unsigned long long)(u & 0x80000000u) << 32) |
                                   (((unsigned long long)a + ((unsigned long long)(896 + k) << 23)) << 29);
   return __longlong_as_double((long long)bits);
@@ -128,302 +128,551 @@ __device__ __forceinline__ void d4_weights_f(int i, int n, float w[5]) {
   }
 }
 
-// ---------------------------------------------------------------- chunked warp substitution
+// ---------------------------------------------------------------- CTA-wide affine scans
 
-// In place v <- A^{-1} v for the warp's system in FP32 (forward L g = v, back R x = g).
-// sf: the system's factor planes in shared memory, slot j*32 + lane.
+// x -> [[a, b], [c, d]] x + (u, v): the effect of a chunk of rows on the two carried values.
+struct Aff {
+  float a, b, c, d, u, v;
+};
+
+// `later` applied after `earlier`.
+__device__ __forceinline__ Aff compose(const Aff& L, const Aff& E) {
+  Aff r;
+  r.a = fmaf(L.a, E.a, L.b * E.c);
+  r.b = fmaf(L.a, E.b, L.b * E.d);
+  r.c = fmaf(L.c, E.a, L.d * E.c);
+  r.d = fmaf(L.c, E.b, L.d * E.d);
+  r.u = fmaf(L.a, E.u, fmaf(L.b, E.v, L.u));
+  r.v = fmaf(L.c, E.u, fmaf(L.d, E.v, L.v));
+  return r;
+}
+
+template <bool UP>
+__device__ __forceinline__ Aff shfl_aff(const Aff& x, int d) {
+  Aff r;
+  if (UP) {
+    r.a = __shfl_up_sync(0xffffffffu, x.a, d);
+    r.b = __shfl_up_sync(0xffffffffu, x.b, d);
+    r.c = __shfl_up_sync(0xffffffffu, x.c, d);
+    r.d = __shfl_up_sync(0xffffffffu, x.d, d);
+    r.u = __shfl_up_sync(0xffffffffu, x.u, d);
+    r.v = __shfl_up_sync(0xffffffffu, x.v, d);
+  } else {
+    r.a = __shfl_down_sync(0xffffffffu, x.a, d);
+    r.b = __shfl_down_sync(0xffffffffu, x.b, d);
+    r.c = __shfl_down_sync(0xffffffffu, x.c, d);
+    r.d = __shfl_down_sync(0xffffffffu, x.d, d);
+    r.u = __shfl_down_sync(0xffffffffu, x.u, d);
+    r.v = __shfl_down_sync(0xffffffffu, x.v, d);
+  }
+  return r;
+}
+
+// Coupling below this norm is dropped from the scans: it changes the carried
+// values by less than FP32 resolution, and the refinement corrects the FP32
+// solve anyway.
+constexpr float kScanTol = 9.3132257e-10f;  // 2^-30
+
+__device__ __forceinline__ float mat_norm(const Aff& m) {
+  return fmaxf(fmaxf(fabsf(m.a), fabsf(m.b)), fmaxf(fabsf(m.c), fabsf(m.d)));
+}
+
+// Entering state of this thread's chunk for a sweep through the CTA's chunks.
+// FWD: chunks are visited in increasing thread order; otherwise decreasing.
+// `a` is this chunk's map (linear part from the factors, affine part from a
+// zero-state pass).  The system is entered with state 0.  The Kogge-Stone
+// levels stop as soon as every lane's window either reaches the warp's first
+// chunk or composes to a negligible linear part, since later levels would only
+// add terms multiplied by it.  sh: 2 float4 per warp.
+template <int W, bool FWD>
+__device__ __forceinline__ void scan_entry(Aff a, int lane, int warp, float4* sh, float& e0, float& e1) {
+#pragma unroll 1
+  for (int d = 1; d < 32; d <<= 1) {
+    const Aff o = shfl_aff<FWD>(a, d);
+    if (FWD ? (lane >= d) : (lane + d < 32)) a = compose(a, o);
+    const bool done = (FWD ? (lane < 2 * d) : (lane + 2 * d > 31)) || mat_norm(a) < kScanTol;
+    if (__all_sync(0xffffffffu, done)) break;
+  }
+  const Aff prev = shfl_aff<FWD>(a, 1);  // inclusive result of the previous chunk in sweep order
+  const bool first = FWD ? (lane == 0) : (lane == 31);
+  float c0 = 0.f, c1 = 0.f;  // state entering this warp
+  if (W > 1) {
+    if (FWD ? (lane == 31) : (lane == 0)) {
+      sh[2 * warp] = make_float4(a.a, a.b, a.c, a.d);
+      sh[2 * warp + 1] = make_float4(a.u, a.v, 0.f, 0.f);
+    }
+    __syncthreads();
+    if (FWD) {
+      for (int w = 0; w < warp; ++w) {
+        const float4 m = sh[2 * w], b = sh[2 * w + 1];
+        const float n0 = fmaf(m.x, c0, fmaf(m.y, c1, b.x));
+        const float n1 = fmaf(m.z, c0, fmaf(m.w, c1, b.y));
+        c0 = n0;
+        c1 = n1;
+      }
+    } else {
+      for (int w = W - 1; w > warp; --w) {
+        const float4 m = sh[2 * w], b = sh[2 * w + 1];
+        const float n0 = fmaf(m.x, c0, fmaf(m.y, c1, b.x));
+        const float n1 = fmaf(m.z, c0, fmaf(m.w, c1, b.y));
+        c0 = n0;
+        c1 = n1;
+      }
+    }
+  }
+  if (first) {
+    e0 = c0;
+    e1 = c1;
+  } else {
+    e0 = fmaf(prev.a, c0, fmaf(prev.b, c1, prev.u));
+    e1 = fmaf(prev.c, c0, fmaf(prev.d, c1, prev.v));
+  }
+}
+
+template <int W>
+__device__ __forceinline__ float block_max(float v, int lane, int warp, float* sh) {
+  v = warp_max(v);
+  if (W == 1) return v;
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  float r = sh[0];
+#pragma unroll
+  for (int w = 1; w < W; ++w) r = fmaxf(r, sh[w]);
+  return r;
+}
+
+template <int W>
+__device__ __forceinline__ int block_max_i(int v, int lane, int warp, int* sh) {
+  v = warp_max_i(v);
+  if (W == 1) return v;
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  int r = sh[0];
+#pragma unroll
+  for (int w = 1; w < W; ++w) r = max(r, sh[w]);
+  return r;
+}
+
+// Shared scratch of one CTA.  Scan and reduction slots rotate through four
+// buffers, so a single barrier per scan separates every write from the reads
+// of the same buffer.
+template <int W>
+struct Smem {
+  float4 scan[4][2 * W];
+  float4 edge[32 * W][2];  // per thread: first two rows (hi, lo), last two rows (hi, lo)
+  float red[4][2 * W];
+  int redi[W];
+};
+
+// Per-thread factors of its L rows and the chunk maps, rebuilt from the stored
+// 1/alpha and beta (see the header comment).
 template <int L>
-__device__ __forceinline__ void warp_solve32(float (&v)[L], const float* __restrict__ sf, const float4 pf,
-                                             const float4 pb, int lane) {
-  const float* A = sf;
-  const float* B = sf + 32 * L;
-  const float* E = sf + 64 * L;
-  const float* G = sf + 96 * L;
-  const float* D = sf + 128 * L;
-  // forward, pass 1: chunk from a zero entering state -> affine part (p2, p1)
+struct ChunkFactors {
+  float A[L];  // 1/alpha_i
+  float B[L];  // beta_i / alpha_i
+  float E[L];  // epsilon_i / alpha_i
+  float G[L];  // gamma_i
+  float D[L];  // delta_i
+  float4 pf;   // forward map (row-major 2x2)
+  float4 pb;   // backward map
+};
+
+// In place v <- A^{-1} v (FP32): forward L g = v, then back R x = g.
+template <int W, int L>
+__device__ __forceinline__ void cta_solve32(float (&v)[L], const ChunkFactors<L>& cf, int lane, int warp, Smem<W>& sm,
+                                            int& phase) {
   float p2 = 0.f, p1 = 0.f;
 #pragma unroll
   for (int j = 0; j < L; ++j) {
-    const int o = j * 32 + lane;
-    const float g = fmaf(-B[o], p1, fmaf(-E[o], p2, A[o] * v[j]));
+    const float g = fmaf(-cf.B[j], p1, fmaf(-cf.E[j], p2, cf.A[j] * v[j]));
     p2 = p1;
     p1 = g;
   }
-  // inclusive scan of affine maps (entering (g_{i-2}, g_{i-1}) -> leaving), earlier lanes first
-  float m00 = pf.x, m01 = pf.y, m10 = pf.z, m11 = pf.w, b0 = p2, b1 = p1;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const float o00 = __shfl_up_sync(0xffffffffu, m00, d), o01 = __shfl_up_sync(0xffffffffu, m01, d);
-    const float o10 = __shfl_up_sync(0xffffffffu, m10, d), o11 = __shfl_up_sync(0xffffffffu, m11, d);
-    const float ob0 = __shfl_up_sync(0xffffffffu, b0, d), ob1 = __shfl_up_sync(0xffffffffu, b1, d);
-    if (lane >= d) {
-      const float n00 = fmaf(m00, o00, m01 * o10), n01 = fmaf(m00, o01, m01 * o11);
-      const float n10 = fmaf(m10, o00, m11 * o10), n11 = fmaf(m10, o01, m11 * o11);
-      const float nb0 = fmaf(m00, ob0, fmaf(m01, ob1, b0));
-      const float nb1 = fmaf(m10, ob0, fmaf(m11, ob1, b1));
-      m00 = n00; m01 = n01; m10 = n10; m11 = n11; b0 = nb0; b1 = nb1;
-    }
-  }
-  p2 = __shfl_up_sync(0xffffffffu, b0, 1);
-  p1 = __shfl_up_sync(0xffffffffu, b1, 1);
-  if (lane == 0) p2 = p1 = 0.f;
-  // forward, pass 2 from the true entering state
+  float e0, e1;
+  scan_entry<W, true>(Aff{cf.pf.x, cf.pf.y, cf.pf.z, cf.pf.w, p2, p1}, lane, warp, sm.scan[phase++ & 3], e0, e1);
+  p2 = e0;
+  p1 = e1;
 #pragma unroll
   for (int j = 0; j < L; ++j) {
-    const int o = j * 32 + lane;
-    const float g = fmaf(-B[o], p1, fmaf(-E[o], p2, A[o] * v[j]));
+    const float g = fmaf(-cf.B[j], p1, fmaf(-cf.E[j], p2, cf.A[j] * v[j]));
     v[j] = g;
     p2 = p1;
     p1 = g;
   }
-  // back, pass 1: descending from a zero entering state (x_{i+1}, x_{i+2})
   float s1 = 0.f, s2 = 0.f;
 #pragma unroll
   for (int j = L - 1; j >= 0; --j) {
-    const int o = j * 32 + lane;
-    const float xv = fmaf(-G[o], s1, fmaf(-D[o], s2, v[j]));
+    const float xv = fmaf(-cf.G[j], s1, fmaf(-cf.D[j], s2, v[j]));
     s2 = s1;
     s1 = xv;
   }
-  m00 = pb.x; m01 = pb.y; m10 = pb.z; m11 = pb.w; b0 = s1; b1 = s2;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const float o00 = __shfl_down_sync(0xffffffffu, m00, d), o01 = __shfl_down_sync(0xffffffffu, m01, d);
-    const float o10 = __shfl_down_sync(0xffffffffu, m10, d), o11 = __shfl_down_sync(0xffffffffu, m11, d);
-    const float ob0 = __shfl_down_sync(0xffffffffu, b0, d), ob1 = __shfl_down_sync(0xffffffffu, b1, d);
-    if (lane + d < 32) {
-      const float n00 = fmaf(m00, o00, m01 * o10), n01 = fmaf(m00, o01, m01 * o11);
-      const float n10 = fmaf(m10, o00, m11 * o10), n11 = fmaf(m10, o01, m11 * o11);
-      const float nb0 = fmaf(m00, ob0, fmaf(m01, ob1, b0));
-      const float nb1 = fmaf(m10, ob0, fmaf(m11, ob1, b1));
-      m00 = n00; m01 = n01; m10 = n10; m11 = n11; b0 = nb0; b1 = nb1;
-    }
-  }
-  s1 = __shfl_down_sync(0xffffffffu, b0, 1);
-  s2 = __shfl_down_sync(0xffffffffu, b1, 1);
-  if (lane == 31) s1 = s2 = 0.f;
+  scan_entry<W, false>(Aff{cf.pb.x, cf.pb.y, cf.pb.z, cf.pb.w, s1, s2}, lane, warp, sm.scan[phase++ & 3], e0, e1);
+  s1 = e0;
+  s2 = e1;
 #pragma unroll
   for (int j = L - 1; j >= 0; --j) {
-    const int o = j * 32 + lane;
-    const float xv = fmaf(-G[o], s1, fmaf(-D[o], s2, v[j]));
+    const float xv = fmaf(-cf.G[j], s1, fmaf(-cf.D[j], s2, v[j]));
     v[j] = xv;
     s2 = s1;
     s1 = xv;
   }
 }
 
-// r = f - (I + sigma D4) x in float-float, rounded to FP32.  f is read from the
-// shared-memory copy (FP64) and split on the fly; x = xh + xl; the two rows on
-// each side of a lane's chunk come from the neighbouring lanes.
-template <int L>
-__device__ __forceinline__ void residual_hyperdiff(const double* __restrict__ sfx, int kshift, const float (&xh)[L],
-                                                   const float (&xl)[L], float (&r)[L], float sgh, float sgl, int n,
-                                                   int lane) {
-  float m2h = __shfl_up_sync(0xffffffffu, xh[L - 2], 1), m1h = __shfl_up_sync(0xffffffffu, xh[L - 1], 1);
-  float m2l = __shfl_up_sync(0xffffffffu, xl[L - 2], 1), m1l = __shfl_up_sync(0xffffffffu, xl[L - 1], 1);
-  float p1h = __shfl_down_sync(0xffffffffu, xh[0], 1), p2h = __shfl_down_sync(0xffffffffu, xh[1], 1);
-  float p1l = __shfl_down_sync(0xffffffffu, xl[0], 1), p2l = __shfl_down_sync(0xffffffffu, xl[1], 1);
-  if (lane == 0) m2h = m1h = m2l = m1l = 0.f;
-  if (lane == 31) p1h = p2h = p1l = p2l = 0.f;
+// D4 x on a row next to a wall (general reflected weights) as an unevaluated
+// pair (S, Er).  Out of line: only the first two and last two rows of a system
+// take it, and keeping one copy keeps the unrolled kernel small.
+__device__ __noinline__ float2 d4_wall_row(int i, int n, float ah, float al, float bh, float bl, float ch, float cl,
+                                           float dh, float dl, float eh, float el) {
+  float w[5];
+  d4_weights_f(i, n, w);
+  const float xs[5] = {ah, bh, ch, dh, eh};
+  const float xls[5] = {al, bl, cl, dl, el};
+  float S = 0.f, Er = 0.f;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    float p, e, sm, e2;
+    two_prod(w[k], xs[k], p, e);
+    two_sum(S, p, sm, e2);
+    S = sm;
+    Er += e + e2 + w[k] * xls[k];
+  }
+  return make_float2(S, Er);
+}
+
+// r = f - (I + sigma D4) x, rounded to FP32, for this thread's rows.  x = xh + xl.
+// Float-float residual: f as (fh, fl), sigma as (sgh, sgl).  Rows away from the
+// walls use the plain [1, -4, 6, -4, 1] stencil.
+__device__ __forceinline__ float residual_row(float ah, float al, float bh, float bl, float ch, float cl, float dh,
+                                              float dl, float eh, float el, float fhj, float flj, float sgh, float sgl,
+                                              int i, int n) {
+  float S, Er;
+  if (i >= 2 && i + 2 < n) {
+    float s1, e1, s2, e2, t, e3, p, e4;
+    two_sum(ah, eh, s1, e1);        // x_{i-2} + x_{i+2}
+    two_sum(bh, dh, s2, e2);        // x_{i-1} + x_{i+1}
+    two_sum(s1, -4.f * s2, t, e3);  // 4 s2 is exact
+    two_prod(6.f, ch, p, e4);
+    two_sum(t, p, S, Er);
+    const float low = fmaf(6.f, cl, fmaf(-4.f, bl + dl, al + el));
+    Er = Er + ((e1 - 4.f * e2) + (e3 + e4) + low);
+  } else {
+    const float2 q = d4_wall_row(i, n, ah, al, bh, bl, ch, cl, dh, dl, eh, el);
+    S = q.x;
+    Er = q.y;
+  }
+  float yh, yl;
+  fast_two_sum(S, Er, yh, yl);
+  float Pp, Pe;  // sigma * y
+  two_prod(sgh, yh, Pp, Pe);
+  Pe = fmaf(sgh, yl, fmaf(sgl, yh, Pe));
+  float a1, a2, b1, b2;
+  two_sum(fhj, -ch, a1, a2);
+  two_sum(a1, -Pp, b1, b2);
+  const float low = ((a2 + b2) + (flj - cl)) - Pe;
+  return (i < n) ? (b1 + low) : 0.f;
+}
+
+template <int W, int L>
+__device__ __forceinline__ void residual_ff(const float (&fh)[L], const float (&fl)[L], const float (&xh)[L],
+                                            const float (&xl)[L], float (&r)[L], float sgh, float sgl, int n, int t,
+                                            Smem<W>& sm) {
+  constexpr int P = 32 * W;
+  sm.edge[t][0] = make_float4(xh[0], xh[1], xl[0], xl[1]);
+  sm.edge[t][1] = make_float4(xh[L - 2], xh[L - 1], xl[L - 2], xl[L - 1]);
+  __syncthreads();
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 prv = (t > 0) ? sm.edge[t - 1][1] : zero;      // rows tL-2, tL-1
+  const float4 nxt = (t + 1 < P) ? sm.edge[t + 1][0] : zero;  // rows tL+L, tL+L+1
 #pragma unroll
   for (int j = 0; j < L; ++j) {
-    const int i = lane * L + j;
-    const float ah = (j >= 2) ? xh[j - 2] : (j == 1 ? m1h : m2h);
-    const float al = (j >= 2) ? xl[j - 2] : (j == 1 ? m1l : m2l);
-    const float bh = (j >= 1) ? xh[j - 1] : m1h;
-    const float bl = (j >= 1) ? xl[j - 1] : m1l;
-    const float dh = (j + 1 < L) ? xh[j + 1] : p1h;
-    const float dl = (j + 1 < L) ? xl[j + 1] : p1l;
-    const float eh = (j + 2 < L) ? xh[j + 2] : (j + 1 < L ? p1h : p2h);
-    const float el = (j + 2 < L) ? xl[j + 2] : (j + 1 < L ? p1l : p2l);
-    const float ch = xh[j], cl = xl[j];
-    float S, Er;  // D4 x as S + Er
+    const float ah = (j >= 2) ? xh[j - 2] : (j == 1 ? prv.y : prv.x);
+    const float al = (j >= 2) ? xl[j - 2] : (j == 1 ? prv.w : prv.z);
+    const float bh = (j >= 1) ? xh[j - 1] : prv.y;
+    const float bl = (j >= 1) ? xl[j - 1] : prv.w;
+    const float dh = (j + 1 < L) ? xh[j + 1] : nxt.x;
+    const float dl = (j + 1 < L) ? xl[j + 1] : nxt.z;
+    const float eh = (j + 2 < L) ? xh[j + 2] : (j + 1 < L ? nxt.x : nxt.y);
+    const float el = (j + 2 < L) ? xl[j + 2] : (j + 1 < L ? nxt.z : nxt.w);
+    r[j] = residual_row(ah, al, bh, bl, xh[j], xl[j], dh, dl, eh, el, fh[j], fl[j], sgh, sgl, t * L + j, n);
+  }
+}
+
+// The same residual in native FP64 (the literal reading: FP64 band from sigma,
+// FP64 x and f).  xd holds x in FP64 (scaled by 2^-kshift like f).
+template <int W, int L>
+__device__ __forceinline__ void residual_f64(const double (&fd)[L], const double (&xd)[L], float (&r)[L], double sg,
+                                             int n, int t, Smem<W>& sm) {
+  constexpr int P = 32 * W;
+  double2* ed = reinterpret_cast<double2*>(sm.edge);  // 4 doubles per thread fit in the edge slots
+  ed[2 * t] = make_double2(xd[0], xd[1]);
+  ed[2 * t + 1] = make_double2(xd[L - 2], xd[L - 1]);
+  __syncthreads();
+  const double2 zero = make_double2(0.0, 0.0);
+  const double2 prv = (t > 0) ? ed[2 * (t - 1) + 1] : zero;
+  const double2 nxt = (t + 1 < P) ? ed[2 * (t + 1)] : zero;
+#pragma unroll
+  for (int j = 0; j < L; ++j) {
+    const int i = t * L + j;
+    const double a = (j >= 2) ? xd[j - 2] : (j == 1 ? prv.y : prv.x);
+    const double b = (j >= 1) ? xd[j - 1] : prv.y;
+    const double d = (j + 1 < L) ? xd[j + 1] : nxt.x;
+    const double e = (j + 2 < L) ? xd[j + 2] : (j + 1 < L ? nxt.x : nxt.y);
+    double y;
     if (i >= 2 && i + 2 < n) {
-      float s1, e1, s2, e2, t, e3, p, e4;
-      two_sum(ah, eh, s1, e1);           // x_{i-2} + x_{i+2}
-      two_sum(bh, dh, s2, e2);           // x_{i-1} + x_{i+1}
-      two_sum(s1, -4.f * s2, t, e3);     // 4 s2 is exact
-      two_prod(6.f, ch, p, e4);
-      two_sum(t, p, S, Er);
-      const float low = fmaf(6.f, cl, fmaf(-4.f, bl + dl, al + el));
-      Er = Er + (e1 - 4.f * e2 + e3 + e4 + low);
+      y = fma(6.0, xd[j], fma(-4.0, b + d, a + e));
     } else {
       float w[5];
       d4_weights_f(i, n, w);
-      const float xs[5] = {ah, bh, ch, dh, eh};
-      const float xls[5] = {al, bl, cl, dl, el};
-      S = 0.f;
-      Er = 0.f;
-#pragma unroll
-      for (int k = 0; k < 5; ++k) {
-        float p, e, s, e2;
-        two_prod(w[k], xs[k], p, e);
-        two_sum(S, p, s, e2);
-        S = s;
-        Er += e + e2 + w[k] * xls[k];
-      }
+      y = (double)w[0] * a + (double)w[1] * b + (double)w[2] * xd[j] + (double)w[3] * d + (double)w[4] * e;
     }
-    float yh, yl;
-    fast_two_sum(S, Er, yh, yl);
-    // sigma * y
-    float P, Pe;
-    two_prod(sgh, yh, P, Pe);
-    Pe = fmaf(sgh, yl, fmaf(sgl, yh, Pe));
-    // f - x - sigma D4 x
-    float fh, fl;
-    split_scaled(sfx[j * 33 + lane], kshift, fh, fl);
-    float a1, a2, b1, b2;
-    two_sum(fh, -ch, a1, a2);
-    two_sum(a1, -P, b1, b2);
-    const float low = ((a2 + b2) + (fl - cl)) - Pe;
-    r[j] = (i < n) ? (b1 + low) : 0.f;
+    const double rr = fma(-sg, y, fd[j] - xd[j]);
+    r[j] = (i < n) ? __double2float_rn(rr) : 0.f;
   }
 }
 
-// One warp per system: FP32 solve, then up to max_refine float-float refinement steps.
-template <int L>
-__global__ void __launch_bounds__(32 * 8) k_solve32r(int64_t batch, int n, int shared, const float* __restrict__ fac,
-                                                     const float* __restrict__ phi, const double* __restrict__ sigma,
-                                                     const double* f, double* x, int max_refine, int tol_log2,
-                                                     unsigned long long* info) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int kFacFloats = 5 * 32 * L;
-  constexpr int kBytesPerWarp = kFacFloats * 4 + L * 33 * 8;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t s = blockIdx.x * (int64_t)(blockDim.x >> 5) + warp;
-  if (s >= batch) return;
-  float* sf = reinterpret_cast<float*>(smem + (size_t)warp * kBytesPerWarp);
-  double* sx = reinterpret_cast<double*>(sf + kFacFloats);
-  const int64_t ms = shared ? 0 : s;
-  const float* gfac = fac + ms * kFacFloats;
-#pragma unroll 4
-  for (int c = lane; c < kFacFloats / 4; c += 32) cp_async16(sf + 4 * c, gfac + 4 * c);
-  const double* gf = f + s * (int64_t)n;
-#pragma unroll 4
-  for (int m = 0; m < L; ++m) {
-    const int i = 32 * m + lane;
-    const int t = i / L, j = i - t * L;
-    if (i < n)
-      cp_async8(sx + j * 33 + t, gf + i);
-    else
-      sx[j * 33 + t] = 0.0;
-  }
-  const float4* gphi = reinterpret_cast<const float4*>(phi + (ms * 32 + lane) * 8);
-  const float4 pf = __ldg(gphi), pb = __ldg(gphi + 1);
-  const double sg = sigma[ms];
-  const float sgh = __double2float_rn(sg);
-  const float sgl = __double2float_rn(sg - (double)sgh);
-  cp_async_wait_all();
-  __syncwarp();
+// epsilon_i = a_i of the hyperdiffusion band: sigma times the weight of x_{i-2}
+// in row i, which is 1 for 2 <= i < n (no wall reflection lands there) and 0
+// otherwise.
+__device__ __forceinline__ float eps_of_row(int i, int n, float sgf) { return (i >= 2 && i < n) ? sgf : 0.f; }
 
-  // per-system power-of-two scale: largest |f| maps just below 1
+// Load 1/alpha and beta of the thread's rows and rebuild epsilon/alpha,
+// beta/alpha, gamma, delta and the two chunk maps.
+template <int W, int L>
+__device__ __forceinline__ void load_chunk_factors(ChunkFactors<L>& cf, const float4* __restrict__ gq, int t, int n,
+                                                   float sgf) {
+  constexpr int P = 32 * W;
+  float beta[L];
+#pragma unroll
+  for (int jq = 0; jq < L / 4; ++jq) {
+    const float4 qa = __ldg(gq + (jq * 2 + 0) * P + t), qb = __ldg(gq + (jq * 2 + 1) * P + t);
+    cf.A[4 * jq] = qa.x; cf.A[4 * jq + 1] = qa.y; cf.A[4 * jq + 2] = qa.z; cf.A[4 * jq + 3] = qa.w;
+    beta[4 * jq] = qb.x; beta[4 * jq + 1] = qb.y; beta[4 * jq + 2] = qb.z; beta[4 * jq + 3] = qb.w;
+  }
+  // beta of the first row of the next thread's chunk (row t L + L)
+  const float beta_next = (t + 1 < P) ? __ldg(reinterpret_cast<const float*>(gq + 1 * P + (t + 1))) : 0.f;
+  const int i0 = t * L;
+#pragma unroll
+  for (int j = 0; j < L; ++j) {
+    const int i = i0 + j;
+    const float bnext = (j + 1 < L) ? beta[j + 1] : beta_next;
+    cf.B[j] = beta[j] * cf.A[j];
+    cf.E[j] = eps_of_row(i, n, sgf) * cf.A[j];
+    cf.G[j] = bnext * cf.A[j];
+    cf.D[j] = eps_of_row(i + 2, n, sgf) * cf.A[j];
+  }
+  // forward map: acc <- M_j acc with M_j = [[0, 1], [-E_j, -B_j]]
+  float f00 = 1.f, f01 = 0.f, f10 = 0.f, f11 = 1.f;
+#pragma unroll
+  for (int j = 0; j < L; ++j) {
+    const float n10 = fmaf(-cf.E[j], f00, -cf.B[j] * f10);
+    const float n11 = fmaf(-cf.E[j], f01, -cf.B[j] * f11);
+    f00 = f10;
+    f01 = f11;
+    f10 = n10;
+    f11 = n11;
+  }
+  cf.pf = make_float4(f00, f01, f10, f11);
+  // backward map: acc <- acc B_j with B_j = [[-G_j, -D_j], [1, 0]], rows ascending
+  float t00 = 1.f, t01 = 0.f, t10 = 0.f, t11 = 1.f;
+#pragma unroll
+  for (int j = 0; j < L; ++j) {
+    const float n00 = fmaf(-t00, cf.G[j], t01), n01 = -t00 * cf.D[j];
+    const float n10 = fmaf(-t10, cf.G[j], t11), n11 = -t10 * cf.D[j];
+    t00 = n00;
+    t01 = n01;
+    t10 = n10;
+    t11 = n11;
+  }
+  cf.pb = make_float4(t00, t01, t10, t11);
+}
+
+// One CTA per system: FP32 solve, then up to max_refine refinement steps.
+// RES64 selects the FP64 residual (and FP64 accumulation of x) instead of float-float.
+// Register budget for up to 8 rows per thread: 512 threads per SM (at most 128
+// registers per thread), so that four 128-thread systems share an SM and hide
+// each other's barriers.  Longer chunks keep their registers.
+template <int W, int L, bool RES64>
+__global__ void __launch_bounds__(32 * W, (L <= 8 && 16 / W > 0) ? 16 / W : 1) k_solve32r(int64_t batch, int n, int shared, const float4* __restrict__ fac,
+                                                     const double* __restrict__ sigma,
+                                                     const float2* __restrict__ sigma2, const double* f, double* x,
+                                                     int max_refine, int tol_log2, int vec_io,
+                                                     unsigned long long* info) {
+  constexpr int P = 32 * W;
+  static_assert(L % 4 == 0, "rows per thread must be a multiple of 4");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem<W>& sm = *reinterpret_cast<Smem<W>*>(smem_raw);
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int64_t s = blockIdx.x;
+  if (s >= batch) return;
+  const int64_t ms = shared ? 0 : s;
+  int phase = 0;
+
+  // ---- loads: factors, right-hand side (all coalesced) ----
+  const float2 sgp = __ldg(sigma2 + ms);  // sigma as an FP32 pair, split at factorisation time
+  const float sgh = sgp.x, sgl = sgp.y;
+  ChunkFactors<L> cf;
+  load_chunk_factors<W, L>(cf, fac + ms * (int64_t)(2 * P * L / 4), t, n, sgh);
+  const double* fs = f + s * (int64_t)n;
+  const int i0 = t * L;
+  double fv[L];
+  if (vec_io && i0 + L <= n) {
+#pragma unroll
+    for (int j = 0; j < L; j += 2) {
+      const double2 q = *reinterpret_cast<const double2*>(fs + i0 + j);
+      fv[j] = q.x;
+      fv[j + 1] = q.y;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < L; ++j) fv[j] = (i0 + j < n) ? fs[i0 + j] : 0.0;
+  }
+
+  // ---- per-system power-of-two scale: the largest |f| maps just below 1 ----
   int emax = 0;
 #pragma unroll
   for (int j = 0; j < L; ++j) {
-    const unsigned top = (unsigned)((unsigned long long)__double_as_longlong(sx[j * 33 + lane]) >> 32);
+    const unsigned top = (unsigned)((unsigned long long)__double_as_longlong(fv[j]) >> 32);
     emax = max(emax, (int)((top >> 20) & 0x7ffu));
   }
-  emax = warp_max_i(emax);
+  emax = block_max_i<W>(emax, lane, warp, sm.redi);
   const int kshift = emax - 1022;
 
-  float xh[L], xl[L], v[L];
+  float v[L], xh[L], xl[L];
+  float fh[L], fl[L];
 #pragma unroll
-  for (int j = 0; j < L; ++j) {
-    float lo;
-    split_scaled(sx[j * 33 + lane], kshift, v[j], lo);
-  }
-  warp_solve32<L>(v, sf, pf, pb, lane);
+  for (int j = 0; j < L; ++j) split_scaled(fv[j], kshift, fh[j], fl[j]);
 #pragma unroll
-  for (int j = 0; j < L; ++j) {
-    xh[j] = v[j];
-    xl[j] = 0.f;
-  }
+  for (int j = 0; j < L; ++j) v[j] = fh[j];
   int steps = 0;
-  float prev = INFINITY;
-  const float tol = ldexpf(1.0f, -tol_log2);
   bool stalled = false;
-  for (int it = 0; it < max_refine; ++it) {
-    residual_hyperdiff<L>(sx, kshift, xh, xl, v, sgh, sgl, n, lane);
-    warp_solve32<L>(v, sf, pf, pb, lane);
-    float dmax = 0.f, xmax = 0.f;
+  if (RES64) {
+    // x kept in FP64 (scaled by 2^-kshift); f in FP64 scaled the same way
+    double xd[L], fd[L];
+    const double scale = ldexp(1.0, -kshift);
+    const double sg = sigma[ms];
 #pragma unroll
-    for (int j = 0; j < L; ++j) {
-      float sh, se;
-      two_sum(xh[j], v[j], sh, se);
-      se = se + xl[j];
-      fast_two_sum(sh, se, xh[j], xl[j]);
-      dmax = fmaxf(dmax, fabsf(v[j]));
-      xmax = fmaxf(xmax, fabsf(xh[j]));
+    for (int j = 0; j < L; ++j) fd[j] = fv[j] * scale;
+    float prev = INFINITY;
+    const float tol = ldexpf(1.0f, -tol_log2);
+#pragma unroll 1
+    for (int it = 0; it <= max_refine; ++it) {
+      if (it > 0) residual_f64<W, L>(fd, xd, v, sg, n, t, sm);
+      cta_solve32<W, L>(v, cf, lane, warp, sm, phase);
+      if (it == 0) {
+#pragma unroll
+        for (int j = 0; j < L; ++j) xd[j] = (double)v[j];
+        continue;
+      }
+      float dmax = 0.f, xmax = 0.f;
+#pragma unroll
+      for (int j = 0; j < L; ++j) {
+        xd[j] += (double)v[j];
+        dmax = fmaxf(dmax, fabsf(v[j]));
+        xmax = fmaxf(xmax, fabsf((float)xd[j]));
+      }
+      steps = it;
+      if (it < max_refine) {
+        dmax = block_max<W>(dmax, lane, warp, sm.red[phase & 3]);
+        xmax = block_max<W>(xmax, lane, warp, sm.red[phase & 3] + W);
+        ++phase;
+        if (dmax <= tol * xmax) break;
+        if (it > 1 && dmax > 0.5f * prev) {
+          stalled = true;
+          break;
+        }
+        prev = dmax;
+      }
     }
-    dmax = warp_max(dmax);
-    xmax = warp_max(xmax);
-    steps = it + 1;
-    if (dmax <= tol * xmax) break;
-    if (it > 0 && dmax > 0.5f * prev) {
-      stalled = true;
-      break;
+#pragma unroll
+    for (int j = 0; j < L; ++j) fv[j] = ldexp(xd[j], kshift);
+  } else {
+    float prev = INFINITY;
+    const float tol = ldexpf(1.0f, -tol_log2);
+    // it = 0 solves for f (its FP32 part); every later pass solves for the
+    // float-float residual of the current x and adds the correction.  One
+    // solve call site keeps the unrolled kernel compact.
+#pragma unroll 1
+    for (int it = 0; it <= max_refine; ++it) {
+      if (it > 0) residual_ff<W, L>(fh, fl, xh, xl, v, sgh, sgl, n, t, sm);
+      cta_solve32<W, L>(v, cf, lane, warp, sm, phase);
+      if (it == 0) {
+#pragma unroll
+        for (int j = 0; j < L; ++j) {
+          xh[j] = v[j];
+          xl[j] = 0.f;
+        }
+        continue;
+      }
+      float dmax = 0.f, xmax = 0.f;
+#pragma unroll
+      for (int j = 0; j < L; ++j) {
+        float sh, se;
+        two_sum(xh[j], v[j], sh, se);
+        se = se + xl[j];
+        fast_two_sum(sh, se, xh[j], xl[j]);
+        dmax = fmaxf(dmax, fabsf(v[j]));
+        xmax = fmaxf(xmax, fabsf(xh[j]));
+      }
+      steps = it;
+      if (it < max_refine) {  // the stopping tests only matter if another step may follow
+        dmax = block_max<W>(dmax, lane, warp, sm.red[phase & 3]);
+        xmax = block_max<W>(xmax, lane, warp, sm.red[phase & 3] + W);
+        ++phase;
+        if (dmax <= tol * xmax) break;
+        if (it > 1 && dmax > 0.5f * prev) {
+          stalled = true;
+          break;
+        }
+        prev = dmax;
+      }
     }
-    prev = dmax;
+#pragma unroll
+    for (int j = 0; j < L; ++j) fv[j] = f2d_shift(xh[j], kshift) + f2d_shift(xl[j], kshift);
   }
-  if (lane == 0) {
+  if (t == 0) {
     if (steps > 0) atomicMax(info + 1, (unsigned long long)steps);
     if (stalled) atomicOr(info + 2, 1ull);
   }
-  // x = 2^k (xh + xl) in FP64, transposed through shared memory for coalesced stores
-  __syncwarp();
+  // ---- store x (a thread's rows are contiguous) ----
+  double* xs = x + s * (int64_t)n;
+  if (vec_io && i0 + L <= n) {
 #pragma unroll
-  for (int j = 0; j < L; ++j) sx[j * 33 + lane] = f2d_shift(xh[j], kshift) + f2d_shift(xl[j], kshift);
-  __syncwarp();
-  double* gx = x + s * (int64_t)n;
-#pragma unroll 4
-  for (int m = 0; m < L; ++m) {
-    const int i = 32 * m + lane;
-    const int t = i / L, j = i - t * L;
-    if (i < n) gx[i] = sx[j * 33 + t];
+    for (int j = 0; j < L; j += 2) *reinterpret_cast<double2*>(xs + i0 + j) = make_double2(fv[j], fv[j + 1]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < L; ++j)
+      if (i0 + j < n) xs[i0 + j] = fv[j];
   }
 }
 
-// Factor one system per thread in FP64 (Sec. 2.4), round the factors to FP32
-// into the warp-per-system layout, and build each lane-chunk's 2x2 transfer
-// maps from the rounded factors.
-__global__ void k_factor32(DevPlan P, int n, int L, const double* __restrict__ a, const double* __restrict__ b,
-                           const double* __restrict__ c, const double* __restrict__ d, const double* __restrict__ e,
-                           const double* __restrict__ sigma, float* __restrict__ fac, float* __restrict__ phi) {
+// Factor A = I + sigma D4 of one system per thread in FP64 (Sec. 2.4,
+// factorisation steps 1-14) and store 1/alpha and beta rounded to FP32 in the
+// CTA-per-system layout: float4 ((s * L/4 + j/4) * 2 + p) * P + t holds rows
+// t L + 4 (j/4) .. + 3 of plane p (0: 1/alpha, 1: beta).
+__global__ void k_factor32(DevPlan P, int n, int Pt, int L, const double* __restrict__ sigma, float* __restrict__ fac,
+                           float2* __restrict__ sigma2) {
   const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t nsys = P.shared ? 1 : P.batch;
   if (s >= nsys) return;
-  const int64_t o = P.shared ? 0 : s * (int64_t)n;
-  const double sg = sigma ? sigma[s] : 0.0;
-  const int64_t plane = 32 * (int64_t)L;
-  float* F = fac + s * 5 * plane;
-  float* Ph = phi + s * 32 * 8;
+  const double sg = sigma[s];
+  {
+    const float hi = __double2float_rn(sg);
+    sigma2[s] = make_float2(hi, __double2float_rn(sg - (double)hi));
+  }
+  float* F = fac + s * (int64_t)2 * Pt * L;
   double gam2 = 0.0, del2 = 0.0, gam1 = 0.0, del1 = 0.0;
   bool failed = false;
-  double f00 = 1, f01 = 0, f10 = 0, f11 = 1;  // forward chunk map accumulator
-  double t00 = 1, t01 = 0, t10 = 0, t11 = 1;  // backward chunk map accumulator
-  for (int i = 0; i < 32 * L; ++i) {
-    float ainv = 1.f, bp = 0.f, ep = 0.f, ga = 0.f, de = 0.f;
+  const int rows = Pt * L;
+  for (int i = 0; i < rows; ++i) {
+    float ainv = 1.f, bt = 0.f;
     if (i < n && !failed) {
-      double ar, br, cr, dr, er;
-      if (sigma) {
-        float w[5];
-        d4_weights_f(i, n, w);
-        ar = sg * w[0];
-        br = sg * w[1];
-        cr = 1.0 + sg * w[2];
-        dr = sg * w[3];
-        er = sg * w[4];
-      } else {
-        cr = c[o + i];
-        ar = (i >= 2) ? a[o + i] : 0.0;
-        br = (i >= 1) ? b[o + i] : 0.0;
-        dr = (i + 1 < n) ? d[o + i] : 0.0;
-        er = (i + 2 < n) ? e[o + i] : 0.0;
-      }
-      if (i < 2) ar = 0.0;
-      if (i < 1) br = 0.0;
-      if (i + 1 >= n) dr = 0.0;
-      if (i + 2 >= n) er = 0.0;
+      float w[5];
+      d4_weights_f(i, n, w);
+      const double ar = (i >= 2) ? sg * w[0] : 0.0;
+      const double br = (i >= 1) ? sg * w[1] : 0.0;
+      const double cr = 1.0 + sg * w[2];
+      const double dr = (i + 1 < n) ? sg * w[3] : 0.0;
+      const double er = (i + 2 < n) ? sg * w[4] : 0.0;
       const double beta = br - ar * gam2;
       const double alpha = cr - ar * del2 - beta * gam1;
       if (!(alpha != 0.0) || !isfinite(alpha)) {
@@ -434,10 +683,7 @@ __global__ void k_factor32(DevPlan P, int n, int L, const double* __restrict__ a
         const double gamma = (dr - beta * del1) / alpha;
         const double delta = er / alpha;
         ainv = (float)(1.0 / alpha);
-        bp = (float)(beta / alpha);
-        ep = (float)(ar / alpha);
-        ga = (float)gamma;
-        de = (float)delta;
+        bt = (float)beta;
         gam2 = gam1;
         del2 = del1;
         gam1 = gamma;
@@ -445,75 +691,66 @@ __global__ void k_factor32(DevPlan P, int n, int L, const double* __restrict__ a
       }
     }
     const int t = i / L, j = i - t * L;
-    F[0 * plane + j * 32 + t] = ainv;
-    F[1 * plane + j * 32 + t] = bp;
-    F[2 * plane + j * 32 + t] = ep;
-    F[3 * plane + j * 32 + t] = ga;
-    F[4 * plane + j * 32 + t] = de;
-    // forward row map M = [[0, 1], [-ep, -bp]] applied after the accumulated ones: acc <- M acc
-    {
-      const double n00 = f10, n01 = f11;
-      const double n10 = -(double)ep * f00 - (double)bp * f10;
-      const double n11 = -(double)ep * f01 - (double)bp * f11;
-      f00 = n00; f01 = n01; f10 = n10; f11 = n11;
-    }
-    // backward row map B = [[-ga, -de], [1, 0]] applied before the accumulated ones: acc <- acc B
-    {
-      const double n00 = -t00 * (double)ga + t01, n01 = -t00 * (double)de;
-      const double n10 = -t10 * (double)ga + t11, n11 = -t10 * (double)de;
-      t00 = n00; t01 = n01; t10 = n10; t11 = n11;
-    }
-    if (j == L - 1) {
-      float* q = Ph + t * 8;
-      q[0] = (float)f00; q[1] = (float)f01; q[2] = (float)f10; q[3] = (float)f11;
-      q[4] = (float)t00; q[5] = (float)t01; q[6] = (float)t10; q[7] = (float)t11;
-      f00 = 1; f01 = 0; f10 = 0; f11 = 1;
-      t00 = 1; t01 = 0; t10 = 0; t11 = 1;
-    }
+    const int64_t base = ((int64_t)(j / 4) * 2) * Pt * 4 + (int64_t)t * 4 + (j & 3);
+    F[base] = ainv;
+    F[base + (int64_t)Pt * 4] = bt;
   }
 }
 
-template <int L>
-cudaError_t launch_solve32r_L(int64_t batch, int n, int shared, const F32Factors& F, const double* sigma,
-                              const double* f, double* x, int max_refine, int tol_log2, unsigned long long* info,
-                              cudaStream_t st) {
-  constexpr int kBytesPerWarp = 5 * 32 * L * 4 + L * 33 * 8;
-  int warps = (int)((200 * 1024) / kBytesPerWarp);
-  warps = warps < 1 ? 1 : (warps > 8 ? 8 : warps);
-  const size_t smem = (size_t)warps * kBytesPerWarp;
-  static bool attr_set = false;  // once per process (the attribute is not a stream operation)
-  if (!attr_set) {
-    cudaError_t err = cudaFuncSetAttribute(k_solve32r<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return err;
-    attr_set = true;
+template <int W, int L, bool RES64>
+cudaError_t launch_solve32r_WL(const DevPlan& P, const F32Factors& F, const double* sigma, int n, const double* f,
+                               double* x, int max_refine, int tol_log2, cudaStream_t st) {
+  const int vec = ((((uintptr_t)f) | ((uintptr_t)x)) % 16 == 0) && (n % 2 == 0);
+  constexpr size_t smem = sizeof(Smem<W>);
+  static bool attr = false;  // once per process; not a stream operation
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_solve32r<W, L, RES64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
   }
-  const int64_t grid = (batch + warps - 1) / warps;
-  k_solve32r<L><<<(unsigned)grid, 32 * warps, smem, st>>>(batch, n, shared, F.fac, F.phi, sigma, f, x, max_refine,
-                                                         tol_log2, info);
+  k_solve32r<W, L, RES64><<<(unsigned)P.batch, 32 * W, smem, st>>>(P.batch, n, P.shared,
+                                                                 reinterpret_cast<const float4*>(F.fac), sigma,
+                                                                 reinterpret_cast<const float2*>(F.sigma2), f, x,
+                                                                 max_refine, tol_log2, vec, P.info);
   return cudaGetLastError();
+}
+
+template <bool RES64>
+cudaError_t dispatch32(const DevPlan& P, const F32Factors& F, const double* sigma, int n, const double* f, double* x,
+                       int max_refine, int tol_log2, cudaStream_t st) {
+#define PENT_CASE(W_, L_) \
+  if (F.W == W_ && F.L == L_) return launch_solve32r_WL<W_, L_, RES64>(P, F, sigma, n, f, x, max_refine, tol_log2, st);
+  PENT_CASE(1, 4) PENT_CASE(1, 8) PENT_CASE(1, 16)
+  PENT_CASE(2, 4) PENT_CASE(2, 8) PENT_CASE(2, 16)
+  PENT_CASE(4, 4) PENT_CASE(4, 8) PENT_CASE(4, 16)
+  PENT_CASE(8, 4) PENT_CASE(8, 8) PENT_CASE(8, 16)
+  PENT_CASE(16, 8)
+#undef PENT_CASE
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
-cudaError_t launch_factor32(const DevPlan& P, const double* a, const double* b, const double* c, const double* d,
-                            const double* e, const double* sigma, F32Factors F, int n, cudaStream_t st) {
+bool f32_shape_supported(int W, int L) {
+  static const int shapes[][2] = {{1, 4}, {1, 8}, {1, 16}, {2, 4}, {2, 8}, {2, 16}, {4, 4},
+                                  {4, 8}, {4, 16}, {8, 4}, {8, 8}, {8, 16}, {16, 8}};
+  for (const auto& sh : shapes)
+    if (sh[0] == W && sh[1] == L) return true;
+  return false;
+}
+
+cudaError_t launch_factor32(const DevPlan& P, const double* sigma, F32Factors F, int n, cudaStream_t st) {
   const int64_t nsys = P.shared ? 1 : P.batch;
   const int block = 128;
-  k_factor32<<<(unsigned)((nsys + block - 1) / block), block, 0, st>>>(P, n, F.L, a, b, c, d, e, sigma, F.fac, F.phi);
+  k_factor32<<<(unsigned)((nsys + block - 1) / block), block, 0, st>>>(P, n, 32 * F.W, F.L, sigma, F.fac,
+                                                                       reinterpret_cast<float2*>(F.sigma2));
   return cudaGetLastError();
 }
 
 cudaError_t launch_solve32r(const DevPlan& P, F32Factors F, const double* sigma, int n, const double* f, double* x,
                             int max_refine, int residual_f64, int tol_log2, cudaStream_t st) {
-  (void)residual_f64;
-  switch (F.L) {
-    case 2: return launch_solve32r_L<2>(P.batch, n, P.shared, F, sigma, f, x, max_refine, tol_log2, P.info, st);
-    case 4: return launch_solve32r_L<4>(P.batch, n, P.shared, F, sigma, f, x, max_refine, tol_log2, P.info, st);
-    case 8: return launch_solve32r_L<8>(P.batch, n, P.shared, F, sigma, f, x, max_refine, tol_log2, P.info, st);
-    case 16: return launch_solve32r_L<16>(P.batch, n, P.shared, F, sigma, f, x, max_refine, tol_log2, P.info, st);
-    case 32: return launch_solve32r_L<32>(P.batch, n, P.shared, F, sigma, f, x, max_refine, tol_log2, P.info, st);
-    default: return cudaErrorInvalidValue;
-  }
+  return residual_f64 ? dispatch32<true>(P, F, sigma, n, f, x, max_refine, tol_log2, st)
+                      : dispatch32<false>(P, F, sigma, n, f, x, max_refine, tol_log2, st);
 }
 
 }  // namespace pent

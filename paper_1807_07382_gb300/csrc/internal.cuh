@@ -39,23 +39,24 @@ struct F64Factors {
   double* bwd;
 };
 
-// FP32 warp-per-system storage for system s (uniform length n, L = rows per lane, n <= 32 L):
-//   rows i = t*L + j of lane t are stored at slot j*32 + t of each plane;
-//   fac[(s*5 + p)*32*L + j*32 + t], p = 0: 1/alpha, 1: beta/alpha, 2: epsilon/alpha, 3: gamma, 4: delta
-//   phi[(s*32 + t)*8 + k]: k = 0..3 forward chunk map (row-major 2x2), 4..7 backward chunk map.
+// FP32 CTA-per-system storage of the symmetric hyperdiffusion factors for system s
+// (uniform length n, P = 32 W threads of L rows, n <= P L):
+//   float4 ((s * L/4 + j/4) * 2 + p) * P + t holds rows t L + 4 (j/4) .. + 3 of plane p
+//   (0: 1/alpha, 1: beta); epsilon, gamma and delta are rebuilt from sigma in the solve.
 struct F32Factors {
   float* fac;
-  float* phi;
-  int L;
+  float* sigma2;  // per system: sigma split into an FP32 pair (hi, lo)
+  int W;          // warps per system
+  int L;          // rows per thread
 };
+bool f32_shape_supported(int W, int L);
 
 // ---- launchers (kernels live in the .cu files) ----
 cudaError_t launch_factor64(const DevPlan& P, const double* a, const double* b, const double* c, const double* d,
                             const double* e, const double* sigma, F64Factors F, cudaStream_t st);
-cudaError_t launch_factor32(const DevPlan& P, const double* a, const double* b, const double* c, const double* d,
-                            const double* e, const double* sigma, F32Factors F, int n, cudaStream_t st);
+cudaError_t launch_factor32(const DevPlan& P, const double* sigma, F32Factors F, int n, cudaStream_t st);
 cudaError_t launch_solve64(const DevPlan& P, F64Factors F, const double* f, double* x, double* gscr, int block_warps,
-                           cudaStream_t st);
+                           int unroll, cudaStream_t st);
 cudaError_t launch_adjoint64(const DevPlan& P, F64Factors F, const double* f, double* x, double* gscr,
                              int block_warps, cudaStream_t st);
 cudaError_t launch_solve32r(const DevPlan& P, F32Factors F, const double* sigma, int n, const double* f, double* x,

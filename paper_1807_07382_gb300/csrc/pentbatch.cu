@@ -38,7 +38,8 @@ struct pent_plan {
   // options
   int threads_per_system = 1;
   int residual = PENT_RESIDUAL_FF;
-  int block_warps = 4;
+  int block_warps = 2;
+  int unroll = 4;
   int tol_log2 = 40;
   // thread-per-system grouping (systems sorted by length, longest first)
   std::vector<int32_t> perm;  // [ngroups*32], -1 for padding lanes
@@ -46,10 +47,11 @@ struct pent_plan {
   std::vector<int64_t> goff;
   std::vector<int32_t> glen;
   int64_t grows = 0;  // record rows over all groups
-  // warp-per-system FP32 storage
+  // CTA-per-system FP32 storage: W32 warps of L32 rows per thread
+  int W32 = 0;
   int L32 = 0;
   // workspace regions
-  Region r_info, r_perm, r_off, r_n, r_goff, r_glen, r_sigma, r_fwd, r_bwd, r_scr, r_fac32, r_phi, r_adi;
+  Region r_info, r_perm, r_off, r_n, r_goff, r_glen, r_sigma, r_fwd, r_bwd, r_scr, r_fac32, r_sig32, r_adi;
   size_t ws_bytes = 0;
   // binding / state
   unsigned char* ws = nullptr;
@@ -78,7 +80,7 @@ struct pent_plan {
     return P;
   }
   F64Factors f64() const { return F64Factors{at<double>(r_fwd), at<double>(r_bwd)}; }
-  F32Factors f32() const { return F32Factors{at<float>(r_fac32), at<float>(r_phi), L32}; }
+  F32Factors f32() const { return F32Factors{at<float>(r_fac32), at<float>(r_sig32), W32, L32}; }
   void drop_graphs() {
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
     graphs.clear();
@@ -89,10 +91,19 @@ namespace {
 
 pent_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PENT_OK : PENT_ECUDA; }
 
-int choose_L32(int64_t n) {
-  for (int L : {2, 4, 8, 16, 32})
-    if (n <= 32 * L) return L;
+// Rows per thread for P threads per system: the smallest supported L with P L >= n.
+int rows_per_thread(int64_t n, int W) {
+  for (int L : {4, 8, 16, 32})
+    if ((int64_t)32 * W * L >= n && f32_shape_supported(W, L)) return L;
   return 0;
+}
+
+// Default CTA shape: 8 rows per thread (4 for the shortest systems), as few warps as cover n.
+bool choose_f32_shape(int64_t n, int* W, int* L) {
+  if (n <= 128) { *W = 1; *L = 4; return true; }
+  for (int w : {1, 2, 4, 8, 16})
+    if ((int64_t)32 * w * 8 >= n) { *W = w; *L = 8; return true; }
+  return false;
 }
 
 void layout(pent_plan* p) {
@@ -117,8 +128,8 @@ void layout(pent_plan* p) {
     take(p->r_bwd, (size_t)frows * 2 * lanes * sizeof(double));
     take(p->r_scr, (size_t)p->grows * kWarp * sizeof(double));
   } else {
-    take(p->r_fac32, (size_t)nfac * 5 * 32 * p->L32 * sizeof(float));
-    take(p->r_phi, (size_t)nfac * 32 * 8 * sizeof(float));
+    take(p->r_fac32, (size_t)nfac * 2 * 32 * p->W32 * p->L32 * sizeof(float));
+    take(p->r_sig32, (size_t)nfac * 2 * sizeof(float));
   }
   // ADI scratch: a full field (rows * 1 double) plus the mean accumulator, for shared-matrix plans
   if (p->shared) take(p->r_adi, (size_t)p->rows * sizeof(double) + 256);
@@ -187,6 +198,7 @@ pent_status pent_plan_create(pent_plan** out, int64_t batch, const int64_t* n_pe
       const int32_t s = p->perm[k * kWarp + l];
       if (s >= 0) mx = std::max(mx, p->n[s]);
     }
+    if (!p->shared) mx += (mx & 1);  // per-system records are stored in row pairs
     p->goff[k] = acc;
     p->glen[k] = (int32_t)mx;
     acc += mx;
@@ -197,12 +209,11 @@ pent_status pent_plan_create(pent_plan** out, int64_t batch, const int64_t* n_pe
       delete p;
       return PENT_EINVAL;
     }
-    p->L32 = choose_L32(p->n_uniform);
-    if (p->L32 == 0) {
+    if (!choose_f32_shape(p->n_uniform, &p->W32, &p->L32)) {
       delete p;
       return PENT_EINVAL;
     }
-    p->threads_per_system = 32;
+    p->threads_per_system = 32 * p->W32;
   }
   layout(p);
   *out = p;
@@ -239,12 +250,20 @@ pent_status pent_plan_bind(pent_plan* p, void* ws, void* stream) {
 pent_status pent_plan_set_option(pent_plan* p, int key, int64_t value) {
   if (!p) return PENT_EINVAL;
   switch (key) {
-    case PENT_OPT_THREADS_PER_SYSTEM:
-      if (p->factored) return PENT_EINVAL;
-      if (p->precision == PENT_F64 && value != 1) return PENT_EINVAL;
-      if (p->precision == PENT_F32_REFINE && value != 32) return PENT_EINVAL;
+    case PENT_OPT_THREADS_PER_SYSTEM: {
+      // changes the factor layout and the workspace size: only before binding
+      if (p->bound) return PENT_EINVAL;
+      if (p->precision == PENT_F64) return value == 1 ? PENT_OK : PENT_EINVAL;
+      if (value < 32 || value > 1024 || value % 32 || (value & (value - 1))) return PENT_EINVAL;
+      const int W = (int)(value / 32);
+      const int L = rows_per_thread(p->n_uniform, W);
+      if (L == 0) return PENT_EINVAL;
+      p->W32 = W;
+      p->L32 = L;
       p->threads_per_system = (int)value;
+      layout(p);
       return PENT_OK;
+    }
     case PENT_OPT_RESIDUAL:
       if (value != PENT_RESIDUAL_FF && value != PENT_RESIDUAL_F64) return PENT_EINVAL;
       p->residual = (int)value;
@@ -252,6 +271,11 @@ pent_status pent_plan_set_option(pent_plan* p, int key, int64_t value) {
     case PENT_OPT_BLOCK_WARPS:
       if (value < 1 || value > 8) return PENT_EINVAL;
       p->block_warps = (int)value;
+      p->drop_graphs();
+      return PENT_OK;
+    case PENT_OPT_UNROLL:
+      if (value != 2 && value != 4 && value != 8) return PENT_EINVAL;
+      p->unroll = (int)value;
       p->drop_graphs();
       return PENT_OK;
     case PENT_OPT_REFINE_TOL_LOG2:
@@ -270,6 +294,7 @@ pent_status pent_plan_get_option(const pent_plan* p, int key, int64_t* value) {
     case PENT_OPT_RESIDUAL: *value = p->residual; return PENT_OK;
     case PENT_OPT_BLOCK_WARPS: *value = p->block_warps; return PENT_OK;
     case PENT_OPT_REFINE_TOL_LOG2: *value = p->tol_log2; return PENT_OK;
+    case PENT_OPT_UNROLL: *value = p->unroll; return PENT_OK;
   }
   return PENT_EINVAL;
 }
@@ -302,7 +327,7 @@ static pent_status factor_common(pent_plan* p, const double* a, const double* b,
   if (p->precision == PENT_F64)
     err = launch_factor64(P, a, b, c, d, e, sg, p->f64(), p->stream);
   else
-    err = launch_factor32(P, a, b, c, d, e, sg, p->f32(), (int)p->n_uniform, p->stream);
+    err = launch_factor32(P, sg, p->f32(), (int)p->n_uniform, p->stream);
   if (err != cudaSuccess) return PENT_ECUDA;
   p->factored = sigma ? 2 : 1;
   return PENT_OK;
@@ -324,7 +349,7 @@ static pent_status solve_launch(pent_plan* p, const double* f, double* x, int ma
   const DevPlan P = p->dev();
   cudaError_t err;
   if (p->precision == PENT_F64) {
-    err = launch_solve64(P, p->f64(), f, x, p->at<double>(p->r_scr), p->block_warps, p->stream);
+    err = launch_solve64(P, p->f64(), f, x, p->at<double>(p->r_scr), p->block_warps, p->unroll, p->stream);
   } else {
     err = launch_solve32r(P, p->f32(), p->at<double>(p->r_sigma), (int)p->n_uniform, f, x, max_refine,
                           p->residual == PENT_RESIDUAL_F64, p->tol_log2, p->stream);
@@ -355,7 +380,7 @@ pent_status pent_solve_steps(pent_plan* p, double* x, int64_t nsteps, int max_re
     for (int64_t k = 0; k < nsteps && st == PENT_OK; ++k) st = solve_launch(p, x, x, max_refine);
     return st;
   }
-  const auto key = std::make_tuple((const void*)x, nsteps, max_refine, (int64_t)p->block_warps);
+  const auto key = std::make_tuple((const void*)x, nsteps, max_refine, (int64_t)p->block_warps * 16 + p->unroll);
   auto it = p->graphs.find(key);
   if (it == p->graphs.end()) {
     cudaGraph_t g = nullptr;
