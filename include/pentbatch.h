@@ -176,10 +176,15 @@ pent_status pent_hyperdiff_sigma_grad(pent_plan* plan, const double* mu, const d
  * the Douglas delta form of its semi-implicit step (Sec. 2.1).  Exact dC has
  * zero mean; removing the mean of the computed dC keeps the total mass to
  * rounding of C itself.
- * px: a shared-matrix plan of ny systems of n = nx, factored by
- *     pent_factor_hyperdiff with sigma; it also holds the step's scratch.
- * py: a shared-matrix plan of nx systems of n = ny, factored likewise.
- * Both must be bound to the same stream.  max_refine as in pent_solve_batch.
+ * px: a PENT_F64 shared-matrix plan of ny systems of n = nx, factored by
+ *     pent_factor_hyperdiff with the same sigma; it also holds the step's
+ *     scratch (two fields and one accumulator).
+ * py: a PENT_F64 shared-matrix plan of nx systems of n = ny, factored likewise.
+ * Both must be bound to the same stream.  max_refine must be 0: the sweeps run
+ * in FP64 (at sigma ~ 1e5 the FP32 factorisation would contract the error by
+ * only ~0.2 per refinement step, and the field stays in L2, so there are no
+ * HBM bytes for FP32 streaming to save).  Errors: PENT_EINVAL for mismatched
+ * shapes or plans, PENT_ENOTFACTORED if either plan is not factored from sigma.
  */
 pent_status adi_step_2d(pent_plan* px, pent_plan* py, double* C, int64_t nx, int64_t ny, double gamma, double dt,
                         double dx, int max_refine);

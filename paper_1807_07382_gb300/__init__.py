@@ -21,7 +21,7 @@ from ._lib import (PENT_ENOCONV, PENT_ESINGULAR, PENT_F32_REFINE, PENT_F64, PENT
                    PENT_RESIDUAL_FF, PentError, check)
 
 __all__ = ["Plan", "PentError", "PENT_F64", "PENT_F32_REFINE", "PENT_RESIDUAL_FF", "PENT_RESIDUAL_F64",
-           "library_path", "load_library", "adi_step_2d", "adi_steps_2d"]
+           "library_path", "load_library", "adi_step_2d", "adi_steps_2d", "ADI2D"]
 
 __version__ = "0.1.0"
 
@@ -210,3 +210,34 @@ def adi_steps_2d(px: Plan, py: Plan, C, gamma: float, dt: float, dx: float, nste
     check(_lib.load().adi_steps_2d(px._h, py._h, _dev_ptr(C, "C", torch.float64), nx, ny, float(gamma), float(dt),
                                    float(dx), int(max_refine), int(nsteps)), "adi_steps_2d")
     return C
+
+
+class ADI2D:
+    """Alternating-direction Cahn-Hilliard stepper on an ny x nx no-flux grid.
+
+    Builds and factors the two shared matrices I + sigma D4 (n = nx for the
+    row sweeps, n = ny for the column sweeps), sigma = gamma dt / dx^4, once;
+    `step` advances a device field C (ny x nx, float64, in place).
+    """
+
+    def __init__(self, nx: int, ny: int, gamma: float, dt: float, dx: float, device=None, stream=None):
+        torch = _torch()
+        self.nx, self.ny = int(nx), int(ny)
+        self.gamma, self.dt, self.dx = float(gamma), float(dt), float(dx)
+        self.sigma = self.gamma * self.dt / self.dx ** 4
+        self.mu = self.dt / self.dx ** 2
+        self.px = Plan(self.nx, batch=self.ny, shared=True, device=device, stream=stream)
+        self.py = Plan(self.ny, batch=self.nx, shared=True, device=self.px.device, stream=self.px.stream)
+        sig = torch.full((1,), self.sigma, dtype=torch.float64, device=self.px.device)
+        self.px.factor_hyperdiff(sig)
+        self.py.factor_hyperdiff(sig)
+
+    def step(self, C, nsteps: int = 1):
+        if tuple(C.shape) != (self.ny, self.nx):
+            raise ValueError(f"C must have shape ({self.ny}, {self.nx})")
+        if nsteps == 1:
+            return adi_step_2d(self.px, self.py, C, self.gamma, self.dt, self.dx)
+        return adi_steps_2d(self.px, self.py, C, self.gamma, self.dt, self.dx, nsteps)
+
+    def info(self):
+        return self.px.info(), self.py.info()

@@ -62,11 +62,17 @@ cudaError_t launch_adjoint64(const DevPlan& P, F64Factors F, const double* f, do
 cudaError_t launch_solve32r(const DevPlan& P, F32Factors F, const double* sigma, int n, const double* f, double* x,
                             int max_refine, int residual_f64, int tol_log2, cudaStream_t st);
 cudaError_t launch_sigma_grad(const DevPlan& P, const double* mu, const double* x, double* g_sigma, cudaStream_t st);
-cudaError_t launch_adi_rhs(const double* C, double* rhs, int64_t nx, int64_t ny, double mu, double sigma,
-                           cudaStream_t st);
-cudaError_t launch_adi_xsweep(F64Factors F, double* rhs, int64_t nx, int64_t ny, cudaStream_t st);
-cudaError_t launch_adi_ysweep_update(F64Factors F, const double* w, double* C, double* dcsum, int64_t nx, int64_t ny,
-                                     cudaStream_t st);
-cudaError_t launch_adi_update(double* C, const double* dC, const double* dcsum, int64_t nx, int64_t ny, cudaStream_t st);
+// One ADI step (csrc/adi.cu).  rhsT and W are field-sized scratch, colsum one double.
+struct AdiArgs {
+  double* C;
+  double* rhsT;
+  double* W;
+  double* colsum;
+  int nx, ny;
+  double mu, sigma;
+  F64Factors fx;  // shared-matrix records of I + sigma D4 with n = nx
+  F64Factors fy;  // ... with n = ny
+};
+cudaError_t launch_adi_step(const AdiArgs& a, cudaStream_t st);
 
 }  // namespace pent

@@ -131,8 +131,9 @@ void layout(pent_plan* p) {
     take(p->r_fac32, (size_t)nfac * 2 * 32 * p->W32 * p->L32 * sizeof(float));
     take(p->r_sig32, (size_t)nfac * 2 * sizeof(float));
   }
-  // ADI scratch: a full field (rows * 1 double) plus the mean accumulator, for shared-matrix plans
-  if (p->shared) take(p->r_adi, (size_t)p->rows * sizeof(double) + 256);
+  // ADI scratch, for shared-matrix plans: a full field (rows doubles) plus one partial
+  // sum per warp of the column sweep (at most n / 32 + 4 of them)
+  if (p->shared) take(p->r_adi, (size_t)(p->rows + p->n_uniform / 32 + 8) * sizeof(double));
   p->ws_bytes = cur;
 }
 
@@ -443,16 +444,79 @@ void pent_plan_destroy(pent_plan* p) {
   delete p;
 }
 
+static pent_status adi_check(pent_plan* px, pent_plan* py, double* C, int64_t nx, int64_t ny, double gamma, double dt,
+                             double dx, int max_refine) {
+  if (!px || !py || !C || nx < 1 || ny < 1 || max_refine != 0) return PENT_EINVAL;
+  if (!(gamma > 0.0) || !(dt > 0.0) || !(dx > 0.0)) return PENT_EINVAL;
+  if (nx > INT32_MAX || ny > INT32_MAX) return PENT_EINVAL;
+  if (!px->bound || !py->bound) return PENT_ENOTBOUND;
+  if (px->factored != 2 || py->factored != 2) return PENT_ENOTFACTORED;
+  if (px->precision != PENT_F64 || py->precision != PENT_F64 || !px->shared || !py->shared) return PENT_EINVAL;
+  if (px->batch != ny || px->n_uniform != nx || py->batch != nx || py->n_uniform != ny) return PENT_EINVAL;
+  if (px->stream != py->stream) return PENT_EINVAL;
+  if (((uintptr_t)C) % sizeof(double)) return PENT_EINVAL;
+  return PENT_OK;
+}
+
+static pent_status adi_launch(pent_plan* px, pent_plan* py, double* C, int64_t nx, int64_t ny, double gamma, double dt,
+                              double dx) {
+  AdiArgs a;
+  a.C = C;
+  a.rhsT = px->at<double>(px->r_adi);
+  a.colsum = a.rhsT + nx * ny;
+  a.W = px->at<double>(px->r_scr);
+  a.nx = (int)nx;
+  a.ny = (int)ny;
+  a.mu = dt / (dx * dx);
+  a.sigma = gamma * dt / (dx * dx * dx * dx);
+  a.fx = px->f64();
+  a.fy = py->f64();
+  return cuda_status(launch_adi_step(a, px->stream));
+}
+
 pent_status adi_step_2d(pent_plan* px, pent_plan* py, double* C, int64_t nx, int64_t ny, double gamma, double dt,
                         double dx, int max_refine) {
-  (void)px; (void)py; (void)C; (void)nx; (void)ny; (void)gamma; (void)dt; (void)dx; (void)max_refine;
-  return PENT_EINVAL;
+  pent_status st = adi_check(px, py, C, nx, ny, gamma, dt, dx, max_refine);
+  if (st != PENT_OK) return st;
+  return adi_launch(px, py, C, nx, ny, gamma, dt, dx);
 }
 
 pent_status adi_steps_2d(pent_plan* px, pent_plan* py, double* C, int64_t nx, int64_t ny, double gamma, double dt,
                          double dx, int max_refine, int64_t nsteps) {
-  (void)nsteps;
-  return adi_step_2d(px, py, C, nx, ny, gamma, dt, dx, max_refine);
+  pent_status st = adi_check(px, py, C, nx, ny, gamma, dt, dx, max_refine);
+  if (st != PENT_OK) return st;
+  if (nsteps < 0) return PENT_EINVAL;
+  if (nsteps == 0) return PENT_OK;
+  if (px->stream == nullptr) {
+    for (int64_t k = 0; k < nsteps && st == PENT_OK; ++k) st = adi_launch(px, py, C, nx, ny, gamma, dt, dx);
+    return st;
+  }
+  // graphs of ADI steps are keyed by (C, nsteps, -1, hash of the parameters) in px's cache
+  uint64_t h = 1469598103934665603ull;
+  for (double v : {gamma, dt, dx}) {
+    uint64_t b;
+    std::memcpy(&b, &v, sizeof b);
+    h = (h ^ b) * 1099511628211ull;
+  }
+  h ^= (uint64_t)(uintptr_t)py;
+  const auto key = std::make_tuple((const void*)C, nsteps, -1, (int64_t)(h & 0x7fffffffffffffffull));
+  auto it = px->graphs.find(key);
+  if (it == px->graphs.end()) {
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(px->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return PENT_ECUDA;
+    for (int64_t k = 0; k < nsteps && st == PENT_OK; ++k) st = adi_launch(px, py, C, nx, ny, gamma, dt, dx);
+    cudaError_t e = cudaStreamEndCapture(px->stream, &g);
+    if (st != PENT_OK || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return st != PENT_OK ? st : PENT_ECUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return PENT_ECUDA;
+    it = px->graphs.emplace(key, exec).first;
+  }
+  return cuda_status(cudaGraphLaunch(it->second, px->stream));
 }
 
 }  // extern "C"
