@@ -79,6 +79,7 @@ def lib():
             L.po_adi_step_ms.restype = _i64
             L.po_hyperdiff_loss_grad.argtypes = [_i64, _i64, _dp, _i64, _dp, _dp, _dp, _dp, ctypes.c_int]
             L.po_hyperdiff_loss_grad.restype = ctypes.c_double
+            L.po_hyperdiff_vjp.argtypes = [_i64, _i64, _dp, _i64, _dp, _dp, _dp, _dp, ctypes.c_int]
             _lib = L
     return _lib
 
@@ -262,3 +263,15 @@ def hyperdiff_loss_grad(sigma, T: int, c0, target, nthreads: int = 0):
     gs = np.zeros(batch)
     loss = lib().po_hyperdiff_loss_grad(batch, n, _p(sigma), int(T), _p(c0), _p(target), _p(gc), _p(gs), nthreads)
     return float(loss), gc, gs
+
+
+def hyperdiff_vjp(sigma, T: int, c0, lambda_T, nthreads: int = 0):
+    """(dC0, dsigma) of the T-step map for a given lambda^T = dL/dx^T."""
+    sigma = _f64(sigma)
+    c0 = _f64(c0)
+    lam = _f64(lambda_T)
+    batch, n = c0.shape
+    gc = np.zeros_like(c0)
+    gs = np.zeros(batch)
+    lib().po_hyperdiff_vjp(batch, n, _p(sigma), int(T), _p(c0), _p(lam), _p(gc), _p(gs), nthreads)
+    return gc, gs

@@ -465,3 +465,40 @@ double po_hyperdiff_loss_grad(int64_t batch, int64_t n, const double* sigma, int
   }
   return loss;
 }
+
+/*
+ * Vector-Jacobian product of the T-step map C0 -> x^T (same recurrences as
+ * po_hyperdiff_loss_grad, with lambda^T supplied instead of formed from a
+ * loss): returns dC0 = lambda^0 and dsigma_s = -sum_k mu^k . D4 x^k.
+ */
+void po_hyperdiff_vjp(int64_t batch, int64_t n, const double* sigma, int64_t T, const double* c0,
+                      const double* lambda_T, double* grad_c0, double* grad_sigma, int nthreads) {
+  set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t s = 0; s < batch; ++s) {
+    const double sg = sigma[s];
+    double* w = (double*)malloc((size_t)(35 + (T + 1)) * (size_t)n * sizeof(double));
+    double *a = w, *b = w + n, *c = w + 2 * n, *d = w + 3 * n, *e = w + 4 * n;
+    double *al = w + 5 * n, *be = w + 6 * n, *ga = w + 7 * n, *de = w + 8 * n, *ep = w + 9 * n, *g = w + 10 * n;
+    double *lam = w + 11 * n, *mu = w + 12 * n, *d4x = w + 13 * n;
+    double *qa = w + 14 * n, *qb = w + 15 * n, *qc = w + 16 * n, *qd = w + 17 * n, *qe = w + 18 * n;
+    double* adj_work = w + 19 * n;
+    double* traj = w + 35 * n;
+    po_band_hyperdiff(n, sg, a, b, c, d, e);
+    po_band_d4(n, qa, qb, qc, qd, qe);
+    po_factor(n, a, b, c, d, e, al, be, ga, de, ep);
+    memcpy(traj, c0 + s * n, (size_t)n * sizeof(double));
+    for (int64_t k = 1; k <= T; ++k) po_solve(n, al, be, ga, de, ep, traj + (k - 1) * n, traj + k * n, g);
+    memcpy(lam, lambda_T + s * n, (size_t)n * sizeof(double));
+    double gs = 0.0;
+    for (int64_t k = T; k >= 1; --k) {
+      po_adjoint_solve(n, a, b, c, d, e, lam, mu, adj_work);
+      po_matvec(n, qa, qb, qc, qd, qe, traj + k * n, d4x);
+      for (int64_t i = 0; i < n; ++i) gs -= mu[i] * d4x[i];
+      memcpy(lam, mu, (size_t)n * sizeof(double));
+    }
+    memcpy(grad_c0 + s * n, lam, (size_t)n * sizeof(double));
+    grad_sigma[s] = gs;
+    free(w);
+  }
+}

@@ -399,3 +399,13 @@ def test_loss_gradient_single_mode_closed_form():
     dL_dsigma = 2 * (A0 * G ** T - B0) * vv * A0 * T * G ** (T - 1) * (-lam * G * G)
     assert gs[0] == pytest.approx(dL_dsigma, rel=1e-12)
     assert rel_err(gc[0], 2 * (A0 * G ** T - B0) * G ** T * v) <= 1e-12
+
+
+def test_vjp_equals_loss_gradient_with_its_cotangent():
+    w = synth.adjoint_batch(batch=3, n=40, steps=5)
+    c0 = w.field0.reshape(3, 40)
+    target = oracle.hyperdiff_steps(w.n, w.sigma * 1.01, w.field0, w.steps).reshape(3, 40)
+    _, gc, gs = oracle.hyperdiff_loss_grad(w.sigma, w.steps, c0, target)
+    xT = oracle.hyperdiff_steps(w.n, w.sigma, w.field0, w.steps).reshape(3, 40)
+    vc, vs = oracle.hyperdiff_vjp(w.sigma, w.steps, c0, 2.0 * (xT - target))
+    assert np.array_equal(vc, gc) and np.array_equal(vs, gs)
