@@ -102,8 +102,9 @@ pent_status pent_plan_bind(pent_plan* plan, void* d_workspace, void* cuda_stream
  * pent_plan_workspace_bytes after setting it).
  */
 enum {
-  PENT_OPT_THREADS_PER_SYSTEM = 1, /* PENT_F64: 1 (one thread per system).  PENT_F32_REFINE: 32..512, a power
-                                      of two (one CTA of that many threads per system; n <= 4096) */
+  PENT_OPT_THREADS_PER_SYSTEM = 1, /* PENT_F64: 1 (one thread per system).  PENT_F32_REFINE: threads per
+                                      system, 32 W with W <= 16 (one CTA) or 512 C with C <= 8 (a cluster of C
+                                      CTAs); 8 rows per thread at most; 0 restores the automatic choice */
   PENT_OPT_RESIDUAL = 2,           /* pent_residual */
   PENT_OPT_BLOCK_WARPS = 3,        /* PENT_F64: warps per CTA of the solve kernels (1..8) */
   PENT_OPT_REFINE_TOL_LOG2 = 4,    /* refinement stops once a correction is <= 2^-tol * |x| (default 40) */

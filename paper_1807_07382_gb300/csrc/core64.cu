@@ -32,7 +32,8 @@ __device__ __forceinline__ void d4_weights(int64_t i, int64_t n, double w[5]) {
   for (int k = 0; k < 5; ++k) {
     int64_t j = i + k - 2;
     while (j < 0 || j >= n) j = (j < 0) ? (-1 - j) : (2 * n - 1 - j);
-    w[j - i + 2] += st[k];
+    const int64_t at = j - i + 2;  // within 0..4 for every row 0 <= i < n
+    if (at >= 0 && at < 5) w[at] += st[k];
   }
 }
 

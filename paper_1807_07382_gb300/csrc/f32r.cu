@@ -9,15 +9,17 @@
 // inputs are split into float pairs and results reassembled with integer bit
 // operations instead of conversion instructions.
 //
-// One CTA of P = 32 W threads owns one system of n <= P L rows: thread t holds
+// One CTA of P = 32 W threads -- or, for long systems, a thread-block cluster of
+// C such CTAs on C SMs -- owns one system of n <= C P L rows: thread t holds
 // rows t L .. t L + L - 1, their factors and their right-hand side in registers
 // (all loaded with coalesced 16-byte accesses, since a thread's rows are
 // contiguous).  Each substitution (Sec. 2.4: L g = f, then R x = g) is a
 // second-order linear recurrence, so a thread's chunk acts on the two carried
 // values as an affine map.  The thread runs its chunk from a zero state to get
-// the affine part; the CTA composes the maps with a Kogge-Stone shuffle scan in
-// each warp and a short carry across warps; then every thread reruns its chunk
-// from the true entering state.  The factors are read from HBM once per call
+// the affine part; the maps are composed by a Kogge-Stone shuffle scan in each
+// warp, a short carry across warps and, in a cluster, a carry across CTAs read
+// through distributed shared memory; then every thread reruns its chunk from
+// the true entering state.  The factors are read from HBM once per call
 // and reused by every substitution of every refinement step.
 //
 // The hyperdiffusion matrices are symmetric, so A = L D^{-1} L^T with D the
@@ -26,10 +28,14 @@
 // stencil weight.  Only 1/alpha_i and beta_i are stored (8 bytes per row in
 // FP32); epsilon, gamma, delta and the chunks' 2x2 transfer maps are rebuilt in
 // registers, trading FP32 arithmetic for HBM bytes.
+#include <cooperative_groups.h>
+
 #include <cmath>
 #include <cstdint>
 
 #include "internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace pent {
 namespace {
@@ -114,8 +120,10 @@ __device__ __forceinline__ int warp_max_i(int v) {
   return v;
 }
 
-// Weights of the no-flux fourth difference on row i (n rows), reflected about
-// the cell-centred walls; w[k] multiplies x_{i+k-2}.  Small integers.
+// Weights of the no-flux fourth difference on row i (n rows, 0 <= i < n),
+// reflected about the cell-centred walls; w[k] multiplies x_{i+k-2}.  Small
+// integers.  For rows inside the system every reflected column lies within
+// i-2 .. i+2; the bounds test keeps the local array safe for any argument.
 __device__ __forceinline__ void d4_weights_f(int i, int n, float w[5]) {
   const float st[5] = {1.f, -4.f, 6.f, -4.f, 1.f};
 #pragma unroll
@@ -124,11 +132,12 @@ __device__ __forceinline__ void d4_weights_f(int i, int n, float w[5]) {
   for (int k = 0; k < 5; ++k) {
     int j = i + k - 2;
     while (j < 0 || j >= n) j = (j < 0) ? (-1 - j) : (2 * n - 1 - j);
-    w[j - i + 2] += st[k];
+    const int at = j - i + 2;  // within 0..4 for every row 0 <= i < n
+    if (at >= 0 && at < 5) w[at] += st[k];
   }
 }
 
-// ---------------------------------------------------------------- CTA-wide affine scans
+// ---------------------------------------------------------------- block / cluster scans
 
 // x -> [[a, b], [c, d]] x + (u, v): the effect of a chunk of rows on the two carried values.
 struct Aff {
@@ -177,15 +186,37 @@ __device__ __forceinline__ float mat_norm(const Aff& m) {
   return fmaxf(fmaxf(fabsf(m.a), fabsf(m.b)), fmaxf(fabsf(m.c), fabsf(m.d)));
 }
 
-// Entering state of this thread's chunk for a sweep through the CTA's chunks.
-// FWD: chunks are visited in increasing thread order; otherwise decreasing.
-// `a` is this chunk's map (linear part from the factors, affine part from a
-// zero-state pass).  The system is entered with state 0.  The Kogge-Stone
-// levels stop as soon as every lane's window either reaches the warp's first
-// chunk or composes to a negligible linear part, since later levels would only
-// add terms multiplied by it.  sh: 2 float4 per warp.
-template <int W, bool FWD>
-__device__ __forceinline__ void scan_entry(Aff a, int lane, int warp, float4* sh, float& e0, float& e1) {
+// Barrier over the CTA, or over the whole cluster when the system spans C > 1 CTAs.
+__device__ __forceinline__ void csync(int C) {
+  if (C > 1)
+    cg::this_cluster().sync();
+  else
+    __syncthreads();
+}
+
+// A pointer into the shared memory of CTA `rank` of this cluster.
+template <class T>
+__device__ __forceinline__ T* remote(T* p, int rank) {
+  return cg::this_cluster().map_shared_rank(p, rank);
+}
+
+__device__ __forceinline__ void apply(const float4 m, const float4 b, float& c0, float& c1) {
+  const float n0 = fmaf(m.x, c0, fmaf(m.y, c1, b.x));
+  const float n1 = fmaf(m.z, c0, fmaf(m.w, c1, b.y));
+  c0 = n0;
+  c1 = n1;
+}
+
+// Entering state of this thread's chunk for a sweep through the system's chunks.
+// FWD: chunks in increasing thread order; otherwise decreasing.  `a` is this
+// chunk's map (linear part from the factors, affine part from a zero-state
+// pass); the system is entered with state 0.  The Kogge-Stone levels stop as
+// soon as every lane's window either reaches the warp's first chunk or
+// composes to a negligible linear part (later levels would only add terms
+// multiplied by it).  sh: 2 W + 2 float4 (warp totals, then the CTA total).
+template <bool FWD>
+__device__ __forceinline__ void scan_entry(Aff a, int lane, int warp, int W, int C, int rank, float4* sh, float& e0,
+                                           float& e1) {
 #pragma unroll 1
   for (int d = 1; d < 32; d <<= 1) {
     const Aff o = shfl_aff<FWD>(a, d);
@@ -196,28 +227,42 @@ __device__ __forceinline__ void scan_entry(Aff a, int lane, int warp, float4* sh
   const Aff prev = shfl_aff<FWD>(a, 1);  // inclusive result of the previous chunk in sweep order
   const bool first = FWD ? (lane == 0) : (lane == 31);
   float c0 = 0.f, c1 = 0.f;  // state entering this warp
-  if (W > 1) {
+  if (W > 1 || C > 1) {
     if (FWD ? (lane == 31) : (lane == 0)) {
       sh[2 * warp] = make_float4(a.a, a.b, a.c, a.d);
       sh[2 * warp + 1] = make_float4(a.u, a.v, 0.f, 0.f);
     }
     __syncthreads();
+    if (C > 1) {
+      if (threadIdx.x == 0) {  // the CTA's total map, published for the other CTAs of the cluster
+        float4 tm = make_float4(1.f, 0.f, 0.f, 1.f), tb = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = 0; k < W; ++k) {
+          const int w = FWD ? k : W - 1 - k;
+          const Aff L{sh[2 * w].x, sh[2 * w].y, sh[2 * w].z, sh[2 * w].w, sh[2 * w + 1].x, sh[2 * w + 1].y};
+          const Aff t = compose(L, Aff{tm.x, tm.y, tm.z, tm.w, tb.x, tb.y});
+          tm = make_float4(t.a, t.b, t.c, t.d);
+          tb = make_float4(t.u, t.v, 0.f, 0.f);
+        }
+        sh[2 * W] = tm;
+        sh[2 * W + 1] = tb;
+      }
+      cg::this_cluster().sync();
+      if (FWD) {
+        for (int r = 0; r < rank; ++r) {
+          const float4* q = remote(sh, r);
+          apply(q[2 * W], q[2 * W + 1], c0, c1);
+        }
+      } else {
+        for (int r = C - 1; r > rank; --r) {
+          const float4* q = remote(sh, r);
+          apply(q[2 * W], q[2 * W + 1], c0, c1);
+        }
+      }
+    }
     if (FWD) {
-      for (int w = 0; w < warp; ++w) {
-        const float4 m = sh[2 * w], b = sh[2 * w + 1];
-        const float n0 = fmaf(m.x, c0, fmaf(m.y, c1, b.x));
-        const float n1 = fmaf(m.z, c0, fmaf(m.w, c1, b.y));
-        c0 = n0;
-        c1 = n1;
-      }
+      for (int w = 0; w < warp; ++w) apply(sh[2 * w], sh[2 * w + 1], c0, c1);
     } else {
-      for (int w = W - 1; w > warp; --w) {
-        const float4 m = sh[2 * w], b = sh[2 * w + 1];
-        const float n0 = fmaf(m.x, c0, fmaf(m.y, c1, b.x));
-        const float n1 = fmaf(m.z, c0, fmaf(m.w, c1, b.y));
-        c0 = n0;
-        c1 = n1;
-      }
+      for (int w = W - 1; w > warp; --w) apply(sh[2 * w], sh[2 * w + 1], c0, c1);
     }
   }
   if (first) {
@@ -229,40 +274,54 @@ __device__ __forceinline__ void scan_entry(Aff a, int lane, int warp, float4* sh
   }
 }
 
-template <int W>
-__device__ __forceinline__ float block_max(float v, int lane, int warp, float* sh) {
-  v = warp_max(v);
-  if (W == 1) return v;
+// Maximum over the system's threads (CTA, or cluster).  sh: W + 1 slots.
+template <class T>
+__device__ __forceinline__ T system_max(T v, int lane, int warp, int W, int C, T* sh) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    const T o = __shfl_xor_sync(0xffffffffu, v, d);
+    v = v > o ? v : o;
+  }
+  if (W == 1 && C == 1) return v;
   if (lane == 0) sh[warp] = v;
   __syncthreads();
-  float r = sh[0];
-#pragma unroll
-  for (int w = 1; w < W; ++w) r = fmaxf(r, sh[w]);
+  T r = sh[0];
+  for (int w = 1; w < W; ++w) r = r > sh[w] ? r : sh[w];
+  if (C > 1) {
+    if (threadIdx.x == 0) sh[W] = r;
+    cg::this_cluster().sync();
+    for (int k = 0; k < C; ++k) {
+      const T q = remote(sh, k)[W];
+      r = r > q ? r : q;
+    }
+  }
   return r;
 }
 
-template <int W>
-__device__ __forceinline__ int block_max_i(int v, int lane, int warp, int* sh) {
-  v = warp_max_i(v);
-  if (W == 1) return v;
-  if (lane == 0) sh[warp] = v;
-  __syncthreads();
-  int r = sh[0];
-#pragma unroll
-  for (int w = 1; w < W; ++w) r = max(r, sh[w]);
-  return r;
-}
-
-// Shared scratch of one CTA.  Scan and reduction slots rotate through four
-// buffers, so a single barrier per scan separates every write from the reads
-// of the same buffer.
-template <int W>
-struct Smem {
-  float4 scan[4][2 * W];
-  float4 edge[32 * W][2];  // per thread: first two rows (hi, lo), last two rows (hi, lo)
-  float red[4][2 * W];
-  int redi[W];
+// Shared scratch of one CTA (dynamic; W is a launch parameter).  Scan and
+// reduction slots rotate through four buffers, so one barrier per scan
+// separates every write from the reads of the same buffer, in this CTA and in
+// the other CTAs of a cluster.
+struct SmemView {
+  float4* scan;  // [4][2W + 2]
+  float4* edge;  // [P][2]: first two rows (hi, lo), last two rows (hi, lo)
+  float* red;    // [4][W + 1]
+  int* redi;     // [W + 1]
 };
+
+__host__ __device__ inline size_t smem_bytes(int W) {
+  return sizeof(float4) * (size_t)(4 * (2 * W + 2) + 2 * 32 * W) + sizeof(float) * (size_t)(4 * (W + 1)) +
+         sizeof(int) * (size_t)(W + 1);
+}
+
+__device__ __forceinline__ SmemView smem_view(unsigned char* base, int W) {
+  SmemView v;
+  v.scan = reinterpret_cast<float4*>(base);
+  v.edge = v.scan + 4 * (2 * W + 2);
+  v.red = reinterpret_cast<float*>(v.edge + 2 * 32 * W);
+  v.redi = reinterpret_cast<int*>(v.red + 4 * (W + 1));
+  return v;
+}
 
 // Per-thread factors of its L rows and the chunk maps, rebuilt from the stored
 // 1/alpha and beta (see the header comment).
@@ -277,10 +336,14 @@ struct ChunkFactors {
   float4 pb;   // backward map
 };
 
+struct Ctx {
+  int lane, warp, W, C, rank;
+  int phase;
+};
+
 // In place v <- A^{-1} v (FP32): forward L g = v, then back R x = g.
-template <int W, int L>
-__device__ __forceinline__ void cta_solve32(float (&v)[L], const ChunkFactors<L>& cf, int lane, int warp, Smem<W>& sm,
-                                            int& phase) {
+template <int L>
+__device__ __forceinline__ void cta_solve32(float (&v)[L], const ChunkFactors<L>& cf, Ctx& cx, const SmemView& sm) {
   float p2 = 0.f, p1 = 0.f;
 #pragma unroll
   for (int j = 0; j < L; ++j) {
@@ -289,7 +352,8 @@ __device__ __forceinline__ void cta_solve32(float (&v)[L], const ChunkFactors<L>
     p1 = g;
   }
   float e0, e1;
-  scan_entry<W, true>(Aff{cf.pf.x, cf.pf.y, cf.pf.z, cf.pf.w, p2, p1}, lane, warp, sm.scan[phase++ & 3], e0, e1);
+  scan_entry<true>(Aff{cf.pf.x, cf.pf.y, cf.pf.z, cf.pf.w, p2, p1}, cx.lane, cx.warp, cx.W, cx.C, cx.rank,
+                   sm.scan + (cx.phase++ & 3) * (2 * cx.W + 2), e0, e1);
   p2 = e0;
   p1 = e1;
 #pragma unroll
@@ -306,7 +370,8 @@ __device__ __forceinline__ void cta_solve32(float (&v)[L], const ChunkFactors<L>
     s2 = s1;
     s1 = xv;
   }
-  scan_entry<W, false>(Aff{cf.pb.x, cf.pb.y, cf.pb.z, cf.pb.w, s1, s2}, lane, warp, sm.scan[phase++ & 3], e0, e1);
+  scan_entry<false>(Aff{cf.pb.x, cf.pb.y, cf.pb.z, cf.pb.w, s1, s2}, cx.lane, cx.warp, cx.W, cx.C, cx.rank,
+                    sm.scan + (cx.phase++ & 3) * (2 * cx.W + 2), e0, e1);
   s1 = e0;
   s2 = e1;
 #pragma unroll
@@ -339,12 +404,13 @@ __device__ __noinline__ float2 d4_wall_row(int i, int n, float ah, float al, flo
   return make_float2(S, Er);
 }
 
-// r = f - (I + sigma D4) x, rounded to FP32, for this thread's rows.  x = xh + xl.
-// Float-float residual: f as (fh, fl), sigma as (sgh, sgl).  Rows away from the
-// walls use the plain [1, -4, 6, -4, 1] stencil.
+// r = f - (I + sigma D4) x for one row, in float-float (x = xh + xl, f = fh + fl,
+// sigma = sgh + sgl), rounded to FP32.  Rows away from the walls use the plain
+// [1, -4, 6, -4, 1] stencil.
 __device__ __forceinline__ float residual_row(float ah, float al, float bh, float bl, float ch, float cl, float dh,
                                               float dl, float eh, float el, float fhj, float flj, float sgh, float sgl,
                                               int i, int n) {
+  if (i >= n) return 0.f;  // padding row past the end of the system
   float S, Er;
   if (i >= 2 && i + 2 < n) {
     float s1, e1, s2, e2, t, e3, p, e4;
@@ -369,20 +435,36 @@ __device__ __forceinline__ float residual_row(float ah, float al, float bh, floa
   two_sum(fhj, -ch, a1, a2);
   two_sum(a1, -Pp, b1, b2);
   const float low = ((a2 + b2) + (flj - cl)) - Pe;
-  return (i < n) ? (b1 + low) : 0.f;
+  return b1 + low;
 }
 
-template <int W, int L>
+// The neighbouring rows of this thread's chunk: the last two rows of the
+// previous chunk and the first two of the next, across warps through shared
+// memory and across CTAs of a cluster through distributed shared memory.
+template <int L>
+__device__ __forceinline__ void exchange_edges(float4 own_first, float4 own_last, int t, int P, const Ctx& cx,
+                                               const SmemView& sm, float4& prv, float4& nxt) {
+  sm.edge[2 * t] = own_first;
+  sm.edge[2 * t + 1] = own_last;
+  csync(cx.C);
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (t > 0)
+    prv = sm.edge[2 * (t - 1) + 1];
+  else
+    prv = (cx.rank > 0) ? remote(sm.edge, cx.rank - 1)[2 * (P - 1) + 1] : zero;
+  if (t + 1 < P)
+    nxt = sm.edge[2 * (t + 1)];
+  else
+    nxt = (cx.rank + 1 < cx.C) ? remote(sm.edge, cx.rank + 1)[0] : zero;
+}
+
+template <int L>
 __device__ __forceinline__ void residual_ff(const float (&fh)[L], const float (&fl)[L], const float (&xh)[L],
                                             const float (&xl)[L], float (&r)[L], float sgh, float sgl, int n, int t,
-                                            Smem<W>& sm) {
-  constexpr int P = 32 * W;
-  sm.edge[t][0] = make_float4(xh[0], xh[1], xl[0], xl[1]);
-  sm.edge[t][1] = make_float4(xh[L - 2], xh[L - 1], xl[L - 2], xl[L - 1]);
-  __syncthreads();
-  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-  const float4 prv = (t > 0) ? sm.edge[t - 1][1] : zero;      // rows tL-2, tL-1
-  const float4 nxt = (t + 1 < P) ? sm.edge[t + 1][0] : zero;  // rows tL+L, tL+L+1
+                                            int tg, int P, const Ctx& cx, const SmemView& sm) {
+  float4 prv, nxt;
+  exchange_edges<L>(make_float4(xh[0], xh[1], xl[0], xl[1]), make_float4(xh[L - 2], xh[L - 1], xl[L - 2], xl[L - 1]),
+                    t, P, cx, sm, prv, nxt);
 #pragma unroll
   for (int j = 0; j < L; ++j) {
     const float ah = (j >= 2) ? xh[j - 2] : (j == 1 ? prv.y : prv.x);
@@ -393,32 +475,33 @@ __device__ __forceinline__ void residual_ff(const float (&fh)[L], const float (&
     const float dl = (j + 1 < L) ? xl[j + 1] : nxt.z;
     const float eh = (j + 2 < L) ? xh[j + 2] : (j + 1 < L ? nxt.x : nxt.y);
     const float el = (j + 2 < L) ? xl[j + 2] : (j + 1 < L ? nxt.z : nxt.w);
-    r[j] = residual_row(ah, al, bh, bl, xh[j], xl[j], dh, dl, eh, el, fh[j], fl[j], sgh, sgl, t * L + j, n);
+    r[j] = residual_row(ah, al, bh, bl, xh[j], xl[j], dh, dl, eh, el, fh[j], fl[j], sgh, sgl, tg * L + j, n);
   }
 }
 
 // The same residual in native FP64 (the literal reading: FP64 band from sigma,
-// FP64 x and f).  xd holds x in FP64 (scaled by 2^-kshift like f).
-template <int W, int L>
+// FP64 x and f).  xd holds x in FP64 (scaled by 2^-kshift like f).  The edge
+// slots carry the neighbouring rows as double pairs.
+template <int L>
 __device__ __forceinline__ void residual_f64(const double (&fd)[L], const double (&xd)[L], float (&r)[L], double sg,
-                                             int n, int t, Smem<W>& sm) {
-  constexpr int P = 32 * W;
-  double2* ed = reinterpret_cast<double2*>(sm.edge);  // 4 doubles per thread fit in the edge slots
-  ed[2 * t] = make_double2(xd[0], xd[1]);
-  ed[2 * t + 1] = make_double2(xd[L - 2], xd[L - 1]);
-  __syncthreads();
-  const double2 zero = make_double2(0.0, 0.0);
-  const double2 prv = (t > 0) ? ed[2 * (t - 1) + 1] : zero;
-  const double2 nxt = (t + 1 < P) ? ed[2 * (t + 1)] : zero;
+                                             int n, int t, int tg, int P, const Ctx& cx, const SmemView& sm) {
+  float4 pf4, nf4;
+  const double2 f2 = make_double2(xd[0], xd[1]), l2 = make_double2(xd[L - 2], xd[L - 1]);
+  exchange_edges<L>(*reinterpret_cast<const float4*>(&f2), *reinterpret_cast<const float4*>(&l2), t, P, cx, sm, pf4,
+                    nf4);
+  const double2 prv = *reinterpret_cast<const double2*>(&pf4);
+  const double2 nxt = *reinterpret_cast<const double2*>(&nf4);
 #pragma unroll
   for (int j = 0; j < L; ++j) {
-    const int i = t * L + j;
+    const int i = tg * L + j;
     const double a = (j >= 2) ? xd[j - 2] : (j == 1 ? prv.y : prv.x);
     const double b = (j >= 1) ? xd[j - 1] : prv.y;
     const double d = (j + 1 < L) ? xd[j + 1] : nxt.x;
     const double e = (j + 2 < L) ? xd[j + 2] : (j + 1 < L ? nxt.x : nxt.y);
     double y;
-    if (i >= 2 && i + 2 < n) {
+    if (i >= n) {  // padding row past the end of the system
+      y = 0.0;
+    } else if (i >= 2 && i + 2 < n) {
       y = fma(6.0, xd[j], fma(-4.0, b + d, a + e));
     } else {
       float w[5];
@@ -436,21 +519,21 @@ __device__ __forceinline__ void residual_f64(const double (&fd)[L], const double
 __device__ __forceinline__ float eps_of_row(int i, int n, float sgf) { return (i >= 2 && i < n) ? sgf : 0.f; }
 
 // Load 1/alpha and beta of the thread's rows and rebuild epsilon/alpha,
-// beta/alpha, gamma, delta and the two chunk maps.
-template <int W, int L>
-__device__ __forceinline__ void load_chunk_factors(ChunkFactors<L>& cf, const float4* __restrict__ gq, int t, int n,
-                                                   float sgf) {
-  constexpr int P = 32 * W;
+// beta/alpha, gamma, delta and the two chunk maps.  gq: the system's factor
+// block; PT threads per system; tg this thread's index in the system.
+template <int L>
+__device__ __forceinline__ void load_chunk_factors(ChunkFactors<L>& cf, const float4* __restrict__ gq, int tg, int PT,
+                                                   int n, float sgf) {
   float beta[L];
 #pragma unroll
   for (int jq = 0; jq < L / 4; ++jq) {
-    const float4 qa = __ldg(gq + (jq * 2 + 0) * P + t), qb = __ldg(gq + (jq * 2 + 1) * P + t);
+    const float4 qa = __ldg(gq + (int64_t)(jq * 2 + 0) * PT + tg), qb = __ldg(gq + (int64_t)(jq * 2 + 1) * PT + tg);
     cf.A[4 * jq] = qa.x; cf.A[4 * jq + 1] = qa.y; cf.A[4 * jq + 2] = qa.z; cf.A[4 * jq + 3] = qa.w;
     beta[4 * jq] = qb.x; beta[4 * jq + 1] = qb.y; beta[4 * jq + 2] = qb.z; beta[4 * jq + 3] = qb.w;
   }
-  // beta of the first row of the next thread's chunk (row t L + L)
-  const float beta_next = (t + 1 < P) ? __ldg(reinterpret_cast<const float*>(gq + 1 * P + (t + 1))) : 0.f;
-  const int i0 = t * L;
+  // beta of the first row of the next thread's chunk (row tg L + L)
+  const float beta_next = (tg + 1 < PT) ? __ldg(reinterpret_cast<const float*>(gq + (int64_t)PT + (tg + 1))) : 0.f;
+  const int i0 = tg * L;
 #pragma unroll
   for (int j = 0; j < L; ++j) {
     const int i = i0 + j;
@@ -486,34 +569,46 @@ __device__ __forceinline__ void load_chunk_factors(ChunkFactors<L>& cf, const fl
   cf.pb = make_float4(t00, t01, t10, t11);
 }
 
-// One CTA per system: FP32 solve, then up to max_refine refinement steps.
-// RES64 selects the FP64 residual (and FP64 accumulation of x) instead of float-float.
-// Register budget for up to 8 rows per thread: 512 threads per SM (at most 128
-// registers per thread), so that four 128-thread systems share an SM and hide
-// each other's barriers.  Longer chunks keep their registers.
-template <int W, int L, bool RES64>
-__global__ void __launch_bounds__(32 * W, (L <= 8 && 16 / W > 0) ? 16 / W : 1) k_solve32r(int64_t batch, int n, int shared, const float4* __restrict__ fac,
-                                                     const double* __restrict__ sigma,
-                                                     const float2* __restrict__ sigma2, const double* f, double* x,
-                                                     int max_refine, int tol_log2, int vec_io,
-                                                     unsigned long long* info) {
-  constexpr int P = 32 * W;
+// One CTA (or one cluster of C CTAs) per system: FP32 solve, then up to
+// max_refine refinement steps.  RES64 selects the FP64 residual (and FP64
+// accumulation of x) instead of float-float.  Register budget: 512 threads per
+// SM (at most 128 registers per thread), so up to four 128-thread systems share
+// an SM and hide each other's barriers.
+// WT > 0 fixes the warp count at compile time (the common one-CTA shapes);
+// WT = 0 takes it from `Wrt`.  CL enables the cluster paths (C = Crt CTAs per
+// system), otherwise C = 1.
+constexpr int min_blocks(int L, int WT) { return WT > 0 ? ((L <= 8 && 16 / WT > 0) ? 16 / WT : 1) : 1; }
+
+template <int L, int WT, bool CL, bool RES64>
+__global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, min_blocks(L, WT))
+    k_solve32r(F32Tables T, const int32_t* __restrict__ sys, int Wrt, int Crt, int shared, const double* f, double* x,
+               int max_refine, int tol_log2, int vec_io) {
   static_assert(L % 4 == 0, "rows per thread must be a multiple of 4");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem<W>& sm = *reinterpret_cast<Smem<W>*>(smem_raw);
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int64_t s = blockIdx.x;
-  if (s >= batch) return;
+  const int W = WT > 0 ? WT : Wrt;
+  const int C = CL ? Crt : 1;
+  const SmemView sm = smem_view(smem_raw, W);
+  const int P = 32 * W, PT = P * C;
+  const int t = threadIdx.x;
+  Ctx cx;
+  cx.lane = t & 31;
+  cx.warp = t >> 5;
+  cx.W = W;
+  cx.C = C;
+  cx.rank = (C > 1) ? (int)cg::this_cluster().block_rank() : 0;
+  cx.phase = 0;
+  const int64_t s = sys[blockIdx.x / C];
   const int64_t ms = shared ? 0 : s;
-  int phase = 0;
+  const int n = T.n[s];
+  const int tg = cx.rank * P + t;
 
   // ---- loads: factors, right-hand side (all coalesced) ----
-  const float2 sgp = __ldg(sigma2 + ms);  // sigma as an FP32 pair, split at factorisation time
+  const float2 sgp = __ldg(T.sig2 + ms);  // sigma as an FP32 pair, split at factorisation time
   const float sgh = sgp.x, sgl = sgp.y;
   ChunkFactors<L> cf;
-  load_chunk_factors<W, L>(cf, fac + ms * (int64_t)(2 * P * L / 4), t, n, sgh);
-  const double* fs = f + s * (int64_t)n;
-  const int i0 = t * L;
+  load_chunk_factors<L>(cf, reinterpret_cast<const float4*>(T.fac) + T.foff[ms], tg, PT, n, sgh);
+  const double* fs = f + T.off[s];
+  const int i0 = tg * L;
   double fv[L];
   if (vec_io && i0 + L <= n) {
 #pragma unroll
@@ -534,7 +629,7 @@ __global__ void __launch_bounds__(32 * W, (L <= 8 && 16 / W > 0) ? 16 / W : 1) k
     const unsigned top = (unsigned)((unsigned long long)__double_as_longlong(fv[j]) >> 32);
     emax = max(emax, (int)((top >> 20) & 0x7ffu));
   }
-  emax = block_max_i<W>(emax, lane, warp, sm.redi);
+  emax = system_max<int>(emax, cx.lane, cx.warp, W, C, sm.redi);
   const int kshift = emax - 1022;
 
   float v[L], xh[L], xl[L];
@@ -545,19 +640,19 @@ __global__ void __launch_bounds__(32 * W, (L <= 8 && 16 / W > 0) ? 16 / W : 1) k
   for (int j = 0; j < L; ++j) v[j] = fh[j];
   int steps = 0;
   bool stalled = false;
+  const float tol = ldexpf(1.0f, -tol_log2);
+  float prev = INFINITY;
   if (RES64) {
     // x kept in FP64 (scaled by 2^-kshift); f in FP64 scaled the same way
     double xd[L], fd[L];
     const double scale = ldexp(1.0, -kshift);
-    const double sg = sigma[ms];
+    const double sg = T.sigma[ms];
 #pragma unroll
     for (int j = 0; j < L; ++j) fd[j] = fv[j] * scale;
-    float prev = INFINITY;
-    const float tol = ldexpf(1.0f, -tol_log2);
 #pragma unroll 1
     for (int it = 0; it <= max_refine; ++it) {
-      if (it > 0) residual_f64<W, L>(fd, xd, v, sg, n, t, sm);
-      cta_solve32<W, L>(v, cf, lane, warp, sm, phase);
+      if (it > 0) residual_f64<L>(fd, xd, v, sg, n, t, tg, P, cx, sm);
+      cta_solve32<L>(v, cf, cx, sm);
       if (it == 0) {
 #pragma unroll
         for (int j = 0; j < L; ++j) xd[j] = (double)v[j];
@@ -572,9 +667,12 @@ __global__ void __launch_bounds__(32 * W, (L <= 8 && 16 / W > 0) ? 16 / W : 1) k
       }
       steps = it;
       if (it < max_refine) {
-        dmax = block_max<W>(dmax, lane, warp, sm.red[phase & 3]);
-        xmax = block_max<W>(xmax, lane, warp, sm.red[phase & 3] + W);
-        ++phase;
+        float* rs = sm.red + (cx.phase & 3) * (W + 1);
+        ++cx.phase;
+        dmax = system_max<float>(dmax, cx.lane, cx.warp, W, C, rs);
+        float* rs2 = sm.red + (cx.phase & 3) * (W + 1);
+        ++cx.phase;
+        xmax = system_max<float>(xmax, cx.lane, cx.warp, W, C, rs2);
         if (dmax <= tol * xmax) break;
         if (it > 1 && dmax > 0.5f * prev) {
           stalled = true;
@@ -586,15 +684,13 @@ __global__ void __launch_bounds__(32 * W, (L <= 8 && 16 / W > 0) ? 16 / W : 1) k
 #pragma unroll
     for (int j = 0; j < L; ++j) fv[j] = ldexp(xd[j], kshift);
   } else {
-    float prev = INFINITY;
-    const float tol = ldexpf(1.0f, -tol_log2);
     // it = 0 solves for f (its FP32 part); every later pass solves for the
     // float-float residual of the current x and adds the correction.  One
     // solve call site keeps the unrolled kernel compact.
 #pragma unroll 1
     for (int it = 0; it <= max_refine; ++it) {
-      if (it > 0) residual_ff<W, L>(fh, fl, xh, xl, v, sgh, sgl, n, t, sm);
-      cta_solve32<W, L>(v, cf, lane, warp, sm, phase);
+      if (it > 0) residual_ff<L>(fh, fl, xh, xl, v, sgh, sgl, n, t, tg, P, cx, sm);
+      cta_solve32<L>(v, cf, cx, sm);
       if (it == 0) {
 #pragma unroll
         for (int j = 0; j < L; ++j) {
@@ -615,9 +711,12 @@ __global__ void __launch_bounds__(32 * W, (L <= 8 && 16 / W > 0) ? 16 / W : 1) k
       }
       steps = it;
       if (it < max_refine) {  // the stopping tests only matter if another step may follow
-        dmax = block_max<W>(dmax, lane, warp, sm.red[phase & 3]);
-        xmax = block_max<W>(xmax, lane, warp, sm.red[phase & 3] + W);
-        ++phase;
+        float* rs = sm.red + (cx.phase & 3) * (W + 1);
+        ++cx.phase;
+        dmax = system_max<float>(dmax, cx.lane, cx.warp, W, C, rs);
+        float* rs2 = sm.red + (cx.phase & 3) * (W + 1);
+        ++cx.phase;
+        xmax = system_max<float>(xmax, cx.lane, cx.warp, W, C, rs2);
         if (dmax <= tol * xmax) break;
         if (it > 1 && dmax > 0.5f * prev) {
           stalled = true;
@@ -629,12 +728,12 @@ __global__ void __launch_bounds__(32 * W, (L <= 8 && 16 / W > 0) ? 16 / W : 1) k
 #pragma unroll
     for (int j = 0; j < L; ++j) fv[j] = f2d_shift(xh[j], kshift) + f2d_shift(xl[j], kshift);
   }
-  if (t == 0) {
-    if (steps > 0) atomicMax(info + 1, (unsigned long long)steps);
-    if (stalled) atomicOr(info + 2, 1ull);
+  if (t == 0 && cx.rank == 0) {
+    if (steps > 0) atomicMax(T.info + 1, (unsigned long long)steps);
+    if (stalled) atomicOr(T.info + 2, 1ull);
   }
   // ---- store x (a thread's rows are contiguous) ----
-  double* xs = x + s * (int64_t)n;
+  double* xs = x + T.off[s];
   if (vec_io && i0 + L <= n) {
 #pragma unroll
     for (int j = 0; j < L; j += 2) *reinterpret_cast<double2*>(xs + i0 + j) = make_double2(fv[j], fv[j + 1]);
@@ -643,26 +742,28 @@ __global__ void __launch_bounds__(32 * W, (L <= 8 && 16 / W > 0) ? 16 / W : 1) k
     for (int j = 0; j < L; ++j)
       if (i0 + j < n) xs[i0 + j] = fv[j];
   }
+  if (C > 1) cg::this_cluster().sync();  // keep this CTA's shared memory alive for the cluster's readers
 }
 
 // Factor A = I + sigma D4 of one system per thread in FP64 (Sec. 2.4,
 // factorisation steps 1-14) and store 1/alpha and beta rounded to FP32 in the
-// CTA-per-system layout: float4 ((s * L/4 + j/4) * 2 + p) * P + t holds rows
-// t L + 4 (j/4) .. + 3 of plane p (0: 1/alpha, 1: beta).
-__global__ void k_factor32(DevPlan P, int n, int Pt, int L, const double* __restrict__ sigma, float* __restrict__ fac,
-                           float2* __restrict__ sigma2) {
+// system's block: float4 ((j / 4) * 2 + p) * PT + tg holds rows tg L + 4 (j/4)
+// .. + 3 of plane p (0: 1/alpha, 1: beta), PT threads of L rows per system.
+__global__ void k_factor32(F32Tables T, int64_t nsys, const int32_t* __restrict__ shape,
+                           const double* __restrict__ sigma) {
   const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t nsys = P.shared ? 1 : P.batch;
   if (s >= nsys) return;
+  const int n = T.n[s];
+  const int PT = shape[s] & 0xffff, L = shape[s] >> 16;
   const double sg = sigma[s];
   {
     const float hi = __double2float_rn(sg);
-    sigma2[s] = make_float2(hi, __double2float_rn(sg - (double)hi));
+    T.sig2[s] = make_float2(hi, __double2float_rn(sg - (double)hi));
   }
-  float* F = fac + s * (int64_t)2 * Pt * L;
+  float* F = T.fac + T.foff[s] * 4;
   double gam2 = 0.0, del2 = 0.0, gam1 = 0.0, del1 = 0.0;
   bool failed = false;
-  const int rows = Pt * L;
+  const int rows = PT * L;
   for (int i = 0; i < rows; ++i) {
     float ainv = 1.f, bt = 0.f;
     if (i < n && !failed) {
@@ -677,7 +778,7 @@ __global__ void k_factor32(DevPlan P, int n, int Pt, int L, const double* __rest
       const double alpha = cr - ar * del2 - beta * gam1;
       if (!(alpha != 0.0) || !isfinite(alpha)) {
         const unsigned long long key = ((unsigned long long)s << 32) | (unsigned long long)(uint32_t)i;
-        atomicMin(P.info, key);
+        atomicMin(T.info, key);
         failed = true;
       } else {
         const double gamma = (dr - beta * del1) / alpha;
@@ -690,67 +791,70 @@ __global__ void k_factor32(DevPlan P, int n, int Pt, int L, const double* __rest
         del1 = delta;
       }
     }
-    const int t = i / L, j = i - t * L;
-    const int64_t base = ((int64_t)(j / 4) * 2) * Pt * 4 + (int64_t)t * 4 + (j & 3);
+    const int tgi = i / L, j = i - tgi * L;
+    const int64_t base = ((int64_t)(j / 4) * 2) * PT * 4 + (int64_t)tgi * 4 + (j & 3);
     F[base] = ainv;
-    F[base + (int64_t)Pt * 4] = bt;
+    F[base + (int64_t)PT * 4] = bt;
   }
 }
 
-template <int W, int L, bool RES64>
-cudaError_t launch_solve32r_WL(const DevPlan& P, const F32Factors& F, const double* sigma, int n, const double* f,
-                               double* x, int max_refine, int tol_log2, cudaStream_t st) {
-  const int vec = ((((uintptr_t)f) | ((uintptr_t)x)) % 16 == 0) && (n % 2 == 0);
-  constexpr size_t smem = sizeof(Smem<W>);
-  static bool attr = false;  // once per process; not a stream operation
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_solve32r<W, L, RES64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
+template <int L, int WT, bool CL, bool RES64>
+cudaError_t launch_bucket(const F32Tables& T, const int32_t* sys, const F32Bucket& b, int shared, const double* f,
+                          double* x, int max_refine, int tol_log2, cudaStream_t st) {
+  const int vec = ((((uintptr_t)f) | ((uintptr_t)x)) % 16 == 0) && b.even_offsets;
+  const size_t smem = smem_bytes(b.W);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(b.count * b.C));
+  cfg.blockDim = dim3(32 * b.W);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  if (b.C > 1) {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = b.C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
   }
-  k_solve32r<W, L, RES64><<<(unsigned)P.batch, 32 * W, smem, st>>>(P.batch, n, P.shared,
-                                                                 reinterpret_cast<const float4*>(F.fac), sigma,
-                                                                 reinterpret_cast<const float2*>(F.sigma2), f, x,
-                                                                 max_refine, tol_log2, vec, P.info);
-  return cudaGetLastError();
+  return cudaLaunchKernelEx(&cfg, k_solve32r<L, WT, CL, RES64>, T, sys + b.first, b.W, b.C, shared, f, x, max_refine,
+                            tol_log2, vec);
 }
 
-template <bool RES64>
-cudaError_t dispatch32(const DevPlan& P, const F32Factors& F, const double* sigma, int n, const double* f, double* x,
-                       int max_refine, int tol_log2, cudaStream_t st) {
-#define PENT_CASE(W_, L_) \
-  if (F.W == W_ && F.L == L_) return launch_solve32r_WL<W_, L_, RES64>(P, F, sigma, n, f, x, max_refine, tol_log2, st);
-  PENT_CASE(1, 4) PENT_CASE(1, 8) PENT_CASE(1, 16)
-  PENT_CASE(2, 4) PENT_CASE(2, 8) PENT_CASE(2, 16)
-  PENT_CASE(4, 4) PENT_CASE(4, 8) PENT_CASE(4, 16)
-  PENT_CASE(8, 4) PENT_CASE(8, 8) PENT_CASE(8, 16)
-  PENT_CASE(16, 8)
-#undef PENT_CASE
-  return cudaErrorInvalidValue;
+template <int L, bool RES64>
+cudaError_t dispatch_bucket(const F32Tables& T, const int32_t* sys, const F32Bucket& b, int shared, const double* f,
+                            double* x, int max_refine, int tol_log2, cudaStream_t st) {
+  if (b.C > 1) return launch_bucket<L, 0, true, RES64>(T, sys, b, shared, f, x, max_refine, tol_log2, st);
+  if (!RES64) {
+    switch (b.W) {
+      case 1: return launch_bucket<L, 1, false, RES64>(T, sys, b, shared, f, x, max_refine, tol_log2, st);
+      case 2: return launch_bucket<L, 2, false, RES64>(T, sys, b, shared, f, x, max_refine, tol_log2, st);
+      case 4: return launch_bucket<L, 4, false, RES64>(T, sys, b, shared, f, x, max_refine, tol_log2, st);
+      case 8: return launch_bucket<L, 8, false, RES64>(T, sys, b, shared, f, x, max_refine, tol_log2, st);
+      case 16: return launch_bucket<L, 16, false, RES64>(T, sys, b, shared, f, x, max_refine, tol_log2, st);
+      default: break;
+    }
+  }
+  return launch_bucket<L, 0, false, RES64>(T, sys, b, shared, f, x, max_refine, tol_log2, st);
 }
 
 }  // namespace
 
-bool f32_shape_supported(int W, int L) {
-  static const int shapes[][2] = {{1, 4}, {1, 8}, {1, 16}, {2, 4}, {2, 8}, {2, 16}, {4, 4},
-                                  {4, 8}, {4, 16}, {8, 4}, {8, 8}, {8, 16}, {16, 8}};
-  for (const auto& sh : shapes)
-    if (sh[0] == W && sh[1] == L) return true;
-  return false;
-}
-
-cudaError_t launch_factor32(const DevPlan& P, const double* sigma, F32Factors F, int n, cudaStream_t st) {
-  const int64_t nsys = P.shared ? 1 : P.batch;
+cudaError_t launch_factor32(const F32Tables& T, const int32_t* shape, int64_t nsys, const double* sigma,
+                            cudaStream_t st) {
   const int block = 128;
-  k_factor32<<<(unsigned)((nsys + block - 1) / block), block, 0, st>>>(P, n, 32 * F.W, F.L, sigma, F.fac,
-                                                                       reinterpret_cast<float2*>(F.sigma2));
+  k_factor32<<<(unsigned)((nsys + block - 1) / block), block, 0, st>>>(T, nsys, shape, sigma);
   return cudaGetLastError();
 }
 
-cudaError_t launch_solve32r(const DevPlan& P, F32Factors F, const double* sigma, int n, const double* f, double* x,
-                            int max_refine, int residual_f64, int tol_log2, cudaStream_t st) {
-  return residual_f64 ? dispatch32<true>(P, F, sigma, n, f, x, max_refine, tol_log2, st)
-                      : dispatch32<false>(P, F, sigma, n, f, x, max_refine, tol_log2, st);
+cudaError_t launch_solve32r(const F32Tables& T, const int32_t* sys, const F32Bucket& b, int shared, const double* f,
+                            double* x, int max_refine, int residual_f64, int tol_log2, cudaStream_t st) {
+  if (b.count == 0) return cudaSuccess;
+  if (b.L == 4) return residual_f64 ? dispatch_bucket<4, true>(T, sys, b, shared, f, x, max_refine, tol_log2, st)
+                                    : dispatch_bucket<4, false>(T, sys, b, shared, f, x, max_refine, tol_log2, st);
+  if (b.L == 8) return residual_f64 ? dispatch_bucket<8, true>(T, sys, b, shared, f, x, max_refine, tol_log2, st)
+                                    : dispatch_bucket<8, false>(T, sys, b, shared, f, x, max_refine, tol_log2, st);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace pent

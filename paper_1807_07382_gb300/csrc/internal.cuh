@@ -39,28 +39,39 @@ struct F64Factors {
   double* bwd;
 };
 
-// FP32 CTA-per-system storage of the symmetric hyperdiffusion factors for system s
-// (uniform length n, P = 32 W threads of L rows, n <= P L):
-//   float4 ((s * L/4 + j/4) * 2 + p) * P + t holds rows t L + 4 (j/4) .. + 3 of plane p
-//   (0: 1/alpha, 1: beta); epsilon, gamma and delta are rebuilt from sigma in the solve.
-struct F32Factors {
-  float* fac;
-  float* sigma2;  // per system: sigma split into an FP32 pair (hi, lo)
-  int W;          // warps per system
-  int L;          // rows per thread
+// FP32 storage of the symmetric hyperdiffusion factors, one block per system s
+// (P T = 32 W C threads of L rows, n_s <= P T L): float4 T.foff[s] + ((j / 4) * 2 + p) * P T + t
+// holds rows t L + 4 (j/4) .. + 3 of plane p (0: 1/alpha, 1: beta); epsilon, gamma and
+// delta are rebuilt from sigma in the solve.  Shared-matrix plans use block 0.
+struct F32Tables {
+  const int32_t* n;       // [batch] rows
+  const int64_t* off;     // [batch] first row in f / x
+  const int64_t* foff;    // [nfac] first float4 of the factor block
+  float2* sig2;           // [nfac] sigma split into an FP32 pair (hi, lo)
+  const double* sigma;    // [nfac] sigma in FP64 (FP64-residual variant)
+  float* fac;             // factor storage
+  unsigned long long* info;
 };
-bool f32_shape_supported(int W, int L);
+
+// Systems solved by one launch: sys[first .. first + count) share the CTA shape
+// (L rows per thread, W warps per CTA, C CTAs per system in a cluster).
+struct F32Bucket {
+  int L, W, C;
+  int64_t first, count;
+  int even_offsets;  // every system of the bucket starts at an even row (16-byte vector access)
+};
 
 // ---- launchers (kernels live in the .cu files) ----
 cudaError_t launch_factor64(const DevPlan& P, const double* a, const double* b, const double* c, const double* d,
                             const double* e, const double* sigma, F64Factors F, cudaStream_t st);
-cudaError_t launch_factor32(const DevPlan& P, const double* sigma, F32Factors F, int n, cudaStream_t st);
+cudaError_t launch_factor32(const F32Tables& T, const int32_t* shape, int64_t nsys, const double* sigma,
+                            cudaStream_t st);
 cudaError_t launch_solve64(const DevPlan& P, F64Factors F, const double* f, double* x, double* gscr, int block_warps,
                            int unroll, cudaStream_t st);
 cudaError_t launch_adjoint64(const DevPlan& P, F64Factors F, const double* f, double* x, double* gscr,
                              int block_warps, cudaStream_t st);
-cudaError_t launch_solve32r(const DevPlan& P, F32Factors F, const double* sigma, int n, const double* f, double* x,
-                            int max_refine, int residual_f64, int tol_log2, cudaStream_t st);
+cudaError_t launch_solve32r(const F32Tables& T, const int32_t* sys, const F32Bucket& b, int shared, const double* f,
+                            double* x, int max_refine, int residual_f64, int tol_log2, cudaStream_t st);
 cudaError_t launch_sigma_grad(const DevPlan& P, const double* mu, const double* x, double* g_sigma, cudaStream_t st);
 // One ADI step (csrc/adi.cu).  rhsT and W are field-sized scratch, colsum one double.
 struct AdiArgs {

@@ -47,11 +47,23 @@ struct pent_plan {
   std::vector<int64_t> goff;
   std::vector<int32_t> glen;
   int64_t grows = 0;  // record rows over all groups
-  // CTA-per-system FP32 storage: W32 warps of L32 rows per thread
-  int W32 = 0;
-  int L32 = 0;
+  // FP32 (refined) solve: per factored system a CTA shape (L rows per thread,
+  // W warps per CTA, C CTAs per cluster), grouped into buckets of equal shape
+  struct Shape {
+    int L, W, C;
+    bool operator<(const Shape& o) const { return std::tie(L, W, C) < std::tie(o.L, o.W, o.C); }
+  };
+  std::vector<Shape> shape;       // [nfac]
+  std::vector<int64_t> foff;      // [nfac] float4 offset of each factor block
+  int64_t fac_float4 = 0;         // total float4 of factor storage
+  std::vector<int32_t> sys32;     // [batch] systems in bucket order
+  std::vector<F32Bucket> buckets;
+  int64_t tps_override = 0;       // PENT_OPT_THREADS_PER_SYSTEM for FP32 (0: automatic)
+  std::vector<cudaStream_t> side; // extra streams so that bucket launches overlap
+  std::vector<cudaEvent_t> ev;    // fork/join events
   // workspace regions
-  Region r_info, r_perm, r_off, r_n, r_goff, r_glen, r_sigma, r_fwd, r_bwd, r_scr, r_fac32, r_sig32, r_adi;
+  Region r_info, r_perm, r_off, r_n, r_goff, r_glen, r_sigma, r_fwd, r_bwd, r_scr, r_fac32, r_sig32, r_foff, r_shape,
+      r_sys32, r_adi;
   size_t ws_bytes = 0;
   // binding / state
   unsigned char* ws = nullptr;
@@ -80,10 +92,26 @@ struct pent_plan {
     return P;
   }
   F64Factors f64() const { return F64Factors{at<double>(r_fwd), at<double>(r_bwd)}; }
-  F32Factors f32() const { return F32Factors{at<float>(r_fac32), at<float>(r_sig32), W32, L32}; }
+  F32Tables f32() const {
+    F32Tables T;
+    T.n = at<int32_t>(r_n);
+    T.off = at<int64_t>(r_off);
+    T.foff = at<int64_t>(r_foff);
+    T.sig2 = at<float2>(r_sig32);
+    T.sigma = at<double>(r_sigma);
+    T.fac = at<float>(r_fac32);
+    T.info = at<unsigned long long>(r_info);
+    return T;
+  }
   void drop_graphs() {
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
     graphs.clear();
+  }
+  void drop_streams() {
+    for (auto e : ev) cudaEventDestroy(e);
+    for (auto st : side) cudaStreamDestroy(st);
+    ev.clear();
+    side.clear();
   }
 };
 
@@ -91,19 +119,76 @@ namespace {
 
 pent_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PENT_OK : PENT_ECUDA; }
 
-// Rows per thread for P threads per system: the smallest supported L with P L >= n.
-int rows_per_thread(int64_t n, int W) {
-  for (int L : {4, 8, 16, 32})
-    if ((int64_t)32 * W * L >= n && f32_shape_supported(W, L)) return L;
-  return 0;
+using Shape = pent_plan::Shape;
+
+// Default FP32 CTA shape for n rows: 8 rows per thread (4 for the shortest
+// systems), the fewest warps that cover n in one CTA of at most 16 warps, and
+// beyond 4096 rows a cluster of C CTAs (at most 8) with as few warps each as
+// cover n.  Padding is below 256 rows per system.
+bool default_shape(int64_t n, Shape* sh) {
+  if (n <= 128) { *sh = Shape{4, 1, 1}; return true; }
+  const int64_t t8 = (n + 7) / 8;  // threads needed at 8 rows each
+  if (t8 <= 512) { *sh = Shape{8, (int)((t8 + 31) / 32), 1}; return true; }
+  const int64_t C = (t8 + 511) / 512;
+  if (C > 8) return false;
+  *sh = Shape{8, (int)((t8 + 32 * C - 1) / (32 * C)), (int)C};
+  return true;
 }
 
-// Default CTA shape: 8 rows per thread (4 for the shortest systems), as few warps as cover n.
-bool choose_f32_shape(int64_t n, int* W, int* L) {
-  if (n <= 128) { *W = 1; *L = 4; return true; }
-  for (int w : {1, 2, 4, 8, 16})
-    if ((int64_t)32 * w * 8 >= n) { *W = w; *L = 8; return true; }
+// Shape for a requested number of threads per system (32 W C, W <= 16).
+bool shape_for_threads(int64_t n, int64_t tps, Shape* sh) {
+  if (tps < 32 || tps % 32) return false;
+  int C = 1;
+  if (tps > 512) {
+    if (tps % 512) return false;
+    C = (int)(tps / 512);
+    if (C > 8) return false;
+  }
+  const int W = (int)(tps / (32 * C));
+  for (int L : {4, 8})
+    if ((int64_t)32 * W * C * L >= n) { *sh = Shape{L, W, C}; return true; }
   return false;
+}
+
+bool build_f32_shapes(pent_plan* p) {
+  const int64_t nfac = p->shared ? 1 : p->batch;
+  p->shape.assign(nfac, Shape{0, 0, 0});
+  p->foff.assign(nfac, 0);
+  int64_t acc = 0;
+  for (int64_t s = 0; s < nfac; ++s) {
+    const int64_t n = p->n[s];
+    const bool ok = p->tps_override ? shape_for_threads(n, p->tps_override, &p->shape[s]) : default_shape(n, &p->shape[s]);
+    if (!ok) return false;
+    p->foff[s] = acc;
+    const Shape& sh = p->shape[s];
+    acc += (int64_t)2 * 32 * sh.W * sh.C * sh.L / 4;
+  }
+  p->fac_float4 = acc;
+  // buckets: systems grouped by shape, longest shapes first
+  std::map<Shape, std::vector<int32_t>> groups;
+  for (int64_t s = 0; s < p->batch; ++s) groups[p->shape[p->shared ? 0 : s]].push_back((int32_t)s);
+  std::vector<std::pair<Shape, std::vector<int32_t>>> order(groups.begin(), groups.end());
+  std::sort(order.begin(), order.end(), [](const auto& a, const auto& b) {
+    return (int64_t)a.first.W * a.first.C * a.first.L > (int64_t)b.first.W * b.first.C * b.first.L;
+  });
+  p->sys32.clear();
+  p->buckets.clear();
+  for (auto& kv : order) {
+    F32Bucket b;
+    b.L = kv.first.L;
+    b.W = kv.first.W;
+    b.C = kv.first.C;
+    b.first = (int64_t)p->sys32.size();
+    b.count = (int64_t)kv.second.size();
+    b.even_offsets = 1;
+    for (int32_t s : kv.second) {
+      if (p->off[s] & 1) b.even_offsets = 0;
+      p->sys32.push_back(s);
+    }
+    p->buckets.push_back(b);
+  }
+  p->threads_per_system = p->shared || p->uniform ? 32 * p->shape[0].W * p->shape[0].C : 0;
+  return true;
 }
 
 void layout(pent_plan* p) {
@@ -128,8 +213,11 @@ void layout(pent_plan* p) {
     take(p->r_bwd, (size_t)frows * 2 * lanes * sizeof(double));
     take(p->r_scr, (size_t)p->grows * kWarp * sizeof(double));
   } else {
-    take(p->r_fac32, (size_t)nfac * 2 * 32 * p->W32 * p->L32 * sizeof(float));
+    take(p->r_fac32, (size_t)p->fac_float4 * 4 * sizeof(float));
     take(p->r_sig32, (size_t)nfac * 2 * sizeof(float));
+    take(p->r_foff, (size_t)nfac * sizeof(int64_t));
+    take(p->r_shape, (size_t)nfac * sizeof(int32_t));
+    take(p->r_sys32, (size_t)p->batch * sizeof(int32_t));
   }
   // ADI scratch, for shared-matrix plans: a full field (rows doubles) plus one partial
   // sum per warp of the column sweep (at most n / 32 + 4 of them)
@@ -206,15 +294,10 @@ pent_status pent_plan_create(pent_plan** out, int64_t batch, const int64_t* n_pe
   }
   p->grows = acc;
   if (precision == PENT_F32_REFINE) {
-    if (!p->uniform) {
+    if (!build_f32_shapes(p)) {
       delete p;
       return PENT_EINVAL;
     }
-    if (!choose_f32_shape(p->n_uniform, &p->W32, &p->L32)) {
-      delete p;
-      return PENT_EINVAL;
-    }
-    p->threads_per_system = 32 * p->W32;
   }
   layout(p);
   *out = p;
@@ -242,6 +325,26 @@ pent_status pent_plan_bind(pent_plan* p, void* ws, void* stream) {
   up(p->r_glen, p->glen.data(), p->glen.size() * sizeof(int32_t));
   const unsigned long long init[kInfoWords] = {kInfoNone, 0, 0, 0};
   up(p->r_info, init, sizeof(init));
+  if (p->precision == PENT_F32_REFINE) {
+    std::vector<int32_t> shp(p->shape.size());
+    for (size_t k = 0; k < shp.size(); ++k)
+      shp[k] = (32 * p->shape[k].W * p->shape[k].C) | (p->shape[k].L << 16);
+    up(p->r_foff, p->foff.data(), p->foff.size() * sizeof(int64_t));
+    up(p->r_shape, shp.data(), shp.size() * sizeof(int32_t));
+    up(p->r_sys32, p->sys32.data(), p->sys32.size() * sizeof(int32_t));
+    p->drop_streams();
+    const int nside = (int)std::min<size_t>(3, p->buckets.size() > 1 ? p->buckets.size() - 1 : 0);
+    for (int k = 0; k < nside && e == cudaSuccess; ++k) {
+      cudaStream_t ss;
+      e = cudaStreamCreateWithFlags(&ss, cudaStreamNonBlocking);
+      if (e == cudaSuccess) p->side.push_back(ss);
+    }
+    for (int k = 0; k < 2 * nside + 1 && e == cudaSuccess; ++k) {
+      cudaEvent_t ee;
+      e = cudaEventCreateWithFlags(&ee, cudaEventDisableTiming);
+      if (e == cudaSuccess) p->ev.push_back(ee);
+    }
+  }
   if (e != cudaSuccess) return PENT_ECUDA;
   p->bound = true;
   p->factored = 0;
@@ -255,13 +358,13 @@ pent_status pent_plan_set_option(pent_plan* p, int key, int64_t value) {
       // changes the factor layout and the workspace size: only before binding
       if (p->bound) return PENT_EINVAL;
       if (p->precision == PENT_F64) return value == 1 ? PENT_OK : PENT_EINVAL;
-      if (value < 32 || value > 1024 || value % 32 || (value & (value - 1))) return PENT_EINVAL;
-      const int W = (int)(value / 32);
-      const int L = rows_per_thread(p->n_uniform, W);
-      if (L == 0) return PENT_EINVAL;
-      p->W32 = W;
-      p->L32 = L;
-      p->threads_per_system = (int)value;
+      const int64_t keep = p->tps_override;
+      p->tps_override = value;
+      if (!build_f32_shapes(p)) {
+        p->tps_override = keep;
+        build_f32_shapes(p);
+        return PENT_EINVAL;
+      }
       layout(p);
       return PENT_OK;
     }
@@ -328,7 +431,7 @@ static pent_status factor_common(pent_plan* p, const double* a, const double* b,
   if (p->precision == PENT_F64)
     err = launch_factor64(P, a, b, c, d, e, sg, p->f64(), p->stream);
   else
-    err = launch_factor32(P, sg, p->f32(), (int)p->n_uniform, p->stream);
+    err = launch_factor32(p->f32(), p->at<int32_t>(p->r_shape), p->shared ? 1 : p->batch, sg, p->stream);
   if (err != cudaSuccess) return PENT_ECUDA;
   p->factored = sigma ? 2 : 1;
   return PENT_OK;
@@ -346,14 +449,40 @@ pent_status pent_factor_hyperdiff(pent_plan* p, const double* d_sigma) {
   return factor_common(p, nullptr, nullptr, nullptr, nullptr, nullptr, d_sigma);
 }
 
+// The FP32 solve of every bucket; with several buckets the launches are spread
+// over the plan's side streams (forked from and joined back to the plan's
+// stream with events, which also works inside a stream capture).
+static cudaError_t solve32_buckets(pent_plan* p, const double* f, double* x, int max_refine) {
+  const F32Tables T = p->f32();
+  const int32_t* sys = p->at<int32_t>(p->r_sys32);
+  const int rf = p->residual == PENT_RESIDUAL_F64;
+  const int ns = (int)p->side.size();
+  cudaError_t e = cudaSuccess;
+  if (ns == 0) {
+    for (const auto& b : p->buckets)
+      if (e == cudaSuccess) e = launch_solve32r(T, sys, b, p->shared, f, x, max_refine, rf, p->tol_log2, p->stream);
+    return e;
+  }
+  e = cudaEventRecord(p->ev[0], p->stream);
+  for (int k = 0; k < ns && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(p->side[k], p->ev[0], 0);
+  for (size_t i = 0; i < p->buckets.size() && e == cudaSuccess; ++i) {
+    cudaStream_t st = (i % (ns + 1) == 0) ? p->stream : p->side[i % (ns + 1) - 1];
+    e = launch_solve32r(T, sys, p->buckets[i], p->shared, f, x, max_refine, rf, p->tol_log2, st);
+  }
+  for (int k = 0; k < ns && e == cudaSuccess; ++k) {
+    e = cudaEventRecord(p->ev[1 + k], p->side[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->stream, p->ev[1 + k], 0);
+  }
+  return e;
+}
+
 static pent_status solve_launch(pent_plan* p, const double* f, double* x, int max_refine) {
   const DevPlan P = p->dev();
   cudaError_t err;
   if (p->precision == PENT_F64) {
     err = launch_solve64(P, p->f64(), f, x, p->at<double>(p->r_scr), p->block_warps, p->unroll, p->stream);
   } else {
-    err = launch_solve32r(P, p->f32(), p->at<double>(p->r_sigma), (int)p->n_uniform, f, x, max_refine,
-                          p->residual == PENT_RESIDUAL_F64, p->tol_log2, p->stream);
+    err = solve32_buckets(p, f, x, max_refine);
   }
   return cuda_status(err);
 }
@@ -441,6 +570,7 @@ pent_status pent_clear_info(pent_plan* p) {
 void pent_plan_destroy(pent_plan* p) {
   if (!p) return;
   p->drop_graphs();
+  p->drop_streams();
   delete p;
 }
 

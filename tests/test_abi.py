@@ -59,8 +59,7 @@ def _create(L, batch, n=None, n_uniform=0, shared=0, prec=0):
     dict(batch=3, n=[4, 0, 5]),
     dict(batch=2, n=[4, 5], shared=1),
     dict(batch=2, n_uniform=8, prec=7),
-    dict(batch=2, n=[40, 50], prec=1),          # FP32 refinement needs uniform lengths
-    dict(batch=2, n_uniform=5000, prec=1),      # ... and n <= 4096 (one CTA per system)
+    dict(batch=2, n_uniform=40000, prec=1),     # FP32 refinement: n <= 32768 (a cluster of 8 CTAs)
 ])
 def test_plan_create_rejects_bad_arguments(L, args):
     st, h = _create(L, **args)
@@ -100,13 +99,14 @@ def test_f32_threads_per_system_option_relayouts_before_bind(L):
     v = ctypes.c_int64()
     assert L.pent_plan_get_option(h, _lib.PENT_OPT_THREADS_PER_SYSTEM, ctypes.byref(v)) == 0
     default_tps = v.value
-    assert default_tps in (32, 64, 128, 256)
+    assert default_tps == 128
     base = L.pent_plan_workspace_bytes(h)
-    for tps in (64, 128, 256):
+    for tps in (128, 256, 512, 1024, 2048):
         assert L.pent_plan_set_option(h, _lib.PENT_OPT_THREADS_PER_SYSTEM, tps) == 0
         # FP32 factors are 8 B per padded row (1/alpha and beta)
         assert L.pent_plan_workspace_bytes(h) >= 8 * 1024 * 8
-    for bad in (0, 48, 1024, 16, 32):
+    for bad in (48, 16, 32, 64, 1536 + 32, 8192):
         assert L.pent_plan_set_option(h, _lib.PENT_OPT_THREADS_PER_SYSTEM, bad) == _lib.PENT_EINVAL
-    assert base > 0
+    assert L.pent_plan_set_option(h, _lib.PENT_OPT_THREADS_PER_SYSTEM, 0) == 0  # back to the automatic shape
+    assert L.pent_plan_workspace_bytes(h) == base
     L.pent_plan_destroy(h)

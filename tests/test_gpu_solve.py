@@ -198,3 +198,66 @@ def test_full_size_parametric_sampled():
         assert sys_rel_err(xs, ref, np.full(len(idx), n)) <= TOL
         del plan, x
         torch.cuda.empty_cache()
+
+
+# ----------------------------------------------------------------------------- FP32 shapes and uneven batches
+
+@pytest.mark.parametrize("tps", [128, 256, 512, 1024, 2048])
+def test_f32_refine_threads_per_system(tps):
+    """One CTA of up to 512 threads, or a cluster of CTAs (1024: 2, 2048: 4) per system."""
+    n = 1024
+    w = synth.hyperdiff_parametric(batch=40, n=n, steps=1)
+    ref = oracle.hyperdiff_steps(w.n, w.sigma, w.field0, 1)
+    L = pb._lib.load()
+    import ctypes
+    h = ctypes.c_void_p()
+    assert L.pent_plan_create(ctypes.byref(h), w.batch, None, n, 0, pb.PENT_F32_REFINE, None) == 0
+    assert L.pent_plan_set_option(h, pb.PENT_OPT_THREADS_PER_SYSTEM, tps) == 0
+    ws = torch.empty(L.pent_plan_workspace_bytes(h), dtype=torch.uint8, device="cuda")
+    assert L.pent_plan_bind(h, ws.data_ptr(), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)) == 0
+    sig = dev(w.sigma)
+    assert L.pent_factor_hyperdiff(h, ctypes.c_void_p(sig.data_ptr())) == 0
+    f = dev(w.field0)
+    x = torch.empty_like(f)
+    assert L.pent_solve_batch(h, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(x.data_ptr()), 2) == 0
+    torch.cuda.synchronize()
+    L.pent_plan_destroy(h)
+    assert sys_rel_err(host(x), ref, w.n) <= TOL
+
+
+@pytest.mark.parametrize("n,batch", [(4097, 6), (8192, 5), (16384, 4), (32768, 2)])
+def test_f32_refine_long_systems_in_clusters(n, batch):
+    w = synth.hyperdiff_parametric(batch=batch, n=n, steps=1, sigma_range=(1e-2, 10.0))
+    ref = oracle.hyperdiff_steps(w.n, w.sigma, w.field0, 1)
+    plan = pb.Plan(n, batch=batch, precision=pb.PENT_F32_REFINE)
+    plan.factor_hyperdiff(dev(w.sigma))
+    x = plan.solve(dev(w.field0), max_refine=2)
+    assert plan.info()[0] == pb.PENT_OK
+    assert sys_rel_err(host(x), ref, w.n) <= TOL
+
+
+def test_f32_refine_uneven_batch():
+    """Log-uniform lengths in [64, 16384] (the uneven workload's distribution),
+    many shape buckets launched over the plan's side streams, plus a CUDA graph."""
+    w = synth.uneven(batch=300, steps=3)
+    ref = oracle.hyperdiff_steps(w.n, w.sigma, w.field0, w.steps)
+    plan = pb.Plan(list(w.n), precision=pb.PENT_F32_REFINE)
+    plan.factor_hyperdiff(dev(w.sigma))
+    x = dev(w.field0)
+    plan.solve_steps(x, w.steps, max_refine=2)
+    assert plan.info()[0] == pb.PENT_OK
+    assert sys_rel_err(host(x), ref, w.n) <= TOL
+    y = dev(w.field0)
+    for _ in range(w.steps):
+        plan.solve(y, y, max_refine=2)
+    assert torch.equal(x, y)
+
+
+def test_f64_uneven_batch_full_range():
+    w = synth.uneven(batch=300, steps=2)
+    ref = oracle.hyperdiff_steps(w.n, w.sigma, w.field0, w.steps)
+    plan = pb.Plan(list(w.n))
+    plan.factor_hyperdiff(dev(w.sigma))
+    x = dev(w.field0)
+    plan.solve_steps(x, w.steps)
+    assert sys_rel_err(host(x), ref, w.n) <= TOL
