@@ -107,7 +107,8 @@ enum {
                                       CTAs); 8 rows per thread at most; 0 restores the automatic choice */
   PENT_OPT_RESIDUAL = 2,           /* pent_residual */
   PENT_OPT_BLOCK_WARPS = 3,        /* PENT_F64: warps per CTA of the solve kernels (1..8) */
-  PENT_OPT_REFINE_TOL_LOG2 = 4,    /* refinement stops once a correction is <= 2^-tol * |x| (default 40) */
+  PENT_OPT_REFINE_TOL_LOG2 = 4,    /* refinement stops once the estimated remaining error, (max|dx| / max|x|)^2
+                                      relative to max|x| after a step with correction dx, is <= 2^-tol (default 43) */
   PENT_OPT_UNROLL = 5              /* PENT_F64: rows loaded ahead of the arithmetic: 2, 4 or 8 (default 4) */
 };
 pent_status pent_plan_set_option(pent_plan* plan, int key, int64_t value);

@@ -45,7 +45,9 @@ __device__ __forceinline__ void report_bad_pivot(unsigned long long* info, int64
 // Factor one system per thread (Sec. 2.4, factorisation steps 1-14, written as
 // the generic row step with out-of-range quantities zero) and write its FP64
 // records.  Rows after a failed pivot and padding rows get identity records
-// (1/alpha = 1, all couplings 0), so later solves stay finite.
+// (1/alpha = 1, all couplings 0), so later solves stay finite.  With F.sig the
+// hyperdiffusion records are written instead (1/alpha and beta; epsilon is
+// sigma), and those rows get 1/alpha = 0, which zeroes their g.
 __global__ void k_factor64(DevPlan P, const double* __restrict__ a, const double* __restrict__ b,
                            const double* __restrict__ c, const double* __restrict__ d, const double* __restrict__ e,
                            const double* __restrict__ sigma, F64Factors F) {
@@ -57,8 +59,10 @@ __global__ void k_factor64(DevPlan P, const double* __restrict__ a, const double
   const int lane = (int)(q % kWarp);
   const int64_t Lg = P.shared ? P.n_shared : P.glen[k];
   const int64_t R0 = P.shared ? 0 : P.goff[k];
+  const bool hyp = !P.shared && F.sig != nullptr;
+  const int np = hyp ? 2 : 3;
   auto fwd_at = [&](int64_t r, int p) -> double& {
-    return P.shared ? F.fwd[r * 3 + p] : F.fwd[(((R0 + r) >> 1) * 3 + p) * 2 * kWarp + lane * 2 + ((R0 + r) & 1)];
+    return P.shared ? F.fwd[r * 3 + p] : F.fwd[(((R0 + r) >> 1) * np + p) * 2 * kWarp + lane * 2 + ((R0 + r) & 1)];
   };
   auto bwd_at = [&](int64_t r, int p) -> double& {
     return P.shared ? F.bwd[r * 2 + p] : F.bwd[(((R0 + r) >> 1) * 2 + p) * 2 * kWarp + lane * 2 + ((R0 + r) & 1)];
@@ -99,8 +103,12 @@ __global__ void k_factor64(DevPlan P, const double* __restrict__ a, const double
       const double gamma = (dr - beta * del1) / alpha;
       const double delta = er / alpha;
       fwd_at(r, 0) = 1.0 / alpha;
-      fwd_at(r, 1) = beta / alpha;
-      fwd_at(r, 2) = ar / alpha;
+      if (hyp) {
+        fwd_at(r, 1) = beta;
+      } else {
+        fwd_at(r, 1) = beta / alpha;
+        fwd_at(r, 2) = ar / alpha;
+      }
       bwd_at(r, 0) = gamma;
       bwd_at(r, 1) = delta;
       gam2 = gam1;
@@ -110,15 +118,16 @@ __global__ void k_factor64(DevPlan P, const double* __restrict__ a, const double
     }
   }
   for (; r < Lg; ++r) {
-    fwd_at(r, 0) = 1.0;
+    fwd_at(r, 0) = hyp ? 0.0 : 1.0;
     fwd_at(r, 1) = 0.0;
-    fwd_at(r, 2) = 0.0;
+    if (!hyp) fwd_at(r, 2) = 0.0;
     bwd_at(r, 0) = 0.0;
     bwd_at(r, 1) = 0.0;
   }
 }
 
 struct Lane {
+  int64_t s;   // system index (-1 for an empty lane)
   int64_t n;   // rows of this lane's system (0 for an empty lane)
   int64_t fo;  // first row of the system in f/x
   int64_t Lg;  // rows walked by the warp
@@ -130,12 +139,14 @@ __device__ __forceinline__ Lane lane_setup(const DevPlan& P, int64_t k, int lane
   Lane L;
   const int64_t q = k * kWarp + lane;
   if (SHARED) {
+    L.s = (q < P.batch) ? q : -1;
     L.n = (q < P.batch) ? P.n_shared : 0;
     L.fo = (q < P.batch) ? q * P.n_shared : 0;
     L.Lg = P.n_shared;
     L.R0 = k * P.n_shared;
   } else {
     const int s = P.perm[q];
+    L.s = s;
     L.n = (s >= 0) ? P.n[s] : 0;
     L.fo = (s >= 0) ? P.off[s] : 0;
     L.Lg = P.glen[k];
@@ -144,9 +155,9 @@ __device__ __forceinline__ Lane lane_setup(const DevPlan& P, int64_t k, int lane
   return L;
 }
 
-template <bool SHARED>
+template <bool SHARED, int NP = 3>
 __device__ __forceinline__ int64_t fwd_idx(const Lane& L, int64_t r, int p, int lane) {
-  return SHARED ? r * 3 + p : (((L.R0 + r) >> 1) * 3 + p) * 2 * kWarp + lane * 2 + ((L.R0 + r) & 1);
+  return SHARED ? r * 3 + p : (((L.R0 + r) >> 1) * NP + p) * 2 * kWarp + lane * 2 + ((L.R0 + r) & 1);
 }
 template <bool SHARED>
 __device__ __forceinline__ int64_t bwd_idx(const Lane& L, int64_t r, int p, int lane) {
@@ -253,8 +264,10 @@ __global__ void __launch_bounds__(256) k_solve64(DevPlan P, F64Factors F, const 
 // The same substitutions for per-system factors, walking row pairs: every
 // factor plane, the scratch g and (when aligned) f and x move 16 bytes per lane
 // per access.  Loads run U2 pairs ahead of the arithmetic (register double
-// buffering).
-template <int U2>
+// buffering).  HYP: hyperdiffusion records, g_i = (1/alpha_i)(f_i - beta_i
+// g_{i-1} - sigma g_{i-2}) with sigma in a register -- one factor plane (8 bytes
+// per row) less to read than the general form, for the same FP64 operations.
+template <int U2, bool HYP>
 __global__ void __launch_bounds__(128) k_solve64_pair(DevPlan P, F64Factors F, const double* f, double* x,
                                                       double* __restrict__ gscr) {
   const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kWarp;
@@ -268,6 +281,8 @@ __global__ void __launch_bounds__(128) k_solve64_pair(DevPlan P, F64Factors F, c
   const int64_t P0 = L.R0 >> 1;   // first record pair of the warp
   const bool fvec = ((L.fo & 1) == 0) && ((((uintptr_t)f) & 15) == 0);
   const bool xvec = ((L.fo & 1) == 0) && ((((uintptr_t)x) & 15) == 0);
+  const double sg = (HYP && L.s >= 0) ? F.sig[L.s] : 0.0;
+  constexpr int NP = HYP ? 2 : 3;
 
   // ---- forward: L g = f ----
   double2 ca[U2], cb[U2], ce[U2], cf[U2];
@@ -277,10 +292,10 @@ __global__ void __launch_bounds__(128) k_solve64_pair(DevPlan P, F64Factors F, c
     for (int u = 0; u < U2; ++u) {
       const int64_t q = q0 + u;
       if (q < np) {
-        const double2* rec = fwd + ((P0 + q) * 3) * kWarp + lane;
+        const double2* rec = fwd + ((P0 + q) * NP) * kWarp + lane;
         A[u] = __ldg(rec);
         B[u] = __ldg(rec + kWarp);
-        E[u] = __ldg(rec + 2 * kWarp);
+        if (!HYP) E[u] = __ldg(rec + 2 * kWarp);
         const int64_t r = 2 * q;
         if (fvec && r + 1 < L.n) {
           Fv[u] = *reinterpret_cast<const double2*>(f + L.fo + r);
@@ -299,8 +314,14 @@ __global__ void __launch_bounds__(128) k_solve64_pair(DevPlan P, F64Factors F, c
     for (int u = 0; u < U2; ++u) {
       const int64_t q = q0 + u;
       if (q < np) {
-        const double ga = fma(-cb[u].x, g1, fma(-ce[u].x, g2, ca[u].x * cf[u].x));
-        const double gb = fma(-cb[u].y, ga, fma(-ce[u].y, g1, ca[u].y * cf[u].y));
+        double ga, gb;
+        if (HYP) {
+          ga = ca[u].x * fma(-cb[u].x, g1, fma(-sg, g2, cf[u].x));
+          gb = ca[u].y * fma(-cb[u].y, ga, fma(-sg, g1, cf[u].y));
+        } else {
+          ga = fma(-cb[u].x, g1, fma(-ce[u].x, g2, ca[u].x * cf[u].x));
+          gb = fma(-cb[u].y, ga, fma(-ce[u].y, g1, ca[u].y * cf[u].y));
+        }
         g2s[(P0 + q) * kWarp + lane] = make_double2(ga, gb);
         g2 = ga;
         g1 = gb;
@@ -367,7 +388,9 @@ __global__ void __launch_bounds__(128) k_solve64_pair(DevPlan P, F64Factors F, c
 //   y_i = (1/alpha_i) w_i.
 // Each sweep reads one record row per step; the couplings of later rows are
 // carried in registers.
-template <bool SHARED>
+// HYP (hyperdiffusion records): (beta/alpha)_{i+1} = beta_{i+1} (1/alpha)_{i+1} and
+// (eps/alpha)_{i+2} = sigma (1/alpha)_{i+2}, formed from the two stored planes.
+template <bool SHARED, bool HYP>
 __global__ void __launch_bounds__(256) k_adjoint64(DevPlan P, F64Factors F, const double* f, double* y,
                                                    double* __restrict__ zscr) {
   const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kWarp;
@@ -390,18 +413,25 @@ __global__ void __launch_bounds__(256) k_adjoint64(DevPlan P, F64Factors F, cons
     del_m1 = __ldg(bwd + bwd_idx<SHARED>(L, r, 1, lane));
   }
   // descending: w, y
+  constexpr int NP = HYP ? 2 : 3;
+  const double sg = (HYP && L.s >= 0) ? F.sig[L.s] : 0.0;
   double w1 = 0.0, w2 = 0.0;          // w_{i+1}, w_{i+2}
   double bp_p1 = 0.0, ep_p1 = 0.0, ep_p2 = 0.0;  // (beta/alpha)_{i+1}, (eps/alpha)_{i+1}, (eps/alpha)_{i+2}
   for (int64_t r = L.Lg - 1; r >= 0; --r) {
-    const double ainv = __ldg(fwd + fwd_idx<SHARED>(L, r, 0, lane));
+    const double ainv = __ldg(fwd + fwd_idx<SHARED, NP>(L, r, 0, lane));
     const double z = zscr[scr_idx<SHARED>(L, r, lane)];
     const double w = fma(-bp_p1, w1, fma(-ep_p2, w2, z));
     if (r < L.n) y[L.fo + r] = ainv * w;
     w2 = w1;
     w1 = w;
     ep_p2 = ep_p1;
-    bp_p1 = __ldg(fwd + fwd_idx<SHARED>(L, r, 1, lane));
-    ep_p1 = __ldg(fwd + fwd_idx<SHARED>(L, r, 2, lane));
+    if (HYP) {
+      bp_p1 = __ldg(fwd + fwd_idx<SHARED, NP>(L, r, 1, lane)) * ainv;
+      ep_p1 = (r >= 2) ? sg * ainv : 0.0;
+    } else {
+      bp_p1 = __ldg(fwd + fwd_idx<SHARED, NP>(L, r, 1, lane));
+      ep_p1 = __ldg(fwd + fwd_idx<SHARED, NP>(L, r, 2, lane));
+    }
   }
 }
 
@@ -457,11 +487,18 @@ cudaError_t launch_solve64(const DevPlan& P, F64Factors F, const double* f, doub
     return cudaErrorInvalidValue;
   }
   // per-system factors: row pairs, unroll rows = 2 x pairs ahead
-  if (unroll == 2) k_solve64_pair<1><<<grid, block, 0, st>>>(P, F, f, x, gscr);
-  else if (unroll == 4) k_solve64_pair<2><<<grid, block, 0, st>>>(P, F, f, x, gscr);
-  else if (unroll == 8) k_solve64_pair<4><<<grid, block, 0, st>>>(P, F, f, x, gscr);
-  else return cudaErrorInvalidValue;
-  return cudaGetLastError();
+  const bool hyp = F.sig != nullptr;
+#define PENT_U2(U_, U2_)                                                       \
+  if (unroll == U_) {                                                          \
+    if (hyp)                                                                   \
+      k_solve64_pair<U2_, true><<<grid, block, 0, st>>>(P, F, f, x, gscr);    \
+    else                                                                       \
+      k_solve64_pair<U2_, false><<<grid, block, 0, st>>>(P, F, f, x, gscr);   \
+    return cudaGetLastError();                                                 \
+  }
+  PENT_U2(2, 1) PENT_U2(4, 2) PENT_U2(8, 4)
+#undef PENT_U2
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_adjoint64(const DevPlan& P, F64Factors F, const double* f, double* x, double* gscr,
@@ -469,9 +506,11 @@ cudaError_t launch_adjoint64(const DevPlan& P, F64Factors F, const double* f, do
   const int block = kWarp * block_warps;
   const int grid = grid_for(P.ngroups * kWarp, block);
   if (P.shared)
-    k_adjoint64<true><<<grid, block, 0, st>>>(P, F, f, x, gscr);
+    k_adjoint64<true, false><<<grid, block, 0, st>>>(P, F, f, x, gscr);
+  else if (F.sig)
+    k_adjoint64<false, true><<<grid, block, 0, st>>>(P, F, f, x, gscr);
   else
-    k_adjoint64<false><<<grid, block, 0, st>>>(P, F, f, x, gscr);
+    k_adjoint64<false, false><<<grid, block, 0, st>>>(P, F, f, x, gscr);
   return cudaGetLastError();
 }
 

@@ -15,19 +15,21 @@
 // (all loaded with coalesced 16-byte accesses, since a thread's rows are
 // contiguous).  Each substitution (Sec. 2.4: L g = f, then R x = g) is a
 // second-order linear recurrence, so a thread's chunk acts on the two carried
-// values as an affine map.  The thread runs its chunk from a zero state to get
-// the affine part; the maps are composed by a Kogge-Stone shuffle scan in each
-// warp, a short carry across warps and, in a cluster, a carry across CTAs read
-// through distributed shared memory; then every thread reruns its chunk from
-// the true entering state.  The factors are read from HBM once per call
-// and reused by every substitution of every refinement step.
+// values as an affine map whose linear part depends on the factors only.  Once
+// per launch the linear parts are composed by a Kogge-Stone shuffle scan in each
+// warp and every level's window map is kept in shared memory (the "scan plan");
+// each substitution then runs its chunk from a zero state for the affine part,
+// scans only those two numbers with the stored window maps, carries them across
+// warps and, in a cluster, across CTAs through distributed shared memory, and
+// reruns the chunk from the true entering state.  The factors are read from HBM
+// once per call and reused by every substitution of every refinement step.
 //
 // The hyperdiffusion matrices are symmetric, so A = L D^{-1} L^T with D the
 // diagonal alpha of L: R = D^{-1} L^T, gamma_i = beta_{i+1} / alpha_i and
-// delta_i = epsilon_{i+2} / alpha_i, and epsilon_i = a_i is sigma times a
-// stencil weight.  Only 1/alpha_i and beta_i are stored (8 bytes per row in
-// FP32); epsilon, gamma, delta and the chunks' 2x2 transfer maps are rebuilt in
-// registers, trading FP32 arithmetic for HBM bytes.
+// delta_i = epsilon_{i+2} / alpha_i, and epsilon_i = a_i = sigma for every row
+// i >= 2.  Only 1/alpha_i and beta_i are stored (8 bytes per row in FP32); the
+// substitutions use them directly, g_i = (1/alpha_i)(v_i - beta_i g_{i-1} -
+// sigma g_{i-2}) and x_i = g_i - (1/alpha_i)(beta_{i+1} x_{i+1} + sigma x_{i+2}).
 #include <cooperative_groups.h>
 
 #include <cmath>
@@ -65,9 +67,10 @@ __device__ __forceinline__ float small_uint_to_float(unsigned v) {
 }
 
 // v * 2^-k split into hi + lo floats (hi: v truncated to 24 significant bits,
-// lo: the next 24 bits, rounded), using integer operations only.  Values whose
-// scaled magnitude is below 2^-126 are flushed to zero; the caller picks k so
-// that the largest |v| of the system scales to just below 1.
+// lo: the next 23 bits, truncated; together 47 bits, a relative error below
+// 2^-47), using integer operations only.  Values whose scaled magnitude is below
+// 2^-126 are flushed to zero; the caller picks k so that the largest |v| of the
+// system scales to just below 1.
 __device__ __forceinline__ void split_scaled(double v, int k, float& hi, float& lo) {
   const unsigned long long U = (unsigned long long)__double_as_longlong(v);
   const unsigned top = (unsigned)(U >> 32);
@@ -81,43 +84,43 @@ __device__ __forceinline__ void split_scaled(double v, int k, float& hi, float& 
   }
   const unsigned mant_hi = (unsigned)((U >> 29) & 0x7fffffu);
   hi = __uint_as_float(sign | ((unsigned)(Es - 896) << 23) | mant_hi);
-  if (Es < 949) {
+  if (Es < 943) {
     lo = 0.0f;
     return;
   }
-  const unsigned rem = (unsigned)(U & 0x1fffffffu);  // low 29 mantissa bits
-  const float r = __fmaf_rn(small_uint_to_float(rem >> 6), 64.0f, small_uint_to_float(rem & 63u));
-  const float scale = __uint_as_float((unsigned)(Es - 948) << 23);  // 2^(Es - 1075)
-  lo = __uint_as_float(__float_as_uint(__fmul_rn(r, scale)) ^ sign);
+  const unsigned rem = (unsigned)(U >> 6) & 0x7fffffu;  // mantissa bits 6..28 (the 23 below hi's)
+  const float scale = __uint_as_float((unsigned)(Es - 942) << 23);  // 2^(Es - 1069)
+  lo = __uint_as_float(__float_as_uint(__fmul_rn(small_uint_to_float(rem), scale)) ^ sign);
 }
 
-// Rare path of f2d_shift (subnormal float or a result outside the normal double
-// range).  Kept out of line so that its FP64 arithmetic is never if-converted
-// into the common path.
-__device__ __noinline__ double f2d_shift_slow(float v, int k) { return ldexp((double)v, k); }
+// Rare path of ff_to_double_shift (h outside the range the fast path covers):
+// exact conversions and one FP64 add, out of line.
+__device__ __noinline__ double ff_to_double_slow(float h, float l, int k) { return ldexp((double)h, k) + ldexp((double)l, k); }
 
-// Exact v * 2^k as a double, by moving v's exponent and mantissa bit fields.
-__device__ __forceinline__ double f2d_shift(float v, int k) {
-  const unsigned u = __float_as_uint(v);
-  const unsigned a = u & 0x7fffffffu;
-  if (a == 0u) return 0.0;
-  const int e = (int)(a >> 23);
-  const int de = e + 896 + k;
-  if (e == 0 || e == 255 || de < 1 || de > 2046) return f2d_shift_slow(v, k);
-  const unsigned long long bits = ((unsigned long long)(u & 0x80000000u) << 32) |
-                                  (((unsigned long long)a + ((unsigned long long)(896 + k) << 23)) << 29);
-  return __longlong_as_double((long long)bits);
-}
-
-__device__ __forceinline__ float warp_max(float v) {
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, d));
-  return v;
-}
-__device__ __forceinline__ int warp_max_i(int v) {
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, d));
-  return v;
+// (h + l) * 2^k as a double for a normalised float-float pair (|l| <= ulp(h) / 2),
+// without FP64 instructions: h's bits are moved into a double, and l, counted
+// in units in the last place of that double (l * 2^(52 - e(h)), an integer
+// below 2^29 in magnitude, rounded towards zero: an error under one unit), is
+// added to its 64-bit pattern.  Where h is a power of two and the sum is
+// smaller, it falls in the binade below, whose units are half as large.  The
+// sum cannot reach the binade above (|l| <= ulp(h) / 2).  The fast path needs
+// 2^-74 <= |h| < 2^128 (so that l's scaling stays in the normal float range);
+// the caller's scaling puts every nonzero |x| there unless it lies 75 binades
+// below the largest.
+__device__ __forceinline__ double ff_to_double_shift(float h, float l, int k) {
+  const unsigned uh = __float_as_uint(h);
+  const unsigned ah = uh & 0x7fffffffu;
+  const int eh = (int)(ah >> 23);
+  if (ah == 0u) return 0.0;  // then l == 0 too
+  if (eh < 53 || eh == 255 || eh + 896 + k < 2 || eh + 896 + k > 2045) return ff_to_double_slow(h, l, k);
+  // l in units of the double's last place, signed as the change of |h + l|
+  const float units = __fmul_rn(l, __uint_as_float((unsigned)(306 - eh) << 23));  // l * 2^(179 - eh) = l * 2^(52 - e(h))
+  int kk = __float2int_rz(units);
+  kk = (uh & 0x80000000u) ? -kk : kk;
+  if ((ah & 0x7fffffu) == 0u && kk < 0) kk *= 2;
+  const unsigned long long bits = ((unsigned long long)(uh & 0x80000000u) << 32) |
+                                  (((unsigned long long)ah + ((unsigned long long)(896 + k) << 23)) << 29);
+  return __longlong_as_double((long long)(bits + (unsigned long long)(long long)kk));
 }
 
 // Weights of the no-flux fourth difference on row i (n rows, 0 <= i < n),
@@ -137,54 +140,41 @@ __device__ __forceinline__ void d4_weights_f(int i, int n, float w[5]) {
   }
 }
 
-// ---------------------------------------------------------------- block / cluster scans
+// ---------------------------------------------------------------- chunk maps and scans
 
-// x -> [[a, b], [c, d]] x + (u, v): the effect of a chunk of rows on the two carried values.
-struct Aff {
-  float a, b, c, d, u, v;
-};
-
-// `later` applied after `earlier`.
-__device__ __forceinline__ Aff compose(const Aff& L, const Aff& E) {
-  Aff r;
-  r.a = fmaf(L.a, E.a, L.b * E.c);
-  r.b = fmaf(L.a, E.b, L.b * E.d);
-  r.c = fmaf(L.c, E.a, L.d * E.c);
-  r.d = fmaf(L.c, E.b, L.d * E.d);
-  r.u = fmaf(L.a, E.u, fmaf(L.b, E.v, L.u));
-  r.v = fmaf(L.c, E.u, fmaf(L.d, E.v, L.v));
-  return r;
+// 2x2 matrices are float4 (x y / z w, row-major); states are (c0, c1).
+__device__ __forceinline__ float4 mmul(const float4 a, const float4 b) {  // a * b
+  return make_float4(fmaf(a.x, b.x, a.y * b.z), fmaf(a.x, b.y, a.y * b.w), fmaf(a.z, b.x, a.w * b.z),
+                     fmaf(a.z, b.y, a.w * b.w));
 }
 
+__device__ __forceinline__ float mnorm(const float4 m) {
+  return fmaxf(fmaxf(fabsf(m.x), fabsf(m.y)), fmaxf(fabsf(m.z), fabsf(m.w)));
+}
+
+// Value of lane - d (UP) or lane + d (down) of the warp.
 template <bool UP>
-__device__ __forceinline__ Aff shfl_aff(const Aff& x, int d) {
-  Aff r;
-  if (UP) {
-    r.a = __shfl_up_sync(0xffffffffu, x.a, d);
-    r.b = __shfl_up_sync(0xffffffffu, x.b, d);
-    r.c = __shfl_up_sync(0xffffffffu, x.c, d);
-    r.d = __shfl_up_sync(0xffffffffu, x.d, d);
-    r.u = __shfl_up_sync(0xffffffffu, x.u, d);
-    r.v = __shfl_up_sync(0xffffffffu, x.v, d);
-  } else {
-    r.a = __shfl_down_sync(0xffffffffu, x.a, d);
-    r.b = __shfl_down_sync(0xffffffffu, x.b, d);
-    r.c = __shfl_down_sync(0xffffffffu, x.c, d);
-    r.d = __shfl_down_sync(0xffffffffu, x.d, d);
-    r.u = __shfl_down_sync(0xffffffffu, x.u, d);
-    r.v = __shfl_down_sync(0xffffffffu, x.v, d);
-  }
-  return r;
+__device__ __forceinline__ float shfl(float v, int d) {
+  return UP ? __shfl_up_sync(0xffffffffu, v, d) : __shfl_down_sync(0xffffffffu, v, d);
+}
+template <bool UP>
+__device__ __forceinline__ float4 shfl4(const float4 v, int d) {
+  return make_float4(shfl<UP>(v.x, d), shfl<UP>(v.y, d), shfl<UP>(v.z, d), shfl<UP>(v.w, d));
+}
+
+// c <- m c + b.
+__device__ __forceinline__ void apply(const float4 m, const float2 b, float& c0, float& c1) {
+  const float n0 = fmaf(m.x, c0, fmaf(m.y, c1, b.x));
+  const float n1 = fmaf(m.z, c0, fmaf(m.w, c1, b.y));
+  c0 = n0;
+  c1 = n1;
 }
 
 // Coupling below this norm is dropped from the scans: it changes the carried
 // values by less than FP32 resolution, and the refinement corrects the FP32
 // solve anyway.
 constexpr float kScanTol = 9.3132257e-10f;  // 2^-30
-
-__device__ __forceinline__ float mat_norm(const Aff& m) {
-  return fmaxf(fmaxf(fabsf(m.a), fabsf(m.b)), fmaxf(fabsf(m.c), fabsf(m.d)));
-}
+constexpr int kMaxLev = 5;                  // Kogge-Stone levels of a 32-lane warp
 
 // Barrier over the CTA, or over the whole cluster when the system spans C > 1 CTAs.
 __device__ __forceinline__ void csync(int C) {
@@ -198,80 +188,6 @@ __device__ __forceinline__ void csync(int C) {
 template <class T>
 __device__ __forceinline__ T* remote(T* p, int rank) {
   return cg::this_cluster().map_shared_rank(p, rank);
-}
-
-__device__ __forceinline__ void apply(const float4 m, const float4 b, float& c0, float& c1) {
-  const float n0 = fmaf(m.x, c0, fmaf(m.y, c1, b.x));
-  const float n1 = fmaf(m.z, c0, fmaf(m.w, c1, b.y));
-  c0 = n0;
-  c1 = n1;
-}
-
-// Entering state of this thread's chunk for a sweep through the system's chunks.
-// FWD: chunks in increasing thread order; otherwise decreasing.  `a` is this
-// chunk's map (linear part from the factors, affine part from a zero-state
-// pass); the system is entered with state 0.  The Kogge-Stone levels stop as
-// soon as every lane's window either reaches the warp's first chunk or
-// composes to a negligible linear part (later levels would only add terms
-// multiplied by it).  sh: 2 W + 2 float4 (warp totals, then the CTA total).
-template <bool FWD>
-__device__ __forceinline__ void scan_entry(Aff a, int lane, int warp, int W, int C, int rank, float4* sh, float& e0,
-                                           float& e1) {
-#pragma unroll 1
-  for (int d = 1; d < 32; d <<= 1) {
-    const Aff o = shfl_aff<FWD>(a, d);
-    if (FWD ? (lane >= d) : (lane + d < 32)) a = compose(a, o);
-    const bool done = (FWD ? (lane < 2 * d) : (lane + 2 * d > 31)) || mat_norm(a) < kScanTol;
-    if (__all_sync(0xffffffffu, done)) break;
-  }
-  const Aff prev = shfl_aff<FWD>(a, 1);  // inclusive result of the previous chunk in sweep order
-  const bool first = FWD ? (lane == 0) : (lane == 31);
-  float c0 = 0.f, c1 = 0.f;  // state entering this warp
-  if (W > 1 || C > 1) {
-    if (FWD ? (lane == 31) : (lane == 0)) {
-      sh[2 * warp] = make_float4(a.a, a.b, a.c, a.d);
-      sh[2 * warp + 1] = make_float4(a.u, a.v, 0.f, 0.f);
-    }
-    __syncthreads();
-    if (C > 1) {
-      if (threadIdx.x == 0) {  // the CTA's total map, published for the other CTAs of the cluster
-        float4 tm = make_float4(1.f, 0.f, 0.f, 1.f), tb = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int k = 0; k < W; ++k) {
-          const int w = FWD ? k : W - 1 - k;
-          const Aff L{sh[2 * w].x, sh[2 * w].y, sh[2 * w].z, sh[2 * w].w, sh[2 * w + 1].x, sh[2 * w + 1].y};
-          const Aff t = compose(L, Aff{tm.x, tm.y, tm.z, tm.w, tb.x, tb.y});
-          tm = make_float4(t.a, t.b, t.c, t.d);
-          tb = make_float4(t.u, t.v, 0.f, 0.f);
-        }
-        sh[2 * W] = tm;
-        sh[2 * W + 1] = tb;
-      }
-      cg::this_cluster().sync();
-      if (FWD) {
-        for (int r = 0; r < rank; ++r) {
-          const float4* q = remote(sh, r);
-          apply(q[2 * W], q[2 * W + 1], c0, c1);
-        }
-      } else {
-        for (int r = C - 1; r > rank; --r) {
-          const float4* q = remote(sh, r);
-          apply(q[2 * W], q[2 * W + 1], c0, c1);
-        }
-      }
-    }
-    if (FWD) {
-      for (int w = 0; w < warp; ++w) apply(sh[2 * w], sh[2 * w + 1], c0, c1);
-    } else {
-      for (int w = W - 1; w > warp; --w) apply(sh[2 * w], sh[2 * w + 1], c0, c1);
-    }
-  }
-  if (first) {
-    e0 = c0;
-    e1 = c1;
-  } else {
-    e0 = fmaf(prev.a, c0, fmaf(prev.b, c1, prev.u));
-    e1 = fmaf(prev.c, c0, fmaf(prev.d, c1, prev.v));
-  }
 }
 
 // Maximum over the system's threads (CTA, or cluster).  sh: W + 1 slots.
@@ -298,67 +214,201 @@ __device__ __forceinline__ T system_max(T v, int lane, int warp, int W, int C, T
   return r;
 }
 
-// Shared scratch of one CTA (dynamic; W is a launch parameter).  Scan and
-// reduction slots rotate through four buffers, so one barrier per scan
-// separates every write from the reads of the same buffer, in this CTA and in
-// the other CTAs of a cluster.
+// Shared scratch of one CTA (dynamic; W is a launch parameter).  The scan plan
+// (win, pprev, wtot) is written once per launch; the per-scan slots (utot, red)
+// rotate through four buffers, so one barrier per scan separates every write
+// from the reads of the same buffer, in this CTA and in the other CTAs of a
+// cluster.
 struct SmemView {
-  float4* scan;  // [4][2W + 2]
-  float4* edge;  // [P][2]: first two rows (hi, lo), last two rows (hi, lo)
-  float* red;    // [4][W + 1]
-  int* redi;     // [W + 1]
+  float4* win;    // [2][kMaxLev][P]: window map of every Kogge-Stone level (dir 0 forward, 1 back)
+  float4* pprev;  // [2][P]: inclusive window map of the previous chunk in sweep order
+  float4* wtot;   // [2][W + 1]: map of each warp's chunks, then of the whole CTA
+  float4* edge;   // [P][2]: first two rows (hi, lo), last two rows (hi, lo)
+  float2* utot;   // [4][W + 1]: affine parts of the warp and CTA maps of one scan
+  float* red;     // [4][W + 1]
+  int* redi;      // [W + 1]
 };
 
 __host__ __device__ inline size_t smem_bytes(int W) {
-  return sizeof(float4) * (size_t)(4 * (2 * W + 2) + 2 * 32 * W) + sizeof(float) * (size_t)(4 * (W + 1)) +
-         sizeof(int) * (size_t)(W + 1);
+  const size_t P = 32 * (size_t)W;
+  return sizeof(float4) * (2 * kMaxLev * P + 2 * P + 2 * (W + 1) + 2 * P) + sizeof(float2) * 4 * (W + 1) +
+         sizeof(float) * 4 * (W + 1) + sizeof(int) * (W + 1);
 }
 
 __device__ __forceinline__ SmemView smem_view(unsigned char* base, int W) {
+  const int P = 32 * W;
   SmemView v;
-  v.scan = reinterpret_cast<float4*>(base);
-  v.edge = v.scan + 4 * (2 * W + 2);
-  v.red = reinterpret_cast<float*>(v.edge + 2 * 32 * W);
+  v.win = reinterpret_cast<float4*>(base);
+  v.pprev = v.win + 2 * kMaxLev * P;
+  v.wtot = v.pprev + 2 * P;
+  v.edge = v.wtot + 2 * (W + 1);
+  v.utot = reinterpret_cast<float2*>(v.edge + 2 * P);
+  v.red = reinterpret_cast<float*>(v.utot + 4 * (W + 1));
   v.redi = reinterpret_cast<int*>(v.red + 4 * (W + 1));
   return v;
 }
 
-// Per-thread factors of its L rows and the chunk maps, rebuilt from the stored
-// 1/alpha and beta (see the header comment).
-template <int L>
-struct ChunkFactors {
-  float A[L];  // 1/alpha_i
-  float B[L];  // beta_i / alpha_i
-  float E[L];  // epsilon_i / alpha_i
-  float G[L];  // gamma_i
-  float D[L];  // delta_i
-  float4 pf;   // forward map (row-major 2x2)
-  float4 pb;   // backward map
-};
-
 struct Ctx {
-  int lane, warp, W, C, rank;
+  int lane, warp, t, P, W, C, rank;
+  int nlev[2];  // Kogge-Stone levels of the forward and the back scan (warp-uniform)
   int phase;
 };
 
-// In place v <- A^{-1} v (FP32): forward L g = v, then back R x = g.
+// Scan plan of one sweep direction from this chunk's map m: the window map of
+// every Kogge-Stone level (the map of the 2^l chunks ending at this one, before
+// level l composes it further), the inclusive map of the previous chunk and
+// each warp's total map.  These depend on the factors only, so every scan of
+// the launch reuses them and composes just the affine parts.  The levels stop
+// once every window either reaches the warp's first chunk or composes to a
+// negligible map (later levels would only add terms multiplied by it).
+template <bool FWD>
+__device__ __forceinline__ int scan_setup(float4 m, const Ctx& cx, const SmemView& sm) {
+  const int dir = FWD ? 0 : 1;
+  float4* win = sm.win + dir * kMaxLev * cx.P;
+  int nlev = 0;
+#pragma unroll 1
+  for (int l = 0; l < kMaxLev; ++l) {
+    const int d = 1 << l;
+    const bool done = (FWD ? (cx.lane < d) : (cx.lane + d > 31)) || mnorm(m) < kScanTol;
+    if (__all_sync(0xffffffffu, done)) break;
+    win[l * cx.P + cx.t] = m;
+    const float4 o = shfl4<FWD>(m, d);
+    if (FWD ? (cx.lane >= d) : (cx.lane + d < 32)) m = mmul(m, o);
+    nlev = l + 1;
+  }
+  sm.pprev[dir * cx.P + cx.t] = shfl4<FWD>(m, 1);  // not read by the warp's first chunk
+  if (FWD ? (cx.lane == 31) : (cx.lane == 0)) sm.wtot[dir * (cx.W + 1) + cx.warp] = m;
+  return nlev;
+}
+
+// The CTA's total maps (cluster launches): the warp maps composed in sweep order.
+__device__ __forceinline__ void cta_total_maps(const Ctx& cx, const SmemView& sm) {
+  for (int dir = 0; dir < 2; ++dir) {
+    const float4* wt = sm.wtot + dir * (cx.W + 1);
+    float4 tm = make_float4(1.f, 0.f, 0.f, 1.f);
+    for (int k = 0; k < cx.W; ++k) tm = mmul(wt[dir == 0 ? k : cx.W - 1 - k], tm);
+    sm.wtot[dir * (cx.W + 1) + cx.W] = tm;
+  }
+}
+
+// State entering this thread's chunk for a sweep through the system's chunks
+// (FWD: increasing thread order, else decreasing), given the affine part
+// (u0, u1) of this chunk's map (its result from a zero entering state).  The
+// system is entered with state 0.
+template <bool FWD>
+__device__ __forceinline__ void scan_entry(float u0, float u1, Ctx& cx, const SmemView& sm, float& e0, float& e1) {
+  const int dir = FWD ? 0 : 1;
+  const float4* win = sm.win + dir * kMaxLev * cx.P;
+#pragma unroll 1
+  for (int l = 0; l < cx.nlev[dir]; ++l) {
+    const int d = 1 << l;
+    const float o0 = shfl<FWD>(u0, d), o1 = shfl<FWD>(u1, d);
+    if (FWD ? (cx.lane >= d) : (cx.lane + d < 32)) {
+      const float4 w = win[l * cx.P + cx.t];
+      u0 = fmaf(w.x, o0, fmaf(w.y, o1, u0));
+      u1 = fmaf(w.z, o0, fmaf(w.w, o1, u1));
+    }
+  }
+  const float p0 = shfl<FWD>(u0, 1), p1 = shfl<FWD>(u1, 1);  // inclusive result of the previous chunk
+  float c0 = 0.f, c1 = 0.f;                                  // state entering this warp
+  const int W = cx.W, C = cx.C;
+  if (W > 1 || C > 1) {
+    float2* ut = sm.utot + (cx.phase++ & 3) * (W + 1);
+    const float4* wt = sm.wtot + dir * (W + 1);
+    if (FWD ? (cx.lane == 31) : (cx.lane == 0)) ut[cx.warp] = make_float2(u0, u1);
+    __syncthreads();
+    if (C > 1) {
+      if (cx.t == 0) {  // the CTA's total affine part, published for the other CTAs of the cluster
+        float a0 = 0.f, a1 = 0.f;
+        for (int k = 0; k < W; ++k) {
+          const int w = FWD ? k : W - 1 - k;
+          apply(wt[w], ut[w], a0, a1);
+        }
+        ut[W] = make_float2(a0, a1);
+      }
+      cg::this_cluster().sync();
+      if (FWD) {
+        for (int r = 0; r < cx.rank; ++r) apply(remote(wt, r)[W], remote(ut, r)[W], c0, c1);
+      } else {
+        for (int r = C - 1; r > cx.rank; --r) apply(remote(wt, r)[W], remote(ut, r)[W], c0, c1);
+      }
+    }
+    if (FWD) {
+      for (int w = 0; w < cx.warp; ++w) apply(wt[w], ut[w], c0, c1);
+    } else {
+      for (int w = W - 1; w > cx.warp; --w) apply(wt[w], ut[w], c0, c1);
+    }
+  }
+  if (FWD ? (cx.lane == 0) : (cx.lane == 31)) {
+    e0 = c0;
+    e1 = c1;
+  } else {
+    const float4 m = sm.pprev[dir * cx.P + cx.t];
+    e0 = fmaf(m.x, c0, fmaf(m.y, c1, p0));
+    e1 = fmaf(m.z, c0, fmaf(m.w, c1, p1));
+  }
+}
+
+// The thread's factors: 1/alpha and beta of its L rows and beta of the next
+// chunk's first row.  The symmetric hyperdiffusion band gives the rest:
+// epsilon_i = sigma (i >= 2), gamma_i = beta_{i+1} / alpha_i, delta_i = sigma /
+// alpha_i (i + 2 < n); the walls need no special case because the system is
+// entered with state 0 at both ends and padding rows carry 1/alpha = 0.
 template <int L>
-__device__ __forceinline__ void cta_solve32(float (&v)[L], const ChunkFactors<L>& cf, Ctx& cx, const SmemView& sm) {
+struct Fac {
+  float A[L];   // 1/alpha_i
+  float Bt[L];  // beta_i
+  float bnext;  // beta of row t L + L
+  float sg;     // sigma (FP32)
+};
+
+// Forward map of the chunk on (g_{i-2}, g_{i-1}): g_i = A_i (v_i - beta_i g_{i-1} - sigma g_{i-2}).
+template <int L>
+__device__ __forceinline__ float4 fwd_chunk_map(const Fac<L>& fc) {
+  float4 F = make_float4(1.f, 0.f, 0.f, 1.f);
+#pragma unroll
+  for (int j = 0; j < L; ++j) {
+    const float n0 = -fc.A[j] * fmaf(fc.sg, F.x, fc.Bt[j] * F.z);
+    const float n1 = -fc.A[j] * fmaf(fc.sg, F.y, fc.Bt[j] * F.w);
+    F = make_float4(F.z, F.w, n0, n1);
+  }
+  return F;
+}
+
+// Back map of the chunk on (x_{i+1}, x_{i+2}): x_i = g_i - A_i (beta_{i+1} x_{i+1} + sigma x_{i+2}).
+template <int L>
+__device__ __forceinline__ float4 bwd_chunk_map(const Fac<L>& fc) {
+  float4 T = make_float4(1.f, 0.f, 0.f, 1.f);
+#pragma unroll
+  for (int j = L - 1; j >= 0; --j) {
+    const float bn = (j + 1 < L) ? fc.Bt[j + 1] : fc.bnext;
+    const float n0 = -fc.A[j] * fmaf(bn, T.x, fc.sg * T.z);
+    const float n1 = -fc.A[j] * fmaf(bn, T.y, fc.sg * T.w);
+    T = make_float4(n0, n1, T.x, T.y);
+  }
+  return T;
+}
+
+// In place v <- A^{-1} v (FP32): forward L g = v, then back R x = g (Sec. 2.4),
+// each as a zero-state pass over the chunk, a scan for the entering state, and
+// a second pass from it.
+template <int L>
+__device__ __forceinline__ void cta_solve32(float (&v)[L], const Fac<L>& fc, Ctx& cx, const SmemView& sm) {
+  const float sg = fc.sg;
   float p2 = 0.f, p1 = 0.f;
 #pragma unroll
   for (int j = 0; j < L; ++j) {
-    const float g = fmaf(-cf.B[j], p1, fmaf(-cf.E[j], p2, cf.A[j] * v[j]));
+    const float g = fc.A[j] * fmaf(-fc.Bt[j], p1, fmaf(-sg, p2, v[j]));
     p2 = p1;
     p1 = g;
   }
   float e0, e1;
-  scan_entry<true>(Aff{cf.pf.x, cf.pf.y, cf.pf.z, cf.pf.w, p2, p1}, cx.lane, cx.warp, cx.W, cx.C, cx.rank,
-                   sm.scan + (cx.phase++ & 3) * (2 * cx.W + 2), e0, e1);
+  scan_entry<true>(p2, p1, cx, sm, e0, e1);
   p2 = e0;
   p1 = e1;
 #pragma unroll
   for (int j = 0; j < L; ++j) {
-    const float g = fmaf(-cf.B[j], p1, fmaf(-cf.E[j], p2, cf.A[j] * v[j]));
+    const float g = fc.A[j] * fmaf(-fc.Bt[j], p1, fmaf(-sg, p2, v[j]));
     v[j] = g;
     p2 = p1;
     p1 = g;
@@ -366,66 +416,40 @@ __device__ __forceinline__ void cta_solve32(float (&v)[L], const ChunkFactors<L>
   float s1 = 0.f, s2 = 0.f;
 #pragma unroll
   for (int j = L - 1; j >= 0; --j) {
-    const float xv = fmaf(-cf.G[j], s1, fmaf(-cf.D[j], s2, v[j]));
+    const float bn = (j + 1 < L) ? fc.Bt[j + 1] : fc.bnext;
+    const float xv = fmaf(-fc.A[j], fmaf(bn, s1, sg * s2), v[j]);
     s2 = s1;
     s1 = xv;
   }
-  scan_entry<false>(Aff{cf.pb.x, cf.pb.y, cf.pb.z, cf.pb.w, s1, s2}, cx.lane, cx.warp, cx.W, cx.C, cx.rank,
-                    sm.scan + (cx.phase++ & 3) * (2 * cx.W + 2), e0, e1);
+  scan_entry<false>(s1, s2, cx, sm, e0, e1);
   s1 = e0;
   s2 = e1;
 #pragma unroll
   for (int j = L - 1; j >= 0; --j) {
-    const float xv = fmaf(-cf.G[j], s1, fmaf(-cf.D[j], s2, v[j]));
+    const float bn = (j + 1 < L) ? fc.Bt[j + 1] : fc.bnext;
+    const float xv = fmaf(-fc.A[j], fmaf(bn, s1, sg * s2), v[j]);
     v[j] = xv;
     s2 = s1;
     s1 = xv;
   }
 }
 
-// D4 x on a row next to a wall (general reflected weights) as an unevaluated
-// pair (S, Er).  Out of line: only the first two and last two rows of a system
-// take it, and keeping one copy keeps the unrolled kernel small.
-__device__ __noinline__ float2 d4_wall_row(int i, int n, float ah, float al, float bh, float bl, float ch, float cl,
-                                           float dh, float dl, float eh, float el) {
-  float w[5];
-  d4_weights_f(i, n, w);
-  const float xs[5] = {ah, bh, ch, dh, eh};
-  const float xls[5] = {al, bl, cl, dl, el};
-  float S = 0.f, Er = 0.f;
-#pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    float p, e, sm, e2;
-    two_prod(w[k], xs[k], p, e);
-    two_sum(S, p, sm, e2);
-    S = sm;
-    Er += e + e2 + w[k] * xls[k];
-  }
-  return make_float2(S, Er);
-}
 
 // r = f - (I + sigma D4) x for one row, in float-float (x = xh + xl, f = fh + fl,
-// sigma = sgh + sgl), rounded to FP32.  Rows away from the walls use the plain
-// [1, -4, 6, -4, 1] stencil.
+// sigma = sgh + sgl), rounded to FP32, with the [1, -4, 6, -4, 1] stencil on
+// the row's neighbours a, b, (c), d, e.  Rows next to a wall get their
+// reflected (ghost) neighbours from the caller.
 __device__ __forceinline__ float residual_row(float ah, float al, float bh, float bl, float ch, float cl, float dh,
-                                              float dl, float eh, float el, float fhj, float flj, float sgh, float sgl,
-                                              int i, int n) {
-  if (i >= n) return 0.f;  // padding row past the end of the system
-  float S, Er;
-  if (i >= 2 && i + 2 < n) {
-    float s1, e1, s2, e2, t, e3, p, e4;
-    two_sum(ah, eh, s1, e1);        // x_{i-2} + x_{i+2}
-    two_sum(bh, dh, s2, e2);        // x_{i-1} + x_{i+1}
-    two_sum(s1, -4.f * s2, t, e3);  // 4 s2 is exact
-    two_prod(6.f, ch, p, e4);
-    two_sum(t, p, S, Er);
-    const float low = fmaf(6.f, cl, fmaf(-4.f, bl + dl, al + el));
-    Er = Er + ((e1 - 4.f * e2) + (e3 + e4) + low);
-  } else {
-    const float2 q = d4_wall_row(i, n, ah, al, bh, bl, ch, cl, dh, dl, eh, el);
-    S = q.x;
-    Er = q.y;
-  }
+                                              float dl, float eh, float el, float fhj, float flj, float sgh,
+                                              float sgl) {
+  float s1, e1, s2, e2, t, e3, p, e4, S, Er;
+  two_sum(ah, eh, s1, e1);        // x_{i-2} + x_{i+2}
+  two_sum(bh, dh, s2, e2);        // x_{i-1} + x_{i+1}
+  two_sum(s1, -4.f * s2, t, e3);  // 4 s2 is exact
+  two_prod(6.f, ch, p, e4);
+  two_sum(t, p, S, Er);
+  const float low = fmaf(6.f, cl, fmaf(-4.f, bl + dl, al + el));
+  Er = Er + ((e1 - 4.f * e2) + (e3 + e4) + low);
   float yh, yl;
   fast_two_sum(S, Er, yh, yl);
   float Pp, Pe;  // sigma * y
@@ -434,16 +458,61 @@ __device__ __forceinline__ float residual_row(float ah, float al, float bh, floa
   float a1, a2, b1, b2;
   two_sum(fhj, -ch, a1, a2);
   two_sum(a1, -Pp, b1, b2);
-  const float low = ((a2 + b2) + (flj - cl)) - Pe;
-  return b1 + low;
+  const float lo2 = ((a2 + b2) + (flj - cl)) - Pe;
+  return b1 + lo2;
+}
+
+// Index of the row whose value the cell-centred no-flux walls reflect into
+// position g of an n-row system (-1 -> 0, -2 -> 1, n -> n-1, n+1 -> n-2, and
+// repeatedly for systems shorter than the stencil).
+__device__ __forceinline__ int reflect_row(int g, int n) {
+  while (g < 0 || g >= n) g = (g < 0) ? (-1 - g) : (2 * n - 1 - g);
+  return g;
+}
+
+// Replace the ghost entries of a neighbour window w[0 .. L+3] (rows tg L - 2 ..
+// tg L + L + 1 of the system) by the rows the walls reflect them to.  Only the
+// first chunk of a system and the chunks whose window reaches row n have ghosts, and
+// for n >= 4 each ghost is a copy of a real row two or fewer positions away
+// (w[k] for row -1 is row 0, for row n it is row n - 1, ...).  Systems with
+// n < 4 lie in one chunk and take the general reflection.
+template <int L>
+__device__ __forceinline__ void fill_ghosts(float (&w)[L + 4], int tg, int n) {
+  const int m = n - tg * L;  // row n sits at window position m + 2
+  if (n < 4) {
+    if (tg == 0) {
+      float src[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) src[k] = w[2 + k];
+#pragma unroll
+      for (int q = 0; q < L + 4; ++q) {
+        const int g = reflect_row(q - 2, n);  // 0 <= g < n <= 3
+        w[q] = (g == 0) ? src[0] : ((g == 1) ? src[1] : src[2]);
+      }
+    }
+    return;
+  }
+  if (tg == 0) {  // rows -2, -1 reflect to 1, 0
+    w[0] = w[3];
+    w[1] = w[2];
+  }
+  if (m >= 1 && m <= L + 1) {  // rows n, n + 1 (inside the window) reflect to n - 1, n - 2
+#pragma unroll
+    for (int q = 3; q < L + 4; ++q) {
+      if (q - 2 == m)
+        w[q] = w[q - 1];
+      else if (q - 2 == m + 1)
+        w[q] = w[q - 3];
+    }
+  }
 }
 
 // The neighbouring rows of this thread's chunk: the last two rows of the
 // previous chunk and the first two of the next, across warps through shared
 // memory and across CTAs of a cluster through distributed shared memory.
-template <int L>
-__device__ __forceinline__ void exchange_edges(float4 own_first, float4 own_last, int t, int P, const Ctx& cx,
-                                               const SmemView& sm, float4& prv, float4& nxt) {
+__device__ __forceinline__ void exchange_edges(float4 own_first, float4 own_last, const Ctx& cx, const SmemView& sm,
+                                               float4& prv, float4& nxt) {
+  const int t = cx.t, P = cx.P;
   sm.edge[2 * t] = own_first;
   sm.edge[2 * t + 1] = own_last;
   csync(cx.C);
@@ -458,24 +527,38 @@ __device__ __forceinline__ void exchange_edges(float4 own_first, float4 own_last
     nxt = (cx.rank + 1 < cx.C) ? remote(sm.edge, cx.rank + 1)[0] : zero;
 }
 
-template <int L>
+// XL0: every xl is zero (the first refinement step), so the low parts drop out.
+template <int L, bool XL0>
 __device__ __forceinline__ void residual_ff(const float (&fh)[L], const float (&fl)[L], const float (&xh)[L],
-                                            const float (&xl)[L], float (&r)[L], float sgh, float sgl, int n, int t,
-                                            int tg, int P, const Ctx& cx, const SmemView& sm) {
+                                            const float (&xl)[L], float (&r)[L], float sgh, float sgl, int n, int tg,
+                                            const Ctx& cx, const SmemView& sm) {
   float4 prv, nxt;
-  exchange_edges<L>(make_float4(xh[0], xh[1], xl[0], xl[1]), make_float4(xh[L - 2], xh[L - 1], xl[L - 2], xl[L - 1]),
-                    t, P, cx, sm, prv, nxt);
+  exchange_edges(make_float4(xh[0], xh[1], XL0 ? 0.f : xl[0], XL0 ? 0.f : xl[1]),
+                 make_float4(xh[L - 2], xh[L - 1], XL0 ? 0.f : xl[L - 2], XL0 ? 0.f : xl[L - 1]), cx, sm, prv, nxt);
+  // neighbour windows: rows tg L - 2 .. tg L + L + 1
+  float wh[L + 4], wl[L + 4];
+  wh[0] = prv.x;
+  wh[1] = prv.y;
+  wh[L + 2] = nxt.x;
+  wh[L + 3] = nxt.y;
+  wl[0] = prv.z;
+  wl[1] = prv.w;
+  wl[L + 2] = nxt.z;
+  wl[L + 3] = nxt.w;
 #pragma unroll
   for (int j = 0; j < L; ++j) {
-    const float ah = (j >= 2) ? xh[j - 2] : (j == 1 ? prv.y : prv.x);
-    const float al = (j >= 2) ? xl[j - 2] : (j == 1 ? prv.w : prv.z);
-    const float bh = (j >= 1) ? xh[j - 1] : prv.y;
-    const float bl = (j >= 1) ? xl[j - 1] : prv.w;
-    const float dh = (j + 1 < L) ? xh[j + 1] : nxt.x;
-    const float dl = (j + 1 < L) ? xl[j + 1] : nxt.z;
-    const float eh = (j + 2 < L) ? xh[j + 2] : (j + 1 < L ? nxt.x : nxt.y);
-    const float el = (j + 2 < L) ? xl[j + 2] : (j + 1 < L ? nxt.z : nxt.w);
-    r[j] = residual_row(ah, al, bh, bl, xh[j], xl[j], dh, dl, eh, el, fh[j], fl[j], sgh, sgl, tg * L + j, n);
+    wh[j + 2] = xh[j];
+    wl[j + 2] = XL0 ? 0.f : xl[j];
+  }
+  fill_ghosts<L>(wh, tg, n);
+  if (!XL0) fill_ghosts<L>(wl, tg, n);
+#pragma unroll
+  for (int j = 0; j < L; ++j) {
+    const float res = XL0 ? residual_row(wh[j], 0.f, wh[j + 1], 0.f, wh[j + 2], 0.f, wh[j + 3], 0.f, wh[j + 4], 0.f,
+                                         fh[j], fl[j], sgh, sgl)
+                          : residual_row(wh[j], wl[j], wh[j + 1], wl[j + 1], wh[j + 2], wl[j + 2], wh[j + 3],
+                                         wl[j + 3], wh[j + 4], wl[j + 4], fh[j], fl[j], sgh, sgl);
+    r[j] = (tg * L + j < n) ? res : 0.f;  // padding rows past the end of the system
   }
 }
 
@@ -484,11 +567,10 @@ __device__ __forceinline__ void residual_ff(const float (&fh)[L], const float (&
 // slots carry the neighbouring rows as double pairs.
 template <int L>
 __device__ __forceinline__ void residual_f64(const double (&fd)[L], const double (&xd)[L], float (&r)[L], double sg,
-                                             int n, int t, int tg, int P, const Ctx& cx, const SmemView& sm) {
+                                             int n, int tg, const Ctx& cx, const SmemView& sm) {
   float4 pf4, nf4;
   const double2 f2 = make_double2(xd[0], xd[1]), l2 = make_double2(xd[L - 2], xd[L - 1]);
-  exchange_edges<L>(*reinterpret_cast<const float4*>(&f2), *reinterpret_cast<const float4*>(&l2), t, P, cx, sm, pf4,
-                    nf4);
+  exchange_edges(*reinterpret_cast<const float4*>(&f2), *reinterpret_cast<const float4*>(&l2), cx, sm, pf4, nf4);
   const double2 prv = *reinterpret_cast<const double2*>(&pf4);
   const double2 nxt = *reinterpret_cast<const double2*>(&nf4);
 #pragma unroll
@@ -513,71 +595,29 @@ __device__ __forceinline__ void residual_f64(const double (&fd)[L], const double
   }
 }
 
-// epsilon_i = a_i of the hyperdiffusion band: sigma times the weight of x_{i-2}
-// in row i, which is 1 for 2 <= i < n (no wall reflection lands there) and 0
-// otherwise.
-__device__ __forceinline__ float eps_of_row(int i, int n, float sgf) { return (i >= 2 && i < n) ? sgf : 0.f; }
-
-// Load 1/alpha and beta of the thread's rows and rebuild epsilon/alpha,
-// beta/alpha, gamma, delta and the two chunk maps.  gq: the system's factor
-// block; PT threads per system; tg this thread's index in the system.
+// Load the thread's 1/alpha and beta (stored as float4 planes, see k_factor32).
+// gq: the system's factor block; PT threads per system; tg this thread's index.
 template <int L>
-__device__ __forceinline__ void load_chunk_factors(ChunkFactors<L>& cf, const float4* __restrict__ gq, int tg, int PT,
-                                                   int n, float sgf) {
-  float beta[L];
+__device__ __forceinline__ void load_factors(Fac<L>& fc, const float4* __restrict__ gq, int tg, int PT) {
 #pragma unroll
   for (int jq = 0; jq < L / 4; ++jq) {
     const float4 qa = __ldg(gq + (int64_t)(jq * 2 + 0) * PT + tg), qb = __ldg(gq + (int64_t)(jq * 2 + 1) * PT + tg);
-    cf.A[4 * jq] = qa.x; cf.A[4 * jq + 1] = qa.y; cf.A[4 * jq + 2] = qa.z; cf.A[4 * jq + 3] = qa.w;
-    beta[4 * jq] = qb.x; beta[4 * jq + 1] = qb.y; beta[4 * jq + 2] = qb.z; beta[4 * jq + 3] = qb.w;
+    fc.A[4 * jq] = qa.x; fc.A[4 * jq + 1] = qa.y; fc.A[4 * jq + 2] = qa.z; fc.A[4 * jq + 3] = qa.w;
+    fc.Bt[4 * jq] = qb.x; fc.Bt[4 * jq + 1] = qb.y; fc.Bt[4 * jq + 2] = qb.z; fc.Bt[4 * jq + 3] = qb.w;
   }
-  // beta of the first row of the next thread's chunk (row tg L + L)
-  const float beta_next = (tg + 1 < PT) ? __ldg(reinterpret_cast<const float*>(gq + (int64_t)PT + (tg + 1))) : 0.f;
-  const int i0 = tg * L;
-#pragma unroll
-  for (int j = 0; j < L; ++j) {
-    const int i = i0 + j;
-    const float bnext = (j + 1 < L) ? beta[j + 1] : beta_next;
-    cf.B[j] = beta[j] * cf.A[j];
-    cf.E[j] = eps_of_row(i, n, sgf) * cf.A[j];
-    cf.G[j] = bnext * cf.A[j];
-    cf.D[j] = eps_of_row(i + 2, n, sgf) * cf.A[j];
-  }
-  // forward map: acc <- M_j acc with M_j = [[0, 1], [-E_j, -B_j]]
-  float f00 = 1.f, f01 = 0.f, f10 = 0.f, f11 = 1.f;
-#pragma unroll
-  for (int j = 0; j < L; ++j) {
-    const float n10 = fmaf(-cf.E[j], f00, -cf.B[j] * f10);
-    const float n11 = fmaf(-cf.E[j], f01, -cf.B[j] * f11);
-    f00 = f10;
-    f01 = f11;
-    f10 = n10;
-    f11 = n11;
-  }
-  cf.pf = make_float4(f00, f01, f10, f11);
-  // backward map: acc <- acc B_j with B_j = [[-G_j, -D_j], [1, 0]], rows ascending
-  float t00 = 1.f, t01 = 0.f, t10 = 0.f, t11 = 1.f;
-#pragma unroll
-  for (int j = 0; j < L; ++j) {
-    const float n00 = fmaf(-t00, cf.G[j], t01), n01 = -t00 * cf.D[j];
-    const float n10 = fmaf(-t10, cf.G[j], t11), n11 = -t10 * cf.D[j];
-    t00 = n00;
-    t01 = n01;
-    t10 = n10;
-    t11 = n11;
-  }
-  cf.pb = make_float4(t00, t01, t10, t11);
+  fc.bnext = (tg + 1 < PT) ? __ldg(reinterpret_cast<const float*>(gq + (int64_t)PT + (tg + 1))) : 0.f;
 }
 
 // One CTA (or one cluster of C CTAs) per system: FP32 solve, then up to
 // max_refine refinement steps.  RES64 selects the FP64 residual (and FP64
-// accumulation of x) instead of float-float.  Register budget: 512 threads per
-// SM (at most 128 registers per thread), so up to four 128-thread systems share
-// an SM and hide each other's barriers.
+// accumulation of x) instead of float-float.
+// Refinement stops early once the error left after a step, estimated as the
+// step's correction times its size relative to x (the contraction of the
+// iteration), is below 2^-tol_log2 |x|: (max|dx| / max|x|)^2 <= 2^-tol_log2.
 // WT > 0 fixes the warp count at compile time (the common one-CTA shapes);
 // WT = 0 takes it from `Wrt`.  CL enables the cluster paths (C = Crt CTAs per
-// system), otherwise C = 1.
-constexpr int min_blocks(int L, int WT) { return WT > 0 ? ((L <= 8 && 16 / WT > 0) ? 16 / WT : 1) : 1; }
+// system), otherwise C = 1.  Register budget: 5 CTAs of 4 warps per SM.
+constexpr int min_blocks(int L, int WT) { return WT > 0 ? ((L <= 8 && 20 / WT > 0) ? 20 / WT : 1) : 1; }
 
 template <int L, int WT, bool CL, bool RES64>
 __global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, min_blocks(L, WT))
@@ -593,6 +633,8 @@ __global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, min_blocks(L, WT))
   Ctx cx;
   cx.lane = t & 31;
   cx.warp = t >> 5;
+  cx.t = t;
+  cx.P = P;
   cx.W = W;
   cx.C = C;
   cx.rank = (C > 1) ? (int)cg::this_cluster().block_rank() : 0;
@@ -605,8 +647,9 @@ __global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, min_blocks(L, WT))
   // ---- loads: factors, right-hand side (all coalesced) ----
   const float2 sgp = __ldg(T.sig2 + ms);  // sigma as an FP32 pair, split at factorisation time
   const float sgh = sgp.x, sgl = sgp.y;
-  ChunkFactors<L> cf;
-  load_chunk_factors<L>(cf, reinterpret_cast<const float4*>(T.fac) + T.foff[ms], tg, PT, n, sgh);
+  Fac<L> fc;
+  fc.sg = sgh;
+  load_factors<L>(fc, reinterpret_cast<const float4*>(T.fac) + T.foff[ms], tg, PT);
   const double* fs = f + T.off[s];
   const int i0 = tg * L;
   double fv[L];
@@ -622,6 +665,10 @@ __global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, min_blocks(L, WT))
     for (int j = 0; j < L; ++j) fv[j] = (i0 + j < n) ? fs[i0 + j] : 0.0;
   }
 
+  // ---- scan plan of both sweeps (factors only) ----
+  cx.nlev[0] = scan_setup<true>(fwd_chunk_map<L>(fc), cx, sm);
+  cx.nlev[1] = scan_setup<false>(bwd_chunk_map<L>(fc), cx, sm);
+
   // ---- per-system power-of-two scale: the largest |f| maps just below 1 ----
   int emax = 0;
 #pragma unroll
@@ -629,7 +676,9 @@ __global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, min_blocks(L, WT))
     const unsigned top = (unsigned)((unsigned long long)__double_as_longlong(fv[j]) >> 32);
     emax = max(emax, (int)((top >> 20) & 0x7ffu));
   }
+  // (the barrier inside also orders the scan plan's writes before any read)
   emax = system_max<int>(emax, cx.lane, cx.warp, W, C, sm.redi);
+  if (C > 1 && t == 0) cta_total_maps(cx, sm);  // read by the other CTAs after the first scan's cluster barrier
   const int kshift = emax - 1022;
 
   float v[L], xh[L], xl[L];
@@ -651,8 +700,8 @@ __global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, min_blocks(L, WT))
     for (int j = 0; j < L; ++j) fd[j] = fv[j] * scale;
 #pragma unroll 1
     for (int it = 0; it <= max_refine; ++it) {
-      if (it > 0) residual_f64<L>(fd, xd, v, sg, n, t, tg, P, cx, sm);
-      cta_solve32<L>(v, cf, cx, sm);
+      if (it > 0) residual_f64<L>(fd, xd, v, sg, n, tg, cx, sm);
+      cta_solve32<L>(v, fc, cx, sm);
       if (it == 0) {
 #pragma unroll
         for (int j = 0; j < L; ++j) xd[j] = (double)v[j];
@@ -667,13 +716,11 @@ __global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, min_blocks(L, WT))
       }
       steps = it;
       if (it < max_refine) {
-        float* rs = sm.red + (cx.phase & 3) * (W + 1);
-        ++cx.phase;
+        float* rs = sm.red + (cx.phase++ & 3) * (W + 1);
         dmax = system_max<float>(dmax, cx.lane, cx.warp, W, C, rs);
-        float* rs2 = sm.red + (cx.phase & 3) * (W + 1);
-        ++cx.phase;
+        float* rs2 = sm.red + (cx.phase++ & 3) * (W + 1);
         xmax = system_max<float>(xmax, cx.lane, cx.warp, W, C, rs2);
-        if (dmax <= tol * xmax) break;
+        if (dmax * dmax <= tol * xmax * xmax) break;
         if (it > 1 && dmax > 0.5f * prev) {
           stalled = true;
           break;
@@ -686,11 +733,14 @@ __global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, min_blocks(L, WT))
   } else {
     // it = 0 solves for f (its FP32 part); every later pass solves for the
     // float-float residual of the current x and adds the correction.  One
-    // solve call site keeps the unrolled kernel compact.
+    // solve call site keeps the unrolled kernel compact (instruction cache).
 #pragma unroll 1
     for (int it = 0; it <= max_refine; ++it) {
-      if (it > 0) residual_ff<L>(fh, fl, xh, xl, v, sgh, sgl, n, t, tg, P, cx, sm);
-      cta_solve32<L>(v, cf, cx, sm);
+      if (it == 1)
+        residual_ff<L, true>(fh, fl, xh, xl, v, sgh, sgl, n, tg, cx, sm);  // x is still one float per row
+      else if (it > 1)
+        residual_ff<L, false>(fh, fl, xh, xl, v, sgh, sgl, n, tg, cx, sm);
+      cta_solve32<L>(v, fc, cx, sm);
       if (it == 0) {
 #pragma unroll
         for (int j = 0; j < L; ++j) {
@@ -711,13 +761,11 @@ __global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, min_blocks(L, WT))
       }
       steps = it;
       if (it < max_refine) {  // the stopping tests only matter if another step may follow
-        float* rs = sm.red + (cx.phase & 3) * (W + 1);
-        ++cx.phase;
+        float* rs = sm.red + (cx.phase++ & 3) * (W + 1);
         dmax = system_max<float>(dmax, cx.lane, cx.warp, W, C, rs);
-        float* rs2 = sm.red + (cx.phase & 3) * (W + 1);
-        ++cx.phase;
+        float* rs2 = sm.red + (cx.phase++ & 3) * (W + 1);
         xmax = system_max<float>(xmax, cx.lane, cx.warp, W, C, rs2);
-        if (dmax <= tol * xmax) break;
+        if (dmax * dmax <= tol * xmax * xmax) break;
         if (it > 1 && dmax > 0.5f * prev) {
           stalled = true;
           break;
@@ -726,7 +774,7 @@ __global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, min_blocks(L, WT))
       }
     }
 #pragma unroll
-    for (int j = 0; j < L; ++j) fv[j] = f2d_shift(xh[j], kshift) + f2d_shift(xl[j], kshift);
+    for (int j = 0; j < L; ++j) fv[j] = ff_to_double_shift(xh[j], xl[j], kshift);
   }
   if (t == 0 && cx.rank == 0) {
     if (steps > 0) atomicMax(T.info + 1, (unsigned long long)steps);
@@ -765,7 +813,7 @@ __global__ void k_factor32(F32Tables T, int64_t nsys, const int32_t* __restrict_
   bool failed = false;
   const int rows = PT * L;
   for (int i = 0; i < rows; ++i) {
-    float ainv = 1.f, bt = 0.f;
+    float ainv = 0.f, bt = 0.f;  // padding rows and rows after a failed pivot: g = x = 0
     if (i < n && !failed) {
       float w[5];
       d4_weights_f(i, n, w);
@@ -803,6 +851,11 @@ cudaError_t launch_bucket(const F32Tables& T, const int32_t* sys, const F32Bucke
                           double* x, int max_refine, int tol_log2, cudaStream_t st) {
   const int vec = ((((uintptr_t)f) | ((uintptr_t)x)) % 16 == 0) && b.even_offsets;
   const size_t smem = smem_bytes(b.W);
+  if (smem > 48 * 1024) {  // above the default dynamic shared memory limit (a function attribute, not a stream op)
+    const cudaError_t e = cudaFuncSetAttribute(k_solve32r<L, WT, CL, RES64>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(b.count * b.C));
   cfg.blockDim = dim3(32 * b.W);

@@ -30,13 +30,17 @@ struct DevPlan {
   unsigned long long* info;
 };
 
-// FP64 factor records, per group of 32 systems and row r (record row R = goff[k] + r):
-//   fwd[(R*3 + p)*32 + lane], p = 0: 1/alpha, 1: beta/alpha, 2: epsilon/alpha
-//   bwd[(R*2 + p)*32 + lane], p = 0: gamma,   1: delta
-// For a shared matrix: fwd[r*3 + p], bwd[r*2 + p].
+// FP64 factor records, per group of 32 systems and row r (record row R = goff[k] + r),
+// stored in row pairs (see core64.cu):
+//   general band:   fwd planes p = 0: 1/alpha, 1: beta/alpha, 2: epsilon/alpha
+//   hyperdiffusion: fwd planes p = 0: 1/alpha, 1: beta (epsilon_i = sigma_s for every
+//                   row i >= 2, so it is not stored; padding rows have 1/alpha = 0)
+//   bwd planes p = 0: gamma, 1: delta
+// For a shared matrix (always the general form): fwd[r*3 + p], bwd[r*2 + p].
 struct F64Factors {
   double* fwd;
   double* bwd;
+  const double* sig;  // per-system sigma of hyperdiffusion records, nullptr for the general form
 };
 
 // FP32 storage of the symmetric hyperdiffusion factors, one block per system s

@@ -40,7 +40,7 @@ struct pent_plan {
   int residual = PENT_RESIDUAL_FF;
   int block_warps = 2;
   int unroll = 4;
-  int tol_log2 = 40;
+  int tol_log2 = 43;
   // thread-per-system grouping (systems sorted by length, longest first)
   std::vector<int32_t> perm;  // [ngroups*32], -1 for padding lanes
   int64_t ngroups = 0;
@@ -91,7 +91,10 @@ struct pent_plan {
     P.info = at<unsigned long long>(r_info);
     return P;
   }
-  F64Factors f64() const { return F64Factors{at<double>(r_fwd), at<double>(r_bwd)}; }
+  // Hyperdiffusion factors of per-system matrices use the constant-epsilon records.
+  F64Factors f64() const {
+    return F64Factors{at<double>(r_fwd), at<double>(r_bwd), (factored == 2 && !shared) ? at<double>(r_sigma) : nullptr};
+  }
   F32Tables f32() const {
     F32Tables T;
     T.n = at<int32_t>(r_n);
@@ -428,8 +431,11 @@ static pent_status factor_common(pent_plan* p, const double* a, const double* b,
   }
   const double* sg = sigma ? p->at<double>(p->r_sigma) : nullptr;
   cudaError_t err;
-  if (p->precision == PENT_F64)
-    err = launch_factor64(P, a, b, c, d, e, sg, p->f64(), p->stream);
+  if (p->precision == PENT_F64) {
+    F64Factors F = p->f64();
+    F.sig = (sigma && !p->shared) ? sg : nullptr;
+    err = launch_factor64(P, a, b, c, d, e, sg, F, p->stream);
+  }
   else
     err = launch_factor32(p->f32(), p->at<int32_t>(p->r_shape), p->shared ? 1 : p->batch, sg, p->stream);
   if (err != cudaSuccess) return PENT_ECUDA;
