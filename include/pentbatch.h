@@ -75,7 +75,8 @@ typedef struct pent_plan pent_plan;
  *                 benchmark case, Sec. 3): the band/sigma arguments then
  *                 describe a single system and n_per_system must be NULL.
  *   precision:    PENT_F64 or PENT_F32_REFINE.
- *   tune_cache:   path of a JSON autotuning cache to read (may be NULL).
+ *   tune_cache:   path of an autotuning cache (text, format below) or NULL for
+ *                 the built-in choices.
  * The plan is a host object; it records shapes and choices only.
  * Errors: PENT_EINVAL for batch < 1, a row count < 1, shared_matrix with
  * uneven sizes, or a NULL `plan`.
@@ -96,6 +97,22 @@ size_t pent_plan_workspace_bytes(const pent_plan* plan);
 pent_status pent_plan_bind(pent_plan* plan, void* d_workspace, void* cuda_stream);
 
 /*
+ * Autotuning cache.  A text file of rules, one per line; '#' starts a comment.
+ *   f32 <n_lo> <n_hi> <rows_per_thread> <threads_per_system>
+ *   f64 <n_lo> <n_hi> <unroll> <block_warps>
+ * A PENT_F32_REFINE plan solves every system of n rows, n_lo <= n <= n_hi, with
+ * the given CTA shape (rows per thread 4 or 8; threads per system as for
+ * PENT_OPT_THREADS_PER_SYSTEM, their product covering n, or 0 for the fewest
+ * threads that cover n with that many rows each).  A PENT_F64 plan
+ * launches its groups of 32 systems (sorted by length) in runs of equal
+ * settings, each group taking the rule of its longest system.  The first
+ * matching rule of the plan's precision wins; systems no rule covers keep the
+ * built-in choice.  pent_plan_create returns PENT_EINVAL for a cache that
+ * cannot be read or has a malformed or impossible rule.  The cache is written
+ * by the Python module paper_1807_07382_gb300.autotune, which times the
+ * candidates on the GPU at hand.  Options set later with
+ * pent_plan_set_option take precedence over the cache.
+ *
  * Tuning options (keys below); values are integers.  Unknown keys or values
  * return PENT_EINVAL.  PENT_OPT_THREADS_PER_SYSTEM changes the factor layout
  * and the workspace size, so it is accepted only before pent_plan_bind (query
@@ -109,10 +126,20 @@ enum {
   PENT_OPT_BLOCK_WARPS = 3,        /* PENT_F64: warps per CTA of the solve kernels (1..8) */
   PENT_OPT_REFINE_TOL_LOG2 = 4,    /* refinement stops once the estimated remaining error, (max|dx| / max|x|)^2
                                       relative to max|x| after a step with correction dx, is <= 2^-tol (default 43) */
-  PENT_OPT_UNROLL = 5              /* PENT_F64: rows loaded ahead of the arithmetic: 2, 4 or 8 (default 4) */
+  PENT_OPT_UNROLL = 5,             /* PENT_F64: rows loaded ahead of the arithmetic: 2, 4 or 8 (default 4) */
+  PENT_OPT_ROWS_PER_THREAD = 6     /* PENT_F32_REFINE: rows per thread, 4 or 8, or 0 for the automatic choice
+                                      (before pent_plan_bind, like PENT_OPT_THREADS_PER_SYSTEM) */
 };
 pent_status pent_plan_set_option(pent_plan* plan, int key, int64_t value);
 pent_status pent_plan_get_option(const pent_plan* plan, int key, int64_t* value);
+
+/*
+ * The settings that solve system `system` (0 <= system < batch), as chosen by
+ * options, the tune cache or the built-in rules: for PENT_F32_REFINE
+ * *a = rows per thread and *b = threads per system; for PENT_F64 *a = unroll
+ * and *b = warps per CTA of the launch that covers the system.
+ */
+pent_status pent_plan_system_config(const pent_plan* plan, int64_t system, int64_t* a, int64_t* b);
 
 /*
  * Factor every system's band (Sec. 2.4, factorisation steps 1-14) into the

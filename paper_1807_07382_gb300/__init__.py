@@ -17,7 +17,8 @@ from typing import Optional, Sequence
 
 from . import _lib
 from ._lib import (PENT_ENOCONV, PENT_ESINGULAR, PENT_F32_REFINE, PENT_F64, PENT_OK, PENT_OPT_BLOCK_WARPS,
-                   PENT_OPT_REFINE_TOL_LOG2, PENT_OPT_RESIDUAL, PENT_OPT_THREADS_PER_SYSTEM, PENT_OPT_UNROLL, PENT_RESIDUAL_F64,
+                   PENT_OPT_REFINE_TOL_LOG2, PENT_OPT_RESIDUAL, PENT_OPT_ROWS_PER_THREAD, PENT_OPT_THREADS_PER_SYSTEM,
+                   PENT_OPT_UNROLL, PENT_RESIDUAL_F64,
                    PENT_RESIDUAL_FF, PentError, check)
 
 __all__ = ["Plan", "PentError", "PENT_F64", "PENT_F32_REFINE", "PENT_RESIDUAL_FF", "PENT_RESIDUAL_F64",
@@ -62,7 +63,7 @@ class Plan:
     """
 
     def __init__(self, n, batch: Optional[int] = None, shared: bool = False, precision: int = PENT_F64,
-                 device=None, stream=None, tune_cache: Optional[str] = None):
+                 device=None, stream=None, tune_cache: Optional[str] = None, options: Optional[dict] = None):
         torch = _torch()
         L = _lib.load()
         self._L = L
@@ -86,6 +87,8 @@ class Plan:
         self.rows = sum(self.n)
         check(L.pent_plan_create(ctypes.byref(self._h), self.batch, nptr, n_uniform, int(self.shared),
                                  self.precision, tune_cache.encode() if tune_cache else None), "pent_plan_create")
+        for key, value in (options or {}).items():  # layout options must precede pent_plan_bind
+            check(L.pent_plan_set_option(self._h, int(key), int(value)), "pent_plan_set_option")
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         nbytes = int(L.pent_plan_workspace_bytes(self._h))
         self.workspace = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
@@ -121,6 +124,13 @@ class Plan:
         v = ctypes.c_int64()
         check(self._L.pent_plan_get_option(self._h, key, ctypes.byref(v)), "pent_plan_get_option")
         return int(v.value)
+
+    def system_config(self, system: int) -> tuple:
+        """(rows per thread, threads per system) for FP32+refine, (unroll, warps per CTA) for FP64."""
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        check(self._L.pent_plan_system_config(self._h, int(system), ctypes.byref(a), ctypes.byref(b)),
+              "pent_plan_system_config")
+        return int(a.value), int(b.value)
 
     # -- factorisation
     def factor(self, a, b, c, d, e):

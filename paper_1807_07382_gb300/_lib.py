@@ -28,6 +28,7 @@ PENT_OPT_RESIDUAL = 2
 PENT_OPT_BLOCK_WARPS = 3
 PENT_OPT_REFINE_TOL_LOG2 = 4
 PENT_OPT_UNROLL = 5
+PENT_OPT_ROWS_PER_THREAD = 6
 
 # every symbol the header declares, with (restype, argtypes)
 _vp = ctypes.c_void_p
@@ -43,6 +44,7 @@ SIGNATURES = {
     "pent_plan_bind": (_int, [_vp, _vp, _vp]),
     "pent_plan_set_option": (_int, [_vp, _int, _i64]),
     "pent_plan_get_option": (_int, [_vp, _int, _i64p]),
+    "pent_plan_system_config": (_int, [_vp, _i64, _i64p, _i64p]),
     "pent_factor_batch": (_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "pent_factor_hyperdiff": (_int, [_vp, _vp]),
     "pent_solve_batch": (_int, [_vp, _vp, _vp, _int]),

@@ -178,9 +178,9 @@ __device__ __forceinline__ int64_t scr_idx(const Lane& L, int64_t r, int lane) {
 // lane keeps several independent memory requests in flight.
 template <bool SHARED, int U>
 __global__ void __launch_bounds__(256) k_solve64(DevPlan P, F64Factors F, const double* f, double* x,
-                                                 double* __restrict__ gscr) {
-  const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kWarp;
-  if (k >= P.ngroups) return;
+                                                 double* __restrict__ gscr, int64_t kbeg, int64_t kend) {
+  const int64_t k = kbeg + (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kWarp;
+  if (k >= kend) return;
   const int lane = threadIdx.x & (kWarp - 1);
   const Lane L = lane_setup<SHARED>(P, k, lane);
   const double* __restrict__ fwd = F.fwd;
@@ -269,9 +269,9 @@ __global__ void __launch_bounds__(256) k_solve64(DevPlan P, F64Factors F, const 
 // per row) less to read than the general form, for the same FP64 operations.
 template <int U2, bool HYP>
 __global__ void __launch_bounds__(128) k_solve64_pair(DevPlan P, F64Factors F, const double* f, double* x,
-                                                      double* __restrict__ gscr) {
-  const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kWarp;
-  if (k >= P.ngroups) return;
+                                                      double* __restrict__ gscr, int64_t kbeg, int64_t kend) {
+  const int64_t k = kbeg + (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kWarp;
+  if (k >= kend) return;
   const int lane = threadIdx.x & (kWarp - 1);
   const Lane L = lane_setup<false>(P, k, lane);
   const double2* __restrict__ fwd = reinterpret_cast<const double2*>(F.fwd);
@@ -473,13 +473,14 @@ cudaError_t launch_factor64(const DevPlan& P, const double* a, const double* b, 
 }
 
 cudaError_t launch_solve64(const DevPlan& P, F64Factors F, const double* f, double* x, double* gscr, int block_warps,
-                           int unroll, cudaStream_t st) {
+                           int unroll, int64_t g0, int64_t g1, cudaStream_t st) {
+  if (g1 <= g0) return cudaSuccess;
   const int block = kWarp * block_warps;
-  const int grid = grid_for(P.ngroups * kWarp, block);
+  const int grid = grid_for((g1 - g0) * kWarp, block);
   if (P.shared) {
 #define PENT_U(U_)                                                   \
   if (unroll == U_) {                                                \
-    k_solve64<true, U_><<<grid, block, 0, st>>>(P, F, f, x, gscr);   \
+    k_solve64<true, U_><<<grid, block, 0, st>>>(P, F, f, x, gscr, g0, g1); \
     return cudaGetLastError();                                       \
   }
     PENT_U(2) PENT_U(4) PENT_U(8)
@@ -491,9 +492,9 @@ cudaError_t launch_solve64(const DevPlan& P, F64Factors F, const double* f, doub
 #define PENT_U2(U_, U2_)                                                       \
   if (unroll == U_) {                                                          \
     if (hyp)                                                                   \
-      k_solve64_pair<U2_, true><<<grid, block, 0, st>>>(P, F, f, x, gscr);    \
-    else                                                                       \
-      k_solve64_pair<U2_, false><<<grid, block, 0, st>>>(P, F, f, x, gscr);   \
+      k_solve64_pair<U2_, true><<<grid, block, 0, st>>>(P, F, f, x, gscr, g0, g1);  \
+    else                                                                             \
+      k_solve64_pair<U2_, false><<<grid, block, 0, st>>>(P, F, f, x, gscr, g0, g1); \
     return cudaGetLastError();                                                 \
   }
   PENT_U2(2, 1) PENT_U2(4, 2) PENT_U2(8, 4)

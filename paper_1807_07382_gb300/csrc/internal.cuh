@@ -70,8 +70,9 @@ cudaError_t launch_factor64(const DevPlan& P, const double* a, const double* b, 
                             const double* e, const double* sigma, F64Factors F, cudaStream_t st);
 cudaError_t launch_factor32(const F32Tables& T, const int32_t* shape, int64_t nsys, const double* sigma,
                             cudaStream_t st);
+// Groups [g0, g1) of the plan (all of them for a shared matrix: g0 = 0, g1 = ngroups).
 cudaError_t launch_solve64(const DevPlan& P, F64Factors F, const double* f, double* x, double* gscr, int block_warps,
-                           int unroll, cudaStream_t st);
+                           int unroll, int64_t g0, int64_t g1, cudaStream_t st);
 cudaError_t launch_adjoint64(const DevPlan& P, F64Factors F, const double* f, double* x, double* gscr,
                              int block_warps, cudaStream_t st);
 cudaError_t launch_solve32r(const F32Tables& T, const int32_t* sys, const F32Bucket& b, int shared, const double* f,

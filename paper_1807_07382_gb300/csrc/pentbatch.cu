@@ -4,7 +4,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <fstream>
 #include <map>
+#include <sstream>
+#include <string>
 #include <numeric>
 #include <tuple>
 #include <vector>
@@ -41,11 +44,27 @@ struct pent_plan {
   int block_warps = 2;
   int unroll = 4;
   int tol_log2 = 43;
+  // tuning: rules from the tune cache, option overrides, FP64 launch runs
+  struct Rule {
+    int prec;
+    int64_t lo, hi;
+    int a, b;  // f32: rows per thread, threads per system; f64: unroll, block warps
+  };
+  std::vector<Rule> rules;
+  int64_t rpt_override = 0;   // PENT_OPT_ROWS_PER_THREAD (0: not set)
+  bool f64_explicit = false;  // PENT_OPT_UNROLL / PENT_OPT_BLOCK_WARPS set: one launch for all groups
+  struct F64Run {
+    int64_t g0, g1;  // groups [g0, g1)
+    int unroll, bw;
+  };
+  std::vector<F64Run> runs;
+  int64_t cfg_version = 0;  // bumped whenever launch settings change (graph cache key)
   // thread-per-system grouping (systems sorted by length, longest first)
   std::vector<int32_t> perm;  // [ngroups*32], -1 for padding lanes
   int64_t ngroups = 0;
   std::vector<int64_t> goff;
   std::vector<int32_t> glen;
+  std::vector<int64_t> gmax;  // longest system of each group (unpadded)
   int64_t grows = 0;  // record rows over all groups
   // FP32 (refined) solve: per factored system a CTA shape (L rows per thread,
   // W warps per CTA, C CTAs per cluster), grouped into buckets of equal shape
@@ -70,7 +89,7 @@ struct pent_plan {
   cudaStream_t stream = nullptr;
   bool bound = false;
   int factored = 0;  // 0 none, 1 general band, 2 hyperdiffusion
-  // graph cache: (x, nsteps, max_refine) -> exec
+  // graph cache: (x, nsteps, max_refine, settings version) -> exec
   std::map<std::tuple<const void*, int64_t, int, int64_t>, cudaGraphExec_t> graphs;
 
   template <class T>
@@ -124,22 +143,28 @@ pent_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PENT_OK : PEN
 
 using Shape = pent_plan::Shape;
 
-// Default FP32 CTA shape for n rows: 8 rows per thread (4 for the shortest
-// systems), the fewest warps that cover n in one CTA of at most 16 warps, and
-// beyond 4096 rows a cluster of C CTAs (at most 8) with as few warps each as
-// cover n.  Padding is below 256 rows per system.
-bool default_shape(int64_t n, Shape* sh) {
-  if (n <= 128) { *sh = Shape{4, 1, 1}; return true; }
-  const int64_t t8 = (n + 7) / 8;  // threads needed at 8 rows each
-  if (t8 <= 512) { *sh = Shape{8, (int)((t8 + 31) / 32), 1}; return true; }
-  const int64_t C = (t8 + 511) / 512;
+// FP32 CTA shape for n rows with L rows per thread: the fewest warps that cover
+// n in one CTA of at most 16 warps, and beyond that a cluster of C CTAs (at
+// most 8) with as few warps each as cover n.
+bool shape_with_rows(int64_t n, int L, Shape* sh) {
+  const int64_t t = (n + L - 1) / L;  // threads needed
+  if (t <= 512) { *sh = Shape{L, (int)((t + 31) / 32), 1}; return true; }
+  const int64_t C = (t + 511) / 512;
   if (C > 8) return false;
-  *sh = Shape{8, (int)((t8 + 32 * C - 1) / (32 * C)), (int)C};
+  *sh = Shape{L, (int)((t + 32 * C - 1) / (32 * C)), (int)C};
   return true;
 }
 
-// Shape for a requested number of threads per system (32 W C, W <= 16).
-bool shape_for_threads(int64_t n, int64_t tps, Shape* sh) {
+// Built-in FP32 shape: 8 rows per thread (4 for the shortest systems).
+// Padding is below 256 rows per system.
+bool default_shape(int64_t n, Shape* sh) {
+  if (n <= 128) { *sh = Shape{4, 1, 1}; return true; }
+  return shape_with_rows(n, 8, sh);
+}
+
+// Shape for a requested number of threads per system (32 W, W <= 16, or
+// 512 C, C <= 8) and rows per thread (4 or 8; 0: the fewer that covers n).
+bool shape_for_threads(int64_t n, int64_t tps, int rpt, Shape* sh) {
   if (tps < 32 || tps % 32) return false;
   int C = 1;
   if (tps > 512) {
@@ -148,9 +173,87 @@ bool shape_for_threads(int64_t n, int64_t tps, Shape* sh) {
     if (C > 8) return false;
   }
   const int W = (int)(tps / (32 * C));
-  for (int L : {4, 8})
+  if (W > 16) return false;
+  for (int L : {4, 8}) {
+    if (rpt && L != rpt) continue;
     if ((int64_t)32 * W * C * L >= n) { *sh = Shape{L, W, C}; return true; }
+  }
   return false;
+}
+
+const pent_plan::Rule* find_rule(const pent_plan* p, int prec, int64_t n) {
+  for (const auto& r : p->rules)
+    if (r.prec == prec && r.lo <= n && n <= r.hi) return &r;
+  return nullptr;
+}
+
+// Shape of an n-row system: options, then the tune cache, then the built-in rule.
+bool choose_shape(const pent_plan* p, int64_t n, Shape* sh) {
+  if (p->tps_override) return shape_for_threads(n, p->tps_override, (int)p->rpt_override, sh);
+  if (p->rpt_override) return shape_with_rows(n, (int)p->rpt_override, sh);
+  if (const pent_plan::Rule* r = find_rule(p, PENT_F32_REFINE, n))
+    return r->b ? shape_for_threads(n, r->b, r->a, sh) : shape_with_rows(n, r->a, sh);
+  return default_shape(n, sh);
+}
+
+// Read a tune cache (format in pentbatch.h).  False for an unreadable file or
+// a malformed line.
+bool parse_tune_cache(const char* path, std::vector<pent_plan::Rule>* out) {
+  std::ifstream in(path);
+  if (!in) return false;
+  std::string line;
+  while (std::getline(in, line)) {
+    const size_t h = line.find('#');
+    if (h != std::string::npos) line.resize(h);
+    std::istringstream ls(line);
+    std::string kind;
+    if (!(ls >> kind)) continue;  // blank or comment
+    pent_plan::Rule r{};
+    long long lo, hi, a, b;
+    if (!(ls >> lo >> hi >> a >> b)) return false;
+    std::string extra;
+    if (ls >> extra) return false;
+    if (lo < 1 || hi < lo) return false;
+    if (kind == "f32") {
+      if ((a != 4 && a != 8) || b < 0 || (b && (b % 32 || b > 4096))) return false;
+      r.prec = PENT_F32_REFINE;
+    } else if (kind == "f64") {
+      if ((a != 2 && a != 4 && a != 8) || b < 1 || b > 8) return false;
+      r.prec = PENT_F64;
+    } else {
+      return false;
+    }
+    r.lo = lo;
+    r.hi = hi;
+    r.a = (int)a;
+    r.b = (int)b;
+    out->push_back(r);
+  }
+  return true;
+}
+
+// FP64 launches: groups (longest first) in runs of equal unroll / block warps.
+void build_f64_runs(pent_plan* p) {
+  p->runs.clear();
+  auto knobs = [&](int64_t len) {
+    if (p->f64_explicit) return std::make_pair(p->unroll, p->block_warps);
+    if (const pent_plan::Rule* r = find_rule(p, PENT_F64, len)) return std::make_pair(r->a, r->b);
+    // built-in: the GB300 tuning at 2^26 rows (tune_gb300.txt): a group of long systems is
+    // bound by the latency of its own serial walk, so it keeps 8 rows of loads in flight
+    return len > 1024 ? std::make_pair(8, 1) : std::make_pair(4, 2);
+  };
+  if (p->shared) {
+    const auto kb = knobs(p->n_uniform);
+    p->runs.push_back({0, p->ngroups, kb.first, kb.second});
+    return;
+  }
+  for (int64_t k = 0; k < p->ngroups; ++k) {
+    const auto kb = knobs(p->gmax[k]);
+    if (!p->runs.empty() && p->runs.back().unroll == kb.first && p->runs.back().bw == kb.second)
+      p->runs.back().g1 = k + 1;
+    else
+      p->runs.push_back({k, k + 1, kb.first, kb.second});
+  }
 }
 
 bool build_f32_shapes(pent_plan* p) {
@@ -160,8 +263,7 @@ bool build_f32_shapes(pent_plan* p) {
   int64_t acc = 0;
   for (int64_t s = 0; s < nfac; ++s) {
     const int64_t n = p->n[s];
-    const bool ok = p->tps_override ? shape_for_threads(n, p->tps_override, &p->shape[s]) : default_shape(n, &p->shape[s]);
-    if (!ok) return false;
+    if (!choose_shape(p, n, &p->shape[s])) return false;
     p->foff[s] = acc;
     const Shape& sh = p->shape[s];
     acc += (int64_t)2 * 32 * sh.W * sh.C * sh.L / 4;
@@ -228,6 +330,28 @@ void layout(pent_plan* p) {
   p->ws_bytes = cur;
 }
 
+// Launch count(i) for i = 0..n-1: on the plan's stream alone, or spread over
+// the plan's side streams (forked from and joined back to the plan's stream
+// with events, which also works inside a stream capture).
+template <class F>
+cudaError_t fork_join(pent_plan* p, size_t n, F launch) {
+  const int ns = (int)p->side.size();
+  cudaError_t e = cudaSuccess;
+  if (ns == 0 || n < 2) {
+    for (size_t i = 0; i < n && e == cudaSuccess; ++i) e = launch(i, p->stream);
+    return e;
+  }
+  e = cudaEventRecord(p->ev[0], p->stream);
+  for (int k = 0; k < ns && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(p->side[k], p->ev[0], 0);
+  for (size_t i = 0; i < n && e == cudaSuccess; ++i)
+    e = launch(i, (i % (ns + 1) == 0) ? p->stream : p->side[i % (ns + 1) - 1]);
+  for (int k = 0; k < ns && e == cudaSuccess; ++k) {
+    e = cudaEventRecord(p->ev[1 + k], p->side[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->stream, p->ev[1 + k], 0);
+  }
+  return e;
+}
+
 }  // namespace
 
 extern "C" {
@@ -249,13 +373,16 @@ const char* pent_status_string(pent_status s) {
 
 pent_status pent_plan_create(pent_plan** out, int64_t batch, const int64_t* n_per_system, int64_t n_uniform,
                              int shared_matrix, pent_precision precision, const char* tune_cache) {
-  (void)tune_cache;
   if (!out) return PENT_EINVAL;
   *out = nullptr;
   if (batch < 1 || batch > (int64_t)INT32_MAX) return PENT_EINVAL;
   if (precision != PENT_F64 && precision != PENT_F32_REFINE) return PENT_EINVAL;
   if (shared_matrix && n_per_system) return PENT_EINVAL;
   pent_plan* p = new pent_plan();
+  if (tune_cache && !parse_tune_cache(tune_cache, &p->rules)) {
+    delete p;
+    return PENT_EINVAL;
+  }
   p->batch = batch;
   p->shared = shared_matrix != 0;
   p->precision = precision;
@@ -283,6 +410,7 @@ pent_status pent_plan_create(pent_plan** out, int64_t batch, const int64_t* n_pe
   for (int64_t q = 0; q < batch; ++q) p->perm[q] = order[q];
   p->goff.resize(p->ngroups);
   p->glen.resize(p->ngroups);
+  p->gmax.resize(p->ngroups);
   int64_t acc = 0;
   for (int64_t k = 0; k < p->ngroups; ++k) {
     int64_t mx = 0;
@@ -290,12 +418,14 @@ pent_status pent_plan_create(pent_plan** out, int64_t batch, const int64_t* n_pe
       const int32_t s = p->perm[k * kWarp + l];
       if (s >= 0) mx = std::max(mx, p->n[s]);
     }
+    p->gmax[k] = mx;
     if (!p->shared) mx += (mx & 1);  // per-system records are stored in row pairs
     p->goff[k] = acc;
     p->glen[k] = (int32_t)mx;
     acc += mx;
   }
   p->grows = acc;
+  build_f64_runs(p);
   if (precision == PENT_F32_REFINE) {
     if (!build_f32_shapes(p)) {
       delete p;
@@ -335,18 +465,20 @@ pent_status pent_plan_bind(pent_plan* p, void* ws, void* stream) {
     up(p->r_foff, p->foff.data(), p->foff.size() * sizeof(int64_t));
     up(p->r_shape, shp.data(), shp.size() * sizeof(int32_t));
     up(p->r_sys32, p->sys32.data(), p->sys32.size() * sizeof(int32_t));
-    p->drop_streams();
-    const int nside = (int)std::min<size_t>(3, p->buckets.size() > 1 ? p->buckets.size() - 1 : 0);
-    for (int k = 0; k < nside && e == cudaSuccess; ++k) {
-      cudaStream_t ss;
-      e = cudaStreamCreateWithFlags(&ss, cudaStreamNonBlocking);
-      if (e == cudaSuccess) p->side.push_back(ss);
-    }
-    for (int k = 0; k < 2 * nside + 1 && e == cudaSuccess; ++k) {
-      cudaEvent_t ee;
-      e = cudaEventCreateWithFlags(&ee, cudaEventDisableTiming);
-      if (e == cudaSuccess) p->ev.push_back(ee);
-    }
+  }
+  // side streams (and fork/join events) so that several launches of one solve overlap
+  p->drop_streams();
+  const size_t nlaunch = p->precision == PENT_F64 ? p->runs.size() : p->buckets.size();
+  const int nside = (int)std::min<size_t>(3, nlaunch > 1 ? nlaunch - 1 : 0);
+  for (int k = 0; k < nside && e == cudaSuccess; ++k) {
+    cudaStream_t ss;
+    e = cudaStreamCreateWithFlags(&ss, cudaStreamNonBlocking);
+    if (e == cudaSuccess) p->side.push_back(ss);
+  }
+  for (int k = 0; k < 2 * nside + 1 && e == cudaSuccess; ++k) {
+    cudaEvent_t ee;
+    e = cudaEventCreateWithFlags(&ee, cudaEventDisableTiming);
+    if (e == cudaSuccess) p->ev.push_back(ee);
   }
   if (e != cudaSuccess) return PENT_ECUDA;
   p->bound = true;
@@ -371,6 +503,20 @@ pent_status pent_plan_set_option(pent_plan* p, int key, int64_t value) {
       layout(p);
       return PENT_OK;
     }
+    case PENT_OPT_ROWS_PER_THREAD: {
+      if (p->bound) return PENT_EINVAL;
+      if (p->precision == PENT_F64) return PENT_EINVAL;
+      if (value != 0 && value != 4 && value != 8) return PENT_EINVAL;
+      const int64_t keep = p->rpt_override;
+      p->rpt_override = value;
+      if (!build_f32_shapes(p)) {
+        p->rpt_override = keep;
+        build_f32_shapes(p);
+        return PENT_EINVAL;
+      }
+      layout(p);
+      return PENT_OK;
+    }
     case PENT_OPT_RESIDUAL:
       if (value != PENT_RESIDUAL_FF && value != PENT_RESIDUAL_F64) return PENT_EINVAL;
       p->residual = (int)value;
@@ -378,16 +524,23 @@ pent_status pent_plan_set_option(pent_plan* p, int key, int64_t value) {
     case PENT_OPT_BLOCK_WARPS:
       if (value < 1 || value > 8) return PENT_EINVAL;
       p->block_warps = (int)value;
+      p->f64_explicit = true;
+      build_f64_runs(p);
+      ++p->cfg_version;
       p->drop_graphs();
       return PENT_OK;
     case PENT_OPT_UNROLL:
       if (value != 2 && value != 4 && value != 8) return PENT_EINVAL;
       p->unroll = (int)value;
+      p->f64_explicit = true;
+      build_f64_runs(p);
+      ++p->cfg_version;
       p->drop_graphs();
       return PENT_OK;
     case PENT_OPT_REFINE_TOL_LOG2:
       if (value < 1 || value > 60) return PENT_EINVAL;
       p->tol_log2 = (int)value;
+      ++p->cfg_version;
       p->drop_graphs();
       return PENT_OK;
   }
@@ -402,7 +555,31 @@ pent_status pent_plan_get_option(const pent_plan* p, int key, int64_t* value) {
     case PENT_OPT_BLOCK_WARPS: *value = p->block_warps; return PENT_OK;
     case PENT_OPT_REFINE_TOL_LOG2: *value = p->tol_log2; return PENT_OK;
     case PENT_OPT_UNROLL: *value = p->unroll; return PENT_OK;
+    case PENT_OPT_ROWS_PER_THREAD: *value = p->rpt_override; return PENT_OK;
   }
+  return PENT_EINVAL;
+}
+
+pent_status pent_plan_system_config(const pent_plan* p, int64_t system, int64_t* a, int64_t* b) {
+  if (!p || !a || !b || system < 0 || system >= p->batch) return PENT_EINVAL;
+  if (p->precision == PENT_F32_REFINE) {
+    const auto& sh = p->shape[p->shared ? 0 : system];
+    *a = sh.L;
+    *b = 32 * sh.W * sh.C;
+    return PENT_OK;
+  }
+  // the group holding the system (sorted position q = group * 32 + lane)
+  int64_t k = 0;
+  if (!p->shared) {
+    const auto it = std::find(p->perm.begin(), p->perm.end(), (int32_t)system);
+    k = (int64_t)(it - p->perm.begin()) / kWarp;
+  }
+  for (const auto& r : p->runs)
+    if (r.g0 <= k && k < r.g1) {
+      *a = r.unroll;
+      *b = r.bw;
+      return PENT_OK;
+    }
   return PENT_EINVAL;
 }
 
@@ -455,40 +632,23 @@ pent_status pent_factor_hyperdiff(pent_plan* p, const double* d_sigma) {
   return factor_common(p, nullptr, nullptr, nullptr, nullptr, nullptr, d_sigma);
 }
 
-// The FP32 solve of every bucket; with several buckets the launches are spread
-// over the plan's side streams (forked from and joined back to the plan's
-// stream with events, which also works inside a stream capture).
-static cudaError_t solve32_buckets(pent_plan* p, const double* f, double* x, int max_refine) {
-  const F32Tables T = p->f32();
-  const int32_t* sys = p->at<int32_t>(p->r_sys32);
-  const int rf = p->residual == PENT_RESIDUAL_F64;
-  const int ns = (int)p->side.size();
-  cudaError_t e = cudaSuccess;
-  if (ns == 0) {
-    for (const auto& b : p->buckets)
-      if (e == cudaSuccess) e = launch_solve32r(T, sys, b, p->shared, f, x, max_refine, rf, p->tol_log2, p->stream);
-    return e;
-  }
-  e = cudaEventRecord(p->ev[0], p->stream);
-  for (int k = 0; k < ns && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(p->side[k], p->ev[0], 0);
-  for (size_t i = 0; i < p->buckets.size() && e == cudaSuccess; ++i) {
-    cudaStream_t st = (i % (ns + 1) == 0) ? p->stream : p->side[i % (ns + 1) - 1];
-    e = launch_solve32r(T, sys, p->buckets[i], p->shared, f, x, max_refine, rf, p->tol_log2, st);
-  }
-  for (int k = 0; k < ns && e == cudaSuccess; ++k) {
-    e = cudaEventRecord(p->ev[1 + k], p->side[k]);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->stream, p->ev[1 + k], 0);
-  }
-  return e;
-}
-
 static pent_status solve_launch(pent_plan* p, const double* f, double* x, int max_refine) {
-  const DevPlan P = p->dev();
   cudaError_t err;
   if (p->precision == PENT_F64) {
-    err = launch_solve64(P, p->f64(), f, x, p->at<double>(p->r_scr), p->block_warps, p->unroll, p->stream);
+    const DevPlan P = p->dev();
+    const F64Factors F = p->f64();
+    double* gscr = p->at<double>(p->r_scr);
+    err = fork_join(p, p->runs.size(), [&](size_t i, cudaStream_t st) {
+      const auto& r = p->runs[i];
+      return launch_solve64(P, F, f, x, gscr, r.bw, r.unroll, r.g0, r.g1, st);
+    });
   } else {
-    err = solve32_buckets(p, f, x, max_refine);
+    const F32Tables T = p->f32();
+    const int32_t* sys = p->at<int32_t>(p->r_sys32);
+    const int rf = p->residual == PENT_RESIDUAL_F64;
+    err = fork_join(p, p->buckets.size(), [&](size_t i, cudaStream_t st) {
+      return launch_solve32r(T, sys, p->buckets[i], p->shared, f, x, max_refine, rf, p->tol_log2, st);
+    });
   }
   return cuda_status(err);
 }
@@ -516,7 +676,7 @@ pent_status pent_solve_steps(pent_plan* p, double* x, int64_t nsteps, int max_re
     for (int64_t k = 0; k < nsteps && st == PENT_OK; ++k) st = solve_launch(p, x, x, max_refine);
     return st;
   }
-  const auto key = std::make_tuple((const void*)x, nsteps, max_refine, (int64_t)p->block_warps * 16 + p->unroll);
+  const auto key = std::make_tuple((const void*)x, nsteps, max_refine, p->cfg_version);
   auto it = p->graphs.find(key);
   if (it == p->graphs.end()) {
     cudaGraph_t g = nullptr;
