@@ -78,17 +78,32 @@ cudaError_t launch_adjoint64(const DevPlan& P, F64Factors F, const double* f, do
 cudaError_t launch_solve32r(const F32Tables& T, const int32_t* sys, const F32Bucket& b, int shared, const double* f,
                             double* x, int max_refine, int residual_f64, int tol_log2, cudaStream_t st);
 cudaError_t launch_sigma_grad(const DevPlan& P, const double* mu, const double* x, double* g_sigma, cudaStream_t st);
-// One ADI step (csrc/adi.cu).  rhsT and W are field-sized scratch, colsum one double.
+// Rows per chunk of the partitioned column sweeps of the ADI step.
+constexpr int kAdiChunk = 64;
+
+// Scratch of one partitioned sweep of `ncols` columns of n rows (nchunks = ceil(n / kAdiChunk)).
+struct SweepArgs {
+  F64Factors f;        // shared-matrix records (n rows)
+  const double* cmap;  // [nchunks][8] chunk maps (k_chunk_maps)
+  double2* U;          // [nchunks][ncols] affine parts
+  double2* E;          // [nchunks][ncols] entering states
+};
+
+// One ADI step (csrc/adi.cu).  rhsT and W are field-sized scratch; parts holds
+// ceil(nx / 32) * ceil(ny / kAdiChunk) partial sums and mean one double.
 struct AdiArgs {
   double* C;
   double* rhsT;
   double* W;
-  double* colsum;
+  double* parts;
+  double* mean;
   int nx, ny;
   double mu, sigma;
-  F64Factors fx;  // shared-matrix records of I + sigma D4 with n = nx
-  F64Factors fy;  // ... with n = ny
+  SweepArgs sx;  // x sweep: I + sigma D4 with n = nx, ny columns
+  SweepArgs sy;  // y sweep: n = ny, nx columns
 };
 cudaError_t launch_adi_step(const AdiArgs& a, cudaStream_t st);
+// Chunk maps of a shared FP64 factorisation with n rows (once per factorisation).
+cudaError_t launch_chunk_maps(F64Factors F, int n, double* cmap, cudaStream_t st);
 
 }  // namespace pent

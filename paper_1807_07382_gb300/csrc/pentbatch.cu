@@ -82,7 +82,7 @@ struct pent_plan {
   std::vector<cudaEvent_t> ev;    // fork/join events
   // workspace regions
   Region r_info, r_perm, r_off, r_n, r_goff, r_glen, r_sigma, r_fwd, r_bwd, r_scr, r_fac32, r_sig32, r_foff, r_shape,
-      r_sys32, r_adi;
+      r_sys32, r_adi, r_cmap, r_swU, r_swE;
   size_t ws_bytes = 0;
   // binding / state
   unsigned char* ws = nullptr;
@@ -324,9 +324,17 @@ void layout(pent_plan* p) {
     take(p->r_shape, (size_t)nfac * sizeof(int32_t));
     take(p->r_sys32, (size_t)p->batch * sizeof(int32_t));
   }
-  // ADI scratch, for shared-matrix plans: a full field (rows doubles) plus one partial
-  // sum per warp of the column sweep (at most n / 32 + 4 of them)
-  if (p->shared) take(p->r_adi, (size_t)(p->rows + p->n_uniform / 32 + 8) * sizeof(double));
+  // ADI scratch, for shared-matrix plans whose batch is the number of columns of
+  // a sweep: a full field (rows doubles), the partial sums of the sweep
+  // (ceil(batch / 32) per chunk) and the mean; the chunk maps of the
+  // factorisation and the per-(chunk, column) affine parts / entering states.
+  if (p->shared) {
+    const int64_t nch = (p->n_uniform + kAdiChunk - 1) / kAdiChunk;
+    take(p->r_adi, (size_t)(p->rows + nch * ((p->batch + 31) / 32) + 8) * sizeof(double));
+    take(p->r_cmap, (size_t)nch * 8 * sizeof(double));
+    take(p->r_swU, (size_t)nch * p->batch * 2 * sizeof(double));
+    take(p->r_swE, (size_t)nch * p->batch * 2 * sizeof(double));
+  }
   p->ws_bytes = cur;
 }
 
@@ -612,6 +620,8 @@ static pent_status factor_common(pent_plan* p, const double* a, const double* b,
     F64Factors F = p->f64();
     F.sig = (sigma && !p->shared) ? sg : nullptr;
     err = launch_factor64(P, a, b, c, d, e, sg, F, p->stream);
+    // chunk maps of a shared factorisation, for the partitioned sweeps of the ADI step
+    if (err == cudaSuccess && p->shared) err = launch_chunk_maps(F, (int)p->n_uniform, p->at<double>(p->r_cmap), p->stream);
   }
   else
     err = launch_factor32(p->f32(), p->at<int32_t>(p->r_shape), p->shared ? 1 : p->batch, sg, p->stream);
@@ -759,14 +769,16 @@ static pent_status adi_launch(pent_plan* px, pent_plan* py, double* C, int64_t n
   AdiArgs a;
   a.C = C;
   a.rhsT = px->at<double>(px->r_adi);
-  a.colsum = a.rhsT + nx * ny;
   a.W = px->at<double>(px->r_scr);
+  a.parts = py->at<double>(py->r_adi) + nx * ny;
+  const int64_t nchy = (ny + kAdiChunk - 1) / kAdiChunk;
+  a.mean = a.parts + nchy * ((nx + 31) / 32);
   a.nx = (int)nx;
   a.ny = (int)ny;
   a.mu = dt / (dx * dx);
   a.sigma = gamma * dt / (dx * dx * dx * dx);
-  a.fx = px->f64();
-  a.fy = py->f64();
+  a.sx = SweepArgs{px->f64(), px->at<double>(px->r_cmap), px->at<double2>(px->r_swU), px->at<double2>(px->r_swE)};
+  a.sy = SweepArgs{py->f64(), py->at<double>(py->r_cmap), py->at<double2>(py->r_swU), py->at<double2>(py->r_swE)};
   return cuda_status(launch_adi_step(a, px->stream));
 }
 
