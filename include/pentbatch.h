@@ -127,8 +127,13 @@ enum {
   PENT_OPT_REFINE_TOL_LOG2 = 4,    /* refinement stops once the estimated remaining error, (max|dx| / max|x|)^2
                                       relative to max|x| after a step with correction dx, is <= 2^-tol (default 43) */
   PENT_OPT_UNROLL = 5,             /* PENT_F64: rows loaded ahead of the arithmetic: 2, 4 or 8 (default 4) */
-  PENT_OPT_ROWS_PER_THREAD = 6     /* PENT_F32_REFINE: rows per thread, 4 or 8, or 0 for the automatic choice
+  PENT_OPT_ROWS_PER_THREAD = 6,    /* PENT_F32_REFINE: rows per thread, 4 or 8, or 0 for the automatic choice
                                       (before pent_plan_bind, like PENT_OPT_THREADS_PER_SYSTEM) */
+  PENT_OPT_PARTITION_ROWS = 7      /* PENT_F64 per-system matrices: groups of 32 systems whose longest system
+                                      has at least this many rows are solved in chunks of 256 rows joined by
+                                      scans, instead of one serial walk per system; 0 never, -1 automatic
+                                      (the default: where a walk would outlast the whole batch's streaming
+                                      time, and at least 2048 rows).  Before pent_plan_bind. */
 };
 pent_status pent_plan_set_option(pent_plan* plan, int key, int64_t value);
 pent_status pent_plan_get_option(const pent_plan* plan, int key, int64_t* value);
@@ -137,7 +142,8 @@ pent_status pent_plan_get_option(const pent_plan* plan, int key, int64_t* value)
  * The settings that solve system `system` (0 <= system < batch), as chosen by
  * options, the tune cache or the built-in rules: for PENT_F32_REFINE
  * *a = rows per thread and *b = threads per system; for PENT_F64 *a = unroll
- * and *b = warps per CTA of the launch that covers the system.
+ * and *b = warps per CTA of the launch that covers the system, or *a = 0 and
+ * *b = rows per chunk when its group is solved by the partitioned kernels.
  */
 pent_status pent_plan_system_config(const pent_plan* plan, int64_t system, int64_t* a, int64_t* b);
 

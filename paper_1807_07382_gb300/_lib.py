@@ -29,6 +29,7 @@ PENT_OPT_BLOCK_WARPS = 3
 PENT_OPT_REFINE_TOL_LOG2 = 4
 PENT_OPT_UNROLL = 5
 PENT_OPT_ROWS_PER_THREAD = 6
+PENT_OPT_PARTITION_ROWS = 7
 
 # every symbol the header declares, with (restype, argtypes)
 _vp = ctypes.c_void_p

@@ -381,6 +381,242 @@ __global__ void __launch_bounds__(128) k_solve64_pair(DevPlan P, F64Factors F, c
   }
 }
 
+// ---- partitioned solve of groups of long systems ----
+//
+// A group's serial walk takes time proportional to its length however few of
+// them there are, so groups of long systems are cut into chunks of kLongChunk
+// rows and walked by one warp per (group, chunk).  The substitutions are
+// second-order linear recurrences: a chunk maps the two values carried into
+// it affinely, with a linear part that depends on the factors only (computed
+// once per factorisation, k_cmaps64).  Pass 1 runs every chunk forward from a
+// zero state; a scan per lane over the group's chunks gives the true entering
+// states; pass 2 reruns the forward sweep (g to the scratch) and runs the back
+// sweep from a zero state; a second scan; pass 3 reruns the back sweep (x).
+
+struct PChunk {
+  int64_t id;  // global chunk index
+  int64_t k;   // group
+  int64_t q0, q1;  // row pairs [q0, q1) of the chunk (relative to the group)
+  bool active;
+};
+
+__device__ __forceinline__ PChunk pchunk(const DevPlan& P, const F64Part& X, int64_t c0, int64_t c1) {
+  PChunk c;
+  c.id = c0 + (int64_t)blockIdx.x * blockDim.y + threadIdx.y;
+  c.active = c.id < c1;
+  if (!c.active) return c;
+  c.k = X.ck[c.id];
+  const int64_t r0 = (int64_t)X.cc[c.id] * kLongChunk;
+  c.q0 = r0 >> 1;
+  c.q1 = min((int64_t)P.glen[c.k], r0 + kLongChunk) >> 1;
+  return c;
+}
+
+// One forward row in either record form, and its homogeneous map on (g_{i-2}, g_{i-1}):
+// g_i = -cE g_{i-2} - cB g_{i-1} + (inhomogeneous part).
+template <bool HYP>
+__device__ __forceinline__ double fwd_row(double a, double b, double e, double sg, double fv, double g1, double g2) {
+  return HYP ? a * fma(-b, g1, fma(-sg, g2, fv)) : fma(-b, g1, fma(-e, g2, a * fv));
+}
+
+// Forward over the chunk's pairs from (g2, g1); WRITE stores g in the scratch.
+template <bool HYP, bool WRITE>
+__device__ __forceinline__ void pfwd(const Lane& L, const PChunk& c, const double2* __restrict__ fwd,
+                                     const double* f, double2* __restrict__ g2s, double sg, bool fvec, int lane,
+                                     double& g2, double& g1) {
+  constexpr int NP = HYP ? 2 : 3;
+  constexpr int B = 4;  // pairs loaded per batch
+  const int64_t P0 = L.R0 >> 1;
+  for (int64_t qb = c.q0; qb < c.q1; qb += B) {
+    double2 A[B], Bv[B], Ev[B], Fv[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const int64_t q = qb + u;
+      if (q < c.q1) {
+        const double2* rec = fwd + ((P0 + q) * NP) * kWarp + lane;
+        A[u] = __ldg(rec);
+        Bv[u] = __ldg(rec + kWarp);
+        Ev[u] = HYP ? make_double2(0.0, 0.0) : __ldg(rec + 2 * kWarp);
+        const int64_t r = 2 * q;
+        if (fvec && r + 1 < L.n) {
+          Fv[u] = *reinterpret_cast<const double2*>(f + L.fo + r);
+        } else {
+          Fv[u].x = (r < L.n) ? f[L.fo + r] : 0.0;
+          Fv[u].y = (r + 1 < L.n) ? f[L.fo + r + 1] : 0.0;
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const int64_t q = qb + u;
+      if (q < c.q1) {
+        const double ga = fwd_row<HYP>(A[u].x, Bv[u].x, Ev[u].x, sg, Fv[u].x, g1, g2);
+        const double gb = fwd_row<HYP>(A[u].y, Bv[u].y, Ev[u].y, sg, Fv[u].y, ga, g1);
+        if (WRITE) g2s[(P0 + q) * kWarp + lane] = make_double2(ga, gb);
+        g2 = ga;
+        g1 = gb;
+      }
+    }
+  }
+}
+
+// Back over the chunk's pairs (descending) from (x1, x2) = (x_{r1}, x_{r1+1});
+// WRITE stores x.
+template <bool WRITE>
+__device__ __forceinline__ void pbwd(const Lane& L, const PChunk& c, const double2* __restrict__ bwd,
+                                     const double2* __restrict__ g2s, double* x, bool xvec, int lane, double& x1,
+                                     double& x2) {
+  constexpr int B = 4;
+  const int64_t P0 = L.R0 >> 1;
+  for (int64_t qb = c.q1 - 1; qb >= c.q0; qb -= B) {
+    double2 G[B], D[B], Gv[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const int64_t q = qb - u;
+      if (q >= c.q0) {
+        const double2* rec = bwd + ((P0 + q) * 2) * kWarp + lane;
+        G[u] = __ldg(rec);
+        D[u] = __ldg(rec + kWarp);
+        Gv[u] = g2s[(P0 + q) * kWarp + lane];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const int64_t q = qb - u;
+      if (q >= c.q0) {
+        const double xb = fma(-G[u].y, x1, fma(-D[u].y, x2, Gv[u].y));
+        const double xa = fma(-G[u].x, xb, fma(-D[u].x, x1, Gv[u].x));
+        if (WRITE) {
+          const int64_t r = 2 * q;
+          if (xvec && r + 1 < L.n) {
+            *reinterpret_cast<double2*>(x + L.fo + r) = make_double2(xa, xb);
+          } else {
+            if (r < L.n) x[L.fo + r] = xa;
+            if (r + 1 < L.n) x[L.fo + r + 1] = xb;
+          }
+        }
+        x2 = xb;
+        x1 = xa;
+      }
+    }
+  }
+}
+
+// Chunk maps from the records: forward on (g_{r0-2}, g_{r0-1}) -> (g_{r1-2}, g_{r1-1}),
+// back on (x_{r1}, x_{r1+1}) -> (x_{r0}, x_{r0+1}); cmap[(id * 8 + e) * 32 + lane].
+template <bool HYP>
+__global__ void __launch_bounds__(256) k_cmaps64(DevPlan P, F64Factors F, F64Part X, int64_t c0, int64_t c1) {
+  const PChunk c = pchunk(P, X, c0, c1);
+  if (!c.active) return;
+  const int lane = threadIdx.x;
+  const Lane L = lane_setup<false>(P, c.k, lane);
+  const double sg = (HYP && L.s >= 0) ? F.sig[L.s] : 0.0;
+  constexpr int NP = HYP ? 2 : 3;
+  const double2* fwd = reinterpret_cast<const double2*>(F.fwd);
+  const double2* bwd = reinterpret_cast<const double2*>(F.bwd);
+  const int64_t P0 = L.R0 >> 1;
+  double f00 = 1.0, f01 = 0.0, f10 = 0.0, f11 = 1.0;
+  for (int64_t q = c.q0; q < c.q1; ++q) {
+    const double2* rec = fwd + ((P0 + q) * NP) * kWarp + lane;
+    const double2 A = rec[0], Bv = rec[kWarp];
+    const double2 Ev = HYP ? make_double2(0.0, 0.0) : rec[2 * kWarp];
+    const double cB[2] = {HYP ? A.x * Bv.x : Bv.x, HYP ? A.y * Bv.y : Bv.y};
+    const double cE[2] = {HYP ? A.x * sg : Ev.x, HYP ? A.y * sg : Ev.y};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const double n10 = -cE[h] * f00 - cB[h] * f10, n11 = -cE[h] * f01 - cB[h] * f11;
+      f00 = f10;
+      f01 = f11;
+      f10 = n10;
+      f11 = n11;
+    }
+  }
+  double b00 = 1.0, b01 = 0.0, b10 = 0.0, b11 = 1.0;
+  for (int64_t q = c.q1 - 1; q >= c.q0; --q) {
+    const double2* rec = bwd + ((P0 + q) * 2) * kWarp + lane;
+    const double2 G = rec[0], D = rec[kWarp];
+    const double gg[2] = {G.y, G.x}, dd[2] = {D.y, D.x};  // row 2q+1 first, then 2q
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const double n00 = -gg[h] * b00 - dd[h] * b10, n01 = -gg[h] * b01 - dd[h] * b11;
+      b10 = b00;
+      b11 = b01;
+      b00 = n00;
+      b01 = n01;
+    }
+  }
+  double* m = X.cmap + (c.id * 8) * kWarp + lane;
+  m[0 * kWarp] = f00; m[1 * kWarp] = f01; m[2 * kWarp] = f10; m[3 * kWarp] = f11;
+  m[4 * kWarp] = b00; m[5 * kWarp] = b01; m[6 * kWarp] = b10; m[7 * kWarp] = b11;
+}
+
+template <bool HYP>
+__global__ void __launch_bounds__(256) k_pfwd0(DevPlan P, F64Factors F, F64Part X, const double* f, int64_t c0,
+                                               int64_t c1) {
+  const PChunk c = pchunk(P, X, c0, c1);
+  if (!c.active) return;
+  const int lane = threadIdx.x;
+  const Lane L = lane_setup<false>(P, c.k, lane);
+  const double sg = (HYP && L.s >= 0) ? F.sig[L.s] : 0.0;
+  const bool fvec = ((L.fo & 1) == 0) && ((((uintptr_t)f) & 15) == 0);
+  double g2 = 0.0, g1 = 0.0;
+  pfwd<HYP, false>(L, c, reinterpret_cast<const double2*>(F.fwd), f, nullptr, sg, fvec, lane, g2, g1);
+  X.U[c.id * kWarp + lane] = make_double2(g2, g1);
+}
+
+// Entering states of a group's chunks (thread per (group, lane)), in sweep order.
+template <bool FWD>
+__global__ void __launch_bounds__(256) k_pscan64(F64Part X, int64_t kbeg, int64_t kend) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t k = kbeg + t / kWarp;
+  if (k >= kend) return;
+  const int lane = (int)(t % kWarp);
+  const int64_t base = X.cbase[k];
+  const int nch = X.cnum[k];
+  double e0 = 0.0, e1 = 0.0;
+  for (int j = 0; j < nch; ++j) {
+    const int64_t id = base + (FWD ? j : nch - 1 - j);
+    X.E[id * kWarp + lane] = make_double2(e0, e1);
+    const double* m = X.cmap + (id * 8 + (FWD ? 0 : 4)) * kWarp + lane;
+    const double2 u = X.U[id * kWarp + lane];
+    const double n0 = fma(m[0], e0, fma(m[kWarp], e1, u.x));
+    const double n1 = fma(m[2 * kWarp], e0, fma(m[3 * kWarp], e1, u.y));
+    e0 = n0;
+    e1 = n1;
+  }
+}
+
+template <bool HYP>
+__global__ void __launch_bounds__(256) k_pmid(DevPlan P, F64Factors F, F64Part X, const double* f, double* gscr,
+                                              int64_t c0, int64_t c1) {
+  const PChunk c = pchunk(P, X, c0, c1);
+  if (!c.active) return;
+  const int lane = threadIdx.x;
+  const Lane L = lane_setup<false>(P, c.k, lane);
+  const double sg = (HYP && L.s >= 0) ? F.sig[L.s] : 0.0;
+  const bool fvec = ((L.fo & 1) == 0) && ((((uintptr_t)f) & 15) == 0);
+  double2* g2s = reinterpret_cast<double2*>(gscr);
+  const double2 e = X.E[c.id * kWarp + lane];
+  double g2 = e.x, g1 = e.y;
+  pfwd<HYP, true>(L, c, reinterpret_cast<const double2*>(F.fwd), f, g2s, sg, fvec, lane, g2, g1);
+  double x1 = 0.0, x2 = 0.0;
+  pbwd<false>(L, c, reinterpret_cast<const double2*>(F.bwd), g2s, nullptr, false, lane, x1, x2);
+  X.U[c.id * kWarp + lane] = make_double2(x1, x2);
+}
+
+__global__ void __launch_bounds__(256) k_pbwd(DevPlan P, F64Factors F, F64Part X, double* gscr, double* x,
+                                              int64_t c0, int64_t c1) {
+  const PChunk c = pchunk(P, X, c0, c1);
+  if (!c.active) return;
+  const int lane = threadIdx.x;
+  const Lane L = lane_setup<false>(P, c.k, lane);
+  const bool xvec = ((L.fo & 1) == 0) && ((((uintptr_t)x) & 15) == 0);
+  const double2 e = X.E[c.id * kWarp + lane];
+  double x1 = e.x, x2 = e.y;
+  pbwd<true>(L, c, reinterpret_cast<const double2*>(F.bwd), reinterpret_cast<const double2*>(gscr), x, xvec, lane,
+             x1, x2);
+}
+
 // y = A^{-T} f from the stored factors.  With L = D_alpha Lhat (Lhat unit lower
 // with beta/alpha, epsilon/alpha) and A = L R:  A^T = R^T Lhat^T D_alpha, so
 //   R^T z = f:      z_i = f_i - gamma_{i-1} z_{i-1} - delta_{i-2} z_{i-2}       (ascending)
@@ -500,6 +736,38 @@ cudaError_t launch_solve64(const DevPlan& P, F64Factors F, const double* f, doub
   PENT_U2(2, 1) PENT_U2(4, 2) PENT_U2(8, 4)
 #undef PENT_U2
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_chunk_maps64(const DevPlan& P, F64Factors F, const F64Part& X, int64_t c0, int64_t c1,
+                                cudaStream_t st) {
+  if (c1 <= c0) return cudaSuccess;
+  const dim3 blk(kWarp, 8);
+  const unsigned grid = (unsigned)((c1 - c0 + 7) / 8);
+  if (F.sig)
+    k_cmaps64<true><<<grid, blk, 0, st>>>(P, F, X, c0, c1);
+  else
+    k_cmaps64<false><<<grid, blk, 0, st>>>(P, F, X, c0, c1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_solve64_part(const DevPlan& P, F64Factors F, const F64Part& X, const double* f, double* x,
+                                double* gscr, int64_t kbeg, int64_t kend, int64_t c0, int64_t c1, cudaStream_t st) {
+  if (c1 <= c0) return cudaSuccess;
+  const dim3 blk(kWarp, 8);
+  const unsigned grid = (unsigned)((c1 - c0 + 7) / 8);
+  const unsigned sgrid = (unsigned)grid_for((kend - kbeg) * kWarp, 256);
+  if (F.sig) {
+    k_pfwd0<true><<<grid, blk, 0, st>>>(P, F, X, f, c0, c1);
+    k_pscan64<true><<<sgrid, 256, 0, st>>>(X, kbeg, kend);
+    k_pmid<true><<<grid, blk, 0, st>>>(P, F, X, f, gscr, c0, c1);
+  } else {
+    k_pfwd0<false><<<grid, blk, 0, st>>>(P, F, X, f, c0, c1);
+    k_pscan64<true><<<sgrid, 256, 0, st>>>(X, kbeg, kend);
+    k_pmid<false><<<grid, blk, 0, st>>>(P, F, X, f, gscr, c0, c1);
+  }
+  k_pscan64<false><<<sgrid, 256, 0, st>>>(X, kbeg, kend);
+  k_pbwd<<<grid, blk, 0, st>>>(P, F, X, gscr, x, c0, c1);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint64(const DevPlan& P, F64Factors F, const double* f, double* x, double* gscr,

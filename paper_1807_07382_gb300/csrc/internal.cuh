@@ -65,6 +65,20 @@ struct F32Bucket {
   int even_offsets;  // every system of the bucket starts at an even row (16-byte vector access)
 };
 
+// Partitioned FP64 solve of groups whose systems are long: each group's rows are
+// cut into chunks of kLongChunk rows, one warp per (group, chunk), joined by
+// per-lane scans over the chunks (csrc/core64.cu).
+constexpr int kLongChunk = 256;  // even: chunks hold whole row pairs
+struct F64Part {
+  const int32_t* ck;     // [nchunks] group of each chunk (chunks of a group are consecutive)
+  const int32_t* cc;     // [nchunks] index of the chunk within its group
+  const int64_t* cbase;  // [ngroups] first chunk of each partitioned group
+  const int32_t* cnum;   // [ngroups] chunks of each partitioned group (0 otherwise)
+  double* cmap;          // [nchunks][8][32]: forward (0..3) and back (4..7) 2x2 maps per lane
+  double2* U;            // [nchunks][32] affine parts
+  double2* E;            // [nchunks][32] entering states
+};
+
 // ---- launchers (kernels live in the .cu files) ----
 cudaError_t launch_factor64(const DevPlan& P, const double* a, const double* b, const double* c, const double* d,
                             const double* e, const double* sigma, F64Factors F, cudaStream_t st);
@@ -73,6 +87,12 @@ cudaError_t launch_factor32(const F32Tables& T, const int32_t* shape, int64_t ns
 // Groups [g0, g1) of the plan (all of them for a shared matrix: g0 = 0, g1 = ngroups).
 cudaError_t launch_solve64(const DevPlan& P, F64Factors F, const double* f, double* x, double* gscr, int block_warps,
                            int unroll, int64_t g0, int64_t g1, cudaStream_t st);
+// Chunk maps of chunks [c0, c1) (after the factorisation), and the partitioned
+// solve of groups [kbeg, kend) whose chunks are [c0, c1).
+cudaError_t launch_chunk_maps64(const DevPlan& P, F64Factors F, const F64Part& X, int64_t c0, int64_t c1,
+                                cudaStream_t st);
+cudaError_t launch_solve64_part(const DevPlan& P, F64Factors F, const F64Part& X, const double* f, double* x,
+                                double* gscr, int64_t kbeg, int64_t kend, int64_t c0, int64_t c1, cudaStream_t st);
 cudaError_t launch_adjoint64(const DevPlan& P, F64Factors F, const double* f, double* x, double* gscr,
                              int block_warps, cudaStream_t st);
 cudaError_t launch_solve32r(const F32Tables& T, const int32_t* sys, const F32Bucket& b, int shared, const double* f,

@@ -56,8 +56,15 @@ struct pent_plan {
   struct F64Run {
     int64_t g0, g1;  // groups [g0, g1)
     int unroll, bw;
+    bool part;       // partitioned solve of long groups (chunks [c0, c1))
+    int64_t c0, c1;
   };
   std::vector<F64Run> runs;
+  int64_t part_rows = -1;  // PENT_OPT_PARTITION_ROWS (-1: automatic)
+  // partitioned groups: chunk list and per-group chunk ranges
+  std::vector<int32_t> pck, pcc, pcnum;
+  std::vector<int64_t> pcbase;
+  int64_t pchunks = 0;
   int64_t cfg_version = 0;  // bumped whenever launch settings change (graph cache key)
   // thread-per-system grouping (systems sorted by length, longest first)
   std::vector<int32_t> perm;  // [ngroups*32], -1 for padding lanes
@@ -82,7 +89,7 @@ struct pent_plan {
   std::vector<cudaEvent_t> ev;    // fork/join events
   // workspace regions
   Region r_info, r_perm, r_off, r_n, r_goff, r_glen, r_sigma, r_fwd, r_bwd, r_scr, r_fac32, r_sig32, r_foff, r_shape,
-      r_sys32, r_adi, r_cmap, r_swU, r_swE;
+      r_sys32, r_adi, r_cmap, r_swU, r_swE, r_pck, r_pcc, r_pcbase, r_pcnum, r_pcmap, r_pU, r_pE;
   size_t ws_bytes = 0;
   // binding / state
   unsigned char* ws = nullptr;
@@ -113,6 +120,17 @@ struct pent_plan {
   // Hyperdiffusion factors of per-system matrices use the constant-epsilon records.
   F64Factors f64() const {
     return F64Factors{at<double>(r_fwd), at<double>(r_bwd), (factored == 2 && !shared) ? at<double>(r_sigma) : nullptr};
+  }
+  F64Part part() const {
+    F64Part X;
+    X.ck = at<int32_t>(r_pck);
+    X.cc = at<int32_t>(r_pcc);
+    X.cbase = at<int64_t>(r_pcbase);
+    X.cnum = at<int32_t>(r_pcnum);
+    X.cmap = at<double>(r_pcmap);
+    X.U = at<double2>(r_pU);
+    X.E = at<double2>(r_pE);
+    return X;
   }
   F32Tables f32() const {
     F32Tables T;
@@ -232,9 +250,27 @@ bool parse_tune_cache(const char* path, std::vector<pent_plan::Rule>* out) {
   return true;
 }
 
-// FP64 launches: groups (longest first) in runs of equal unroll / block warps.
+// Groups whose longest system has at least this many rows are solved by the
+// partitioned kernels: a thread-per-system walk takes time proportional to its
+// length, about 0.3 us per row on GB300, while the whole batch streams at
+// about 64 bytes per row at ~6 TB/s; a group is cut into chunks when its walk
+// would outlast the batch, and never below 2048 rows (where the doubled
+// arithmetic of the partitioned passes costs more than it hides).
+int64_t part_threshold(const pent_plan* p) {
+  if (p->shared || p->part_rows == 0) return INT64_MAX;
+  if (p->part_rows > 0) return p->part_rows;
+  return std::max<int64_t>(2048, p->rows / 28000);
+}
+
+// FP64 launches: groups (longest first) in runs of equal unroll / block warps,
+// the long groups in partitioned runs with their chunk lists.
 void build_f64_runs(pent_plan* p) {
   p->runs.clear();
+  p->pck.clear();
+  p->pcc.clear();
+  p->pcnum.assign(p->ngroups, 0);
+  p->pcbase.assign(p->ngroups, 0);
+  p->pchunks = 0;
   auto knobs = [&](int64_t len) {
     if (p->f64_explicit) return std::make_pair(p->unroll, p->block_warps);
     if (const pent_plan::Rule* r = find_rule(p, PENT_F64, len)) return std::make_pair(r->a, r->b);
@@ -244,15 +280,31 @@ void build_f64_runs(pent_plan* p) {
   };
   if (p->shared) {
     const auto kb = knobs(p->n_uniform);
-    p->runs.push_back({0, p->ngroups, kb.first, kb.second});
+    p->runs.push_back({0, p->ngroups, kb.first, kb.second, false, 0, 0});
     return;
   }
+  const int64_t thr = part_threshold(p);
   for (int64_t k = 0; k < p->ngroups; ++k) {
-    const auto kb = knobs(p->gmax[k]);
-    if (!p->runs.empty() && p->runs.back().unroll == kb.first && p->runs.back().bw == kb.second)
-      p->runs.back().g1 = k + 1;
-    else
-      p->runs.push_back({k, k + 1, kb.first, kb.second});
+    const bool part = p->gmax[k] >= thr;
+    const auto kb = part ? std::make_pair(0, 0) : knobs(p->gmax[k]);
+    if (part) {
+      const int nch = (int)((p->glen[k] + kLongChunk - 1) / kLongChunk);
+      p->pcbase[k] = p->pchunks;
+      p->pcnum[k] = nch;
+      for (int c = 0; c < nch; ++c) {
+        p->pck.push_back((int32_t)k);
+        p->pcc.push_back(c);
+      }
+      p->pchunks += nch;
+    }
+    auto& b = p->runs;
+    if (!b.empty() && b.back().part == part && b.back().unroll == kb.first && b.back().bw == kb.second) {
+      b.back().g1 = k + 1;
+      b.back().c1 = p->pchunks;
+    } else {
+      const int64_t c0 = part ? p->pcbase[k] : p->pchunks;
+      b.push_back({k, k + 1, kb.first, kb.second, part, c0, p->pchunks});
+    }
   }
 }
 
@@ -317,6 +369,13 @@ void layout(pent_plan* p) {
     take(p->r_fwd, (size_t)frows * 3 * lanes * sizeof(double));
     take(p->r_bwd, (size_t)frows * 2 * lanes * sizeof(double));
     take(p->r_scr, (size_t)p->grows * kWarp * sizeof(double));
+    take(p->r_pck, (size_t)p->pchunks * sizeof(int32_t));
+    take(p->r_pcc, (size_t)p->pchunks * sizeof(int32_t));
+    take(p->r_pcbase, (size_t)p->ngroups * sizeof(int64_t));
+    take(p->r_pcnum, (size_t)p->ngroups * sizeof(int32_t));
+    take(p->r_pcmap, (size_t)p->pchunks * 8 * kWarp * sizeof(double));
+    take(p->r_pU, (size_t)p->pchunks * kWarp * 2 * sizeof(double));
+    take(p->r_pE, (size_t)p->pchunks * kWarp * 2 * sizeof(double));
   } else {
     take(p->r_fac32, (size_t)p->fac_float4 * 4 * sizeof(float));
     take(p->r_sig32, (size_t)nfac * 2 * sizeof(float));
@@ -466,6 +525,12 @@ pent_status pent_plan_bind(pent_plan* p, void* ws, void* stream) {
   up(p->r_glen, p->glen.data(), p->glen.size() * sizeof(int32_t));
   const unsigned long long init[kInfoWords] = {kInfoNone, 0, 0, 0};
   up(p->r_info, init, sizeof(init));
+  if (p->precision == PENT_F64 && !p->shared) {
+    up(p->r_pck, p->pck.data(), p->pck.size() * sizeof(int32_t));
+    up(p->r_pcc, p->pcc.data(), p->pcc.size() * sizeof(int32_t));
+    up(p->r_pcbase, p->pcbase.data(), p->pcbase.size() * sizeof(int64_t));
+    up(p->r_pcnum, p->pcnum.data(), p->pcnum.size() * sizeof(int32_t));
+  }
   if (p->precision == PENT_F32_REFINE) {
     std::vector<int32_t> shp(p->shape.size());
     for (size_t k = 0; k < shp.size(); ++k)
@@ -511,6 +576,13 @@ pent_status pent_plan_set_option(pent_plan* p, int key, int64_t value) {
       layout(p);
       return PENT_OK;
     }
+    case PENT_OPT_PARTITION_ROWS:
+      if (p->bound || p->precision != PENT_F64) return PENT_EINVAL;
+      if (value < -1) return PENT_EINVAL;
+      p->part_rows = value;
+      build_f64_runs(p);
+      layout(p);
+      return PENT_OK;
     case PENT_OPT_ROWS_PER_THREAD: {
       if (p->bound) return PENT_EINVAL;
       if (p->precision == PENT_F64) return PENT_EINVAL;
@@ -564,6 +636,7 @@ pent_status pent_plan_get_option(const pent_plan* p, int key, int64_t* value) {
     case PENT_OPT_REFINE_TOL_LOG2: *value = p->tol_log2; return PENT_OK;
     case PENT_OPT_UNROLL: *value = p->unroll; return PENT_OK;
     case PENT_OPT_ROWS_PER_THREAD: *value = p->rpt_override; return PENT_OK;
+    case PENT_OPT_PARTITION_ROWS: *value = p->part_rows; return PENT_OK;
   }
   return PENT_EINVAL;
 }
@@ -584,8 +657,8 @@ pent_status pent_plan_system_config(const pent_plan* p, int64_t system, int64_t*
   }
   for (const auto& r : p->runs)
     if (r.g0 <= k && k < r.g1) {
-      *a = r.unroll;
-      *b = r.bw;
+      *a = r.part ? 0 : r.unroll;
+      *b = r.part ? kLongChunk : r.bw;
       return PENT_OK;
     }
   return PENT_EINVAL;
@@ -622,6 +695,8 @@ static pent_status factor_common(pent_plan* p, const double* a, const double* b,
     err = launch_factor64(P, a, b, c, d, e, sg, F, p->stream);
     // chunk maps of a shared factorisation, for the partitioned sweeps of the ADI step
     if (err == cudaSuccess && p->shared) err = launch_chunk_maps(F, (int)p->n_uniform, p->at<double>(p->r_cmap), p->stream);
+    // chunk maps of the partitioned groups
+    if (err == cudaSuccess && p->pchunks > 0) err = launch_chunk_maps64(P, F, p->part(), 0, p->pchunks, p->stream);
   }
   else
     err = launch_factor32(p->f32(), p->at<int32_t>(p->r_shape), p->shared ? 1 : p->batch, sg, p->stream);
@@ -648,8 +723,10 @@ static pent_status solve_launch(pent_plan* p, const double* f, double* x, int ma
     const DevPlan P = p->dev();
     const F64Factors F = p->f64();
     double* gscr = p->at<double>(p->r_scr);
+    const F64Part X = p->part();
     err = fork_join(p, p->runs.size(), [&](size_t i, cudaStream_t st) {
       const auto& r = p->runs[i];
+      if (r.part) return launch_solve64_part(P, F, X, f, x, gscr, r.g0, r.g1, r.c0, r.c1, st);
       return launch_solve64(P, F, f, x, gscr, r.bw, r.unroll, r.g0, r.g1, st);
     });
   } else {

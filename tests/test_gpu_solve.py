@@ -261,3 +261,46 @@ def test_f64_uneven_batch_full_range():
     x = dev(w.field0)
     plan.solve_steps(x, w.steps)
     assert sys_rel_err(host(x), ref, w.n) <= TOL
+
+
+# ----------------------------------------------------------------------------- partitioned FP64 groups
+
+@pytest.mark.parametrize("part_rows", [50, 600])
+def test_f64_partitioned_general_bands(part_rows):
+    """Groups at or above `part_rows` rows are cut into 256-row chunks joined by scans:
+    ragged lengths (odd, below, at and across chunk edges), general bands, in place."""
+    ns = np.array([1, 2, 3, 5, 255, 256, 257, 511, 512, 513, 700, 1000, 64, 2049, 31, 3000] * 4)
+    bands = [synth.random_bands(1, int(m), seed=int(m) * 13 + i, kind=("spd" if i % 2 else "diagdom"))
+             for i, m in enumerate(ns)]
+    band = cat_bands(bands)
+    f = synth.uniform(91, 0, int(ns.sum()), -1, 1)
+    fac, _, _ = oracle.factor_batch(ns, band)
+    ref = oracle.solve_batch(ns, fac, f)
+    plan = pb.Plan(list(ns), options={pb.PENT_OPT_PARTITION_ROWS: part_rows})
+    assert plan.system_config(int(np.argmax(ns)))[0] == 0  # the longest group is partitioned
+    plan.factor(*[dev(v) for v in band])
+    x = plan.solve(dev(f))
+    assert plan.info()[0] == pb.PENT_OK
+    assert sys_rel_err(host(x), ref, ns) <= TOL
+    fx = dev(f)
+    plan.solve(fx, fx)
+    assert sys_rel_err(host(fx), ref, ns) <= TOL
+
+
+def test_f64_partitioned_hyperdiff_uneven_steps_and_graph():
+    w = synth.uneven(batch=200, steps=3)
+    ref = oracle.hyperdiff_steps(w.n, w.sigma, w.field0, w.steps)
+    plan = pb.Plan(list(w.n), options={pb.PENT_OPT_PARTITION_ROWS: 1024})
+    plan.factor_hyperdiff(dev(w.sigma))
+    x = dev(w.field0)
+    plan.solve_steps(x, w.steps)
+    assert sys_rel_err(host(x), ref, w.n) <= TOL
+    # the same steps without the graph, bitwise equal
+    y = dev(w.field0)
+    for _ in range(w.steps):
+        plan.solve(y, y)
+    assert torch.equal(x, y)
+    # and the adjoint of a partitioned plan still runs the thread-per-system adjoint
+    mu = plan.adjoint_solve(dev(w.field0))
+    mref = oracle.hyperdiff_steps(w.n, w.sigma, w.field0, 1)  # A is symmetric: A^-T f = A^-1 f
+    assert sys_rel_err(host(mu), mref, w.n) <= TOL

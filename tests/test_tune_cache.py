@@ -93,6 +93,7 @@ def test_f64_groups_take_the_rule_of_their_longest_system(L, tmp_path):
     st, h = create(L, ns, F64, cache)
     assert st == 0
     try:
+        assert L.pent_plan_set_option(h, _lib.PENT_OPT_PARTITION_ROWS, 0) == 0  # every group walked whole
         for s in range(64):
             assert config(L, h, s) == (8, 1)
         for s in range(64, 104):
@@ -152,5 +153,29 @@ def test_cache_text_round_trips_through_the_parser(L, tmp_path):
         if prec == F32:
             assert config(L, h, 1) == (8, 2560)   # 20000 / 8 = 2500 threads -> 5 CTAs of 16 warps
         else:
+            assert config(L, h, 1) == (0, 256)    # 20,000 rows: partitioned automatically
+            assert L.pent_plan_set_option(h, _lib.PENT_OPT_PARTITION_ROWS, 0) == 0
             assert config(L, h, 1) == (8, 1)      # the last rule extends to longer systems
         L.pent_plan_destroy(h)
+
+
+def test_long_groups_are_partitioned_automatically(L):
+    # 64 systems of 16,384 rows (two groups) and 1,000 of 100: 1.2 M rows, threshold 2,048 rows
+    ns = [16384] * 64 + [100] * 1000
+    st, h = create(L, ns, F64)
+    assert st == 0
+    try:
+        assert config(L, h, 0) == (0, 256)           # partitioned, 256-row chunks
+        assert config(L, h, 63) == (0, 256)
+        assert config(L, h, 64)[0] in (2, 4, 8)      # short systems keep the thread-per-system walk
+        assert L.pent_plan_set_option(h, _lib.PENT_OPT_PARTITION_ROWS, 0) == 0
+        assert config(L, h, 0)[0] in (2, 4, 8)
+        assert L.pent_plan_set_option(h, _lib.PENT_OPT_PARTITION_ROWS, 50) == 0
+        assert config(L, h, 64) == (0, 256)
+        assert L.pent_plan_set_option(h, _lib.PENT_OPT_PARTITION_ROWS, -2) == _lib.PENT_EINVAL
+    finally:
+        L.pent_plan_destroy(h)
+    # a uniform batch of 1024-row systems is never partitioned by default
+    st, h = create(L, [1024] * 4096, F64)
+    assert st == 0 and config(L, h, 0)[0] in (2, 4, 8)
+    L.pent_plan_destroy(h)
