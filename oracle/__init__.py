@@ -11,6 +11,10 @@ in Sec. 4.
 Only the tests, `__graft_entry__.smoke()` and the CPU-baseline leg of
 `bench.py` may import this package.  The CUDA library and its Python binding
 never import it; the two share no code.
+
+Periodic systems (Sec. 2.3) are solved by Navon's reduction as the paper
+states it: the last two unknowns from the 2x2 system of Eq. (first_two), then
+the rest from Eq. (solve).
 """
 from __future__ import annotations
 
@@ -80,6 +84,15 @@ def lib():
             L.po_hyperdiff_loss_grad.argtypes = [_i64, _i64, _dp, _i64, _dp, _dp, _dp, _dp, ctypes.c_int]
             L.po_hyperdiff_loss_grad.restype = ctypes.c_double
             L.po_hyperdiff_vjp.argtypes = [_i64, _i64, _dp, _i64, _dp, _dp, _dp, _dp, ctypes.c_int]
+            L.po_periodic_matvec.argtypes = [_i64] + [_dp] * 7
+            L.po_band_periodic_hyperdiff.argtypes = [_i64, ctypes.c_double] + [_dp] * 5
+            L.po_periodic_cn_rhs.argtypes = [_i64, ctypes.c_double, _dp, _dp]
+            L.po_periodic_solve.argtypes = [_i64] + [_dp] * 7
+            L.po_periodic_solve.restype = _i64
+            L.po_periodic_solve_batch.argtypes = [_i64, _i64] + [_dp] * 7 + [ctypes.c_int]
+            L.po_periodic_solve_batch.restype = _i64
+            L.po_periodic_steps.argtypes = [_i64, _i64, _dp, ctypes.c_int, _i64, ctypes.c_int, _dp, ctypes.c_int]
+            L.po_periodic_steps.restype = _i64
             _lib = L
     return _lib
 
@@ -275,3 +288,66 @@ def hyperdiff_vjp(sigma, T: int, c0, lambda_T, nthreads: int = 0):
     gs = np.zeros(batch)
     lib().po_hyperdiff_vjp(batch, n, _p(sigma), int(T), _p(c0), _p(lam), _p(gc), _p(gs), nthreads)
     return gc, gs
+
+
+# ----------------------------------------------------------------------------- periodic (Sec. 2.3)
+
+def band_periodic_hyperdiff(n: int, sigma: float):
+    """Cyclic band of Eq. (matrix_sys): a = e = sigma, b = d = -4 sigma, c = 1 + 6 sigma."""
+    out = [np.zeros(n) for _ in range(5)]
+    lib().po_band_periodic_hyperdiff(n, float(sigma), *[_p(o) for o in out])
+    return tuple(out)
+
+
+def periodic_matvec(band, x):
+    """y = A x for a cyclic band (column indices modulo n)."""
+    x = _f64(x)
+    y = np.zeros_like(x)
+    lib().po_periodic_matvec(x.shape[0], *[_p(_f64(b)) for b in band], _p(x), _p(y))
+    return y
+
+
+def periodic_cn_rhs(sigma: float, C):
+    """Crank-Nicolson right-hand side of Eq. (matrix_sys), periodic."""
+    C = _f64(C)
+    f = np.zeros_like(C)
+    lib().po_periodic_cn_rhs(C.shape[0], float(sigma), _p(C), _p(f))
+    return f
+
+
+def periodic_solve(band, f):
+    """x = A^{-1} f for one cyclic system by Navon's reduction; raises on a failed pivot."""
+    f = _f64(f)
+    x = np.zeros_like(f)
+    r = lib().po_periodic_solve(f.shape[0], *[_p(_f64(b)) for b in band], _p(f), _p(x))
+    if r >= 0:
+        raise ArithmeticError(f"periodic reduction failed at row {r}")
+    return x
+
+
+def periodic_solve_row(band, f) -> int:
+    """The failing row of the reduction (-1 if none)."""
+    f = _f64(f)
+    x = np.zeros_like(f)
+    return int(lib().po_periodic_solve(f.shape[0], *[_p(_f64(b)) for b in band], _p(f), _p(x)))
+
+
+def periodic_solve_batch(n: int, band, f, nthreads: int = 0):
+    """Cyclic solve for every system of a batch of n-row systems (system-major)."""
+    f = _f64(f)
+    x = np.zeros_like(f)
+    bad = lib().po_periodic_solve_batch(f.shape[0] // n, n, *[_p(_f64(b)) for b in band], _p(f), _p(x), nthreads)
+    if bad >= 0:
+        raise ArithmeticError(f"periodic reduction failed in system {bad}")
+    return x
+
+
+def periodic_steps(n: int, sigma, field0, steps: int, cn: bool = True, shared: bool = False, nthreads: int = 0):
+    """`steps` periodic hyperdiffusion steps (Crank-Nicolson or implicit Euler) on every system."""
+    field = np.array(field0, dtype=np.float64, copy=True)
+    sig = _f64(np.asarray(sigma, dtype=np.float64).reshape(-1))
+    bad = lib().po_periodic_steps(field.shape[0] // n, n, _p(sig), int(bool(shared)), int(steps), int(bool(cn)),
+                                  _p(field), nthreads)
+    if bad >= 0:
+        raise ArithmeticError(f"periodic reduction failed in system {bad}")
+    return field

@@ -502,3 +502,208 @@ void po_hyperdiff_vjp(int64_t batch, int64_t n, const double* sigma, int64_t T, 
     free(w);
   }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Periodic (cyclic) pentadiagonal systems: Navon's reduction (Sec. 2.3).    */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Cyclic band: row i reads a_i x_{i-2} + b_i x_{i-1} + c_i x_i + d_i x_{i+1}
+ * + e_i x_{i+2} with every column index taken modulo n (Eq. matrix_sys1: the
+ * corner entries a, b of the first rows and d, e of the last rows close the
+ * period).  n >= 5, so the five columns of a row are distinct.
+ */
+void po_periodic_matvec(int64_t n, const double* a, const double* b, const double* c, const double* d,
+                        const double* e, const double* x, double* y) {
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t im2 = (i + n - 2) % n, im1 = (i + n - 1) % n, ip1 = (i + 1) % n, ip2 = (i + 2) % n;
+    y[i] = a[i] * x[im2] + b[i] * x[im1] + c[i] * x[i] + d[i] * x[ip1] + e[i] * x[ip2];
+  }
+}
+
+/* The periodic hyperdiffusion matrix of Eq. (matrix_sys): a = e = sigma_x,
+ * b = d = -4 sigma_x, c = 1 + 6 sigma_x on every row. */
+void po_band_periodic_hyperdiff(int64_t n, double sigma, double* a, double* b, double* c, double* d, double* e) {
+  for (int64_t i = 0; i < n; ++i) {
+    a[i] = sigma;
+    b[i] = -4.0 * sigma;
+    c[i] = 1.0 + 6.0 * sigma;
+    d[i] = -4.0 * sigma;
+    e[i] = sigma;
+  }
+}
+
+/*
+ * Right-hand side of the Crank-Nicolson step, Eq. (matrix_sys):
+ *   f_i = -sigma C_{i-2} + 4 sigma C_{i-1} + (1 - 6 sigma) C_i + 4 sigma C_{i+1} - sigma C_{i+2},
+ * indices modulo n.
+ */
+void po_periodic_cn_rhs(int64_t n, double sigma, const double* C, double* f) {
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t im2 = (i + n - 2) % n, im1 = (i + n - 1) % n, ip1 = (i + 1) % n, ip2 = (i + 2) % n;
+    f[i] = -sigma * C[im2] + 4.0 * sigma * C[im1] + (1.0 - 6.0 * sigma) * C[i] + 4.0 * sigma * C[ip1] -
+           sigma * C[ip2];
+  }
+}
+
+/*
+ * Navon's reduction of a cyclic system, prepared once per matrix (Sec. 2.3:
+ * the 2x2 inverse of Eq. (first_two) and the products with E^{-1} are formed
+ * at the start and reused for every right-hand side).  With m = n - 2:
+ *   E  = the leading m x m block of A (the last two rows and columns removed),
+ *   k  = the m x 2 block of A in columns n-2, n-1 (paper: x_{N-1}, x_N),
+ *   h^T = the 2 x m block of A in rows n-2, n-1,
+ *   D  = the trailing 2 x 2 block [[c, d], [b, c]].
+ * Stored: the factors of E (Sec. 2.4), Q = E^{-1} k (two columns), and
+ * S^{-1} = (D - h^T E^{-1} k)^{-1}.
+ */
+typedef struct {
+  int64_t n, m;
+  double *al, *be, *ga, *de, *ep; /* factors of E */
+  double *k0, *k1;                /* columns of k */
+  double *h0, *h1;                /* columns of h: h^T's rows n-2, n-1 */
+  double *q0, *q1;                /* E^{-1} k */
+  double *g;                      /* solve scratch */
+  double Sinv[4];
+  double* mem;
+} po_navon;
+
+static void po_navon_free(po_navon* P) { free(P->mem); P->mem = NULL; }
+
+/* Returns -1, or the failing row: a row of E, or n-2 when the 2x2 Schur complement is singular. */
+static int64_t po_navon_prepare(po_navon* P, int64_t n, const double* a, const double* b, const double* c,
+                                const double* d, const double* e) {
+  const int64_t m = n - 2;
+  P->n = n;
+  P->m = m;
+  P->mem = (double*)calloc((size_t)16 * (size_t)m, sizeof(double));
+  double* w = P->mem;
+  double *Ea = w, *Eb = w + m, *Ec = w + 2 * m, *Ed = w + 3 * m, *Ee = w + 4 * m;
+  P->al = w + 5 * m; P->be = w + 6 * m; P->ga = w + 7 * m; P->de = w + 8 * m; P->ep = w + 9 * m;
+  P->k0 = w + 10 * m; P->k1 = w + 11 * m; P->h0 = w + 12 * m; P->h1 = w + 13 * m;
+  P->q0 = w + 14 * m; P->q1 = w + 15 * m;
+  /* E: rows 0..m-1 of A restricted to columns 0..m-1 (po_factor ignores the out-of-range entries) */
+  for (int64_t i = 0; i < m; ++i) { Ea[i] = a[i]; Eb[i] = b[i]; Ec[i] = c[i]; Ed[i] = d[i]; Ee[i] = e[i]; }
+  /* k: the entries of rows 0..m-1 in columns n-2 and n-1 */
+  P->k0[0] += a[0];          /* row 0, column (0 - 2) mod n = n-2 */
+  P->k1[0] += b[0];          /* row 0, column n-1 */
+  P->k1[1] += a[1];          /* row 1, column n-1 */
+  P->k0[m - 2] += e[m - 2];  /* row m-2, column m = n-2 */
+  P->k0[m - 1] += d[m - 1];  /* row m-1, column n-2 */
+  P->k1[m - 1] += e[m - 1];  /* row m-1, column n-1 */
+  /* h^T: the entries of rows n-2 and n-1 in columns 0..m-1 */
+  P->h0[m - 2] += a[n - 2];  /* row n-2, column n-4 = m-2 */
+  P->h0[m - 1] += b[n - 2];  /* row n-2, column m-1 */
+  P->h0[0] += e[n - 2];      /* row n-2, column n mod n = 0 */
+  P->h1[m - 1] += a[n - 1];  /* row n-1, column m-1 */
+  P->h1[0] += d[n - 1];      /* row n-1, column 0 */
+  P->h1[1] += e[n - 1];      /* row n-1, column 1 */
+  const int64_t r = po_factor(m, Ea, Eb, Ec, Ed, Ee, P->al, P->be, P->ga, P->de, P->ep);
+  if (r >= 0) return r;
+  P->g = Ea; /* the band copy is no longer needed: reuse it as scratch */
+  po_solve(m, P->al, P->be, P->ga, P->de, P->ep, P->k0, P->q0, P->g);
+  po_solve(m, P->al, P->be, P->ga, P->de, P->ep, P->k1, P->q1, P->g);
+  /* S = D - h^T E^{-1} k */
+  double s00 = c[n - 2], s01 = d[n - 2], s10 = b[n - 1], s11 = c[n - 1];
+  for (int64_t i = 0; i < m; ++i) {
+    s00 -= P->h0[i] * P->q0[i];
+    s01 -= P->h0[i] * P->q1[i];
+    s10 -= P->h1[i] * P->q0[i];
+    s11 -= P->h1[i] * P->q1[i];
+  }
+  const double det = s00 * s11 - s01 * s10;
+  if (!(det != 0.0) || !isfinite(det)) return n - 2;
+  P->Sinv[0] = s11 / det;
+  P->Sinv[1] = -s01 / det;
+  P->Sinv[2] = -s10 / det;
+  P->Sinv[3] = s00 / det;
+  return -1;
+}
+
+/* One right-hand side: Eq. (first_two) for x_{n-2}, x_{n-1}, then Eq. (solve) for the rest.
+ * x may alias f; y is scratch of m doubles. */
+static void po_navon_apply(const po_navon* P, const double* f, double* x, double* y) {
+  const int64_t n = P->n, m = P->m;
+  po_solve(m, P->al, P->be, P->ga, P->de, P->ep, f, y, P->g); /* E^{-1} f-hat */
+  double t0 = f[n - 2], t1 = f[n - 1];
+  for (int64_t i = 0; i < m; ++i) {
+    t0 -= P->h0[i] * y[i];
+    t1 -= P->h1[i] * y[i];
+  }
+  const double xa = P->Sinv[0] * t0 + P->Sinv[1] * t1;
+  const double xb = P->Sinv[2] * t0 + P->Sinv[3] * t1;
+  for (int64_t i = 0; i < m; ++i) y[i] = f[i] - P->k0[i] * xa - P->k1[i] * xb; /* f-hat - k x_tail */
+  po_solve(m, P->al, P->be, P->ga, P->de, P->ep, y, x, P->g);
+  x[n - 2] = xa;
+  x[n - 1] = xb;
+}
+
+/* Solve one cyclic system A x = f (n >= 5).  Returns -1 or the failing row. */
+int64_t po_periodic_solve(int64_t n, const double* a, const double* b, const double* c, const double* d,
+                          const double* e, const double* f, double* x) {
+  po_navon P;
+  const int64_t r = po_navon_prepare(&P, n, a, b, c, d, e);
+  if (r < 0) {
+    double* y = (double*)malloc((size_t)(n - 2) * sizeof(double));
+    po_navon_apply(&P, f, x, y);
+    free(y);
+  }
+  po_navon_free(&P);
+  return r;
+}
+
+/* Cyclic solve for every system of a batch of n-row systems (system-major). */
+int64_t po_periodic_solve_batch(int64_t batch, int64_t n, const double* a, const double* b, const double* c,
+                                const double* d, const double* e, const double* f, double* x, int nthreads) {
+  int64_t bad_sys = -1;
+  set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t s = 0; s < batch; ++s) {
+    const int64_t o = s * n;
+    if (po_periodic_solve(n, a + o, b + o, c + o, d + o, e + o, f + o, x + o) >= 0) {
+#pragma omp critical
+      {
+        if (bad_sys < 0 || s < bad_sys) bad_sys = s;
+      }
+    }
+  }
+  return bad_sys;
+}
+
+/*
+ * `steps` periodic hyperdiffusion steps on every system, in place: each step
+ * solves A C^{k+1} = f with A the matrix of Eq. (matrix_sys) and
+ *   cn != 0: f = the Crank-Nicolson right-hand side of Eq. (matrix_sys),
+ *   cn == 0: f = C^k (implicit Euler with the same matrix).
+ * sigma: `batch` values (the paper's sigma_x = dt / (2 dx^4) for Crank-Nicolson),
+ * or one shared value when shared != 0.  The reduction is prepared once per
+ * system and reused for every step (Sec. 2.3).
+ */
+int64_t po_periodic_steps(int64_t batch, int64_t n, const double* sigma, int shared, int64_t steps, int cn,
+                          double* field, int nthreads) {
+  int64_t bad_sys = -1;
+  set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t s = 0; s < batch; ++s) {
+    const double sg = shared ? sigma[0] : sigma[s];
+    double* w = (double*)malloc((size_t)7 * (size_t)n * sizeof(double));
+    double *a = w, *b = w + n, *c = w + 2 * n, *d = w + 3 * n, *e = w + 4 * n, *f = w + 5 * n, *y = w + 6 * n;
+    po_band_periodic_hyperdiff(n, sg, a, b, c, d, e);
+    po_navon P;
+    if (po_navon_prepare(&P, n, a, b, c, d, e) >= 0) {
+#pragma omp critical
+      {
+        if (bad_sys < 0 || s < bad_sys) bad_sys = s;
+      }
+    } else {
+      double* C = field + s * n;
+      for (int64_t k = 0; k < steps; ++k) {
+        if (cn) po_periodic_cn_rhs(n, sg, C, f); else memcpy(f, C, (size_t)n * sizeof(double));
+        po_navon_apply(&P, f, C, y);
+      }
+    }
+    po_navon_free(&P);
+    free(w);
+  }
+  return bad_sys;
+}
