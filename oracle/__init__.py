@@ -93,6 +93,10 @@ def lib():
             L.po_periodic_solve_batch.restype = _i64
             L.po_periodic_steps.argtypes = [_i64, _i64, _dp, ctypes.c_int, _i64, ctypes.c_int, _dp, ctypes.c_int]
             L.po_periodic_steps.restype = _i64
+            L.po_explicit_rhs.argtypes = [_i64, ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp]
+            L.po_explicit_steps.argtypes = [_i64, _ip, ctypes.c_int, _dp, _dp, _dp, ctypes.c_int, _i64, _dp,
+                                            ctypes.c_int]
+            L.po_explicit_steps.restype = _i64
             _lib = L
     return _lib
 
@@ -350,4 +354,32 @@ def periodic_steps(n: int, sigma, field0, steps: int, cn: bool = True, shared: b
                                   _p(field), nthreads)
     if bad >= 0:
         raise ArithmeticError(f"periodic reduction failed in system {bad}")
+    return field
+
+
+# ----------------------------------------------------------------------------- steps with an explicit part
+
+def explicit_rhs(C, mu: float, nu: float, periodic: bool = False):
+    """f = C + mu D2(C^3 - C) - nu D4 C on the no-flux (reflected) or periodic grid."""
+    C = _f64(C)
+    f = np.zeros_like(C)
+    u = np.zeros_like(C)
+    lib().po_explicit_rhs(C.shape[0], int(bool(periodic)), float(mu), float(nu), _p(C), _p(f), _p(u))
+    return f
+
+
+def explicit_steps(n_per_system, sigma, mu, nu, field0, steps: int, periodic: bool = False, shared: bool = False,
+                   nthreads: int = 0):
+    """`steps` steps (I + sigma_s D4) C^{k+1} = C^k + mu_s D2(C^3 - C)^k - nu_s D4 C^k on every system.
+    mu or nu may be None (zero)."""
+    off = offsets(n_per_system)
+    field = np.array(field0, dtype=np.float64, copy=True)
+    sig = _f64(np.asarray(sigma, dtype=np.float64).reshape(-1))
+    m_ = None if mu is None else _f64(np.asarray(mu, dtype=np.float64).reshape(-1))
+    n_ = None if nu is None else _f64(np.asarray(nu, dtype=np.float64).reshape(-1))
+    bad = lib().po_explicit_steps(len(off) - 1, _pi(off), int(bool(periodic)), _p(sig),
+                                  _p(m_) if m_ is not None else None, _p(n_) if n_ is not None else None,
+                                  int(bool(shared)), int(steps), _p(field), nthreads)
+    if bad >= 0:
+        raise ArithmeticError(f"factorisation failed in system {bad}")
     return field

@@ -707,3 +707,87 @@ int64_t po_periodic_steps(int64_t batch, int64_t n, const double* sigma, int sha
   }
   return bad_sys;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Semi-implicit steps with an explicit part (Sec. 2.1 and 2.2).             */
+/* ------------------------------------------------------------------------ */
+
+/* Index j of an n-cell grid mapped into 0..n-1: by even reflection about the
+ * cell-centred no-flux walls (periodic == 0), or modulo n (periodic != 0). */
+static int64_t po_wrap(int64_t j, int64_t n, int periodic) {
+  if (periodic) return ((j % n) + n) % n;
+  while (j < 0 || j >= n) j = (j < 0) ? (-1 - j) : (2 * n - 1 - j);
+  return j;
+}
+
+/*
+ * Explicit part of one step on an n-cell grid:
+ *   f_i = C_i + mu (D2 (C^3 - C))_i - nu (D4 C)_i,
+ * with the centred differences D2 = [1, -2, 1] and D4 = [1, -4, 6, -4, 1]
+ * (Sec. 2.2) on the reflected (no-flux) or periodic grid.  mu = D dt / dx^2,
+ * nu = 0 gives the right-hand side of the semi-implicit Cahn-Hilliard step of
+ * Eq. (temporal); mu = 0, nu = sigma_x the Crank-Nicolson right-hand side of
+ * Eq. (1d_hyper_scheme).  `u` is scratch of n doubles.
+ */
+void po_explicit_rhs(int64_t n, int periodic, double mu, double nu, const double* C, double* f, double* u) {
+  for (int64_t i = 0; i < n; ++i) u[i] = C[i] * C[i] * C[i] - C[i];
+  for (int64_t i = 0; i < n; ++i) {
+    const double d2u = u[po_wrap(i - 1, n, periodic)] - 2.0 * u[i] + u[po_wrap(i + 1, n, periodic)];
+    const double d4c = C[po_wrap(i - 2, n, periodic)] - 4.0 * C[po_wrap(i - 1, n, periodic)] + 6.0 * C[i] -
+                       4.0 * C[po_wrap(i + 1, n, periodic)] + C[po_wrap(i + 2, n, periodic)];
+    f[i] = C[i] + mu * d2u - nu * d4c;
+  }
+}
+
+/*
+ * `steps` steps (I + sigma_s D4) C^{k+1} = f(C^k) on every system, in place on
+ * `field` (system-major), f the explicit part above with per-system mu_s, nu_s.
+ * No-flux grid (periodic == 0): systems of sizes off[s+1] - off[s], the band
+ * of po_band_hyperdiff, factored once (Sec. 2.4, 2.6).  Periodic grid: the
+ * matrix of Eq. (matrix_sys) solved by Navon's reduction (Sec. 2.3).
+ * sigma, mu, nu: `batch` values each, or one shared value when shared != 0;
+ * mu or nu may be NULL for zero.
+ */
+int64_t po_explicit_steps(int64_t batch, const int64_t* off, int periodic, const double* sigma, const double* mu,
+                          const double* nu, int shared, int64_t steps, double* field, int nthreads) {
+  int64_t bad_sys = -1;
+  set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t s = 0; s < batch; ++s) {
+    const int64_t o = off[s], n = off[s + 1] - off[s];
+    const int64_t k = shared ? 0 : s;
+    const double sg = sigma[k], m_ = mu ? mu[k] : 0.0, n_ = nu ? nu[k] : 0.0;
+    double* w = (double*)malloc((size_t)13 * (size_t)(n > 0 ? n : 1) * sizeof(double));
+    double *a = w, *b = w + n, *c = w + 2 * n, *d = w + 3 * n, *e = w + 4 * n;
+    double *al = w + 5 * n, *be = w + 6 * n, *ga = w + 7 * n, *de = w + 8 * n, *ep = w + 9 * n;
+    double *g = w + 10 * n, *f = w + 11 * n, *u = w + 12 * n;
+    double* C = field + o;
+    int ok;
+    po_navon P;
+    P.mem = NULL;
+    if (periodic) {
+      po_band_periodic_hyperdiff(n, sg, a, b, c, d, e);
+      ok = po_navon_prepare(&P, n, a, b, c, d, e) < 0;
+    } else {
+      po_band_hyperdiff(n, sg, a, b, c, d, e);
+      ok = po_factor(n, a, b, c, d, e, al, be, ga, de, ep) < 0;
+    }
+    if (!ok) {
+#pragma omp critical
+      {
+        if (bad_sys < 0 || s < bad_sys) bad_sys = s;
+      }
+    } else {
+      for (int64_t t = 0; t < steps; ++t) {
+        po_explicit_rhs(n, periodic, m_, n_, C, f, u);
+        if (periodic)
+          po_navon_apply(&P, f, C, u);
+        else
+          po_solve(n, al, be, ga, de, ep, f, C, g);
+      }
+    }
+    if (P.mem) po_navon_free(&P);
+    free(w);
+  }
+  return bad_sys;
+}
