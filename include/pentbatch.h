@@ -129,11 +129,23 @@ enum {
   PENT_OPT_UNROLL = 5,             /* PENT_F64: rows loaded ahead of the arithmetic: 2, 4 or 8 (default 4) */
   PENT_OPT_ROWS_PER_THREAD = 6,    /* PENT_F32_REFINE: rows per thread, 4 or 8, or 0 for the automatic choice
                                       (before pent_plan_bind, like PENT_OPT_THREADS_PER_SYSTEM) */
-  PENT_OPT_PARTITION_ROWS = 7      /* PENT_F64 per-system matrices: groups of 32 systems whose longest system
+  PENT_OPT_PARTITION_ROWS = 7,     /* PENT_F64 per-system matrices: groups of 32 systems whose longest system
                                       has at least this many rows are solved in chunks of 256 rows joined by
                                       scans, instead of one serial walk per system; 0 never, -1 automatic
                                       (the default: where a walk would outlast the whole batch's streaming
                                       time, and at least 2048 rows).  Before pent_plan_bind. */
+  PENT_OPT_PERIODIC = 8            /* 1: the systems are cyclic (Sec. 2.3, Eq. matrix_sys1): row i reads
+                                      x_{i-2} .. x_{i+2} with column indices modulo n, so the first two rows
+                                      reach the last two columns and vice versa.  PENT_F64 plans of uniform
+                                      n >= 5 only, before pent_plan_bind.  Solved by Navon's reduction as the
+                                      paper describes it: the last two unknowns from a 2 x 2 system
+                                      (Eq. first_two), the other n - 2 from the pentadiagonal E that remains
+                                      (Eq. solve); everything that depends on the matrix alone (factors of E,
+                                      E^{-T} h, L^{-1} k, the 2 x 2 inverse) is formed by the factorisation,
+                                      so each solve is one forward and one back sweep.  pent_factor_batch takes
+                                      the cyclic band; pent_factor_hyperdiff builds Eq. (matrix_sys) with
+                                      sigma_x = sigma.  Adjoint, sigma-gradient and ADI calls return
+                                      PENT_EINVAL for periodic plans. */
 };
 pent_status pent_plan_set_option(pent_plan* plan, int key, int64_t value);
 pent_status pent_plan_get_option(const pent_plan* plan, int key, int64_t* value);
@@ -183,6 +195,42 @@ pent_status pent_solve_batch(pent_plan* plan, const double* f, double* x, int ma
  * therefore not capture-safe; later calls are single graph launches.
  */
 pent_status pent_solve_steps(pent_plan* plan, double* x, int64_t nsteps, int max_refine);
+
+/*
+ * `nsteps` semi-implicit time steps in place on C (device, system-major), each
+ *   A_s C^{k+1} = f,   f_i = C_i + mu_s (D2 (C^3 - C))_i - nu_s (D4 C)_i,
+ * with f assembled inside the solve kernel from the old field (it is never
+ * written to memory).  D2 and D4 are the centred second and fourth differences
+ * of Sec. 2.2 on the plan's grid: periodic for PENT_OPT_PERIODIC plans, else
+ * the cell-centred no-flux reflection of pent_factor_hyperdiff.  With
+ * A_s = I + sigma_s D4:
+ *   mu = D dt/dx^2, nu = 0, sigma = gamma D dt/dx^4: the semi-implicit
+ *     Cahn-Hilliard step of Sec. 2.1 (Eq. temporal), one parameter set per
+ *     system as in the parameter studies of Sec. 2.1;
+ *   mu = 0, nu = sigma = dt/(2 dx^4): the Crank-Nicolson hyperdiffusion step of
+ *     Sec. 2.2 (Eq. 1d_hyper_scheme).
+ * d_mu, d_nu: device arrays of `batch` doubles (one when the matrix is
+ * shared), or NULL for zero.  Several steps are captured once into a CUDA
+ * graph (keyed by C, nsteps, d_mu, d_nu) and replayed.  PENT_F64 plans whose
+ * systems are periodic, or per-system no-flux plans factored by
+ * pent_factor_hyperdiff; otherwise PENT_EINVAL.  max_refine must be 0.
+ */
+pent_status pent_step_batch(pent_plan* plan, const double* d_mu, const double* d_nu, double* C, int64_t nsteps,
+                            int max_refine);
+
+/*
+ * Re-assemble, re-factor and solve in one call: A_s = I + sigma_s D4 (as
+ * pent_factor_hyperdiff) from a new d_sigma, then x_s = A_s^{-1} f_s.  This is
+ * the paper's "Rewrite" use (Sec. 3), for matrices that change every step
+ * (adaptive dt, varying coefficients).  For per-system matrices whose groups
+ * are walked by one thread per system, the factorisation runs inside the
+ * forward sweep of the same kernel; shared matrices and plans with
+ * partitioned groups factor first and then solve.  The plan is left factored
+ * with the new sigma (later pent_solve_batch calls reuse it); the info word is
+ * reset.  f, x: as pent_solve_batch (x may alias f).  PENT_F64, non-periodic
+ * plans only.
+ */
+pent_status pent_refactor_solve_hyperdiff(pent_plan* plan, const double* d_sigma, const double* f, double* x);
 
 /*
  * Adjoint solve y_s = A_s^{-T} f_s from the stored factors: A^T = R^T L^T, so

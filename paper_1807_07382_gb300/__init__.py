@@ -17,7 +17,7 @@ from typing import Optional, Sequence
 
 from . import _lib
 from ._lib import (PENT_ENOCONV, PENT_ESINGULAR, PENT_F32_REFINE, PENT_F64, PENT_OK, PENT_OPT_BLOCK_WARPS,
-                   PENT_OPT_PARTITION_ROWS, PENT_OPT_REFINE_TOL_LOG2, PENT_OPT_RESIDUAL, PENT_OPT_ROWS_PER_THREAD,
+                   PENT_OPT_PARTITION_ROWS, PENT_OPT_PERIODIC, PENT_OPT_REFINE_TOL_LOG2, PENT_OPT_RESIDUAL, PENT_OPT_ROWS_PER_THREAD,
                    PENT_OPT_THREADS_PER_SYSTEM,
                    PENT_OPT_UNROLL, PENT_RESIDUAL_F64,
                    PENT_RESIDUAL_FF, PentError, check)
@@ -61,10 +61,12 @@ class Plan:
     batch:     number of systems (required when n is an int).
     shared:    all systems share one matrix (band / sigma describe one system).
     precision: PENT_F64 or PENT_F32_REFINE.
+    periodic:  cyclic systems (Sec. 2.3), solved by Navon's reduction (FP64, uniform n >= 5).
     """
 
     def __init__(self, n, batch: Optional[int] = None, shared: bool = False, precision: int = PENT_F64,
-                 device=None, stream=None, tune_cache: Optional[str] = None, options: Optional[dict] = None):
+                 device=None, stream=None, tune_cache: Optional[str] = None, options: Optional[dict] = None,
+                 periodic: bool = False):
         torch = _torch()
         L = _lib.load()
         self._L = L
@@ -88,7 +90,11 @@ class Plan:
         self.rows = sum(self.n)
         check(L.pent_plan_create(ctypes.byref(self._h), self.batch, nptr, n_uniform, int(self.shared),
                                  self.precision, tune_cache.encode() if tune_cache else None), "pent_plan_create")
-        for key, value in (options or {}).items():  # layout options must precede pent_plan_bind
+        options = dict(options or {})
+        if periodic:
+            options[PENT_OPT_PERIODIC] = 1
+        self.periodic = bool(periodic)
+        for key, value in options.items():  # layout options must precede pent_plan_bind
             check(L.pent_plan_set_option(self._h, int(key), int(value)), "pent_plan_set_option")
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         nbytes = int(L.pent_plan_workspace_bytes(self._h))
@@ -146,6 +152,18 @@ class Plan:
         self._sigma_ref = sigma
         check(self._L.pent_factor_hyperdiff(self._h, _dev_ptr(sigma, "sigma", torch.float64)), "pent_factor_hyperdiff")
 
+    def refactor_solve(self, sigma, f, x=None):
+        """Factor A_s = I + sigma_s D4 from a new sigma and solve A_s x = f in one call (the matrix
+        changes every step); the plan stays factored with the new sigma."""
+        torch = _torch()
+        if x is None:
+            x = torch.empty_like(f)
+        self._sigma_ref = sigma
+        check(self._L.pent_refactor_solve_hyperdiff(self._h, _dev_ptr(sigma, "sigma", torch.float64),
+                                                    _dev_ptr(f, "f", torch.float64), _dev_ptr(x, "x", torch.float64)),
+              "pent_refactor_solve_hyperdiff")
+        return x
+
     # -- solves
     def solve(self, f, x=None, max_refine: int = 2):
         """x_s = A_s^{-1} f_s; x may be f (in place)."""
@@ -177,6 +195,19 @@ class Plan:
         check(self._L.pent_solve_steps(self._h, _dev_ptr(x, "x", torch.float64), int(nsteps), int(max_refine)),
               "pent_solve_steps")
         return x
+
+    def step(self, C, mu=None, nu=None, nsteps: int = 1):
+        """nsteps semi-implicit steps in place: A_s C <- C + mu_s D2(C^3 - C) - nu_s D4 C, the right-hand
+        side assembled inside the solve kernel (Cahn-Hilliard: mu = D dt/dx^2; Crank-Nicolson
+        hyperdiffusion: nu = sigma).  mu, nu: device float64 tensors of one value per system (one when
+        the matrix is shared) or None for zero.  Several steps run as one CUDA graph."""
+        torch = _torch()
+        mp = _dev_ptr(mu, "mu", torch.float64) if mu is not None else None
+        np_ = _dev_ptr(nu, "nu", torch.float64) if nu is not None else None
+        self._step_refs = (mu, nu)  # graphs keep the pointers
+        check(self._L.pent_step_batch(self._h, mp, np_, _dev_ptr(C, "C", torch.float64), int(nsteps), 0),
+              "pent_step_batch")
+        return C
 
     def adjoint_solve(self, f, x=None):
         """y_s = A_s^{-T} f_s from the stored factors."""

@@ -30,6 +30,7 @@ PENT_OPT_REFINE_TOL_LOG2 = 4
 PENT_OPT_UNROLL = 5
 PENT_OPT_ROWS_PER_THREAD = 6
 PENT_OPT_PARTITION_ROWS = 7
+PENT_OPT_PERIODIC = 8
 
 # every symbol the header declares, with (restype, argtypes)
 _vp = ctypes.c_void_p
@@ -50,6 +51,8 @@ SIGNATURES = {
     "pent_factor_hyperdiff": (_int, [_vp, _vp]),
     "pent_solve_batch": (_int, [_vp, _vp, _vp, _int]),
     "pent_solve_steps": (_int, [_vp, _vp, _i64, _int]),
+    "pent_step_batch": (_int, [_vp, _vp, _vp, _vp, _i64, _int]),
+    "pent_refactor_solve_hyperdiff": (_int, [_vp, _vp, _vp, _vp]),
     "pent_adjoint_solve_batch": (_int, [_vp, _vp, _vp, _int]),
     "pent_hyperdiff_sigma_grad": (_int, [_vp, _vp, _vp, _vp]),
     "adi_step_2d": (_int, [_vp, _vp, _vp, _i64, _i64, _dbl, _dbl, _dbl, _int]),

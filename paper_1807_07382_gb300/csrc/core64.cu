@@ -381,6 +381,317 @@ __global__ void __launch_bounds__(128) k_solve64_pair(DevPlan P, F64Factors F, c
   }
 }
 
+// ---- time steps with the right-hand side assembled in the solve ----
+//
+// One semi-implicit step per call on the field C (in place), for hyperdiffusion
+// records (A_s = I + sigma_s D4, no-flux walls):
+//   A_s C^{k+1} = f,  f_i = C_i + mu_s (D2 (C^3 - C))_i - nu_s (D4 C)_i,
+// D2 and D4 the second and fourth differences with the same cell-centred
+// reflection as the band (C_{-1} = C_0, C_{-2} = C_1, mirrored at the right).
+// mu = D dt / dx^2, nu = 0 is the semi-implicit Cahn-Hilliard step of
+// Sec. 2.1 (Eq. temporal) on the no-flux grid; mu = 0, nu = sigma gives a
+// Crank-Nicolson step of Sec. 2.2 (Eq. 1d_hyper_scheme).  The forward sweep
+// reads each C pair once, builds f from a window of three pairs and never
+// stores it: the explicit part costs no memory traffic.
+
+// f of rows base+2 and base+3 from v[k] = C_{base+k}, k = 0..5.
+__device__ __forceinline__ void step_rhs_pair(const double (&v)[6], double mu, double nu, double& fa, double& fb) {
+  const double d4a = fma(6.0, v[2], fma(-4.0, v[1] + v[3], v[0] + v[4]));
+  const double d4b = fma(6.0, v[3], fma(-4.0, v[2] + v[4], v[1] + v[5]));
+  fa = fma(-nu, d4a, v[2]);
+  fb = fma(-nu, d4b, v[3]);
+  if (mu != 0.0) {
+    const double u1 = fma(v[1] * v[1], v[1], -v[1]), u2 = fma(v[2] * v[2], v[2], -v[2]);
+    const double u3 = fma(v[3] * v[3], v[3], -v[3]), u4 = fma(v[4] * v[4], v[4], -v[4]);
+    fa = fma(mu, fma(-2.0, u2, u1 + u3), fa);
+    fb = fma(mu, fma(-2.0, u3, u2 + u4), fb);
+  }
+}
+
+// Window v[k] = C_{2q-2+k} of a lane whose system has n rows, with the rows
+// outside 0..n-1 replaced by their reflections (row n -> n-1, n+1 -> n-2,
+// -1 -> 0, -2 -> 1; a one-row system is constant).  Rows past n+1 are only
+// read for padding rows, whose f is discarded.
+__device__ __forceinline__ void step_reflect(double (&v)[6], int64_t q, int64_t n) {
+  const int64_t base = 2 * q - 2;
+  if (n == 1) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v[k] = v[2];
+    return;
+  }
+  if (base + 5 >= n) {
+    double cn1 = 0.0, cn2 = 0.0;  // C_{n-1}, C_{n-2} (inside the window whenever a row < n needs them)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      if (base + k == n - 1) cn1 = v[k];
+      if (base + k == n - 2) cn2 = v[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const int64_t j = base + k;
+      if (j >= n) v[k] = (j == n) ? cn1 : ((j == n + 1) ? cn2 : 0.0);
+    }
+  }
+  if (q == 0) {
+    v[0] = v[3];
+    v[1] = v[2];
+  }
+}
+
+template <int U2>
+__global__ void __launch_bounds__(128) k_step64_pair(DevPlan P, F64Factors F, const double* __restrict__ mu_s,
+                                                     const double* __restrict__ nu_s, double* C,
+                                                     double* __restrict__ gscr, int64_t kbeg, int64_t kend) {
+  const int64_t k = kbeg + (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kWarp;
+  if (k >= kend) return;
+  const int lane = threadIdx.x & (kWarp - 1);
+  const Lane L = lane_setup<false>(P, k, lane);
+  const double2* __restrict__ fwd = reinterpret_cast<const double2*>(F.fwd);
+  const double2* __restrict__ bwd = reinterpret_cast<const double2*>(F.bwd);
+  double2* __restrict__ g2s = reinterpret_cast<double2*>(gscr);
+  const int64_t np = L.Lg >> 1;
+  const int64_t P0 = L.R0 >> 1;
+  const bool cvec = ((L.fo & 1) == 0) && ((((uintptr_t)C) & 15) == 0);
+  const double sg = (L.s >= 0) ? F.sig[L.s] : 0.0;
+  const double mu = (mu_s && L.s >= 0) ? mu_s[L.s] : 0.0;
+  const double nu = (nu_s && L.s >= 0) ? nu_s[L.s] : 0.0;
+
+  // ---- forward: L g = f, f assembled from C ----
+  double2 ca[U2], cb[U2], cc[U2];
+  double2 na[U2], nb[U2], nc[U2];
+  auto load_f = [&](int64_t q0, double2* A, double2* B, double2* Cv) {
+#pragma unroll
+    for (int u = 0; u < U2; ++u) {
+      const int64_t q = q0 + u;
+      A[u] = make_double2(0.0, 0.0);
+      B[u] = A[u];
+      Cv[u] = A[u];
+      if (q < np) {
+        const double2* rec = fwd + ((P0 + q) * 2) * kWarp + lane;
+        A[u] = __ldg(rec);
+        B[u] = __ldg(rec + kWarp);
+        const int64_t r = 2 * q;
+        if (cvec && r + 1 < L.n) {
+          Cv[u] = *reinterpret_cast<const double2*>(C + L.fo + r);
+        } else {
+          Cv[u].x = (r < L.n) ? C[L.fo + r] : 0.0;
+          Cv[u].y = (r + 1 < L.n) ? C[L.fo + r + 1] : 0.0;
+        }
+      }
+    }
+  };
+  double g1 = 0.0, g2 = 0.0;
+  double2 prev = make_double2(0.0, 0.0);  // C pair q - 1
+  load_f(0, ca, cb, cc);
+  for (int64_t q0 = 0; q0 < np; q0 += U2) {
+    const bool more = q0 + U2 < np;
+    if (more) load_f(q0 + U2, na, nb, nc);
+#pragma unroll
+    for (int u = 0; u < U2; ++u) {
+      const int64_t q = q0 + u;
+      if (q < np) {
+        const double2 nx = (u + 1 < U2) ? cc[u + 1] : (more ? nc[0] : make_double2(0.0, 0.0));
+        double v[6] = {prev.x, prev.y, cc[u].x, cc[u].y, nx.x, nx.y};
+        if (q == 0 || 2 * q + 3 >= L.n) step_reflect(v, q, L.n);
+        double fa, fb;
+        step_rhs_pair(v, mu, nu, fa, fb);
+        if (2 * q >= L.n) fa = 0.0;
+        if (2 * q + 1 >= L.n) fb = 0.0;
+        const double ga = ca[u].x * fma(-cb[u].x, g1, fma(-sg, g2, fa));
+        const double gb = ca[u].y * fma(-cb[u].y, ga, fma(-sg, g1, fb));
+        g2s[(P0 + q) * kWarp + lane] = make_double2(ga, gb);
+        g2 = ga;
+        g1 = gb;
+        prev = cc[u];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U2; ++u) {
+      ca[u] = na[u];
+      cb[u] = nb[u];
+      cc[u] = nc[u];
+    }
+  }
+
+  // ---- back: R x = g, x into C ----
+  double2 cg[U2], cd[U2], cG[U2];
+  double2 ng[U2], nd[U2], nG[U2];
+  auto load_b = [&](int64_t q0, double2* Ga, double2* De, double2* Gv) {
+#pragma unroll
+    for (int u = 0; u < U2; ++u) {
+      const int64_t q = q0 - u;
+      if (q >= 0) {
+        const double2* rec = bwd + ((P0 + q) * 2) * kWarp + lane;
+        Ga[u] = __ldg(rec);
+        De[u] = __ldg(rec + kWarp);
+        Gv[u] = g2s[(P0 + q) * kWarp + lane];
+      }
+    }
+  };
+  double x1 = 0.0, x2 = 0.0;
+  load_b(np - 1, cg, cd, cG);
+  for (int64_t q0 = np - 1; q0 >= 0; q0 -= U2) {
+    if (q0 - U2 >= 0) load_b(q0 - U2, ng, nd, nG);
+#pragma unroll
+    for (int u = 0; u < U2; ++u) {
+      const int64_t q = q0 - u;
+      if (q >= 0) {
+        const double xb = fma(-cg[u].y, x1, fma(-cd[u].y, x2, cG[u].y));
+        const double xa = fma(-cg[u].x, xb, fma(-cd[u].x, x1, cG[u].x));
+        const int64_t r = 2 * q;
+        if (cvec && r + 1 < L.n) {
+          *reinterpret_cast<double2*>(C + L.fo + r) = make_double2(xa, xb);
+        } else {
+          if (r < L.n) C[L.fo + r] = xa;
+          if (r + 1 < L.n) C[L.fo + r + 1] = xb;
+        }
+        x2 = xb;
+        x1 = xa;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U2; ++u) {
+      cg[u] = ng[u];
+      cd[u] = nd[u];
+      cG[u] = nG[u];
+    }
+  }
+}
+
+// The same right-hand side written out (for the partitioned groups, whose
+// chunked solve reads f from memory): one CTA per system of groups [kbeg, kend).
+__global__ void __launch_bounds__(256) k_step_rhs(DevPlan P, const double* __restrict__ mu_s,
+                                                  const double* __restrict__ nu_s, const double* __restrict__ C,
+                                                  double* __restrict__ f, int64_t kbeg) {
+  const int64_t q = kbeg * kWarp + blockIdx.x;
+  const int32_t s = P.perm[q];
+  if (s < 0) return;
+  const int64_t n = P.n[s], o = P.off[s];
+  const double mu = mu_s ? mu_s[s] : 0.0, nu = nu_s ? nu_s[s] : 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    double v[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      int64_t j = i + k - 2;
+      while (j < 0 || j >= n) j = (j < 0) ? (-1 - j) : (2 * n - 1 - j);
+      v[k] = C[o + j];
+    }
+    const double d4 = fma(6.0, v[2], fma(-4.0, v[1] + v[3], v[0] + v[4]));
+    double fi = fma(-nu, d4, v[2]);
+    if (mu != 0.0) {
+      const double u1 = fma(v[1] * v[1], v[1], -v[1]), u2 = fma(v[2] * v[2], v[2], -v[2]);
+      const double u3 = fma(v[3] * v[3], v[3], -v[3]);
+      fi = fma(mu, fma(-2.0, u2, u1 + u3), fi);
+    }
+    f[o + i] = fi;
+  }
+}
+
+// ---- refactor and solve in one pass ----
+//
+// The paper's "Rewrite" use (Sec. 3): the matrix changes every call, so each
+// call re-assembles A_s = I + sigma_s D4 from a new sigma_s and factors it
+// (Sec. 2.4, factorisation steps) in the same sweep that runs the forward
+// substitution, instead of a factor kernel followed by a solve that reads the
+// factors back.  The records are still written (row pairs, hyperdiffusion
+// form), so the plan is left factored with the new sigma for later solves.
+__global__ void __launch_bounds__(128) k_refactor_solve64(DevPlan P, F64Factors F, const double* __restrict__ sigma,
+                                                          const double* f, double* x, double* __restrict__ gscr,
+                                                          int64_t kbeg, int64_t kend) {
+  const int64_t k = kbeg + (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kWarp;
+  if (k >= kend) return;
+  const int lane = threadIdx.x & (kWarp - 1);
+  const Lane L = lane_setup<false>(P, k, lane);
+  double2* __restrict__ fwd = reinterpret_cast<double2*>(F.fwd);
+  double2* __restrict__ bwd = reinterpret_cast<double2*>(F.bwd);
+  double2* __restrict__ g2s = reinterpret_cast<double2*>(gscr);
+  double* __restrict__ sig = const_cast<double*>(F.sig);
+  const int64_t np = L.Lg >> 1;
+  const int64_t P0 = L.R0 >> 1;
+  const bool fvec = ((L.fo & 1) == 0) && ((((uintptr_t)f) & 15) == 0);
+  const bool xvec = ((L.fo & 1) == 0) && ((((uintptr_t)x) & 15) == 0);
+  const double sg = (L.s >= 0) ? sigma[L.s] : 0.0;
+  if (L.s >= 0) sig[L.s] = sg;  // the plan's copy of sigma (epsilon of the records)
+
+  // ---- factor + forward: L g = f ----
+  double gam2 = 0.0, del2 = 0.0, gam1 = 0.0, del1 = 0.0;
+  bool failed = L.s < 0;
+  double g1 = 0.0, g2 = 0.0;
+  for (int64_t q = 0; q < np; ++q) {
+    double fv[2];
+    const int64_t r0 = 2 * q;
+    if (fvec && r0 + 1 < L.n) {
+      const double2 t = *reinterpret_cast<const double2*>(f + L.fo + r0);
+      fv[0] = t.x;
+      fv[1] = t.y;
+    } else {
+      fv[0] = (r0 < L.n) ? f[L.fo + r0] : 0.0;
+      fv[1] = (r0 + 1 < L.n) ? f[L.fo + r0 + 1] : 0.0;
+    }
+    double ia[2], bt[2], ga[2], de[2], gg[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t r = r0 + h;
+      ia[h] = bt[h] = ga[h] = de[h] = 0.0;  // padding rows and rows after a failed pivot: g = x = 0
+      if (r < L.n && !failed) {
+        double w[5];
+        d4_weights(r, L.n, w);
+        const double ar = (r >= 2) ? sg * w[0] : 0.0;
+        const double br = (r >= 1) ? sg * w[1] : 0.0;
+        const double cr = 1.0 + sg * w[2];
+        const double dr = (r + 1 < L.n) ? sg * w[3] : 0.0;
+        const double er = (r + 2 < L.n) ? sg * w[4] : 0.0;
+        const double beta = br - ar * gam2;
+        const double alpha = cr - ar * del2 - beta * gam1;
+        if (!(alpha != 0.0) || !isfinite(alpha)) {
+          report_bad_pivot(P.info, L.s, r);
+          failed = true;
+        } else {
+          const double inv = 1.0 / alpha;
+          ia[h] = inv;
+          bt[h] = beta;
+          ga[h] = (dr - beta * del1) * inv;
+          de[h] = er * inv;
+          gam2 = gam1;
+          del2 = del1;
+          gam1 = ga[h];
+          del1 = de[h];
+        }
+      }
+      // forward row in the hyperdiffusion form: g_i = (1/alpha_i)(f_i - beta_i g_{i-1} - sigma g_{i-2})
+      gg[h] = ia[h] * fma(-bt[h], g1, fma(-sg, g2, fv[h]));
+      g2 = g1;
+      g1 = gg[h];
+    }
+    double2* rec = fwd + ((P0 + q) * 2) * kWarp + lane;
+    rec[0] = make_double2(ia[0], ia[1]);
+    rec[kWarp] = make_double2(bt[0], bt[1]);
+    double2* rb = bwd + ((P0 + q) * 2) * kWarp + lane;
+    rb[0] = make_double2(ga[0], ga[1]);
+    rb[kWarp] = make_double2(de[0], de[1]);
+    g2s[(P0 + q) * kWarp + lane] = make_double2(gg[0], gg[1]);
+  }
+
+  // ---- back: R x = g (records just written by this thread) ----
+  double x1 = 0.0, x2 = 0.0;
+  for (int64_t q = np - 1; q >= 0; --q) {
+    const double2 G = bwd[((P0 + q) * 2) * kWarp + lane];
+    const double2 D = bwd[((P0 + q) * 2 + 1) * kWarp + lane];
+    const double2 Gv = g2s[(P0 + q) * kWarp + lane];
+    const double xb = fma(-G.y, x1, fma(-D.y, x2, Gv.y));
+    const double xa = fma(-G.x, xb, fma(-D.x, x1, Gv.x));
+    const int64_t r = 2 * q;
+    if (xvec && r + 1 < L.n) {
+      *reinterpret_cast<double2*>(x + L.fo + r) = make_double2(xa, xb);
+    } else {
+      if (r < L.n) x[L.fo + r] = xa;
+      if (r + 1 < L.n) x[L.fo + r + 1] = xb;
+    }
+    x2 = xb;
+    x1 = xa;
+  }
+}
+
 // ---- partitioned solve of groups of long systems ----
 //
 // A group's serial walk takes time proportional to its length however few of
@@ -736,6 +1047,39 @@ cudaError_t launch_solve64(const DevPlan& P, F64Factors F, const double* f, doub
   PENT_U2(2, 1) PENT_U2(4, 2) PENT_U2(8, 4)
 #undef PENT_U2
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_step64(const DevPlan& P, F64Factors F, const double* mu, const double* nu, double* C,
+                          double* gscr, int block_warps, int unroll, int64_t g0, int64_t g1, cudaStream_t st) {
+  if (g1 <= g0) return cudaSuccess;
+  if (P.shared || !F.sig) return cudaErrorInvalidValue;
+  const int block = kWarp * block_warps;
+  const int grid = grid_for((g1 - g0) * kWarp, block);
+  if (unroll == 2)
+    k_step64_pair<1><<<grid, block, 0, st>>>(P, F, mu, nu, C, gscr, g0, g1);
+  else if (unroll == 4)
+    k_step64_pair<2><<<grid, block, 0, st>>>(P, F, mu, nu, C, gscr, g0, g1);
+  else if (unroll == 8)
+    k_step64_pair<4><<<grid, block, 0, st>>>(P, F, mu, nu, C, gscr, g0, g1);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refactor_solve64(const DevPlan& P, F64Factors F, const double* sigma, const double* f, double* x,
+                                    double* gscr, int block_warps, int64_t g0, int64_t g1, cudaStream_t st) {
+  if (g1 <= g0) return cudaSuccess;
+  if (P.shared || !F.sig) return cudaErrorInvalidValue;
+  const int block = kWarp * block_warps;
+  k_refactor_solve64<<<grid_for((g1 - g0) * kWarp, block), block, 0, st>>>(P, F, sigma, f, x, gscr, g0, g1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_rhs(const DevPlan& P, const double* mu, const double* nu, const double* C, double* f,
+                            int64_t g0, int64_t g1, cudaStream_t st) {
+  if (g1 <= g0) return cudaSuccess;
+  k_step_rhs<<<(unsigned)((g1 - g0) * kWarp), 256, 0, st>>>(P, mu, nu, C, f, g0);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_chunk_maps64(const DevPlan& P, F64Factors F, const F64Part& X, int64_t c0, int64_t c1,

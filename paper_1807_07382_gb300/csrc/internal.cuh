@@ -79,6 +79,21 @@ struct F64Part {
   double2* E;            // [nchunks][32] entering states
 };
 
+// Periodic (cyclic) systems by Navon's reduction (csrc/periodic.cu).  Every
+// per-row array of the reduced matrix E (m = n - 2 rows) is interleaved,
+// p[r * S + s] with S = batch, or p[r] when the matrix is shared.
+struct PerArgs {
+  int64_t batch, n, m;
+  int shared;
+  double *ia, *bb, *ee;  // 1/alpha, beta/alpha, epsilon/alpha of E
+  double *ga, *de;       // gamma, delta of E
+  double *z0, *z1;       // Z = E^{-T} h (h^T: rows n-2, n-1 of A in columns 0..m-1)
+  double *w0, *w1;       // W = L^{-1} k (k: columns n-2, n-1 of A in rows 0..m-1)
+  double* sinv;          // [S][4] inverse of S = D - h^T E^{-1} k, row-major
+  double* gscr;          // [m][batch] forward scratch g
+  unsigned long long* info;
+};
+
 // ---- launchers (kernels live in the .cu files) ----
 cudaError_t launch_factor64(const DevPlan& P, const double* a, const double* b, const double* c, const double* d,
                             const double* e, const double* sigma, F64Factors F, cudaStream_t st);
@@ -93,10 +108,26 @@ cudaError_t launch_chunk_maps64(const DevPlan& P, F64Factors F, const F64Part& X
                                 cudaStream_t st);
 cudaError_t launch_solve64_part(const DevPlan& P, F64Factors F, const F64Part& X, const double* f, double* x,
                                 double* gscr, int64_t kbeg, int64_t kend, int64_t c0, int64_t c1, cudaStream_t st);
+// One time step in place on C with f = C + mu_s D2(C^3 - C) - nu_s D4 C assembled in the
+// forward sweep (hyperdiffusion records, groups [g0, g1)); and the same f written out to
+// `f` for the systems of groups [g0, g1) (used before the partitioned solve).
+cudaError_t launch_step64(const DevPlan& P, F64Factors F, const double* mu, const double* nu, double* C,
+                          double* gscr, int block_warps, int unroll, int64_t g0, int64_t g1, cudaStream_t st);
+cudaError_t launch_step_rhs(const DevPlan& P, const double* mu, const double* nu, const double* C, double* f,
+                            int64_t g0, int64_t g1, cudaStream_t st);
+// Factor A_s = I + sigma_s D4 (hyperdiffusion records, sigma copied into F.sig) and solve
+// A_s x = f in one pass per system, groups [g0, g1).
+cudaError_t launch_refactor_solve64(const DevPlan& P, F64Factors F, const double* sigma, const double* f, double* x,
+                                    double* gscr, int block_warps, int64_t g0, int64_t g1, cudaStream_t st);
 cudaError_t launch_adjoint64(const DevPlan& P, F64Factors F, const double* f, double* x, double* gscr,
                              int block_warps, cudaStream_t st);
 cudaError_t launch_solve32r(const F32Tables& T, const int32_t* sys, const F32Bucket& b, int shared, const double* f,
                             double* x, int max_refine, int residual_f64, int tol_log2, cudaStream_t st);
+cudaError_t launch_factor_periodic(const PerArgs& A, const double* a, const double* b, const double* c,
+                                   const double* d, const double* e, const double* sigma, cudaStream_t st);
+// rhs: assemble f_i = C_i + mu_s (D2 (C^3 - C))_i - nu_s (D4 C)_i from the field in f (periodic stencils).
+cudaError_t launch_solve_periodic(const PerArgs& A, const double* f, double* x, const double* mu, const double* nu,
+                                  bool rhs, cudaStream_t st);
 cudaError_t launch_sigma_grad(const DevPlan& P, const double* mu, const double* x, double* g_sigma, cudaStream_t st);
 // Rows per chunk of the partitioned column sweeps of the ADI step.
 constexpr int kAdiChunk = 64;

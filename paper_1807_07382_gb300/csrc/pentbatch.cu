@@ -61,6 +61,7 @@ struct pent_plan {
   };
   std::vector<F64Run> runs;
   int64_t part_rows = -1;  // PENT_OPT_PARTITION_ROWS (-1: automatic)
+  bool periodic = false;   // PENT_OPT_PERIODIC: cyclic systems (Navon's reduction)
   // partitioned groups: chunk list and per-group chunk ranges
   std::vector<int32_t> pck, pcc, pcnum;
   std::vector<int64_t> pcbase;
@@ -89,7 +90,8 @@ struct pent_plan {
   std::vector<cudaEvent_t> ev;    // fork/join events
   // workspace regions
   Region r_info, r_perm, r_off, r_n, r_goff, r_glen, r_sigma, r_fwd, r_bwd, r_scr, r_fac32, r_sig32, r_foff, r_shape,
-      r_sys32, r_adi, r_cmap, r_swU, r_swE, r_pck, r_pcc, r_pcbase, r_pcnum, r_pcmap, r_pU, r_pE;
+      r_sys32, r_adi, r_cmap, r_swU, r_swE, r_pck, r_pcc, r_pcbase, r_pcnum, r_pcmap, r_pU, r_pE, r_per, r_psinv,
+      r_pg, r_rhs;
   size_t ws_bytes = 0;
   // binding / state
   unsigned char* ws = nullptr;
@@ -131,6 +133,21 @@ struct pent_plan {
     X.U = at<double2>(r_pU);
     X.E = at<double2>(r_pE);
     return X;
+  }
+  PerArgs per() const {
+    PerArgs A;
+    A.batch = batch;
+    A.n = n_uniform;
+    A.m = n_uniform - 2;
+    A.shared = shared ? 1 : 0;
+    const int64_t plane = A.m * (shared ? 1 : batch);
+    double* base = at<double>(r_per);
+    double** planes[9] = {&A.ia, &A.bb, &A.ee, &A.ga, &A.de, &A.z0, &A.z1, &A.w0, &A.w1};
+    for (int k = 0; k < 9; ++k) *planes[k] = base + k * plane;
+    A.sinv = at<double>(r_psinv);
+    A.gscr = at<double>(r_pg);
+    A.info = at<unsigned long long>(r_info);
+    return A;
   }
   F32Tables f32() const {
     F32Tables T;
@@ -363,6 +380,15 @@ void layout(pent_plan* p) {
   take(p->r_goff, (size_t)p->ngroups * sizeof(int64_t));
   take(p->r_glen, (size_t)p->ngroups * sizeof(int32_t));
   take(p->r_sigma, (size_t)nfac * sizeof(double));
+  if (p->periodic) {
+    // Navon's reduction: nine interleaved planes of the reduced matrix, S^{-1}, and g
+    const int64_t m = p->n_uniform - 2;
+    take(p->r_per, (size_t)9 * m * nfac * sizeof(double));
+    take(p->r_psinv, (size_t)4 * nfac * sizeof(double));
+    take(p->r_pg, (size_t)m * p->batch * sizeof(double));
+    p->ws_bytes = cur;
+    return;
+  }
   if (p->precision == PENT_F64) {
     const int64_t frows = p->shared ? p->n_uniform : p->grows;
     const int64_t lanes = p->shared ? 1 : kWarp;
@@ -376,6 +402,8 @@ void layout(pent_plan* p) {
     take(p->r_pcmap, (size_t)p->pchunks * 8 * kWarp * sizeof(double));
     take(p->r_pU, (size_t)p->pchunks * kWarp * 2 * sizeof(double));
     take(p->r_pE, (size_t)p->pchunks * kWarp * 2 * sizeof(double));
+    // right-hand sides of pent_step_batch for the partitioned groups (their chunked solve reads f)
+    take(p->r_rhs, (size_t)(p->pchunks > 0 ? p->rows : 0) * sizeof(double));
   } else {
     take(p->r_fac32, (size_t)p->fac_float4 * 4 * sizeof(float));
     take(p->r_sig32, (size_t)nfac * 2 * sizeof(float));
@@ -583,6 +611,12 @@ pent_status pent_plan_set_option(pent_plan* p, int key, int64_t value) {
       build_f64_runs(p);
       layout(p);
       return PENT_OK;
+    case PENT_OPT_PERIODIC:
+      if (p->bound || (value != 0 && value != 1)) return PENT_EINVAL;
+      if (value == 1 && (p->precision != PENT_F64 || !p->uniform || p->n_uniform < 5)) return PENT_EINVAL;
+      p->periodic = value == 1;
+      layout(p);
+      return PENT_OK;
     case PENT_OPT_ROWS_PER_THREAD: {
       if (p->bound) return PENT_EINVAL;
       if (p->precision == PENT_F64) return PENT_EINVAL;
@@ -637,12 +671,18 @@ pent_status pent_plan_get_option(const pent_plan* p, int key, int64_t* value) {
     case PENT_OPT_UNROLL: *value = p->unroll; return PENT_OK;
     case PENT_OPT_ROWS_PER_THREAD: *value = p->rpt_override; return PENT_OK;
     case PENT_OPT_PARTITION_ROWS: *value = p->part_rows; return PENT_OK;
+    case PENT_OPT_PERIODIC: *value = p->periodic ? 1 : 0; return PENT_OK;
   }
   return PENT_EINVAL;
 }
 
 pent_status pent_plan_system_config(const pent_plan* p, int64_t system, int64_t* a, int64_t* b) {
   if (!p || !a || !b || system < 0 || system >= p->batch) return PENT_EINVAL;
+  if (p->periodic) {  // one thread per system, no tuned settings
+    *a = 1;
+    *b = 1;
+    return PENT_OK;
+  }
   if (p->precision == PENT_F32_REFINE) {
     const auto& sh = p->shape[p->shared ? 0 : system];
     *a = sh.L;
@@ -689,7 +729,9 @@ static pent_status factor_common(pent_plan* p, const double* a, const double* b,
   }
   const double* sg = sigma ? p->at<double>(p->r_sigma) : nullptr;
   cudaError_t err;
-  if (p->precision == PENT_F64) {
+  if (p->periodic) {
+    err = launch_factor_periodic(p->per(), a, b, c, d, e, sg, p->stream);
+  } else if (p->precision == PENT_F64) {
     F64Factors F = p->f64();
     F.sig = (sigma && !p->shared) ? sg : nullptr;
     err = launch_factor64(P, a, b, c, d, e, sg, F, p->stream);
@@ -719,7 +761,9 @@ pent_status pent_factor_hyperdiff(pent_plan* p, const double* d_sigma) {
 
 static pent_status solve_launch(pent_plan* p, const double* f, double* x, int max_refine) {
   cudaError_t err;
-  if (p->precision == PENT_F64) {
+  if (p->periodic) {
+    err = launch_solve_periodic(p->per(), f, x, nullptr, nullptr, false, p->stream);
+  } else if (p->precision == PENT_F64) {
     const DevPlan P = p->dev();
     const F64Factors F = p->f64();
     double* gscr = p->at<double>(p->r_scr);
@@ -740,6 +784,40 @@ static pent_status solve_launch(pent_plan* p, const double* f, double* x, int ma
   return cuda_status(err);
 }
 
+// `nsteps` repetitions of launch() on the plan's stream: captured once into a
+// CUDA graph under `key` and replayed on later calls (plain launches on the
+// legacy stream, which cannot be captured).
+}  // extern "C"
+
+template <class F>
+static pent_status run_steps(pent_plan* p, const std::tuple<const void*, int64_t, int, int64_t>& key, int64_t nsteps,
+                             F launch) {
+  pent_status st = PENT_OK;
+  if (p->stream == nullptr) {
+    for (int64_t k = 0; k < nsteps && st == PENT_OK; ++k) st = launch();
+    return st;
+  }
+  auto it = p->graphs.find(key);
+  if (it == p->graphs.end()) {
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return PENT_ECUDA;
+    for (int64_t k = 0; k < nsteps && st == PENT_OK; ++k) st = launch();
+    cudaError_t e = cudaStreamEndCapture(p->stream, &g);
+    if (st != PENT_OK || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return st != PENT_OK ? st : PENT_ECUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return PENT_ECUDA;
+    it = p->graphs.emplace(key, exec).first;
+  }
+  return cuda_status(cudaGraphLaunch(it->second, p->stream));
+}
+
+extern "C" {
+
 static pent_status check_solve(pent_plan* p, const void* f, const void* x, int max_refine) {
   if (!p || !f || !x || max_refine < 0) return PENT_EINVAL;
   if (!p->bound) return PENT_ENOTBOUND;
@@ -759,34 +837,81 @@ pent_status pent_solve_steps(pent_plan* p, double* x, int64_t nsteps, int max_re
   if (st != PENT_OK) return st;
   if (nsteps < 0) return PENT_EINVAL;
   if (nsteps == 0) return PENT_OK;
-  if (p->stream == nullptr) {  // the legacy stream cannot be captured: plain launches
-    for (int64_t k = 0; k < nsteps && st == PENT_OK; ++k) st = solve_launch(p, x, x, max_refine);
-    return st;
-  }
   const auto key = std::make_tuple((const void*)x, nsteps, max_refine, p->cfg_version);
-  auto it = p->graphs.find(key);
-  if (it == p->graphs.end()) {
-    cudaGraph_t g = nullptr;
-    if (cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return PENT_ECUDA;
-    for (int64_t k = 0; k < nsteps && st == PENT_OK; ++k) st = solve_launch(p, x, x, max_refine);
-    cudaError_t e = cudaStreamEndCapture(p->stream, &g);
-    if (st != PENT_OK || e != cudaSuccess) {
-      if (g) cudaGraphDestroy(g);
-      return st != PENT_OK ? st : PENT_ECUDA;
+  return run_steps(p, key, nsteps, [&]() { return solve_launch(p, x, x, max_refine); });
+}
+
+// One pent_step_batch step on a no-flux FP64 plan: the fused right-hand side
+// and solve for the thread-per-system runs; for partitioned runs the right-hand
+// side is written out first, then solved by the chunked kernels.
+static pent_status step_launch(pent_plan* p, const double* mu, const double* nu, double* C) {
+  const DevPlan P = p->dev();
+  const F64Factors F = p->f64();
+  double* gscr = p->at<double>(p->r_scr);
+  const F64Part X = p->part();
+  double* frhs = p->at<double>(p->r_rhs);
+  const cudaError_t err = fork_join(p, p->runs.size(), [&](size_t i, cudaStream_t st) {
+    const auto& r = p->runs[i];
+    if (r.part) {
+      const cudaError_t e = launch_step_rhs(P, mu, nu, C, frhs, r.g0, r.g1, st);
+      if (e != cudaSuccess) return e;
+      return launch_solve64_part(P, F, X, frhs, C, gscr, r.g0, r.g1, r.c0, r.c1, st);
     }
-    cudaGraphExec_t exec = nullptr;
-    e = cudaGraphInstantiate(&exec, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return PENT_ECUDA;
-    it = p->graphs.emplace(key, exec).first;
+    return launch_step64(P, F, mu, nu, C, gscr, r.bw, r.unroll, r.g0, r.g1, st);
+  });
+  return cuda_status(err);
+}
+
+pent_status pent_step_batch(pent_plan* p, const double* mu, const double* nu, double* C, int64_t nsteps,
+                            int max_refine) {
+  pent_status st = check_solve(p, C, C, max_refine);
+  if (st != PENT_OK) return st;
+  if (nsteps < 0) return PENT_EINVAL;
+  if ((((uintptr_t)mu) | ((uintptr_t)nu)) % sizeof(double)) return PENT_EINVAL;
+  // no-flux plans: per-system FP64 factors from sigma (pent_factor_hyperdiff)
+  if (!p->periodic && (p->precision != PENT_F64 || p->shared || p->factored != 2)) return PENT_EINVAL;
+  if (nsteps == 0) return PENT_OK;
+  auto launch = [&]() -> pent_status {
+    if (p->periodic) return cuda_status(launch_solve_periodic(p->per(), C, C, mu, nu, true, p->stream));
+    return step_launch(p, mu, nu, C);
+  };
+  if (nsteps == 1) return launch();
+  uint64_t h = 1469598103934665603ull;
+  for (uint64_t v : {(uint64_t)(uintptr_t)mu, (uint64_t)(uintptr_t)nu, (uint64_t)p->cfg_version})
+    h = (h ^ v) * 1099511628211ull;
+  const auto key = std::make_tuple((const void*)C, nsteps, -2, (int64_t)(h & 0x7fffffffffffffffull));
+  return run_steps(p, key, nsteps, launch);
+}
+
+pent_status pent_refactor_solve_hyperdiff(pent_plan* p, const double* d_sigma, const double* f, double* x) {
+  if (!p || !d_sigma) return PENT_EINVAL;
+  if (!p->bound) return PENT_ENOTBOUND;
+  if (!f || !x || (((uintptr_t)f) | ((uintptr_t)x) | ((uintptr_t)d_sigma)) % sizeof(double)) return PENT_EINVAL;
+  if (p->precision != PENT_F64 || p->periodic) return PENT_EINVAL;
+  if (p->shared || p->pchunks > 0) {
+    // one matrix for the batch, or groups solved in chunks: factor, then solve
+    pent_status st = factor_common(p, nullptr, nullptr, nullptr, nullptr, nullptr, d_sigma);
+    return st != PENT_OK ? st : solve_launch(p, f, x, 0);
   }
-  return cuda_status(cudaGraphLaunch(it->second, p->stream));
+  pent_status st = reset_info(p);
+  if (st != PENT_OK) return st;
+  const DevPlan P = p->dev();
+  F64Factors F = p->f64();
+  F.sig = p->at<double>(p->r_sigma);
+  double* gscr = p->at<double>(p->r_scr);
+  const cudaError_t err = fork_join(p, p->runs.size(), [&](size_t i, cudaStream_t s) {
+    const auto& r = p->runs[i];
+    return launch_refactor_solve64(P, F, d_sigma, f, x, gscr, r.bw, r.g0, r.g1, s);
+  });
+  if (err != cudaSuccess) return PENT_ECUDA;
+  p->factored = 2;
+  return PENT_OK;
 }
 
 pent_status pent_adjoint_solve_batch(pent_plan* p, const double* f, double* x, int max_refine) {
   pent_status st = check_solve(p, f, x, max_refine);
   if (st != PENT_OK) return st;
-  if (p->precision != PENT_F64) return PENT_EINVAL;
+  if (p->precision != PENT_F64 || p->periodic) return PENT_EINVAL;
   return cuda_status(
       launch_adjoint64(p->dev(), p->f64(), f, x, p->at<double>(p->r_scr), p->block_warps, p->stream));
 }
@@ -794,6 +919,7 @@ pent_status pent_adjoint_solve_batch(pent_plan* p, const double* f, double* x, i
 pent_status pent_hyperdiff_sigma_grad(pent_plan* p, const double* mu, const double* x, double* g_sigma) {
   if (!p || !mu || !x || !g_sigma) return PENT_EINVAL;
   if (!p->bound) return PENT_ENOTBOUND;
+  if (p->periodic || p->precision != PENT_F64) return PENT_EINVAL;
   return cuda_status(launch_sigma_grad(p->dev(), mu, x, g_sigma, p->stream));
 }
 
@@ -835,6 +961,7 @@ static pent_status adi_check(pent_plan* px, pent_plan* py, double* C, int64_t nx
   if (!px->bound || !py->bound) return PENT_ENOTBOUND;
   if (px->factored != 2 || py->factored != 2) return PENT_ENOTFACTORED;
   if (px->precision != PENT_F64 || py->precision != PENT_F64 || !px->shared || !py->shared) return PENT_EINVAL;
+  if (px->periodic || py->periodic) return PENT_EINVAL;
   if (px->batch != ny || px->n_uniform != nx || py->batch != nx || py->n_uniform != ny) return PENT_EINVAL;
   if (px->stream != py->stream) return PENT_EINVAL;
   if (((uintptr_t)C) % sizeof(double)) return PENT_EINVAL;

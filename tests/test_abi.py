@@ -110,3 +110,36 @@ def test_f32_threads_per_system_option_relayouts_before_bind(L):
     assert L.pent_plan_set_option(h, _lib.PENT_OPT_THREADS_PER_SYSTEM, 0) == 0  # back to the automatic shape
     assert L.pent_plan_workspace_bytes(h) == base
     L.pent_plan_destroy(h)
+
+
+def test_periodic_option_host_checks(L):
+    # FP64, uniform n >= 5 only; before binding
+    st, h = _create(L, batch=4, n_uniform=4)
+    assert L.pent_plan_set_option(h, _lib.PENT_OPT_PERIODIC, 1) == _lib.PENT_EINVAL
+    L.pent_plan_destroy(h)
+    st, h = _create(L, batch=4, n_uniform=64, prec=1)
+    assert L.pent_plan_set_option(h, _lib.PENT_OPT_PERIODIC, 1) == _lib.PENT_EINVAL
+    L.pent_plan_destroy(h)
+    st, h = _create(L, batch=2, n=[64, 65])
+    assert L.pent_plan_set_option(h, _lib.PENT_OPT_PERIODIC, 1) == _lib.PENT_EINVAL
+    L.pent_plan_destroy(h)
+    st, h = _create(L, batch=70, n_uniform=64)
+    base = L.pent_plan_workspace_bytes(h)
+    assert L.pent_plan_set_option(h, _lib.PENT_OPT_PERIODIC, 2) == _lib.PENT_EINVAL
+    assert L.pent_plan_set_option(h, _lib.PENT_OPT_PERIODIC, 1) == 0
+    v = ctypes.c_int64()
+    assert L.pent_plan_get_option(h, _lib.PENT_OPT_PERIODIC, ctypes.byref(v)) == 0 and v.value == 1
+    # nine interleaved planes of the reduced matrix (62 rows) per system, S^{-1}, and the g scratch
+    assert L.pent_plan_workspace_bytes(h) >= (9 * 62 * 70 + 4 * 70 + 62 * 70) * 8
+    assert L.pent_plan_set_option(h, _lib.PENT_OPT_PERIODIC, 0) == 0
+    assert L.pent_plan_workspace_bytes(h) == base
+    L.pent_plan_destroy(h)
+
+
+def test_new_entry_points_check_arguments_on_the_host(L):
+    st, h = _create(L, batch=4, n_uniform=32)
+    assert L.pent_step_batch(h, None, None, ctypes.c_void_p(16), 1, 0) == _lib.PENT_ENOTBOUND
+    assert L.pent_refactor_solve_hyperdiff(h, None, ctypes.c_void_p(16), ctypes.c_void_p(16)) == _lib.PENT_EINVAL
+    assert L.pent_refactor_solve_hyperdiff(h, ctypes.c_void_p(16), ctypes.c_void_p(16),
+                                           ctypes.c_void_p(16)) == _lib.PENT_ENOTBOUND
+    L.pent_plan_destroy(h)
