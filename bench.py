@@ -12,6 +12,7 @@ Metric: row-solves/s = sum(N) * steps / time.  The headline precision is
 FP32 + float-float refinement; the FP64 solve is measured beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl own|reference]
+  python bench.py --workload NAME[,NAME...]   (other workloads, one JSON line each)
 
 One JSON line is printed by rank 0.  Under torchrun each rank runs its own
 copy of the batch (weak scaling, no collective on the data path).
@@ -328,6 +329,208 @@ def run_own(args):
         torch.distributed.destroy_process_group()
 
 
+# ----------------------------------------------------------------------------- other workloads
+
+def _sys_err(got, ref):
+    """Per-system max|x - x_ref| / max|x_ref|, maximised over the rows of 2D arrays."""
+    return float(np.max(np.max(np.abs(got - ref), axis=1) / np.max(np.abs(ref), axis=1)))
+
+
+def _time_device(stream, run, steps, dev):
+    """CUDA-event time of run() on `stream` (after a warm call), with clocks sampled meanwhile."""
+    import torch
+    torch.cuda.synchronize(dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index or 0) as cs:
+        ev0.record(stream)
+        run()
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    return ev0.elapsed_time(ev1), cs.summary()
+
+
+def _line(name, workload, rows_per_step, steps, ms, alg_bytes, kernel, err, extra=None, dtype="f64", clocks=None):
+    peak, peak_kind = measured_peaks()
+    ms_step = ms / steps
+    achieved = alg_bytes * rows_per_step / (ms_step / 1e3) / 1e9
+    line = {"workload_name": name, "metric": METRIC, "value": rows_per_step * steps / (ms / 1e3), "unit": UNIT,
+            "n_gpus": 1, "steps": steps, "ms_per_step": ms_step, "higher_is_better": True, "dtype": dtype,
+            "data": "synthetic", "config": {"workload": workload},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "kernel": kernel, "alg_bytes_per_row": alg_bytes, "peak_kind": peak_kind},
+            "max_rel_err_vs_oracle": err, "clocks": clocks}
+    line.update(extra or {})
+    print(json.dumps(line), flush=True)
+
+
+def run_workloads(names, args):
+    import torch
+    import oracle
+    import paper_1807_07382_gb300 as pb
+    from paper_1807_07382_gb300 import build as pbuild
+    from paper_1807_07382_gb300 import autograd as pag
+
+    pbuild.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    tune = os.path.join(ROOT, "paper_1807_07382_gb300", "tune_gb300.txt")
+    for name in names:
+        if name == "cosines":
+            w = synth.hyperdiff_cosines()
+            n = int(w.n[0])
+            plan = pb.Plan(n, batch=w.batch, shared=True, stream=stream)
+            plan.factor_hyperdiff(torch.from_numpy(w.sigma).to(dev))
+            x = torch.from_numpy(w.field0).to(dev)
+            plan.solve_steps(x.clone(), w.steps)
+            ref = oracle.hyperdiff_steps(w.n, w.sigma, w.field0, w.steps, shared=True)
+            ms, ck = _time_device(stream, lambda: plan.solve_steps(x, w.steps), w.steps, dev)
+            err = _sys_err(x.cpu().numpy().reshape(w.batch, n), ref.reshape(w.batch, n))
+            _line(name, "64 systems x N=256, shared sigma=0.5, 4 cosine modes + noise, 100 implicit steps (1 graph)",
+                  w.rows, w.steps, ms, 16, "k_solve64<shared>", err, clocks=ck,
+                  extra={"note": "shared factors broadcast; latency bound (16,384 rows per step)"})
+        elif name == "uneven":
+            w = synth.uneven()
+            f0 = torch.from_numpy(w.field0).to(dev)
+            sig = torch.from_numpy(w.sigma).to(dev)
+            off = w.offsets
+            pick = np.arange(0, w.batch, 97)
+            ref = oracle.hyperdiff_steps(w.n[pick], w.sigma[pick],
+                                         np.concatenate([w.field0[off[s]:off[s + 1]] for s in pick]), 1)
+            for prec, pname, alg, kern in ((pb.PENT_F64, "f64", 56, "k_solve64_pair + partitioned"),
+                                           (pb.PENT_F32_REFINE, "f32_refine", 36, "k_solve32r")):
+                plan = pb.Plan(list(w.n), precision=prec, stream=stream, tune_cache=tune)
+                plan.factor_hyperdiff(sig)
+                one = plan.solve(f0, max_refine=1).cpu().numpy()
+                got = np.concatenate([one[off[s]:off[s + 1]] for s in pick])
+                roff = oracle.offsets(w.n[pick])
+                err = max(float(np.max(np.abs(got[roff[k]:roff[k + 1]] - ref[roff[k]:roff[k + 1]])) /
+                                np.max(np.abs(ref[roff[k]:roff[k + 1]]))) for k in range(len(pick)))
+                x = f0.clone()
+                plan.solve_steps(x, w.steps, max_refine=1)
+                ms, ck = _time_device(stream, lambda: plan.solve_steps(x, w.steps, max_refine=1), w.steps, dev)
+                _line(f"{name}_{pname}", "20,000 systems, N log-U[64,16384] (sum 59.1 M rows), sigma log-U[1e-2,10], "
+                      "200 implicit steps (1 graph), tuned launch settings", w.rows, w.steps, ms, alg, kern, err,
+                      dtype="f64" if prec == pb.PENT_F64 else "f32", clocks=ck,
+                      extra={"max_refine": 1 if prec == pb.PENT_F32_REFINE else 0,
+                             "err_sample": f"{len(pick)} systems, one step"})
+                del plan
+        elif name == "adi":
+            w = synth.ch_adi()
+            adi = pb.ADI2D(w.nx, w.ny, w.gamma, w.dt, w.dx, device=dev, stream=stream)
+            C = torch.from_numpy(w.field0).to(dev)
+            one = adi.step(C.clone()).cpu().numpy()
+            ref = oracle.adi_step(w.field0, w.gamma, w.dt, w.dx)
+            # the exact dC is O(sigma) times the field's rounding: compare the step's change, normwise
+            err = float(np.max(np.abs(one - ref)) / np.max(np.abs(ref - w.field0)))
+            m0 = float(C.sum())
+            adi.step(C.clone(), nsteps=w.steps)
+            ms, ck = _time_device(stream, lambda: adi.step(C, nsteps=w.steps), w.steps, dev)
+            drift = abs(float(C.sum()) - m0) / float(np.abs(w.field0).sum())
+            _line(name, "2048 x 2048 Cahn-Hilliard ADI (Douglas), gamma=0.01, dt=1e-6, dx=1/2048, 500 steps (1 graph)",
+                  2 * w.nx * w.ny, w.steps, ms, 8, "k_adi_rhs_T + partitioned column sweeps", err, clocks=ck,
+                  extra={"mass_drift_rel": drift, "err_metric": "max|dC - dC_ref| / max|dC_ref| after one step",
+                         "note": "rows = both sweeps; 8 B per swept row (C read and written once per step); "
+                                 "the 33.5 MB field stays in L2"})
+        elif name == "adjoint":
+            w = synth.adjoint_batch()
+            n = int(w.n[0])
+            c0 = torch.from_numpy(w.field0.reshape(w.batch, n)).to(dev).requires_grad_(True)
+            sig = torch.from_numpy(w.sigma).to(dev).requires_grad_(True)
+            target = pag.hyperdiff_steps(c0.detach(), sig.detach() * (1 + w.extra["perturb"]), w.steps)
+
+            def grad():
+                xT = pag.hyperdiff_steps(c0, sig, w.steps, 10)
+                loss = ((xT - target) ** 2).sum()
+                return torch.autograd.grad(loss, (c0, sig))
+            gc, gs = grad()
+            pick = np.arange(0, w.batch, 128)
+            _, rgc, rgs = oracle.hyperdiff_loss_grad(w.sigma[pick], w.steps, w.field0.reshape(w.batch, n)[pick],
+                                                     target.detach().cpu().numpy()[pick])
+            err_s = float(np.max(np.abs(gs.cpu().numpy()[pick] - rgs) / np.abs(rgs)))
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            reps = 3
+            for _ in range(reps):
+                grad()
+            torch.cuda.synchronize(dev)
+            ms = (time.perf_counter() - t0) * 1e3 / reps
+            solves = 3 * w.steps  # forward, recompute from checkpoints, adjoint
+            _line(name, "4,096 systems x N=1024, loss over T=50 implicit steps, gradient w.r.t. C0 and sigma "
+                  "(checkpoints every 10 steps)", w.batch * n * solves, 1, ms, 56,
+                  "k_solve64_pair + k_adjoint64 + k_sigma_grad", err_s,
+                  extra={"ms_per_gradient": ms, "err_metric": "relative error of dL/dsigma vs the oracle adjoint "
+                                                              f"({len(pick)} systems)",
+                         "timing": "host wall clock around torch.autograd (3 gradients)"})
+        elif name == "periodic_cn":
+            w = synth.periodic_cn(batch=args.batch or 65536)
+            n = int(w.n[0])
+            plan = pb.Plan(n, batch=w.batch, shared=True, periodic=True, stream=stream)
+            s = torch.from_numpy(w.sigma).to(dev)
+            plan.factor_hyperdiff(s)
+            C = torch.from_numpy(w.field0).to(dev)
+            pick = np.arange(0, w.batch, max(1, w.batch // 128))
+            c1 = C.clone()
+            plan.step(c1, nu=s)
+            ref = oracle.periodic_steps(n, w.sigma, w.field0.reshape(w.batch, n)[pick].reshape(-1), 1, cn=True,
+                                        shared=True)
+            err = _sys_err(c1.cpu().numpy().reshape(w.batch, n)[pick], ref.reshape(len(pick), n))
+            plan.step(C.clone(), nu=s, nsteps=w.steps)
+            ms, ck = _time_device(stream, lambda: plan.step(C, nu=s, nsteps=w.steps), w.steps, dev)
+            _line(name, f"periodic Crank-Nicolson hyperdiffusion (Navon reduction), {w.batch:,} systems x N={n}, shared "
+                  "sigma_x = dt/(2 dx^4) = 343.6 (dt=1e-8, dx=1/512), C0 U[-1,1], 250 steps (1 graph)",
+                  w.rows, w.steps, ms, 16, "k_solve_periodic<shared, rhs>", err, clocks=ck,
+                  extra={"note": "reduction shared by the batch (broadcast); f assembled in the forward sweep",
+                         "err_sample": f"{len(pick)} systems, one step"})
+        elif name == "ch1d":
+            w = synth.ch_batch(batch=args.batch or 65536)
+            n = int(w.n[0])
+            plan = pb.Plan(n, batch=w.batch, stream=stream)
+            plan.factor_hyperdiff(torch.from_numpy(w.sigma).to(dev))
+            mu = torch.from_numpy(w.extra["mu"]).to(dev)
+            C = torch.from_numpy(w.field0).to(dev)
+            pick = np.arange(0, w.batch, max(1, w.batch // 128))
+            c1 = C.clone()
+            plan.step(c1, mu=mu)
+            ref = oracle.explicit_steps(np.full(len(pick), n), w.sigma[pick], w.extra["mu"][pick], None,
+                                        w.field0.reshape(w.batch, n)[pick].reshape(-1), 1)
+            err = _sys_err(c1.cpu().numpy().reshape(w.batch, n)[pick], ref.reshape(len(pick), n))
+            plan.step(C.clone(), mu=mu, nsteps=w.steps)
+            ms, ck = _time_device(stream, lambda: plan.step(C, mu=mu, nsteps=w.steps), w.steps, dev)
+            _line(name, f"1D Cahn-Hilliard parameter batch (semi-implicit, no-flux), {w.batch:,} systems x N={n}, "
+                  "sigma log-U[1e-3,10], mu log-U[1e-4,1e-1], 200 steps (1 graph)", w.rows, w.steps, ms, 48,
+                  "k_step64_pair", err, clocks=ck,
+                  extra={"note": "48 B/row: 4 FP64 record planes + C read + C written; the right-hand side "
+                                 "C + mu D2(C^3 - C) is assembled in the forward sweep",
+                         "err_sample": f"{len(pick)} systems, one step"})
+        elif name == "rewrite":
+            w = synth.hyperdiff_parametric(batch=args.batch or 65536)
+            n = int(w.n[0])
+            K = 20
+            plan = pb.Plan(n, batch=w.batch, stream=stream)
+            sigs = [torch.from_numpy(w.sigma * (1.0 + 1e-3 * k)).to(dev) for k in range(K)]
+            f = torch.from_numpy(w.field0).to(dev)
+            x1 = plan.refactor_solve(sigs[0], f)
+            pick = np.arange(0, w.batch, max(1, w.batch // 128))
+            ref = oracle.hyperdiff_steps(np.full(len(pick), n), w.sigma[pick],
+                                         w.field0.reshape(w.batch, n)[pick].reshape(-1), 1)
+            err = _sys_err(x1.cpu().numpy().reshape(w.batch, n)[pick], ref.reshape(len(pick), n))
+            x = f.clone()
+
+            def run():
+                for k in range(K):
+                    plan.refactor_solve(sigs[k], x, x)
+            run()
+            ms, ck = _time_device(stream, run, K, dev)
+            _line(name, f"refactor + solve every step (the paper's Rewrite), {w.batch:,} systems x N={n}, a new sigma per "
+                  "system and step, 20 steps", w.rows, K, ms, 48, "k_refactor_solve64", err, clocks=ck,
+                  extra={"note": "48 B/row: f read, x written, 4 record planes written (the plan stays factored)",
+                         "err_sample": f"{len(pick)} systems, one step"})
+        else:
+            raise SystemExit(f"unknown workload {name}")
+
+
 # ----------------------------------------------------------------------------- reference arm
 
 def run_reference(args):
@@ -387,13 +590,25 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--batch", type=int, default=BATCH, help="systems (default: the full workload; smaller for profiling)")
+    ap.add_argument("--batch", type=int, default=None,
+                    help="systems (default: the full workload; smaller for profiling, also for --workload "
+                         "periodic_cn, ch1d and rewrite)")
+    ap.add_argument("--workload", default=None,
+                    help="comma-separated other workloads: cosines, uneven, adi, adjoint, periodic_cn, ch1d, rewrite, "
+                         "or all (one JSON line each; the default run is the parametric headline line)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.workload:
+        names = ["cosines", "uneven", "adi", "adjoint", "periodic_cn", "ch1d", "rewrite"] \
+            if args.workload == "all" else args.workload.split(",")
+        run_workloads(names, args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
+        if args.batch is None:
+            args.batch = BATCH
         run_own(args)
 
 

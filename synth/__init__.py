@@ -18,6 +18,10 @@ named in Sec. 4), each drawn from seed BASE_SEED + index:
   2  2048 x 2048 Cahn-Hilliard ADI field, C0 U[-0.1,0.1], 500 steps
   3  20,000 systems, N log-U[64,16384], sigma_i log-U[1e-2,10], RHS U[-1,1], 200 steps
   4  4,096 systems, N=1024, sigma_i log-U[1e-3,10], C0 U[-1,1], T=50
+  5  periodic Crank-Nicolson batch: 65,536 systems, N=512, one shared sigma_x = dt/(2 dx^4)
+     with dt = 1e-8, dx = 1/N (the paper's validation parameters), C0 U[-1,1], 250 steps
+  6  1D Cahn-Hilliard parameter batch: 65,536 systems, N=1024, sigma_i log-U[1e-3,10],
+     mu_i log-U[1e-4,1e-1], C0 U[-1,1], 200 steps
 
 Draw order inside one seed: per-system scalars first (sigma, then N where
 present), then the field, system-major.
@@ -156,6 +160,27 @@ def adjoint_batch(batch: int = 4096, n: int = 1024, steps: int = 50, seed_index:
     w.name = "adjoint"
     w.extra["perturb"] = perturb
     return w
+
+
+def periodic_cn(batch: int = 65536, n: int = 512, steps: int = 250, seed_index: int = 5,
+                dt: float = 1e-8, length: float = 1.0) -> Workload1D:
+    """Shared sigma_x = dt / (2 dx^4), dx = length / n; C0 uniform in [-1, 1]."""
+    seed = BASE_SEED + seed_index
+    dx = length / n
+    f0 = uniform(seed, 0, batch * n, -1.0, 1.0)
+    return Workload1D("periodic_cn", np.full(batch, n, np.int64), np.array([dt / (2 * dx ** 4)]), f0, steps,
+                      shared=True)
+
+
+def ch_batch(batch: int = 65536, n: int = 1024, steps: int = 200, seed_index: int = 6,
+             sigma_range=(1e-3, 10.0), mu_range=(1e-4, 1e-1)) -> Workload1D:
+    """Per-system sigma_i log-uniform in [1e-3, 10] and mu_i log-uniform in [1e-4, 1e-1]
+    (extra["mu"]); C0 uniform in [-1, 1]."""
+    seed = BASE_SEED + seed_index
+    sigma = log_uniform(seed, 0, batch, *sigma_range)
+    mu = log_uniform(seed, batch, batch, *mu_range)
+    f0 = uniform(seed, 2 * batch, batch * n, -1.0, 1.0)
+    return Workload1D("ch_batch", np.full(batch, n, np.int64), sigma, f0, steps, extra={"mu": mu})
 
 
 def random_bands(batch: int, n: int, seed: int, kind: str = "diagdom") -> tuple:
