@@ -486,24 +486,29 @@ def run_workloads(names, args):
         elif name == "ch1d":
             w = synth.ch_batch(batch=args.batch or 65536)
             n = int(w.n[0])
-            plan = pb.Plan(n, batch=w.batch, stream=stream)
-            plan.factor_hyperdiff(torch.from_numpy(w.sigma).to(dev))
             mu = torch.from_numpy(w.extra["mu"]).to(dev)
-            C = torch.from_numpy(w.field0).to(dev)
+            sig = torch.from_numpy(w.sigma).to(dev)
             pick = np.arange(0, w.batch, max(1, w.batch // 128))
-            c1 = C.clone()
-            plan.step(c1, mu=mu)
             ref = oracle.explicit_steps(np.full(len(pick), n), w.sigma[pick], w.extra["mu"][pick], None,
                                         w.field0.reshape(w.batch, n)[pick].reshape(-1), 1)
-            err = _sys_err(c1.cpu().numpy().reshape(w.batch, n)[pick], ref.reshape(len(pick), n))
-            plan.step(C.clone(), mu=mu, nsteps=w.steps)
-            ms, ck = _time_device(stream, lambda: plan.step(C, mu=mu, nsteps=w.steps), w.steps, dev)
-            _line(name, f"1D Cahn-Hilliard parameter batch (semi-implicit, no-flux), {w.batch:,} systems x N={n}, "
-                  "sigma log-U[1e-3,10], mu log-U[1e-4,1e-1], 200 steps (1 graph)", w.rows, w.steps, ms, 48,
-                  "k_step64_pair", err, clocks=ck,
-                  extra={"note": "48 B/row: 4 FP64 record planes + C read + C written; the right-hand side "
-                                 "C + mu D2(C^3 - C) is assembled in the forward sweep",
-                         "err_sample": f"{len(pick)} systems, one step"})
+            for prec, pname, alg, kern in ((pb.PENT_F64, "f64", 48, "k_step64_pair"),
+                                           (pb.PENT_F32_REFINE, "f32_refine", 24, "k_solve32r<step>")):
+                plan = pb.Plan(n, batch=w.batch, stream=stream, precision=prec)
+                plan.factor_hyperdiff(sig)
+                C = torch.from_numpy(w.field0).to(dev)
+                c1 = C.clone()
+                plan.step(c1, mu=mu, max_refine=1)
+                err = _sys_err(c1.cpu().numpy().reshape(w.batch, n)[pick], ref.reshape(len(pick), n))
+                plan.step(C.clone(), mu=mu, nsteps=w.steps, max_refine=1)
+                ms, ck = _time_device(stream, lambda: plan.step(C, mu=mu, nsteps=w.steps, max_refine=1), w.steps, dev)
+                note = ("48 B/row: 4 FP64 record planes + C read + C written" if prec == pb.PENT_F64 else
+                        "24 B/row: FP32 1/alpha and beta + C read + C written; one refinement step")
+                _line(f"{name}_{pname}", f"1D Cahn-Hilliard parameter batch (semi-implicit, no-flux), {w.batch:,} systems "
+                      f"x N={n}, sigma log-U[1e-3,10], mu log-U[1e-4,1e-1], 200 steps (1 graph)", w.rows, w.steps, ms,
+                      alg, kern, err, clocks=ck, dtype="f64" if prec == pb.PENT_F64 else "f32",
+                      extra={"note": note + "; the right-hand side C + mu D2(C^3 - C) is assembled in the kernel",
+                             "err_sample": f"{len(pick)} systems, one step"})
+                del plan
         elif name == "rewrite":
             w = synth.hyperdiff_parametric(batch=args.batch or 65536)
             n = int(w.n[0])

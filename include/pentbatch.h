@@ -211,9 +211,15 @@ pent_status pent_solve_steps(pent_plan* plan, double* x, int64_t nsteps, int max
  *     Sec. 2.2 (Eq. 1d_hyper_scheme).
  * d_mu, d_nu: device arrays of `batch` doubles (one when the matrix is
  * shared), or NULL for zero.  Several steps are captured once into a CUDA
- * graph (keyed by C, nsteps, d_mu, d_nu) and replayed.  PENT_F64 plans whose
- * systems are periodic, or per-system no-flux plans factored by
- * pent_factor_hyperdiff; otherwise PENT_EINVAL.  max_refine must be 0.
+ * graph (keyed by C, nsteps, d_mu, d_nu, max_refine) and replayed.  Plans:
+ *   PENT_F64, periodic (any factorisation) or per-system no-flux factored by
+ *     pent_factor_hyperdiff: f is assembled in FP64; max_refine is ignored;
+ *   PENT_F32_REFINE (float-float residual), factored by pent_factor_hyperdiff:
+ *     f is assembled in float-float arithmetic from C split into float pairs
+ *     (no scaling: |C| must stay below 2^40, larger fields set the
+ *     non-convergence flag), then solved in FP32 with up to max_refine
+ *     refinement steps, as pent_solve_batch.
+ * Other plans: PENT_EINVAL.
  */
 pent_status pent_step_batch(pent_plan* plan, const double* d_mu, const double* d_nu, double* C, int64_t nsteps,
                             int max_refine);

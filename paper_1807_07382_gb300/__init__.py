@@ -196,17 +196,19 @@ class Plan:
               "pent_solve_steps")
         return x
 
-    def step(self, C, mu=None, nu=None, nsteps: int = 1):
+    def step(self, C, mu=None, nu=None, nsteps: int = 1, max_refine: int = 2):
         """nsteps semi-implicit steps in place: A_s C <- C + mu_s D2(C^3 - C) - nu_s D4 C, the right-hand
         side assembled inside the solve kernel (Cahn-Hilliard: mu = D dt/dx^2; Crank-Nicolson
         hyperdiffusion: nu = sigma).  mu, nu: device float64 tensors of one value per system (one when
-        the matrix is shared) or None for zero.  Several steps run as one CUDA graph."""
+        the matrix is shared) or None for zero.  Several steps run as one CUDA graph.  max_refine: the
+        refinement steps of a PENT_F32_REFINE plan (the right-hand side is then assembled in
+        float-float arithmetic)."""
         torch = _torch()
         mp = _dev_ptr(mu, "mu", torch.float64) if mu is not None else None
         np_ = _dev_ptr(nu, "nu", torch.float64) if nu is not None else None
         self._step_refs = (mu, nu)  # graphs keep the pointers
-        check(self._L.pent_step_batch(self._h, mp, np_, _dev_ptr(C, "C", torch.float64), int(nsteps), 0),
-              "pent_step_batch")
+        check(self._L.pent_step_batch(self._h, mp, np_, _dev_ptr(C, "C", torch.float64), int(nsteps),
+                                      int(max_refine)), "pent_step_batch")
         return C
 
     def adjoint_solve(self, f, x=None):

@@ -595,6 +595,118 @@ __device__ __forceinline__ void residual_f64(const double (&fd)[L], const double
   }
 }
 
+// ---------------------------------------------------------------- explicit part of a time step (float-float)
+
+// C^3 - C for C = ch + cl (float-float; cl^2 is below the pair's resolution and dropped).
+__device__ __forceinline__ void cube_minus_ff(float ch, float cl, float& uh, float& ul) {
+  float p, e, c2h, c2l, c3h, c3l;
+  two_prod(ch, ch, p, e);
+  e = fmaf(2.f * ch, cl, e);
+  fast_two_sum(p, e, c2h, c2l);
+  two_prod(c2h, ch, p, e);
+  e = fmaf(c2h, cl, fmaf(c2l, ch, e));
+  fast_two_sum(p, e, c3h, c3l);
+  float s, es;
+  two_sum(c3h, -ch, s, es);
+  es = es + (c3l - cl);
+  fast_two_sum(s, es, uh, ul);
+}
+
+// a + b - 2 c for float-float a, b, c (the second difference).
+__device__ __forceinline__ void d2_ff(float ah, float al, float bh, float bl, float ch, float cl, float& dh,
+                                      float& dl) {
+  float s, e, t, e2;
+  two_sum(ah, bh, s, e);
+  e = e + (al + bl);
+  two_sum(s, -2.f * ch, t, e2);  // 2 c is exact
+  e = e + fmaf(-2.f, cl, e2);
+  fast_two_sum(t, e, dh, dl);
+}
+
+// [1, -4, 6, -4, 1] applied to the float-float window a..e (the fourth difference).
+__device__ __forceinline__ void d4_ff(float ah, float al, float bh, float bl, float ch, float cl, float dh, float dl,
+                                      float eh, float el, float& yh, float& yl) {
+  float s1, e1, s2, e2, t, e3, p, e4, S, Er;
+  two_sum(ah, eh, s1, e1);
+  two_sum(bh, dh, s2, e2);
+  two_sum(s1, -4.f * s2, t, e3);
+  two_prod(6.f, ch, p, e4);
+  two_sum(t, p, S, Er);
+  const float low = fmaf(6.f, cl, fmaf(-4.f, bl + dl, al + el));
+  Er = Er + ((e1 - 4.f * e2) + (e3 + e4) + low);
+  fast_two_sum(S, Er, yh, yl);
+}
+
+// (ph + pl) * (qh + ql) in float-float.
+__device__ __forceinline__ void mul_ff(float ph, float pl, float qh, float ql, float& rh, float& rl) {
+  float p, e;
+  two_prod(ph, qh, p, e);
+  e = fmaf(ph, ql, fmaf(pl, qh, e));
+  fast_two_sum(p, e, rh, rl);
+}
+
+// The right-hand side of a semi-implicit step, f = C + mu D2(C^3 - C) - nu D4 C
+// (Sec. 2.1, Eq. temporal; Sec. 2.2, Eq. 1d_hyper_scheme), for this thread's L
+// rows from the field C in cv (FP64, unscaled), in float-float: each C is split
+// into a float pair, the two rows on either side come from the neighbouring
+// threads (and CTAs of a cluster), the no-flux walls mirror them, and the cube,
+// the differences and the products are error-free transformations.  Rows past
+// the end of the system get f = 0.
+template <int L>
+__device__ __forceinline__ void step_rhs_ff(const double (&cv)[L], float muh, float mul, float nuh, float nul,
+                                            bool has_mu, bool has_nu, float (&fh)[L], float (&fl)[L], int n, int tg,
+                                            const Ctx& cx, const SmemView& sm) {
+  float ch[L], cl[L];
+#pragma unroll
+  for (int j = 0; j < L; ++j) split_scaled(cv[j], 0, ch[j], cl[j]);
+  float4 prv, nxt;
+  exchange_edges(make_float4(ch[0], ch[1], cl[0], cl[1]), make_float4(ch[L - 2], ch[L - 1], cl[L - 2], cl[L - 1]),
+                 cx, sm, prv, nxt);
+  float wh[L + 4], wl[L + 4];  // rows tg L - 2 .. tg L + L + 1
+  wh[0] = prv.x;
+  wh[1] = prv.y;
+  wl[0] = prv.z;
+  wl[1] = prv.w;
+  wh[L + 2] = nxt.x;
+  wh[L + 3] = nxt.y;
+  wl[L + 2] = nxt.z;
+  wl[L + 3] = nxt.w;
+#pragma unroll
+  for (int j = 0; j < L; ++j) {
+    wh[j + 2] = ch[j];
+    wl[j + 2] = cl[j];
+  }
+  fill_ghosts<L>(wh, tg, n);
+  fill_ghosts<L>(wl, tg, n);
+  float uh[L + 2], ul[L + 2];  // C^3 - C at rows tg L - 1 .. tg L + L
+  if (has_mu) {
+#pragma unroll
+    for (int q = 0; q < L + 2; ++q) cube_minus_ff(wh[q + 1], wl[q + 1], uh[q], ul[q]);
+  }
+#pragma unroll
+  for (int j = 0; j < L; ++j) {
+    float sh = wh[j + 2], sl = wl[j + 2];
+    if (has_mu) {
+      float dh, dl, ph, pl, a, e;
+      d2_ff(uh[j], ul[j], uh[j + 2], ul[j + 2], uh[j + 1], ul[j + 1], dh, dl);
+      mul_ff(muh, mul, dh, dl, ph, pl);
+      two_sum(sh, ph, a, e);
+      fast_two_sum(a, e + (sl + pl), sh, sl);
+    }
+    if (has_nu) {
+      float yh, yl, ph, pl, a, e;
+      d4_ff(wh[j], wl[j], wh[j + 1], wl[j + 1], wh[j + 2], wl[j + 2], wh[j + 3], wl[j + 3], wh[j + 4], wl[j + 4], yh,
+            yl);
+      mul_ff(nuh, nul, yh, yl, ph, pl);
+      two_sum(sh, -ph, a, e);
+      fast_two_sum(a, e + (sl - pl), sh, sl);
+    }
+    const bool in = tg * L + j < n;
+    fh[j] = in ? sh : 0.f;
+    fl[j] = in ? sl : 0.f;
+  }
+}
+
 // Load the thread's 1/alpha and beta (stored as float4 planes, see k_factor32).
 // gq: the system's factor block; PT threads per system; tg this thread's index.
 template <int L>
@@ -619,12 +731,19 @@ __device__ __forceinline__ void load_factors(Fac<L>& fc, const float4* __restric
 // system), otherwise C = 1.  Register budget: 6 CTAs of 4 warps per SM (at most
 // 85 registers a thread; the few that spill cost less than the latency the
 // extra CTA hides: 0.63 against 0.70 ms per parametric step at 5 CTAs).
-constexpr int min_blocks(int L, int WT) { return WT > 0 ? ((L <= 8 && 24 / WT > 0) ? 24 / WT : 1) : 1; }
+constexpr int min_blocks(int L, int WT, bool STEP) {
+  return WT > 0 ? ((L <= 8 && (STEP ? 20 : 24) / WT > 0) ? (STEP ? 20 : 24) / WT : 1) : 1;
+}
 
-template <int L, int WT, bool CL, bool RES64>
-__global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, min_blocks(L, WT))
+// STEP: the right-hand side is not given but assembled from the field in f as
+// f = C + mu_s D2(C^3 - C) - nu_s D4 C (step_rhs_ff), with no scaling (the field
+// must stay below 2^40 in magnitude; larger values are flagged as not converged);
+// x (normally = f) receives the new field.
+template <int L, int WT, bool CL, bool RES64, bool STEP = false>
+__global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, min_blocks(L, WT, STEP))
     k_solve32r(F32Tables T, const int32_t* __restrict__ sys, int Wrt, int Crt, int shared, const double* f, double* x,
-               int max_refine, int tol_log2, int vec_io) {
+               int max_refine, int tol_log2, int vec_io, const double* __restrict__ mu_s,
+               const double* __restrict__ nu_s) {
   static_assert(L % 4 == 0, "rows per thread must be a multiple of 4");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int W = WT > 0 ? WT : Wrt;
@@ -681,12 +800,20 @@ __global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, min_blocks(L, WT))
   // (the barrier inside also orders the scan plan's writes before any read)
   emax = system_max<int>(emax, cx.lane, cx.warp, W, C, sm.redi);
   if (C > 1 && t == 0) cta_total_maps(cx, sm);  // read by the other CTAs after the first scan's cluster barrier
-  const int kshift = emax - 1022;
+  const int kshift = STEP ? 0 : emax - 1022;
 
   float v[L], xh[L], xl[L];
   float fh[L], fl[L];
+  if (STEP) {
+    float muh = 0.f, mul = 0.f, nuh = 0.f, nul = 0.f;
+    if (mu_s) split_scaled(mu_s[ms], 0, muh, mul);
+    if (nu_s) split_scaled(nu_s[ms], 0, nuh, nul);
+    if (emax > 1023 + 40 && t == 0) atomicOr(T.info + 2, 1ull);  // field outside the FP32 path's range
+    step_rhs_ff<L>(fv, muh, mul, nuh, nul, muh != 0.f, nuh != 0.f, fh, fl, n, tg, cx, sm);
+  } else {
 #pragma unroll
-  for (int j = 0; j < L; ++j) split_scaled(fv[j], kshift, fh[j], fl[j]);
+    for (int j = 0; j < L; ++j) split_scaled(fv[j], kshift, fh[j], fl[j]);
+  }
 #pragma unroll
   for (int j = 0; j < L; ++j) v[j] = fh[j];
   int steps = 0;
@@ -848,13 +975,14 @@ __global__ void k_factor32(F32Tables T, int64_t nsys, const int32_t* __restrict_
   }
 }
 
-template <int L, int WT, bool CL, bool RES64>
+template <int L, int WT, bool CL, bool RES64, bool STEP>
 cudaError_t launch_bucket(const F32Tables& T, const int32_t* sys, const F32Bucket& b, int shared, const double* f,
-                          double* x, int max_refine, int tol_log2, cudaStream_t st) {
+                          double* x, int max_refine, int tol_log2, const double* mu, const double* nu,
+                          cudaStream_t st) {
   const int vec = ((((uintptr_t)f) | ((uintptr_t)x)) % 16 == 0) && b.even_offsets;
   const size_t smem = smem_bytes(b.W);
   if (smem > 48 * 1024) {  // above the default dynamic shared memory limit (a function attribute, not a stream op)
-    const cudaError_t e = cudaFuncSetAttribute(k_solve32r<L, WT, CL, RES64>,
+    const cudaError_t e = cudaFuncSetAttribute(k_solve32r<L, WT, CL, RES64, STEP>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
@@ -872,25 +1000,27 @@ cudaError_t launch_bucket(const F32Tables& T, const int32_t* sys, const F32Bucke
     cfg.attrs = attr;
     cfg.numAttrs = 1;
   }
-  return cudaLaunchKernelEx(&cfg, k_solve32r<L, WT, CL, RES64>, T, sys + b.first, b.W, b.C, shared, f, x, max_refine,
-                            tol_log2, vec);
+  return cudaLaunchKernelEx(&cfg, k_solve32r<L, WT, CL, RES64, STEP>, T, sys + b.first, b.W, b.C, shared, f, x,
+                            max_refine, tol_log2, vec, mu, nu);
 }
 
-template <int L, bool RES64>
+template <int L, bool RES64, bool STEP>
 cudaError_t dispatch_bucket(const F32Tables& T, const int32_t* sys, const F32Bucket& b, int shared, const double* f,
-                            double* x, int max_refine, int tol_log2, cudaStream_t st) {
-  if (b.C > 1) return launch_bucket<L, 0, true, RES64>(T, sys, b, shared, f, x, max_refine, tol_log2, st);
+                            double* x, int max_refine, int tol_log2, const double* mu, const double* nu,
+                            cudaStream_t st) {
+  if (b.C > 1) return launch_bucket<L, 0, true, RES64, STEP>(T, sys, b, shared, f, x, max_refine, tol_log2, mu, nu, st);
   if (!RES64) {
     switch (b.W) {
-      case 1: return launch_bucket<L, 1, false, RES64>(T, sys, b, shared, f, x, max_refine, tol_log2, st);
-      case 2: return launch_bucket<L, 2, false, RES64>(T, sys, b, shared, f, x, max_refine, tol_log2, st);
-      case 4: return launch_bucket<L, 4, false, RES64>(T, sys, b, shared, f, x, max_refine, tol_log2, st);
-      case 8: return launch_bucket<L, 8, false, RES64>(T, sys, b, shared, f, x, max_refine, tol_log2, st);
-      case 16: return launch_bucket<L, 16, false, RES64>(T, sys, b, shared, f, x, max_refine, tol_log2, st);
+      case 1: return launch_bucket<L, 1, false, RES64, STEP>(T, sys, b, shared, f, x, max_refine, tol_log2, mu, nu, st);
+      case 2: return launch_bucket<L, 2, false, RES64, STEP>(T, sys, b, shared, f, x, max_refine, tol_log2, mu, nu, st);
+      case 4: return launch_bucket<L, 4, false, RES64, STEP>(T, sys, b, shared, f, x, max_refine, tol_log2, mu, nu, st);
+      case 8: return launch_bucket<L, 8, false, RES64, STEP>(T, sys, b, shared, f, x, max_refine, tol_log2, mu, nu, st);
+      case 16:
+        return launch_bucket<L, 16, false, RES64, STEP>(T, sys, b, shared, f, x, max_refine, tol_log2, mu, nu, st);
       default: break;
     }
   }
-  return launch_bucket<L, 0, false, RES64>(T, sys, b, shared, f, x, max_refine, tol_log2, st);
+  return launch_bucket<L, 0, false, RES64, STEP>(T, sys, b, shared, f, x, max_refine, tol_log2, mu, nu, st);
 }
 
 }  // namespace
@@ -903,12 +1033,21 @@ cudaError_t launch_factor32(const F32Tables& T, const int32_t* shape, int64_t ns
 }
 
 cudaError_t launch_solve32r(const F32Tables& T, const int32_t* sys, const F32Bucket& b, int shared, const double* f,
-                            double* x, int max_refine, int residual_f64, int tol_log2, cudaStream_t st) {
+                            double* x, int max_refine, int residual_f64, int tol_log2, cudaStream_t st,
+                            const double* mu, const double* nu, bool step) {
   if (b.count == 0) return cudaSuccess;
-  if (b.L == 4) return residual_f64 ? dispatch_bucket<4, true>(T, sys, b, shared, f, x, max_refine, tol_log2, st)
-                                    : dispatch_bucket<4, false>(T, sys, b, shared, f, x, max_refine, tol_log2, st);
-  if (b.L == 8) return residual_f64 ? dispatch_bucket<8, true>(T, sys, b, shared, f, x, max_refine, tol_log2, st)
-                                    : dispatch_bucket<8, false>(T, sys, b, shared, f, x, max_refine, tol_log2, st);
+  if (step) {  // float-float residual only
+    if (residual_f64) return cudaErrorInvalidValue;
+    if (b.L == 4) return dispatch_bucket<4, false, true>(T, sys, b, shared, f, x, max_refine, tol_log2, mu, nu, st);
+    if (b.L == 8) return dispatch_bucket<8, false, true>(T, sys, b, shared, f, x, max_refine, tol_log2, mu, nu, st);
+    return cudaErrorInvalidValue;
+  }
+  if (b.L == 4)
+    return residual_f64 ? dispatch_bucket<4, true, false>(T, sys, b, shared, f, x, max_refine, tol_log2, mu, nu, st)
+                        : dispatch_bucket<4, false, false>(T, sys, b, shared, f, x, max_refine, tol_log2, mu, nu, st);
+  if (b.L == 8)
+    return residual_f64 ? dispatch_bucket<8, true, false>(T, sys, b, shared, f, x, max_refine, tol_log2, mu, nu, st)
+                        : dispatch_bucket<8, false, false>(T, sys, b, shared, f, x, max_refine, tol_log2, mu, nu, st);
   return cudaErrorInvalidValue;
 }
 

@@ -121,8 +121,11 @@ cudaError_t launch_refactor_solve64(const DevPlan& P, F64Factors F, const double
                                     double* gscr, int block_warps, int64_t g0, int64_t g1, cudaStream_t st);
 cudaError_t launch_adjoint64(const DevPlan& P, F64Factors F, const double* f, double* x, double* gscr,
                              int block_warps, cudaStream_t st);
+// step: f is the field C and the kernel assembles the right-hand side C + mu D2(C^3 - C) - nu D4 C
+// (float-float) before the solve (pent_step_batch); mu, nu per factored system, or NULL.
 cudaError_t launch_solve32r(const F32Tables& T, const int32_t* sys, const F32Bucket& b, int shared, const double* f,
-                            double* x, int max_refine, int residual_f64, int tol_log2, cudaStream_t st);
+                            double* x, int max_refine, int residual_f64, int tol_log2, cudaStream_t st,
+                            const double* mu = nullptr, const double* nu = nullptr, bool step = false);
 cudaError_t launch_factor_periodic(const PerArgs& A, const double* a, const double* b, const double* c,
                                    const double* d, const double* e, const double* sigma, cudaStream_t st);
 // rhs: assemble f_i = C_i + mu_s (D2 (C^3 - C))_i - nu_s (D4 C)_i from the field in f (periodic stencils).

@@ -844,7 +844,15 @@ pent_status pent_solve_steps(pent_plan* p, double* x, int64_t nsteps, int max_re
 // One pent_step_batch step on a no-flux FP64 plan: the fused right-hand side
 // and solve for the thread-per-system runs; for partitioned runs the right-hand
 // side is written out first, then solved by the chunked kernels.
-static pent_status step_launch(pent_plan* p, const double* mu, const double* nu, double* C) {
+static pent_status step_launch(pent_plan* p, const double* mu, const double* nu, double* C, int max_refine) {
+  if (p->precision == PENT_F32_REFINE) {
+    const F32Tables T = p->f32();
+    const int32_t* sys = p->at<int32_t>(p->r_sys32);
+    const cudaError_t err = fork_join(p, p->buckets.size(), [&](size_t i, cudaStream_t st) {
+      return launch_solve32r(T, sys, p->buckets[i], p->shared, C, C, max_refine, 0, p->tol_log2, st, mu, nu, true);
+    });
+    return cuda_status(err);
+  }
   const DevPlan P = p->dev();
   const F64Factors F = p->f64();
   double* gscr = p->at<double>(p->r_scr);
@@ -868,18 +876,21 @@ pent_status pent_step_batch(pent_plan* p, const double* mu, const double* nu, do
   if (st != PENT_OK) return st;
   if (nsteps < 0) return PENT_EINVAL;
   if ((((uintptr_t)mu) | ((uintptr_t)nu)) % sizeof(double)) return PENT_EINVAL;
-  // no-flux plans: per-system FP64 factors from sigma (pent_factor_hyperdiff)
-  if (!p->periodic && (p->precision != PENT_F64 || p->shared || p->factored != 2)) return PENT_EINVAL;
+  // no-flux plans: factors from sigma (pent_factor_hyperdiff); FP64 per-system, or FP32+refine with the
+  // float-float residual
+  if (!p->periodic && p->factored != 2) return PENT_EINVAL;
+  if (!p->periodic && p->precision == PENT_F64 && p->shared) return PENT_EINVAL;
+  if (p->precision == PENT_F32_REFINE && p->residual != PENT_RESIDUAL_FF) return PENT_EINVAL;
   if (nsteps == 0) return PENT_OK;
   auto launch = [&]() -> pent_status {
     if (p->periodic) return cuda_status(launch_solve_periodic(p->per(), C, C, mu, nu, true, p->stream));
-    return step_launch(p, mu, nu, C);
+    return step_launch(p, mu, nu, C, max_refine);
   };
   if (nsteps == 1) return launch();
   uint64_t h = 1469598103934665603ull;
   for (uint64_t v : {(uint64_t)(uintptr_t)mu, (uint64_t)(uintptr_t)nu, (uint64_t)p->cfg_version})
     h = (h ^ v) * 1099511628211ull;
-  const auto key = std::make_tuple((const void*)C, nsteps, -2, (int64_t)(h & 0x7fffffffffffffffull));
+  const auto key = std::make_tuple((const void*)C, nsteps, -2 - max_refine, (int64_t)(h & 0x7fffffffffffffffull));
   return run_steps(p, key, nsteps, launch);
 }
 

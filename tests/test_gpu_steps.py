@@ -163,3 +163,44 @@ def test_refactor_solve_each_step(case):
     f = synth.uniform(841, 0, int(ns.sum()), -1, 1)
     ref = _oracle_refactor_solve(ns, np.broadcast_to(sig, (batch,)) if case == "shared" else sig, f)
     assert sys_err(plan.solve(dev(f)).cpu().numpy(), ref, ns) <= TOL
+
+
+# ----------------------------------------------------------------------------- FP32 + refinement
+
+LONG = np.array([5000, 9000, 4097, 300, 1, 2, 3, 64, 129, 1024, 2048, 4096])
+
+
+@pytest.mark.parametrize("cn", [False, True])
+def test_steps_f32_refine_match_oracle(cn):
+    """FP32+refine steps: the right-hand side in float-float, FP32 solves refined against the float-float
+    residual; uneven lengths from one row to clusters of CTAs (up to 9,000 rows)."""
+    ns = np.concatenate([UNEVEN, LONG])
+    batch = len(ns)
+    sig = synth.log_uniform(850, 0, batch, 1e-3, 10.0)
+    mu = None if cn else synth.log_uniform(850, batch, batch, 1e-4, 0.5)
+    nu = sig if cn else None
+    C0 = synth.uniform(850, 2 * batch, int(ns.sum()), -0.9, 0.9)
+    steps = 5
+    ref = oracle.explicit_steps(ns, sig, mu, nu, C0, steps)
+    plan = pb.Plan(list(ns), precision=pb.PENT_F32_REFINE)
+    plan.factor_hyperdiff(dev(sig))
+    C = dev(C0)
+    plan.step(C, mu=dev(mu) if mu is not None else None, nu=dev(nu) if nu is not None else None, nsteps=steps,
+              max_refine=3)
+    assert plan.info()[0] == pb.PENT_OK
+    assert sys_err(C.cpu().numpy(), ref, ns) <= TOL
+
+
+def test_cahn_hilliard_f32_refine_shared_and_mass():
+    n, batch, steps = 1024, 256, 10
+    sigma, mu = 2.5, 0.05
+    C0 = synth.uniform(860, 0, batch * n, -1, 1)
+    ref = oracle.explicit_steps(np.full(batch, n), [sigma], [mu], None, C0, steps, shared=True)
+    plan = pb.Plan(n, batch=batch, shared=True, precision=pb.PENT_F32_REFINE)
+    plan.factor_hyperdiff(dev([sigma]))
+    C = dev(C0)
+    plan.step(C, mu=dev([mu]), nsteps=steps, max_refine=2)
+    out = C.cpu().numpy()
+    assert sys_err(out, ref, np.full(batch, n)) <= TOL
+    m0 = C0.reshape(batch, n).sum(1)
+    assert np.max(np.abs(out.reshape(batch, n).sum(1) - m0)) <= 1e-12 * np.abs(C0).reshape(batch, n).sum(1).max()
