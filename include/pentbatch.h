@@ -244,7 +244,11 @@ pent_status pent_refactor_solve_hyperdiff(pent_plan* plan, const double* d_sigma
  * then L^T y = z (y_i = (z_i - beta_{i+1} y_{i+1} - epsilon_{i+2} y_{i+2}) /
  * alpha_i).  The transposed solve is not in the paper; it follows from its
  * factors (Sec. 2.4, the definitions of L and R).  Same layout and aliasing
- * rules as pent_solve_batch.  PENT_F64 plans only (others: PENT_EINVAL).
+ * rules as pent_solve_batch.  Matrices built by pent_factor_hyperdiff are
+ * symmetric (A = I + sigma D2N^2), so for them A^{-T} f = A^{-1} f is computed
+ * by the solve itself (either precision; max_refine as pent_solve_batch);
+ * general bands need a PENT_F64 plan (others: PENT_EINVAL); periodic plans:
+ * PENT_EINVAL.
  */
 pent_status pent_adjoint_solve_batch(pent_plan* plan, const double* f, double* x, int max_refine);
 

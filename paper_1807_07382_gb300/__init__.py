@@ -211,13 +211,15 @@ class Plan:
                                       int(max_refine)), "pent_step_batch")
         return C
 
-    def adjoint_solve(self, f, x=None):
-        """y_s = A_s^{-T} f_s from the stored factors."""
+    def adjoint_solve(self, f, x=None, max_refine: int = 2):
+        """y_s = A_s^{-T} f_s from the stored factors (for matrices built from sigma, which are
+        symmetric, by the solve itself; max_refine as in solve)."""
         torch = _torch()
         if x is None:
             x = torch.empty_like(f)
         check(self._L.pent_adjoint_solve_batch(self._h, _dev_ptr(f, "f", torch.float64),
-                                               _dev_ptr(x, "x", torch.float64), 0), "pent_adjoint_solve_batch")
+                                               _dev_ptr(x, "x", torch.float64), int(max_refine)),
+              "pent_adjoint_solve_batch")
         return x
 
     def sigma_grad(self, mu, x, g_sigma):

@@ -272,11 +272,15 @@ bool parse_tune_cache(const char* path, std::vector<pent_plan::Rule>* out) {
 // length, about 0.3 us per row on GB300, while the whole batch streams at
 // about 64 bytes per row at ~6 TB/s; a group is cut into chunks when its walk
 // would outlast the batch, and never below 2048 rows (where the doubled
-// arithmetic of the partitioned passes costs more than it hides).
+// arithmetic of the partitioned passes costs more than it hides) -- unless the
+// batch has fewer than 1024 groups of 32 systems (under about 7 warps per SM
+// of a GB300), when the walks alone cannot hide their latency and chunks pay
+// from 512 rows on (4,096 systems of 1024 rows: 0.25 against 0.44 ms a solve).
 int64_t part_threshold(const pent_plan* p) {
   if (p->shared || p->part_rows == 0) return INT64_MAX;
   if (p->part_rows > 0) return p->part_rows;
-  return std::max<int64_t>(2048, p->rows / 28000);
+  const int64_t floor_rows = p->ngroups < 1024 ? 512 : 2048;
+  return std::max<int64_t>(floor_rows, p->rows / 28000);
 }
 
 // FP64 launches: groups (longest first) in runs of equal unroll / block warps,
@@ -922,7 +926,12 @@ pent_status pent_refactor_solve_hyperdiff(pent_plan* p, const double* d_sigma, c
 pent_status pent_adjoint_solve_batch(pent_plan* p, const double* f, double* x, int max_refine) {
   pent_status st = check_solve(p, f, x, max_refine);
   if (st != PENT_OK) return st;
-  if (p->precision != PENT_F64 || p->periodic) return PENT_EINVAL;
+  if (p->periodic) return PENT_EINVAL;
+  // A = I + sigma D4 with the reflected D4 = D2N^2 is symmetric: A^{-T} f = A^{-1} f, by the
+  // (faster, partitioned where the plan partitions) forward kernels and, for FP32+refine
+  // plans, with their refinement
+  if (p->factored == 2) return solve_launch(p, f, x, max_refine);
+  if (p->precision != PENT_F64) return PENT_EINVAL;
   return cuda_status(
       launch_adjoint64(p->dev(), p->f64(), f, x, p->at<double>(p->r_scr), p->block_warps, p->stream));
 }

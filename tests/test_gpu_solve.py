@@ -300,7 +300,23 @@ def test_f64_partitioned_hyperdiff_uneven_steps_and_graph():
     for _ in range(w.steps):
         plan.solve(y, y)
     assert torch.equal(x, y)
-    # and the adjoint of a partitioned plan still runs the thread-per-system adjoint
+    # the adjoint of the symmetric hyperdiffusion matrix runs through the same (partitioned) solve
     mu = plan.adjoint_solve(dev(w.field0))
     mref = oracle.hyperdiff_steps(w.n, w.sigma, w.field0, 1)  # A is symmetric: A^-T f = A^-1 f
     assert sys_rel_err(host(mu), mref, w.n) <= TOL
+
+
+@pytest.mark.parametrize("prec", [pb.PENT_F64, pb.PENT_F32_REFINE])
+def test_adjoint_of_sigma_built_matrices_matches_transposed_oracle(prec):
+    """Matrices from sigma are symmetric; their adjoint solve runs through the solve kernels and must
+    equal the oracle's adjoint (the transposed band, factored and solved)."""
+    ns = np.array([700, 1024, 33, 2500, 64, 5] * 12)
+    sig = synth.log_uniform(870, 0, len(ns), 1e-3, 10.0)
+    f = synth.uniform(870, len(ns), int(ns.sum()), -1, 1)
+    band = oracle.band_hyperdiff_batch(ns, sig)
+    ref = oracle.adjoint_solve_batch(ns, band, f)
+    plan = pb.Plan(list(ns), precision=prec)
+    plan.factor_hyperdiff(dev(sig))
+    y = plan.adjoint_solve(dev(f), max_refine=3)
+    assert plan.info()[0] == pb.PENT_OK
+    assert sys_rel_err(host(y), ref, ns) <= TOL

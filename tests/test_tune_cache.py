@@ -175,7 +175,14 @@ def test_long_groups_are_partitioned_automatically(L):
         assert L.pent_plan_set_option(h, _lib.PENT_OPT_PARTITION_ROWS, -2) == _lib.PENT_EINVAL
     finally:
         L.pent_plan_destroy(h)
-    # a uniform batch of 1024-row systems is never partitioned by default
+    # a uniform batch of 1024-row systems that fills the GPU (65,536 systems, 2,048 groups) keeps the
+    # thread-per-system walk; a small one (4,096 systems, 128 groups) is cut into chunks from 512 rows
+    st, h = create(L, [1024] * 65536, F64)
+    assert st == 0 and config(L, h, 0)[0] in (2, 4, 8)
+    L.pent_plan_destroy(h)
     st, h = create(L, [1024] * 4096, F64)
+    assert st == 0 and config(L, h, 0) == (0, 256)
+    L.pent_plan_destroy(h)
+    st, h = create(L, [500] * 4096, F64)
     assert st == 0 and config(L, h, 0)[0] in (2, 4, 8)
     L.pent_plan_destroy(h)
