@@ -466,23 +466,31 @@ def run_workloads(names, args):
         elif name == "periodic_cn":
             w = synth.periodic_cn(batch=args.batch or 65536)
             n = int(w.n[0])
-            plan = pb.Plan(n, batch=w.batch, shared=True, periodic=True, stream=stream)
             s = torch.from_numpy(w.sigma).to(dev)
-            plan.factor_hyperdiff(s)
-            C = torch.from_numpy(w.field0).to(dev)
             pick = np.arange(0, w.batch, max(1, w.batch // 128))
-            c1 = C.clone()
-            plan.step(c1, nu=s)
             ref = oracle.periodic_steps(n, w.sigma, w.field0.reshape(w.batch, n)[pick].reshape(-1), 1, cn=True,
                                         shared=True)
-            err = _sys_err(c1.cpu().numpy().reshape(w.batch, n)[pick], ref.reshape(len(pick), n))
-            plan.step(C.clone(), nu=s, nsteps=w.steps)
-            ms, ck = _time_device(stream, lambda: plan.step(C, nu=s, nsteps=w.steps), w.steps, dev)
-            _line(name, f"periodic Crank-Nicolson hyperdiffusion (Navon reduction), {w.batch:,} systems x N={n}, shared "
-                  "sigma_x = dt/(2 dx^4) = 343.6 (dt=1e-8, dx=1/512), C0 U[-1,1], 250 steps (1 graph)",
-                  w.rows, w.steps, ms, 16, "k_solve_periodic<shared, rhs>", err, clocks=ck,
-                  extra={"note": "reduction shared by the batch (broadcast); f assembled in the forward sweep",
-                         "err_sample": f"{len(pick)} systems, one step"})
+            for prec, pname, alg, kern in ((pb.PENT_F64, "f64", 16, "k_solve_periodic<shared, rhs>"),
+                                           (pb.PENT_F32_REFINE, "f32_refine", 16, "k_solve32r<step, periodic>")):
+                plan = pb.Plan(n, batch=w.batch, shared=True, periodic=True, stream=stream, precision=prec)
+                plan.factor_hyperdiff(s)
+                C = torch.from_numpy(w.field0).to(dev)
+                c1 = C.clone()
+                plan.step(c1, nu=s, max_refine=3)
+                err = _sys_err(c1.cpu().numpy().reshape(w.batch, n)[pick], ref.reshape(len(pick), n))
+                used = plan.info()[3]
+                plan.step(C.clone(), nu=s, nsteps=w.steps, max_refine=3)
+                ms, ck = _time_device(stream, lambda: plan.step(C, nu=s, nsteps=w.steps, max_refine=3), w.steps, dev)
+                _line(f"{name}_{pname}", f"periodic Crank-Nicolson hyperdiffusion (Navon reduction), {w.batch:,} systems "
+                      f"x N={n}, shared sigma_x = dt/(2 dx^4) = 343.6 (dt=1e-8, dx=1/512), C0 U[-1,1], 250 steps "
+                      "(1 graph)", w.rows, w.steps, ms, alg, kern, err, clocks=ck,
+                      dtype="f64" if prec == pb.PENT_F64 else "f32",
+                      extra={"note": "reduction shared by the batch; f assembled in the forward sweep"
+                                     + ("" if prec == pb.PENT_F64 else "; FP32 solve of E + 2x2 tail, refined "
+                                        "against the float-float residual (max_refine 3; kappa ~ 5.5e3)"),
+                             "refine_steps_used": used if prec != pb.PENT_F64 else 0,
+                             "err_sample": f"{len(pick)} systems, one step"})
+                del plan
         elif name == "ch1d":
             w = synth.ch_batch(batch=args.batch or 65536)
             n = int(w.n[0])

@@ -136,8 +136,12 @@ enum {
                                       time, and at least 2048 rows).  Before pent_plan_bind. */
   PENT_OPT_PERIODIC = 8            /* 1: the systems are cyclic (Sec. 2.3, Eq. matrix_sys1): row i reads
                                       x_{i-2} .. x_{i+2} with column indices modulo n, so the first two rows
-                                      reach the last two columns and vice versa.  PENT_F64 plans of uniform
-                                      n >= 5 only, before pent_plan_bind.  Solved by Navon's reduction as the
+                                      reach the last two columns and vice versa.  Plans of uniform n >= 5
+                                      only, before pent_plan_bind.  PENT_F32_REFINE periodic plans take the
+                                      periodic hyperdiffusion matrix (pent_factor_hyperdiff) and refine
+                                      against the float-float residual; each FP32 solve is the solve of E
+                                      followed by the 2 x 2 tail, with Z = E^{-1} k stored beside the
+                                      factors (the matrix is symmetric, so h = k).  Solved by Navon's reduction as the
                                       paper describes it: the last two unknowns from a 2 x 2 system
                                       (Eq. first_two), the other n - 2 from the pentadiagonal E that remains
                                       (Eq. solve); everything that depends on the matrix alone (factors of E,

@@ -67,8 +67,9 @@ __device__ __forceinline__ float small_uint_to_float(unsigned v) {
 }
 
 // v * 2^-k split into hi + lo floats (hi: v truncated to 24 significant bits,
-// lo: the next 23 bits, truncated; together 47 bits, a relative error below
-// 2^-47), using integer operations only.  Values whose scaled magnitude is below
+// lo: the next 23 bits, rounded to nearest; together 47 bits, a relative error
+// below 2^-48, unbiased so that it does not build up over many time steps),
+// using integer operations only.  Values whose scaled magnitude is below
 // 2^-126 are flushed to zero; the caller picks k so that the largest |v| of the
 // system scales to just below 1.
 __device__ __forceinline__ void split_scaled(double v, int k, float& hi, float& lo) {
@@ -88,7 +89,8 @@ __device__ __forceinline__ void split_scaled(double v, int k, float& hi, float& 
     lo = 0.0f;
     return;
   }
-  const unsigned rem = (unsigned)(U >> 6) & 0x7fffffu;  // mantissa bits 6..28 (the 23 below hi's)
+  // mantissa bits 6..28 (the 23 below hi's), rounded by bit 5; 2^23 still converts exactly below
+  const unsigned rem = ((unsigned)(U >> 6) & 0x7fffffu) + ((unsigned)(U >> 5) & 1u);
   const float scale = __uint_as_float((unsigned)(Es - 942) << 23);  // 2^(Es - 1069)
   lo = __uint_as_float(__float_as_uint(__fmul_rn(small_uint_to_float(rem), scale)) ^ sign);
 }
@@ -100,8 +102,8 @@ __device__ __noinline__ double ff_to_double_slow(float h, float l, int k) { retu
 // (h + l) * 2^k as a double for a normalised float-float pair (|l| <= ulp(h) / 2),
 // without FP64 instructions: h's bits are moved into a double, and l, counted
 // in units in the last place of that double (l * 2^(52 - e(h)), an integer
-// below 2^29 in magnitude, rounded towards zero: an error under one unit), is
-// added to its 64-bit pattern.  Where h is a power of two and the sum is
+// below 2^29 in magnitude, rounded to nearest: an error of at most half a unit),
+// is added to its 64-bit pattern.  Where h is a power of two and the sum is
 // smaller, it falls in the binade below, whose units are half as large.  The
 // sum cannot reach the binade above (|l| <= ulp(h) / 2).  The fast path needs
 // 2^-74 <= |h| < 2^128 (so that l's scaling stays in the normal float range);
@@ -115,7 +117,7 @@ __device__ __forceinline__ double ff_to_double_shift(float h, float l, int k) {
   if (eh < 53 || eh == 255 || eh + 896 + k < 2 || eh + 896 + k > 2045) return ff_to_double_slow(h, l, k);
   // l in units of the double's last place, signed as the change of |h + l|
   const float units = __fmul_rn(l, __uint_as_float((unsigned)(306 - eh) << 23));  // l * 2^(179 - eh) = l * 2^(52 - e(h))
-  int kk = __float2int_rz(units);
+  int kk = __float2int_rn(units);
   kk = (uh & 0x80000000u) ? -kk : kk;
   if ((ah & 0x7fffffu) == 0u && kk < 0) kk *= 2;
   const unsigned long long bits = ((unsigned long long)(uh & 0x80000000u) << 32) |
@@ -227,12 +229,14 @@ struct SmemView {
   float2* utot;   // [4][W + 1]: affine parts of the warp and CTA maps of one scan
   float* red;     // [4][W + 1]
   int* redi;      // [W + 1]
+  float* wrap;    // [16]: periodic systems: rows 0, 1, n-2, n-1 (hi, lo) for the wrap-around
+                  // neighbours, then the tail of Navon's reduction (CTA 0's copy serves the cluster)
 };
 
 __host__ __device__ inline size_t smem_bytes(int W) {
   const size_t P = 32 * (size_t)W;
   return sizeof(float4) * (2 * kMaxLev * P + 2 * P + 2 * (W + 1) + 2 * P) + sizeof(float2) * 4 * (W + 1) +
-         sizeof(float) * 4 * (W + 1) + sizeof(int) * (W + 1);
+         sizeof(float) * 4 * (W + 1) + sizeof(int) * (W + 1) + sizeof(float) * 16;
 }
 
 __device__ __forceinline__ SmemView smem_view(unsigned char* base, int W) {
@@ -245,6 +249,7 @@ __device__ __forceinline__ SmemView smem_view(unsigned char* base, int W) {
   v.utot = reinterpret_cast<float2*>(v.edge + 2 * P);
   v.red = reinterpret_cast<float*>(v.utot + 4 * (W + 1));
   v.redi = reinterpret_cast<int*>(v.red + 4 * (W + 1));
+  v.wrap = reinterpret_cast<float*>(v.redi + (W + 1));
   return v;
 }
 
@@ -595,6 +600,142 @@ __device__ __forceinline__ void residual_f64(const double (&fd)[L], const double
   }
 }
 
+// ---------------------------------------------------------------- periodic systems (Sec. 2.3)
+//
+// Row r of a periodic system of n rows (n >= 5) lives in thread r / L of the
+// system, slot r % L.  The rows that wrap around -- 0 and 1 after row n - 1,
+// n - 2 and n - 1 before row 0 -- are published by their owners into CTA 0's
+// `wrap` slots before an exchange's barrier and read after it.
+
+__device__ __forceinline__ float* wrap_slots(const Ctx& cx, const SmemView& sm) {
+  return cx.C > 1 ? remote(sm.wrap, 0) : sm.wrap;
+}
+
+// Owners of rows 0, 1, n-2, n-1 write (hi, lo) to slots 0..7.
+template <int L>
+__device__ __forceinline__ void publish_wrap(const float (&h)[L], const float (&l)[L], int tg, int n, float* slots) {
+#pragma unroll
+  for (int j = 0; j < L; ++j) {
+    const int r = tg * L + j;
+    const int k = (r == 0) ? 0 : (r == 1) ? 1 : (r == n - 2) ? 2 : (r == n - 1) ? 3 : -1;
+    if (k >= 0) {
+      slots[2 * k] = h[j];
+      slots[2 * k + 1] = l[j];
+    }
+  }
+}
+
+// Window w[0 .. L+3] holds rows tg L - 2 .. tg L + L + 1; put the wrapped rows in
+// (rows -2, -1 are n-2, n-1; rows n, n+1 are 0, 1).  Rows past n + 1 only feed
+// padding rows.
+template <int L>
+__device__ __forceinline__ void fill_wrap(float (&wh)[L + 4], float (&wl)[L + 4], int tg, int n, const float* slots) {
+  if (tg == 0) {
+    wh[0] = slots[4];
+    wl[0] = slots[5];
+    wh[1] = slots[6];
+    wl[1] = slots[7];
+  }
+#pragma unroll
+  for (int q = 2; q < L + 4; ++q) {
+    const int r = tg * L + q - 2;
+    if (r == n) {
+      wh[q] = slots[0];
+      wl[q] = slots[1];
+    } else if (r == n + 1) {
+      wh[q] = slots[2];
+      wl[q] = slots[3];
+    }
+  }
+}
+
+// Navon's reduction around the FP32 solve of E (the first m = n - 2 rows; rows
+// m, m+1 are padding of the factorisation).  The periodic hyperdiffusion matrix
+// is symmetric, so h = k and E^{-1} k = Z (stored per row): with y = E^{-1} f-hat
+// from the plain solve, Eq. (first_two) gives t = S^{-1} (f_tail - h^T y), where
+// h^T y needs only y_0, y_1, y_{m-2}, y_{m-1}, and Eq. (solve) gives
+// x = E^{-1} (f-hat - k t) = y - Z t.  periodic_tail_rhs publishes f_m, f_{m+1}
+// before the solve; periodic_tail finishes after it.
+template <int L>
+__device__ __forceinline__ void periodic_tail_rhs(const float (&v)[L], int tg, int n, const Ctx& cx,
+                                                  const SmemView& sm) {
+  float* slots = wrap_slots(cx, sm) + 8;
+#pragma unroll
+  for (int j = 0; j < L; ++j) {
+    const int r = tg * L + j;
+    if (r == n - 2) slots[4] = v[j];
+    if (r == n - 1) slots[5] = v[j];
+  }
+}
+
+template <int L, int NPL>
+__device__ __forceinline__ void periodic_tail(float (&v)[L], const float4* __restrict__ gq, int PT, int tg, int n,
+                                              float sg, float4 si, const Ctx& cx, const SmemView& sm) {
+  const int m = n - 2;
+  float* slots = wrap_slots(cx, sm) + 8;
+#pragma unroll
+  for (int j = 0; j < L; ++j) {
+    const int r = tg * L + j;
+    if (r == 0) slots[0] = v[j];
+    if (r == 1) slots[1] = v[j];
+    if (r == m - 2) slots[2] = v[j];
+    if (r == m - 1) slots[3] = v[j];
+  }
+  csync(cx.C);
+  const float y0 = slots[0], y1 = slots[1], ym2 = slots[2], ym1 = slots[3], fa = slots[4], fb = slots[5];
+  // rows n-2 and n-1 of A restricted to E's columns: (sigma @ 0, sigma @ m-2, -4 sigma @ m-1) and
+  // (-4 sigma @ 0, sigma @ 1, sigma @ m-1)
+  const float r0 = fa - sg * fmaf(-4.f, ym1, y0 + ym2);
+  const float r1 = fb - sg * fmaf(-4.f, y0, y1 + ym1);
+  const float t0 = fmaf(si.x, r0, si.y * r1), t1 = fmaf(si.z, r0, si.w * r1);
+#pragma unroll
+  for (int jq = 0; jq < L / 4; ++jq) {
+    const float4 za = __ldg(gq + (int64_t)(jq * NPL + 2) * PT + tg), zb = __ldg(gq + (int64_t)(jq * NPL + 3) * PT + tg);
+    const float z0[4] = {za.x, za.y, za.z, za.w}, z1[4] = {zb.x, zb.y, zb.z, zb.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = 4 * jq + u, r = tg * L + j;
+      v[j] = (r < m) ? fmaf(-z0[u], t0, fmaf(-z1[u], t1, v[j])) : (r == m) ? t0 : (r == m + 1) ? t1 : 0.f;
+    }
+  }
+}
+
+// r = f - A x for a periodic system, in float-float (the stencil of
+// residual_row with wrapped neighbours).
+template <int L, bool XL0>
+__device__ __forceinline__ void residual_ff_per(const float (&fh)[L], const float (&fl)[L], const float (&xh)[L],
+                                                const float (&xl)[L], float (&r)[L], float sgh, float sgl, int n,
+                                                int tg, const Ctx& cx, const SmemView& sm) {
+  float zl[L];
+#pragma unroll
+  for (int j = 0; j < L; ++j) zl[j] = XL0 ? 0.f : xl[j];
+  publish_wrap<L>(xh, zl, tg, n, wrap_slots(cx, sm));
+  float4 prv, nxt;
+  exchange_edges(make_float4(xh[0], xh[1], zl[0], zl[1]), make_float4(xh[L - 2], xh[L - 1], zl[L - 2], zl[L - 1]),
+                 cx, sm, prv, nxt);
+  float wh[L + 4], wl[L + 4];
+  wh[0] = prv.x;
+  wh[1] = prv.y;
+  wh[L + 2] = nxt.x;
+  wh[L + 3] = nxt.y;
+  wl[0] = prv.z;
+  wl[1] = prv.w;
+  wl[L + 2] = nxt.z;
+  wl[L + 3] = nxt.w;
+#pragma unroll
+  for (int j = 0; j < L; ++j) {
+    wh[j + 2] = xh[j];
+    wl[j + 2] = zl[j];
+  }
+  fill_wrap<L>(wh, wl, tg, n, wrap_slots(cx, sm));
+#pragma unroll
+  for (int j = 0; j < L; ++j) {
+    const float res = residual_row(wh[j], wl[j], wh[j + 1], wl[j + 1], wh[j + 2], wl[j + 2], wh[j + 3], wl[j + 3],
+                                   wh[j + 4], wl[j + 4], fh[j], fl[j], sgh, sgl);
+    r[j] = (tg * L + j < n) ? res : 0.f;
+  }
+}
+
 // ---------------------------------------------------------------- explicit part of a time step (float-float)
 
 // C^3 - C for C = ch + cl (float-float; cl^2 is below the pair's resolution and dropped).
@@ -652,13 +793,17 @@ __device__ __forceinline__ void mul_ff(float ph, float pl, float qh, float ql, f
 // threads (and CTAs of a cluster), the no-flux walls mirror them, and the cube,
 // the differences and the products are error-free transformations.  Rows past
 // the end of the system get f = 0.
-template <int L>
+// twice: the Crank-Nicolson form with nu = sigma of the matrix, where
+// A C' = C - sigma D4 C = 2 C - A C: the right-hand side is 2 C + mu D2(C^3 - C)
+// (no cancellation) and the caller subtracts C from the solution.
+template <int L, bool PER = false>
 __device__ __forceinline__ void step_rhs_ff(const double (&cv)[L], float muh, float mul, float nuh, float nul,
-                                            bool has_mu, bool has_nu, float (&fh)[L], float (&fl)[L], int n, int tg,
-                                            const Ctx& cx, const SmemView& sm) {
+                                            bool has_mu, bool has_nu, bool twice, float (&fh)[L], float (&fl)[L],
+                                            int n, int tg, const Ctx& cx, const SmemView& sm) {
   float ch[L], cl[L];
 #pragma unroll
   for (int j = 0; j < L; ++j) split_scaled(cv[j], 0, ch[j], cl[j]);
+  if (PER) publish_wrap<L>(ch, cl, tg, n, wrap_slots(cx, sm));
   float4 prv, nxt;
   exchange_edges(make_float4(ch[0], ch[1], cl[0], cl[1]), make_float4(ch[L - 2], ch[L - 1], cl[L - 2], cl[L - 1]),
                  cx, sm, prv, nxt);
@@ -676,8 +821,12 @@ __device__ __forceinline__ void step_rhs_ff(const double (&cv)[L], float muh, fl
     wh[j + 2] = ch[j];
     wl[j + 2] = cl[j];
   }
-  fill_ghosts<L>(wh, tg, n);
-  fill_ghosts<L>(wl, tg, n);
+  if (PER) {
+    fill_wrap<L>(wh, wl, tg, n, wrap_slots(cx, sm));
+  } else {
+    fill_ghosts<L>(wh, tg, n);
+    fill_ghosts<L>(wl, tg, n);
+  }
   float uh[L + 2], ul[L + 2];  // C^3 - C at rows tg L - 1 .. tg L + L
   if (has_mu) {
 #pragma unroll
@@ -685,7 +834,7 @@ __device__ __forceinline__ void step_rhs_ff(const double (&cv)[L], float muh, fl
   }
 #pragma unroll
   for (int j = 0; j < L; ++j) {
-    float sh = wh[j + 2], sl = wl[j + 2];
+    float sh = twice ? 2.f * wh[j + 2] : wh[j + 2], sl = twice ? 2.f * wl[j + 2] : wl[j + 2];
     if (has_mu) {
       float dh, dl, ph, pl, a, e;
       d2_ff(uh[j], ul[j], uh[j + 2], ul[j + 2], uh[j + 1], ul[j + 1], dh, dl);
@@ -693,7 +842,7 @@ __device__ __forceinline__ void step_rhs_ff(const double (&cv)[L], float muh, fl
       two_sum(sh, ph, a, e);
       fast_two_sum(a, e + (sl + pl), sh, sl);
     }
-    if (has_nu) {
+    if (has_nu && !twice) {
       float yh, yl, ph, pl, a, e;
       d4_ff(wh[j], wl[j], wh[j + 1], wl[j + 1], wh[j + 2], wl[j + 2], wh[j + 3], wl[j + 3], wh[j + 4], wl[j + 4], yh,
             yl);
@@ -709,11 +858,14 @@ __device__ __forceinline__ void step_rhs_ff(const double (&cv)[L], float muh, fl
 
 // Load the thread's 1/alpha and beta (stored as float4 planes, see k_factor32).
 // gq: the system's factor block; PT threads per system; tg this thread's index.
-template <int L>
+// NPL: float4 planes per group of four rows (2; periodic systems 4: their
+// blocks also hold the two columns of Z, see k_factor32_periodic).
+template <int L, int NPL = 2>
 __device__ __forceinline__ void load_factors(Fac<L>& fc, const float4* __restrict__ gq, int tg, int PT) {
 #pragma unroll
   for (int jq = 0; jq < L / 4; ++jq) {
-    const float4 qa = __ldg(gq + (int64_t)(jq * 2 + 0) * PT + tg), qb = __ldg(gq + (int64_t)(jq * 2 + 1) * PT + tg);
+    const float4 qa = __ldg(gq + (int64_t)(jq * NPL + 0) * PT + tg),
+                 qb = __ldg(gq + (int64_t)(jq * NPL + 1) * PT + tg);
     fc.A[4 * jq] = qa.x; fc.A[4 * jq + 1] = qa.y; fc.A[4 * jq + 2] = qa.z; fc.A[4 * jq + 3] = qa.w;
     fc.Bt[4 * jq] = qb.x; fc.Bt[4 * jq + 1] = qb.y; fc.Bt[4 * jq + 2] = qb.z; fc.Bt[4 * jq + 3] = qb.w;
   }
@@ -724,8 +876,9 @@ __device__ __forceinline__ void load_factors(Fac<L>& fc, const float4* __restric
 // max_refine refinement steps.  RES64 selects the FP64 residual (and FP64
 // accumulation of x) instead of float-float.
 // Refinement stops early once the error left after a step, estimated as the
-// step's correction times its size relative to x (the contraction of the
-// iteration), is below 2^-tol_log2 |x|: (max|dx| / max|x|)^2 <= 2^-tol_log2.
+// step's correction times the contraction of the iteration, is below
+// 2^-tol_log2 max|x|; the contraction is estimated by max|dx| / max|x| and, from
+// the second step on, by the ratio of successive corrections if that is larger.
 // WT > 0 fixes the warp count at compile time (the common one-CTA shapes);
 // WT = 0 takes it from `Wrt`.  CL enables the cluster paths (C = Crt CTAs per
 // system), otherwise C = 1.  Register budget: 6 CTAs of 4 warps per SM (at most
@@ -739,8 +892,12 @@ constexpr int min_blocks(int L, int WT, bool STEP) {
 // f = C + mu_s D2(C^3 - C) - nu_s D4 C (step_rhs_ff), with no scaling (the field
 // must stay below 2^40 in magnitude; larger values are flagged as not converged);
 // x (normally = f) receives the new field.
-template <int L, int WT, bool CL, bool RES64, bool STEP = false>
-__global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, min_blocks(L, WT, STEP))
+// PER: a periodic system (Sec. 2.3): the factors are those of the leading
+// n - 2 rows E with two more planes holding Z = E^{-1} k, each FP32 solve is
+// followed by Navon's tail (periodic_tail), and the residual and the
+// right-hand side take wrapped neighbours.
+template <int L, int WT, bool CL, bool RES64, bool STEP = false, bool PER = false>
+__global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, min_blocks(L, WT, STEP || PER))
     k_solve32r(F32Tables T, const int32_t* __restrict__ sys, int Wrt, int Crt, int shared, const double* f, double* x,
                int max_refine, int tol_log2, int vec_io, const double* __restrict__ mu_s,
                const double* __restrict__ nu_s) {
@@ -770,7 +927,10 @@ __global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, min_blocks(L, WT, STEP
   const float sgh = sgp.x, sgl = sgp.y;
   Fac<L> fc;
   fc.sg = sgh;
-  load_factors<L>(fc, reinterpret_cast<const float4*>(T.fac) + T.foff[ms], tg, PT);
+  constexpr int NPL = PER ? 4 : 2;
+  const float4* __restrict__ gq = reinterpret_cast<const float4*>(T.fac) + T.foff[ms];
+  load_factors<L, NPL>(fc, gq, tg, PT);
+  const float4 psi = PER ? __ldg(T.psinv + ms) : make_float4(0.f, 0.f, 0.f, 0.f);
   const double* fs = f + T.off[s];
   const int i0 = tg * L;
   double fv[L];
@@ -804,12 +964,14 @@ __global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, min_blocks(L, WT, STEP
 
   float v[L], xh[L], xl[L];
   float fh[L], fl[L];
+  // Crank-Nicolson with nu = sigma: solve for 2 C + mu D2(C^3 - C), subtract C at the end
+  const bool twice = STEP && nu_s && nu_s[ms] == T.sigma[ms];
   if (STEP) {
     float muh = 0.f, mul = 0.f, nuh = 0.f, nul = 0.f;
     if (mu_s) split_scaled(mu_s[ms], 0, muh, mul);
     if (nu_s) split_scaled(nu_s[ms], 0, nuh, nul);
     if (emax > 1023 + 40 && t == 0) atomicOr(T.info + 2, 1ull);  // field outside the FP32 path's range
-    step_rhs_ff<L>(fv, muh, mul, nuh, nul, muh != 0.f, nuh != 0.f, fh, fl, n, tg, cx, sm);
+    step_rhs_ff<L, PER>(fv, muh, mul, nuh, nul, muh != 0.f, nuh != 0.f, twice, fh, fl, n, tg, cx, sm);
   } else {
 #pragma unroll
     for (int j = 0; j < L; ++j) split_scaled(fv[j], kshift, fh[j], fl[j]);
@@ -849,7 +1011,12 @@ __global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, min_blocks(L, WT, STEP
         dmax = system_max<float>(dmax, cx.lane, cx.warp, W, C, rs);
         float* rs2 = sm.red + (cx.phase++ & 3) * (W + 1);
         xmax = system_max<float>(xmax, cx.lane, cx.warp, W, C, rs2);
-        if (dmax * dmax <= tol * xmax * xmax) break;
+        // error left ~ dmax times the contraction per step, estimated by the correction's size
+        // relative to x and, from the second step on, by the ratio of successive corrections
+        // (the larger: at large condition numbers the first underestimates it)
+        const float q = dmax / xmax;
+        const float rho = (it > 1 && prev > 0.f) ? fmaxf(q, dmax / prev) : q;
+        if (!(dmax > 0.f) || dmax * rho <= tol * xmax) break;
         if (it > 1 && dmax > 0.5f * prev) {
           stalled = true;
           break;
@@ -865,11 +1032,21 @@ __global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, min_blocks(L, WT, STEP
     // solve call site keeps the unrolled kernel compact (instruction cache).
 #pragma unroll 1
     for (int it = 0; it <= max_refine; ++it) {
-      if (it == 1)
-        residual_ff<L, true>(fh, fl, xh, xl, v, sgh, sgl, n, tg, cx, sm);  // x is still one float per row
-      else if (it > 1)
-        residual_ff<L, false>(fh, fl, xh, xl, v, sgh, sgl, n, tg, cx, sm);
-      cta_solve32<L>(v, fc, cx, sm);
+      if (PER) {
+        if (it == 1)
+          residual_ff_per<L, true>(fh, fl, xh, xl, v, sgh, sgl, n, tg, cx, sm);
+        else if (it > 1)
+          residual_ff_per<L, false>(fh, fl, xh, xl, v, sgh, sgl, n, tg, cx, sm);
+        periodic_tail_rhs<L>(v, tg, n, cx, sm);
+        cta_solve32<L>(v, fc, cx, sm);
+        periodic_tail<L, NPL>(v, gq, PT, tg, n, sgh, psi, cx, sm);
+      } else {
+        if (it == 1)
+          residual_ff<L, true>(fh, fl, xh, xl, v, sgh, sgl, n, tg, cx, sm);  // x is still one float per row
+        else if (it > 1)
+          residual_ff<L, false>(fh, fl, xh, xl, v, sgh, sgl, n, tg, cx, sm);
+        cta_solve32<L>(v, fc, cx, sm);
+      }
       if (it == 0) {
 #pragma unroll
         for (int j = 0; j < L; ++j) {
@@ -894,12 +1071,26 @@ __global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, min_blocks(L, WT, STEP
         dmax = system_max<float>(dmax, cx.lane, cx.warp, W, C, rs);
         float* rs2 = sm.red + (cx.phase++ & 3) * (W + 1);
         xmax = system_max<float>(xmax, cx.lane, cx.warp, W, C, rs2);
-        if (dmax * dmax <= tol * xmax * xmax) break;
+        // error left ~ dmax times the contraction per step, estimated by the correction's size
+        // relative to x and, from the second step on, by the ratio of successive corrections
+        // (the larger: at large condition numbers the first underestimates it)
+        const float q = dmax / xmax;
+        const float rho = (it > 1 && prev > 0.f) ? fmaxf(q, dmax / prev) : q;
+        if (!(dmax > 0.f) || dmax * rho <= tol * xmax) break;
         if (it > 1 && dmax > 0.5f * prev) {
           stalled = true;
           break;
         }
         prev = dmax;
+      }
+    }
+    if (twice) {  // C' = A^{-1}(2 C + ...) - C, in float-float; C is re-read (this thread's rows are unchanged)
+#pragma unroll
+      for (int j = 0; j < L; ++j) {
+        float ch, cl, sh, se;
+        split_scaled((i0 + j < n) ? fs[i0 + j] : 0.0, 0, ch, cl);
+        two_sum(xh[j], -ch, sh, se);
+        fast_two_sum(sh, se + (xl[j] - cl), xh[j], xl[j]);
       }
     }
 #pragma unroll
@@ -975,14 +1166,112 @@ __global__ void k_factor32(F32Tables T, int64_t nsys, const int32_t* __restrict_
   }
 }
 
-template <int L, int WT, bool CL, bool RES64, bool STEP>
+// Factor the periodic matrix of Eq. (matrix_sys) for FP32 solves, one thread per
+// system (FP64 arithmetic): E, its first m = n - 2 rows and columns (the band
+// cut off at E's edges), by the Sec. 2.4 steps, stored as 1/alpha and beta in
+// planes 0, 1 of a 4-plane block (float4 ((j / 4) * 4 + p) * PT + tg); rows m and
+// m + 1 and padding rows are zero.  Planes 2, 3: the columns of
+// Z = E^{-1} k, computed as W = L^{-1} k (forward, FP64) then R Z = W (back, with
+// the stored FP32 factors, as the solve uses them); k's nonzeros are a_0 = sigma,
+// e_{m-2} = sigma, d_{m-1} = -4 sigma (column n-2) and b_0 = -4 sigma,
+// a_1 = sigma, e_{m-1} = sigma (column n-1).  S^{-1} = (D - h^T Z)^{-1} (h = k,
+// the matrix being symmetric) goes to psinv.
+__global__ void k_factor32_periodic(F32Tables T, int64_t nsys, const int32_t* __restrict__ shape,
+                                    const double* __restrict__ sigma) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= nsys) return;
+  const int n = T.n[s], m = n - 2;
+  const int PT = shape[s] & 0xffff, L = shape[s] >> 16;
+  const double sg = sigma[s];
+  {
+    const float hi = __double2float_rn(sg);
+    T.sig2[s] = make_float2(hi, __double2float_rn(sg - (double)hi));
+  }
+  float* F = T.fac + T.foff[s] * 4;
+  auto at = [&](int i, int p) -> float& {
+    const int tgi = i / L, j = i - tgi * L;
+    return F[((int64_t)(j / 4) * 4 + p) * PT * 4 + (int64_t)tgi * 4 + (j & 3)];
+  };
+  const int rows = PT * L;
+  double gam2 = 0.0, del2 = 0.0, gam1 = 0.0, del1 = 0.0;
+  double w02 = 0.0, w01 = 0.0, w12 = 0.0, w11 = 0.0;  // W of rows i-2, i-1 (both columns)
+  bool failed = false;
+  for (int i = 0; i < rows; ++i) {
+    float ainv = 0.f, bt = 0.f, wa = 0.f, wb = 0.f;
+    if (i < m && !failed) {
+      const double ar = (i >= 2) ? sg : 0.0, br = (i >= 1) ? -4.0 * sg : 0.0, cr = 1.0 + 6.0 * sg;
+      const double dr = (i + 1 < m) ? -4.0 * sg : 0.0, er = (i + 2 < m) ? sg : 0.0;
+      const double beta = br - ar * gam2;
+      const double alpha = cr - ar * del2 - beta * gam1;
+      if (!(alpha != 0.0) || !isfinite(alpha)) {
+        atomicMin(T.info, ((unsigned long long)s << 32) | (unsigned long long)(uint32_t)i);
+        failed = true;
+      } else {
+        const double k0 = (i == 0 ? sg : 0.0) + (i == m - 2 ? sg : 0.0) + (i == m - 1 ? -4.0 * sg : 0.0);
+        const double k1 = (i == 0 ? -4.0 * sg : 0.0) + (i == 1 ? sg : 0.0) + (i == m - 1 ? sg : 0.0);
+        const double w0 = (k0 - ar * w02 - beta * w01) / alpha;
+        const double w1 = (k1 - ar * w12 - beta * w11) / alpha;
+        w02 = w01;
+        w01 = w0;
+        w12 = w11;
+        w11 = w1;
+        const double gamma = (dr - beta * del1) / alpha;
+        const double delta = er / alpha;
+        ainv = (float)(1.0 / alpha);
+        bt = (float)beta;
+        wa = (float)w0;
+        wb = (float)w1;
+        gam2 = gam1;
+        del2 = del1;
+        gam1 = gamma;
+        del1 = delta;
+      }
+    }
+    at(i, 0) = ainv;
+    at(i, 1) = bt;
+    at(i, 2) = wa;
+    at(i, 3) = wb;
+  }
+  // R Z = W: z_i = w_i - gamma_i z_{i+1} - delta_i z_{i+2}, gamma_i = beta_{i+1} / alpha_i,
+  // delta_i = sigma / alpha_i (zero past E's edge, where z is zero anyway)
+  double z01 = 0.0, z02 = 0.0, z11 = 0.0, z12 = 0.0;  // z of rows i+1, i+2
+  for (int i = m - 1; i >= 0; --i) {
+    const double ia = (double)at(i, 0);
+    const double gamma = (i + 1 < m) ? (double)at(i + 1, 1) * ia : 0.0;
+    const double delta = sg * ia;
+    const double z0 = (double)at(i, 2) - gamma * z01 - delta * z02;
+    const double z1 = (double)at(i, 3) - gamma * z11 - delta * z12;
+    at(i, 2) = (float)z0;
+    at(i, 3) = (float)z1;
+    z02 = z01;
+    z01 = z0;
+    z12 = z11;
+    z11 = z1;
+  }
+  // S = D - h^T Z, h^T's rows: (sigma @ 0, sigma @ m-2, -4 sigma @ m-1), (-4 sigma @ 0, sigma @ 1, sigma @ m-1)
+  auto hz = [&](int c, int row) {
+    const double za = at(0, 2 + c), zb = at(1, 2 + c), zm2 = at(m - 2, 2 + c), zm1 = at(m - 1, 2 + c);
+    return row == 0 ? sg * (za + zm2) - 4.0 * sg * zm1 : -4.0 * sg * za + sg * (zb + zm1);
+  };
+  const double s00 = 1.0 + 6.0 * sg - hz(0, 0), s01 = -4.0 * sg - hz(1, 0);
+  const double s10 = -4.0 * sg - hz(0, 1), s11 = 1.0 + 6.0 * sg - hz(1, 1);
+  const double det = s00 * s11 - s01 * s10;
+  if (failed || !(det != 0.0) || !isfinite(det)) {
+    if (!failed) atomicMin(T.info, ((unsigned long long)s << 32) | (unsigned long long)(uint32_t)(n - 2));
+    T.psinv[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
+  T.psinv[s] = make_float4((float)(s11 / det), (float)(-s01 / det), (float)(-s10 / det), (float)(s00 / det));
+}
+
+template <int L, int WT, bool CL, bool RES64, bool STEP, bool PER = false>
 cudaError_t launch_bucket(const F32Tables& T, const int32_t* sys, const F32Bucket& b, int shared, const double* f,
                           double* x, int max_refine, int tol_log2, const double* mu, const double* nu,
                           cudaStream_t st) {
   const int vec = ((((uintptr_t)f) | ((uintptr_t)x)) % 16 == 0) && b.even_offsets;
   const size_t smem = smem_bytes(b.W);
   if (smem > 48 * 1024) {  // above the default dynamic shared memory limit (a function attribute, not a stream op)
-    const cudaError_t e = cudaFuncSetAttribute(k_solve32r<L, WT, CL, RES64, STEP>,
+    const cudaError_t e = cudaFuncSetAttribute(k_solve32r<L, WT, CL, RES64, STEP, PER>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
@@ -1000,7 +1289,7 @@ cudaError_t launch_bucket(const F32Tables& T, const int32_t* sys, const F32Bucke
     cfg.attrs = attr;
     cfg.numAttrs = 1;
   }
-  return cudaLaunchKernelEx(&cfg, k_solve32r<L, WT, CL, RES64, STEP>, T, sys + b.first, b.W, b.C, shared, f, x,
+  return cudaLaunchKernelEx(&cfg, k_solve32r<L, WT, CL, RES64, STEP, PER>, T, sys + b.first, b.W, b.C, shared, f, x,
                             max_refine, tol_log2, vec, mu, nu);
 }
 
@@ -1032,10 +1321,34 @@ cudaError_t launch_factor32(const F32Tables& T, const int32_t* shape, int64_t ns
   return cudaGetLastError();
 }
 
+// Periodic systems: one kernel shape for every CTA width (the runtime-W form), clusters when needed.
+template <int L, bool STEP>
+cudaError_t dispatch_periodic(const F32Tables& T, const int32_t* sys, const F32Bucket& b, int shared, const double* f,
+                              double* x, int max_refine, int tol_log2, const double* mu, const double* nu,
+                              cudaStream_t st) {
+  if (b.C > 1)
+    return launch_bucket<L, 0, true, false, STEP, true>(T, sys, b, shared, f, x, max_refine, tol_log2, mu, nu, st);
+  if (b.W == 2)
+    return launch_bucket<L, 2, false, false, STEP, true>(T, sys, b, shared, f, x, max_refine, tol_log2, mu, nu, st);
+  if (b.W == 4)
+    return launch_bucket<L, 4, false, false, STEP, true>(T, sys, b, shared, f, x, max_refine, tol_log2, mu, nu, st);
+  return launch_bucket<L, 0, false, false, STEP, true>(T, sys, b, shared, f, x, max_refine, tol_log2, mu, nu, st);
+}
+
 cudaError_t launch_solve32r(const F32Tables& T, const int32_t* sys, const F32Bucket& b, int shared, const double* f,
                             double* x, int max_refine, int residual_f64, int tol_log2, cudaStream_t st,
-                            const double* mu, const double* nu, bool step) {
+                            const double* mu, const double* nu, bool step, bool periodic) {
   if (b.count == 0) return cudaSuccess;
+  if (periodic) {  // float-float residual only
+    if (residual_f64) return cudaErrorInvalidValue;
+    if (b.L == 4)
+      return step ? dispatch_periodic<4, true>(T, sys, b, shared, f, x, max_refine, tol_log2, mu, nu, st)
+                  : dispatch_periodic<4, false>(T, sys, b, shared, f, x, max_refine, tol_log2, mu, nu, st);
+    if (b.L == 8)
+      return step ? dispatch_periodic<8, true>(T, sys, b, shared, f, x, max_refine, tol_log2, mu, nu, st)
+                  : dispatch_periodic<8, false>(T, sys, b, shared, f, x, max_refine, tol_log2, mu, nu, st);
+    return cudaErrorInvalidValue;
+  }
   if (step) {  // float-float residual only
     if (residual_f64) return cudaErrorInvalidValue;
     if (b.L == 4) return dispatch_bucket<4, false, true>(T, sys, b, shared, f, x, max_refine, tol_log2, mu, nu, st);
@@ -1049,6 +1362,13 @@ cudaError_t launch_solve32r(const F32Tables& T, const int32_t* sys, const F32Buc
     return residual_f64 ? dispatch_bucket<8, true, false>(T, sys, b, shared, f, x, max_refine, tol_log2, mu, nu, st)
                         : dispatch_bucket<8, false, false>(T, sys, b, shared, f, x, max_refine, tol_log2, mu, nu, st);
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_factor32_periodic(const F32Tables& T, const int32_t* shape, int64_t nsys, const double* sigma,
+                                     cudaStream_t st) {
+  const int block = 128;
+  k_factor32_periodic<<<(unsigned)((nsys + block - 1) / block), block, 0, st>>>(T, nsys, shape, sigma);
+  return cudaGetLastError();
 }
 
 }  // namespace pent

@@ -55,6 +55,7 @@ struct F32Tables {
   const double* sigma;    // [nfac] sigma in FP64 (FP64-residual variant)
   float* fac;             // factor storage
   unsigned long long* info;
+  float4* psinv;          // [nfac] periodic plans: S^{-1} of Navon's reduction (row-major 2 x 2)
 };
 
 // Systems solved by one launch: sys[first .. first + count) share the CTA shape
@@ -125,7 +126,11 @@ cudaError_t launch_adjoint64(const DevPlan& P, F64Factors F, const double* f, do
 // (float-float) before the solve (pent_step_batch); mu, nu per factored system, or NULL.
 cudaError_t launch_solve32r(const F32Tables& T, const int32_t* sys, const F32Bucket& b, int shared, const double* f,
                             double* x, int max_refine, int residual_f64, int tol_log2, cudaStream_t st,
-                            const double* mu = nullptr, const double* nu = nullptr, bool step = false);
+                            const double* mu = nullptr, const double* nu = nullptr, bool step = false,
+                            bool periodic = false);
+// Periodic FP32 plans: factors of E, the columns of Z = E^{-1} k and S^{-1} (k_factor32_periodic).
+cudaError_t launch_factor32_periodic(const F32Tables& T, const int32_t* shape, int64_t nsys, const double* sigma,
+                                     cudaStream_t st);
 cudaError_t launch_factor_periodic(const PerArgs& A, const double* a, const double* b, const double* c,
                                    const double* d, const double* e, const double* sigma, cudaStream_t st);
 // rhs: assemble f_i = C_i + mu_s (D2 (C^3 - C))_i - nu_s (D4 C)_i from the field in f (periodic stencils).

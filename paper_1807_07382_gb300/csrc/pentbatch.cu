@@ -91,7 +91,7 @@ struct pent_plan {
   // workspace regions
   Region r_info, r_perm, r_off, r_n, r_goff, r_glen, r_sigma, r_fwd, r_bwd, r_scr, r_fac32, r_sig32, r_foff, r_shape,
       r_sys32, r_adi, r_cmap, r_swU, r_swE, r_pck, r_pcc, r_pcbase, r_pcnum, r_pcmap, r_pU, r_pE, r_per, r_psinv,
-      r_pg, r_rhs;
+      r_pg, r_rhs, r_psinv32;
   size_t ws_bytes = 0;
   // binding / state
   unsigned char* ws = nullptr;
@@ -158,6 +158,7 @@ struct pent_plan {
     T.sigma = at<double>(r_sigma);
     T.fac = at<float>(r_fac32);
     T.info = at<unsigned long long>(r_info);
+    T.psinv = periodic ? at<float4>(r_psinv32) : nullptr;
     return T;
   }
   void drop_graphs() {
@@ -339,7 +340,8 @@ bool build_f32_shapes(pent_plan* p) {
     if (!choose_shape(p, n, &p->shape[s])) return false;
     p->foff[s] = acc;
     const Shape& sh = p->shape[s];
-    acc += (int64_t)2 * 32 * sh.W * sh.C * sh.L / 4;
+    const int planes = p->periodic ? 4 : 2;  // periodic blocks also hold Z = E^{-1} k
+    acc += (int64_t)planes * 32 * sh.W * sh.C * sh.L / 4;
   }
   p->fac_float4 = acc;
   // buckets: systems grouped by shape, longest shapes first
@@ -384,7 +386,7 @@ void layout(pent_plan* p) {
   take(p->r_goff, (size_t)p->ngroups * sizeof(int64_t));
   take(p->r_glen, (size_t)p->ngroups * sizeof(int32_t));
   take(p->r_sigma, (size_t)nfac * sizeof(double));
-  if (p->periodic) {
+  if (p->periodic && p->precision == PENT_F64) {
     // Navon's reduction: nine interleaved planes of the reduced matrix, S^{-1}, and g
     const int64_t m = p->n_uniform - 2;
     take(p->r_per, (size_t)9 * m * nfac * sizeof(double));
@@ -414,6 +416,7 @@ void layout(pent_plan* p) {
     take(p->r_foff, (size_t)nfac * sizeof(int64_t));
     take(p->r_shape, (size_t)nfac * sizeof(int32_t));
     take(p->r_sys32, (size_t)p->batch * sizeof(int32_t));
+    if (p->periodic) take(p->r_psinv32, (size_t)nfac * 4 * sizeof(float));
   }
   // ADI scratch, for shared-matrix plans whose batch is the number of columns of
   // a sweep: a full field (rows doubles), the partial sums of the sweep
@@ -617,8 +620,13 @@ pent_status pent_plan_set_option(pent_plan* p, int key, int64_t value) {
       return PENT_OK;
     case PENT_OPT_PERIODIC:
       if (p->bound || (value != 0 && value != 1)) return PENT_EINVAL;
-      if (value == 1 && (p->precision != PENT_F64 || !p->uniform || p->n_uniform < 5)) return PENT_EINVAL;
+      if (value == 1 && (!p->uniform || p->n_uniform < 5)) return PENT_EINVAL;
       p->periodic = value == 1;
+      if (p->precision == PENT_F32_REFINE && !build_f32_shapes(p)) {
+        p->periodic = false;
+        build_f32_shapes(p);
+        return PENT_EINVAL;
+      }
       layout(p);
       return PENT_OK;
     case PENT_OPT_ROWS_PER_THREAD: {
@@ -733,7 +741,7 @@ static pent_status factor_common(pent_plan* p, const double* a, const double* b,
   }
   const double* sg = sigma ? p->at<double>(p->r_sigma) : nullptr;
   cudaError_t err;
-  if (p->periodic) {
+  if (p->periodic && p->precision == PENT_F64) {
     err = launch_factor_periodic(p->per(), a, b, c, d, e, sg, p->stream);
   } else if (p->precision == PENT_F64) {
     F64Factors F = p->f64();
@@ -744,6 +752,8 @@ static pent_status factor_common(pent_plan* p, const double* a, const double* b,
     // chunk maps of the partitioned groups
     if (err == cudaSuccess && p->pchunks > 0) err = launch_chunk_maps64(P, F, p->part(), 0, p->pchunks, p->stream);
   }
+  else if (p->periodic)
+    err = launch_factor32_periodic(p->f32(), p->at<int32_t>(p->r_shape), p->shared ? 1 : p->batch, sg, p->stream);
   else
     err = launch_factor32(p->f32(), p->at<int32_t>(p->r_shape), p->shared ? 1 : p->batch, sg, p->stream);
   if (err != cudaSuccess) return PENT_ECUDA;
@@ -765,7 +775,7 @@ pent_status pent_factor_hyperdiff(pent_plan* p, const double* d_sigma) {
 
 static pent_status solve_launch(pent_plan* p, const double* f, double* x, int max_refine) {
   cudaError_t err;
-  if (p->periodic) {
+  if (p->periodic && p->precision == PENT_F64) {
     err = launch_solve_periodic(p->per(), f, x, nullptr, nullptr, false, p->stream);
   } else if (p->precision == PENT_F64) {
     const DevPlan P = p->dev();
@@ -781,8 +791,10 @@ static pent_status solve_launch(pent_plan* p, const double* f, double* x, int ma
     const F32Tables T = p->f32();
     const int32_t* sys = p->at<int32_t>(p->r_sys32);
     const int rf = p->residual == PENT_RESIDUAL_F64;
+    if (p->periodic && rf) return PENT_EINVAL;  // periodic FP32 plans refine against the float-float residual
     err = fork_join(p, p->buckets.size(), [&](size_t i, cudaStream_t st) {
-      return launch_solve32r(T, sys, p->buckets[i], p->shared, f, x, max_refine, rf, p->tol_log2, st);
+      return launch_solve32r(T, sys, p->buckets[i], p->shared, f, x, max_refine, rf, p->tol_log2, st, nullptr,
+                             nullptr, false, p->periodic);
     });
   }
   return cuda_status(err);
@@ -853,7 +865,8 @@ static pent_status step_launch(pent_plan* p, const double* mu, const double* nu,
     const F32Tables T = p->f32();
     const int32_t* sys = p->at<int32_t>(p->r_sys32);
     const cudaError_t err = fork_join(p, p->buckets.size(), [&](size_t i, cudaStream_t st) {
-      return launch_solve32r(T, sys, p->buckets[i], p->shared, C, C, max_refine, 0, p->tol_log2, st, mu, nu, true);
+      return launch_solve32r(T, sys, p->buckets[i], p->shared, C, C, max_refine, 0, p->tol_log2, st, mu, nu, true,
+                             p->periodic);
     });
     return cuda_status(err);
   }
@@ -887,7 +900,8 @@ pent_status pent_step_batch(pent_plan* p, const double* mu, const double* nu, do
   if (p->precision == PENT_F32_REFINE && p->residual != PENT_RESIDUAL_FF) return PENT_EINVAL;
   if (nsteps == 0) return PENT_OK;
   auto launch = [&]() -> pent_status {
-    if (p->periodic) return cuda_status(launch_solve_periodic(p->per(), C, C, mu, nu, true, p->stream));
+    if (p->periodic && p->precision == PENT_F64)
+      return cuda_status(launch_solve_periodic(p->per(), C, C, mu, nu, true, p->stream));
     return step_launch(p, mu, nu, C, max_refine);
   };
   if (nsteps == 1) return launch();

@@ -117,8 +117,11 @@ def test_periodic_option_host_checks(L):
     st, h = _create(L, batch=4, n_uniform=4)
     assert L.pent_plan_set_option(h, _lib.PENT_OPT_PERIODIC, 1) == _lib.PENT_EINVAL
     L.pent_plan_destroy(h)
+    # FP32+refine periodic plans keep four FP32 planes per row (1/alpha, beta and the two columns of Z)
     st, h = _create(L, batch=4, n_uniform=64, prec=1)
-    assert L.pent_plan_set_option(h, _lib.PENT_OPT_PERIODIC, 1) == _lib.PENT_EINVAL
+    base32 = L.pent_plan_workspace_bytes(h)
+    assert L.pent_plan_set_option(h, _lib.PENT_OPT_PERIODIC, 1) == 0
+    assert L.pent_plan_workspace_bytes(h) >= base32 + 4 * 64 * 2 * 4
     L.pent_plan_destroy(h)
     st, h = _create(L, batch=2, n=[64, 65])
     assert L.pent_plan_set_option(h, _lib.PENT_OPT_PERIODIC, 1) == _lib.PENT_EINVAL

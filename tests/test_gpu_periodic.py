@@ -145,3 +145,105 @@ def test_periodic_rejects_unsupported_calls():
     plan.factor_hyperdiff(dev(np.full(4, 0.5)))
     with pytest.raises(pb.PentError):
         plan.adjoint_solve(dev(np.zeros(64)))
+
+
+# ----------------------------------------------------------------------------- FP32 + refinement
+
+@pytest.mark.parametrize("shared", [False, True])
+@pytest.mark.parametrize("n", [5, 6, 7, 9, 33, 256, 512, 1024, 3000, 6000])
+def test_periodic_f32_refine_solve(n, shared):
+    """The periodic hyperdiffusion matrix in FP32 + refinement: the FP32 solve of E, Navon's 2 x 2 tail, the
+    float-float residual with wrapped neighbours; one CTA per system (a cluster beyond 4,096 rows)."""
+    batch = 37
+    nsig = 1 if shared else batch
+    sig = synth.log_uniform(900 + n, 0, nsig, 1e-3, 10.0)
+    f = synth.uniform(900 + n, nsig, batch * n, -1, 1)
+    full_sig = np.broadcast_to(sig, (batch,))
+    ref = np.concatenate([oracle.periodic_solve(oracle.band_periodic_hyperdiff(n, full_sig[s]), f[s * n:(s + 1) * n])
+                          for s in range(batch)])
+    plan = pb.Plan(n, batch=batch, shared=shared, periodic=True, precision=pb.PENT_F32_REFINE)
+    plan.factor_hyperdiff(dev(sig))
+    x = plan.solve(dev(f), max_refine=4)
+    assert plan.info()[0] == pb.PENT_OK
+    assert sys_err(x.cpu().numpy(), ref, n) <= TOL
+
+
+@pytest.mark.parametrize("cn", [False, True])
+def test_periodic_f32_refine_steps(cn):
+    n, batch, steps = 512, 70, 6
+    sig = synth.log_uniform(910, 0, batch, 1e-3, 10.0)
+    C0 = synth.uniform(910, batch, batch * n, -1, 1)
+    ref = oracle.periodic_steps(n, sig, C0, steps, cn=cn)
+    plan = pb.Plan(n, batch=batch, periodic=True, precision=pb.PENT_F32_REFINE)
+    s = dev(sig)
+    plan.factor_hyperdiff(s)
+    C = dev(C0)
+    if cn:
+        plan.step(C, nu=s, nsteps=steps, max_refine=3)
+    else:
+        plan.solve_steps(C, steps, max_refine=3)
+    assert plan.info()[0] == pb.PENT_OK
+    assert sys_err(C.cpu().numpy(), ref, n) <= TOL
+
+
+def test_periodic_f32_refine_cahn_hilliard():
+    n, batch, steps = 256, 50, 8
+    sig = synth.log_uniform(920, 0, batch, 1e-2, 5.0)
+    mu = synth.log_uniform(920, batch, batch, 1e-3, 0.3)
+    C0 = synth.uniform(920, 2 * batch, batch * n, -0.8, 0.8)
+    ref = oracle.explicit_steps(np.full(batch, n), sig, mu, None, C0, steps, periodic=True)
+    plan = pb.Plan(n, batch=batch, periodic=True, precision=pb.PENT_F32_REFINE)
+    plan.factor_hyperdiff(dev(sig))
+    C = dev(C0)
+    plan.step(C, mu=dev(mu), nsteps=steps, max_refine=3)
+    assert sys_err(C.cpu().numpy(), ref, n) <= TOL
+
+
+def test_periodic_f32_refine_convergence_exponent():
+    """The paper's validation case (Sec. 2.5) in FP32 + refinement: 10^4 Crank-Nicolson steps per N."""
+    g = json.load(open(os.path.join(GOLDEN, "paper_convergence.json")))
+    k = 2 * math.pi * g["n"] / g["L"]
+    T, dt = g["T"], g["dt"]
+    steps = int(round(T / dt))
+    Ns = [16, 32, 64, 128, 256]
+    errs = []
+    for N in Ns:
+        dx = g["L"] / N
+        x = np.arange(N) * dx
+        sigma = g["gamma"] * g["D"] * dt / (2 * dx ** 4)
+        c0 = g["amplitude"] * np.cos(k * x + g["phase"])
+        plan = pb.Plan(N, batch=1, periodic=True, precision=pb.PENT_F32_REFINE)
+        s = dev([sigma])
+        plan.factor_hyperdiff(s)
+        C = dev(c0)
+        plan.step(C, nu=s, nsteps=steps, max_refine=3)
+        num = C.cpu().numpy()
+        ref = oracle.periodic_steps(N, [sigma], c0, steps, cn=True)
+        # the FP32 path carries the field between steps as float pairs (48 bits): the per-step bound of
+        # the FP64 test with 2^-48 in place of u
+        bound = steps * 4 * (1 + 32 * sigma) * 2.0 ** -48 / np.max(np.abs(ref))
+        assert sys_err(num, ref, N) <= bound
+        exact = g["amplitude"] * math.exp(-g["gamma"] * g["D"] * k ** 4 * T) * np.cos(k * x + g["phase"])
+        errs.append(math.sqrt(np.mean((num - exact) ** 2)))
+    slope = np.polyfit(np.log(Ns), np.log(errs), 1)[0]
+    assert abs(slope - g["fitted_exponent"]) < 0.03
+
+
+@pytest.mark.parametrize("prec", [pb.PENT_F64, pb.PENT_F32_REFINE])
+def test_periodic_crank_nicolson_at_the_workloads_sigma(prec):
+    """sigma_x = dt / (2 dx^4) = 343.6 (dt = 1e-8, N = 512: the periodic workload): the Crank-Nicolson
+    right-hand side (I - sigma D4) C sums terms up to (1 + 16 sigma) |C| ~ 5500 |C|, so the FP32 path
+    solves A y = 2 C and takes C' = y - C instead (the same scheme, without the cancellation).  The
+    oracle evaluates that right-hand side in FP64 and is itself uncertain by about
+    2 (1 + 16 sigma) u max|C| per step (u = 2^-53), which sets the bar above 1e-12 here."""
+    w = synth.periodic_cn(batch=64, steps=3)
+    n = int(w.n[0])
+    ref = oracle.periodic_steps(n, w.sigma, w.field0, w.steps, cn=True, shared=True)
+    plan = pb.Plan(n, batch=w.batch, shared=True, periodic=True, precision=prec)
+    s = dev(w.sigma)
+    plan.factor_hyperdiff(s)
+    C = dev(w.field0)
+    plan.step(C, nu=s, nsteps=w.steps, max_refine=3)
+    assert plan.info()[0] == pb.PENT_OK
+    tol = max(TOL, w.steps * 2 * (1 + 16 * w.sigma[0]) * 2.0 ** -53 * np.max(np.abs(w.field0)) / np.max(np.abs(ref)))
+    assert sys_err(C.cpu().numpy(), ref, n) <= tol
