@@ -247,3 +247,24 @@ def test_periodic_crank_nicolson_at_the_workloads_sigma(prec):
     assert plan.info()[0] == pb.PENT_OK
     tol = max(TOL, w.steps * 2 * (1 + 16 * w.sigma[0]) * 2.0 ** -53 * np.max(np.abs(w.field0)) / np.max(np.abs(ref)))
     assert sys_err(C.cpu().numpy(), ref, n) <= tol
+
+
+@pytest.mark.parametrize("prec", [pb.PENT_F64, pb.PENT_F32_REFINE])
+def test_full_size_periodic_crank_nicolson_sampled(prec):
+    """The periodic workload at full size (65,536 systems x 512, shared sigma_x = 343.6) as bench.py times
+    it: one Crank-Nicolson step, 128 sampled systems against the oracle, with the bar of the oracle's own
+    right-hand-side rounding at this sigma (see test_periodic_crank_nicolson_at_the_workloads_sigma)."""
+    w = synth.periodic_cn(steps=1)
+    n = int(w.n[0])
+    plan = pb.Plan(n, batch=w.batch, shared=True, periodic=True, precision=prec)
+    s = dev(w.sigma)
+    plan.factor_hyperdiff(s)
+    C = dev(w.field0)
+    plan.step(C, nu=s, max_refine=3)
+    assert plan.info()[0] == pb.PENT_OK
+    pick = np.arange(0, w.batch, 512)
+    f0 = w.field0.reshape(w.batch, n)[pick].reshape(-1)
+    ref = oracle.periodic_steps(n, w.sigma, f0, 1, cn=True, shared=True)
+    got = C.cpu().numpy().reshape(w.batch, n)[pick].reshape(-1)
+    tol = max(TOL, 2 * (1 + 16 * w.sigma[0]) * 2.0 ** -53 * np.max(np.abs(f0)) / np.max(np.abs(ref)))
+    assert sys_err(got, ref, n) <= tol

@@ -204,3 +204,21 @@ def test_cahn_hilliard_f32_refine_shared_and_mass():
     assert sys_err(out, ref, np.full(batch, n)) <= TOL
     m0 = C0.reshape(batch, n).sum(1)
     assert np.max(np.abs(out.reshape(batch, n).sum(1) - m0)) <= 1e-12 * np.abs(C0).reshape(batch, n).sum(1).max()
+
+
+@pytest.mark.parametrize("prec", [pb.PENT_F64, pb.PENT_F32_REFINE])
+def test_full_size_cahn_hilliard_batch_sampled(prec):
+    """The 1D Cahn-Hilliard workload at full size (65,536 systems x 1024, per-system sigma and mu) in the
+    launch configuration bench.py times: one step, 128 sampled systems against the oracle."""
+    w = synth.ch_batch(steps=1)
+    n = int(w.n[0])
+    plan = pb.Plan(n, batch=w.batch, precision=prec)
+    plan.factor_hyperdiff(dev(w.sigma))
+    C = dev(w.field0)
+    plan.step(C, mu=dev(w.extra["mu"]), max_refine=1)
+    assert plan.info()[0] == pb.PENT_OK
+    pick = np.arange(0, w.batch, 512)
+    ref = oracle.explicit_steps(np.full(len(pick), n), w.sigma[pick], w.extra["mu"][pick], None,
+                                w.field0.reshape(w.batch, n)[pick].reshape(-1), 1)
+    got = C.cpu().numpy().reshape(w.batch, n)[pick].reshape(-1)
+    assert sys_err(got, ref, np.full(len(pick), n)) <= TOL
