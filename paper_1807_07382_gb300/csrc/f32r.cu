@@ -74,25 +74,20 @@ __device__ __forceinline__ float small_uint_to_float(unsigned v) {
 // system scales to just below 1.
 __device__ __forceinline__ void split_scaled(double v, int k, float& hi, float& lo) {
   const unsigned long long U = (unsigned long long)__double_as_longlong(v);
-  const unsigned top = (unsigned)(U >> 32);
+  const unsigned top = (unsigned)(U >> 32), bot = (unsigned)U;
   const int E = (int)((top >> 20) & 0x7ffu);
   const int Es = E - k;
   const unsigned sign = top & 0x80000000u;
-  if (E == 0 || Es < 897) {
-    hi = 0.0f;
-    lo = 0.0f;
-    return;
-  }
-  const unsigned mant_hi = (unsigned)((U >> 29) & 0x7fffffu);
-  hi = __uint_as_float(sign | ((unsigned)(Es - 896) << 23) | mant_hi);
-  if (Es < 943) {
-    lo = 0.0f;
-    return;
-  }
+  const unsigned mant_hi = __funnelshift_l(bot, top, 3) & 0x7fffffu;  // mantissa bits 29..51
+  const unsigned hib = sign | ((unsigned)(Es - 896) << 23) | mant_hi;
   // mantissa bits 6..28 (the 23 below hi's), rounded by bit 5; 2^23 still converts exactly below
-  const unsigned rem = ((unsigned)(U >> 6) & 0x7fffffu) + ((unsigned)(U >> 5) & 1u);
+  const unsigned rem = ((bot >> 6) & 0x7fffffu) + ((bot >> 5) & 1u);
   const float scale = __uint_as_float((unsigned)(Es - 942) << 23);  // 2^(Es - 1069)
-  lo = __uint_as_float(__float_as_uint(__fmul_rn(small_uint_to_float(rem), scale)) ^ sign);
+  const unsigned lob = __float_as_uint(__fmul_rn(small_uint_to_float(rem), scale)) ^ sign;
+  // branch-free: values that scale below FP32's normal range flush to zero
+  const bool okh = (E != 0) && (Es >= 897), okl = okh && (Es >= 943);
+  hi = okh ? __uint_as_float(hib) : 0.0f;
+  lo = okl ? __uint_as_float(lob) : 0.0f;
 }
 
 // Rare path of ff_to_double_shift (h outside the range the fast path covers):
