@@ -21,7 +21,7 @@ import argparse
 import math
 from typing import Iterable, Optional
 
-from . import PENT_F32_REFINE, PENT_F64, PENT_OPT_BLOCK_WARPS, PENT_OPT_ROWS_PER_THREAD, \
+from . import PENT_F32_REFINE, PENT_F64, PENT_OPT_BLOCK_WARPS, PENT_OPT_PARTITION_ROWS, PENT_OPT_ROWS_PER_THREAD, \
     PENT_OPT_THREADS_PER_SYSTEM, PENT_OPT_UNROLL, Plan
 
 DEFAULT_BUCKETS = (64, 128, 256, 512, 1024, 2048, 4096, 8192, 16384)
@@ -100,7 +100,10 @@ def tune(buckets: Iterable[int] = DEFAULT_BUCKETS, rows: int = 1 << 26, steps: i
                          for rpt, tps in f32_candidates(n)]
                 prec = PENT_F32_REFINE
             else:
-                cands = [((u, bw), {PENT_OPT_UNROLL: u, PENT_OPT_BLOCK_WARPS: bw}) for u, bw in f64_candidates(n)]
+                # partitioning off: the knobs tune the thread-per-system walk, which partitioned groups
+                # (long systems, or small batches) do not use
+                cands = [((u, bw), {PENT_OPT_UNROLL: u, PENT_OPT_BLOCK_WARPS: bw, PENT_OPT_PARTITION_ROWS: 0})
+                         for u, bw in f64_candidates(n)]
                 prec = PENT_F64
             best = None
             for knobs, opts in cands:
