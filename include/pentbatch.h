@@ -193,6 +193,21 @@ pent_status pent_factor_hyperdiff(pent_plan* plan, const double* d_sigma);
 pent_status pent_solve_batch(pent_plan* plan, const double* f, double* x, int max_refine);
 
 /*
+ * x_s = A_s^{-1} f_s for right-hand sides held in (pinned) host memory: h_f is
+ * copied to the device staging array d_f, solved into d_x (as
+ * pent_solve_batch; d_x may alias d_f) and copied back to h_x.  The batch is cut
+ * into `nchunks` slices of whole systems that flow through three streams of
+ * the plan, so that the copy of one slice to the device, the solve of the
+ * next and the copy of a third back overlap.  Slicing needs plans of one
+ * system length solved by one launch shape (uniform batches, not periodic, no
+ * partitioned groups); other plans run as one slice.  Asynchronous on the
+ * plan's stream, which waits for every slice; h_f must stay unchanged and h_x
+ * unread until the stream reaches that point.  Not capture-safe (host memory).
+ */
+pent_status pent_solve_host_batch(pent_plan* plan, const double* h_f, double* h_x, double* d_f, double* d_x,
+                                  int nchunks, int max_refine);
+
+/*
  * `nsteps` implicit steps in place: x <- A^{-1} x, repeated.  The sequence is
  * captured once into a CUDA graph (keyed by x and nsteps) and replayed on
  * later calls; the factors stay resident.  The first call for a given key is

@@ -174,19 +174,23 @@ class Plan:
                                        int(max_refine)), "pent_solve_batch")
         return x
 
-    def solve_host(self, f_host, x_host, f_dev=None, x_dev=None, max_refine: int = 2):
-        """Solve for right-hand sides held in (pinned) host memory: copy f to the device,
-        solve, copy x back, all asynchronously on the plan's stream.  f_dev / x_dev are
-        optional device staging buffers."""
+    def solve_host(self, f_host, x_host, f_dev=None, x_dev=None, max_refine: int = 2, chunks: int = 16):
+        """Solve for right-hand sides held in pinned host memory: the library copies f to the
+        device staging buffer, solves and copies x back, in `chunks` slices whose copies and
+        solves overlap (pent_solve_host_batch); asynchronous on the plan's stream.  f_dev / x_dev
+        are device staging buffers (allocated here if not given; x_dev may be f_dev)."""
         torch = _torch()
         if f_host.is_cuda or x_host.is_cuda:
             raise ValueError("solve_host takes host tensors")
-        with torch.cuda.stream(self.stream):
-            fd = f_dev if f_dev is not None else torch.empty(f_host.shape, dtype=torch.float64, device=self.device)
-            xd = x_dev if x_dev is not None else torch.empty_like(fd)
-            fd.copy_(f_host, non_blocking=True)
-            self.solve(fd, xd, max_refine=max_refine)
-            x_host.copy_(xd, non_blocking=True)
+        for t, name in ((f_host, "f_host"), (x_host, "x_host")):
+            if t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != self.rows:
+                raise ValueError(f"{name} must be a contiguous float64 tensor of {self.rows} elements")
+        fd = f_dev if f_dev is not None else torch.empty(self.rows, dtype=torch.float64, device=self.device)
+        xd = x_dev if x_dev is not None else torch.empty_like(fd)
+        self._host_refs = (f_host, x_host, fd, xd)
+        check(self._L.pent_solve_host_batch(self._h, f_host.data_ptr(), x_host.data_ptr(),
+                                            _dev_ptr(fd, "f_dev", torch.float64), _dev_ptr(xd, "x_dev", torch.float64),
+                                            int(chunks), int(max_refine)), "pent_solve_host_batch")
         return x_host
 
     def solve_steps(self, x, nsteps: int, max_refine: int = 2):

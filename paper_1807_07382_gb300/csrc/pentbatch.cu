@@ -88,6 +88,8 @@ struct pent_plan {
   int64_t tps_override = 0;       // PENT_OPT_THREADS_PER_SYSTEM for FP32 (0: automatic)
   std::vector<cudaStream_t> side; // extra streams so that bucket launches overlap
   std::vector<cudaEvent_t> ev;    // fork/join events
+  std::vector<cudaStream_t> pipe; // slices of pent_solve_host_batch (copy in, solve, copy out)
+  std::vector<cudaEvent_t> pev;   // their fork/join events
   // workspace regions
   Region r_info, r_perm, r_off, r_n, r_goff, r_glen, r_sigma, r_fwd, r_bwd, r_scr, r_fac32, r_sig32, r_foff, r_shape,
       r_sys32, r_adi, r_cmap, r_swU, r_swE, r_pck, r_pcc, r_pcbase, r_pcnum, r_pcmap, r_pU, r_pE, r_per, r_psinv,
@@ -168,8 +170,12 @@ struct pent_plan {
   void drop_streams() {
     for (auto e : ev) cudaEventDestroy(e);
     for (auto st : side) cudaStreamDestroy(st);
+    for (auto e : pev) cudaEventDestroy(e);
+    for (auto st : pipe) cudaStreamDestroy(st);
     ev.clear();
     side.clear();
+    pev.clear();
+    pipe.clear();
   }
 };
 
@@ -588,6 +594,18 @@ pent_status pent_plan_bind(pent_plan* p, void* ws, void* stream) {
     e = cudaEventCreateWithFlags(&ee, cudaEventDisableTiming);
     if (e == cudaSuccess) p->ev.push_back(ee);
   }
+  // streams of the host-resident pipeline (pent_solve_host_batch)
+  constexpr int kPipe = 3;
+  for (int k = 0; k < kPipe && e == cudaSuccess; ++k) {
+    cudaStream_t ss;
+    e = cudaStreamCreateWithFlags(&ss, cudaStreamNonBlocking);
+    if (e == cudaSuccess) p->pipe.push_back(ss);
+  }
+  for (int k = 0; k < kPipe + 1 && e == cudaSuccess; ++k) {
+    cudaEvent_t ee;
+    e = cudaEventCreateWithFlags(&ee, cudaEventDisableTiming);
+    if (e == cudaSuccess) p->pev.push_back(ee);
+  }
   if (e != cudaSuccess) return PENT_ECUDA;
   p->bound = true;
   p->factored = 0;
@@ -846,6 +864,58 @@ pent_status pent_solve_batch(pent_plan* p, const double* f, double* x, int max_r
   pent_status st = check_solve(p, f, x, max_refine);
   if (st != PENT_OK) return st;
   return solve_launch(p, f, x, max_refine);
+}
+
+pent_status pent_solve_host_batch(pent_plan* p, const double* h_f, double* h_x, double* d_f, double* d_x,
+                                  int nchunks, int max_refine) {
+  if (!p || !h_f || !h_x || nchunks < 1) return PENT_EINVAL;
+  pent_status st = check_solve(p, d_f, d_x, max_refine);
+  if (st != PENT_OK) return st;
+  if ((((uintptr_t)h_f) | ((uintptr_t)h_x)) % sizeof(double)) return PENT_EINVAL;
+  // slices of whole systems need one launch shape for the batch
+  const bool f32_one = p->precision == PENT_F32_REFINE && !p->periodic && p->buckets.size() == 1 && p->uniform;
+  const bool f64_one = p->precision == PENT_F64 && !p->periodic && p->runs.size() == 1 && !p->runs[0].part &&
+                       p->uniform;
+  int64_t units = f32_one ? p->batch : (f64_one ? p->ngroups : 1);  // slice granularity: systems or groups of 32
+  const int K = (int)std::min<int64_t>(nchunks, units);
+  auto sys_of = [&](int64_t u) { return f64_one ? std::min<int64_t>(u * kWarp, p->batch) : u; };
+  cudaError_t e = cudaSuccess;
+  if (K <= 1 || (!f32_one && !f64_one)) {  // one slice: copy in, solve, copy out on the plan's stream
+    const size_t bytes = (size_t)p->rows * sizeof(double);
+    e = cudaMemcpyAsync(d_f, h_f, bytes, cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess) st = solve_launch(p, d_f, d_x, max_refine);
+    if (e == cudaSuccess && st == PENT_OK) e = cudaMemcpyAsync(h_x, d_x, bytes, cudaMemcpyDeviceToHost, p->stream);
+    return e != cudaSuccess ? PENT_ECUDA : st;
+  }
+  const int np = (int)p->pipe.size();
+  e = cudaEventRecord(p->pev[0], p->stream);
+  for (int k = 0; k < np && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(p->pipe[k], p->pev[0], 0);
+  const int64_t n = p->n_uniform;
+  for (int c = 0; c < K && e == cudaSuccess; ++c) {
+    const int64_t u0 = units * c / K, u1 = units * (c + 1) / K;
+    const int64_t s0 = sys_of(u0), s1 = sys_of(u1);
+    if (s1 <= s0) continue;
+    cudaStream_t ss = p->pipe[c % np];
+    const size_t off = (size_t)(s0 * n), bytes = (size_t)((s1 - s0) * n) * sizeof(double);
+    e = cudaMemcpyAsync(d_f + off, h_f + off, bytes, cudaMemcpyHostToDevice, ss);
+    if (e != cudaSuccess) break;
+    if (f32_one) {
+      F32Bucket b = p->buckets[0];
+      b.first += s0;
+      b.count = s1 - s0;
+      e = launch_solve32r(p->f32(), p->at<int32_t>(p->r_sys32), b, p->shared, d_f, d_x, max_refine,
+                          p->residual == PENT_RESIDUAL_F64, p->tol_log2, ss);
+    } else {
+      const auto& r = p->runs[0];
+      e = launch_solve64(p->dev(), p->f64(), d_f, d_x, p->at<double>(p->r_scr), r.bw, r.unroll, u0, u1, ss);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_x + off, d_x + off, bytes, cudaMemcpyDeviceToHost, ss);
+  }
+  for (int k = 0; k < np && e == cudaSuccess; ++k) {
+    e = cudaEventRecord(p->pev[1 + k], p->pipe[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->stream, p->pev[1 + k], 0);
+  }
+  return cuda_status(e);
 }
 
 pent_status pent_solve_steps(pent_plan* p, double* x, int64_t nsteps, int max_refine) {

@@ -320,3 +320,35 @@ def test_adjoint_of_sigma_built_matrices_matches_transposed_oracle(prec):
     y = plan.adjoint_solve(dev(f), max_refine=3)
     assert plan.info()[0] == pb.PENT_OK
     assert sys_rel_err(host(y), ref, ns) <= TOL
+
+
+@pytest.mark.parametrize("prec", [pb.PENT_F64, pb.PENT_F32_REFINE])
+@pytest.mark.parametrize("chunks", [1, 3, 8])
+def test_solve_host_pipeline(prec, chunks):
+    """Right-hand sides in pinned host memory, solved in slices whose copies overlap the solves
+    (pent_solve_host_batch): equal to the oracle, for a batch that the slices do not divide evenly."""
+    batch, n = 1000, 256
+    sig = synth.log_uniform(880, 0, batch, 1e-3, 10.0)
+    f = synth.uniform(880, batch, batch * n, -1, 1)
+    ref = oracle.hyperdiff_steps(np.full(batch, n), sig, f, 1)
+    plan = pb.Plan(n, batch=batch, precision=prec)
+    plan.factor_hyperdiff(dev(sig))
+    fh = torch.from_numpy(f).pin_memory()
+    xh = torch.zeros_like(fh).pin_memory()
+    plan.solve_host(fh, xh, max_refine=2, chunks=chunks)
+    torch.cuda.synchronize()
+    assert sys_rel_err(xh.numpy(), ref, np.full(batch, n)) <= TOL
+
+
+def test_solve_host_uneven_plan_runs_as_one_slice():
+    ns = np.array([100, 3000, 7, 512] * 9)
+    sig = synth.log_uniform(881, 0, len(ns), 1e-3, 10.0)
+    f = synth.uniform(881, len(ns), int(ns.sum()), -1, 1)
+    ref = oracle.hyperdiff_steps(ns, sig, f, 1)
+    plan = pb.Plan(list(ns))
+    plan.factor_hyperdiff(dev(sig))
+    fh = torch.from_numpy(f).pin_memory()
+    xh = torch.zeros_like(fh).pin_memory()
+    plan.solve_host(fh, xh, chunks=4)
+    torch.cuda.synchronize()
+    assert sys_rel_err(xh.numpy(), ref, ns) <= TOL
