@@ -12,10 +12,21 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/pentbatch.h"
 #include "internal.cuh"
 
 using namespace pent;
+
+namespace {
+// An NVTX range over one library call (header-only NVTX 3: free when no profiler is attached;
+// host-side only, so it is allowed inside a stream capture).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
+}  // namespace
 
 namespace {
 
@@ -781,12 +792,14 @@ static pent_status factor_common(pent_plan* p, const double* a, const double* b,
 
 pent_status pent_factor_batch(pent_plan* p, const double* a, const double* b, const double* c, const double* d,
                               const double* e) {
+  const Range range("pent_factor_batch");
   if (!p || !a || !b || !c || !d || !e) return PENT_EINVAL;
   if (p->precision == PENT_F32_REFINE) return PENT_EINVAL;  // refinement needs the band in closed form (sigma)
   return factor_common(p, a, b, c, d, e, nullptr);
 }
 
 pent_status pent_factor_hyperdiff(pent_plan* p, const double* d_sigma) {
+  const Range range("pent_factor_hyperdiff");
   if (!p || !d_sigma) return PENT_EINVAL;
   return factor_common(p, nullptr, nullptr, nullptr, nullptr, nullptr, d_sigma);
 }
@@ -861,6 +874,7 @@ static pent_status check_solve(pent_plan* p, const void* f, const void* x, int m
 }
 
 pent_status pent_solve_batch(pent_plan* p, const double* f, double* x, int max_refine) {
+  const Range range("pent_solve_batch");
   pent_status st = check_solve(p, f, x, max_refine);
   if (st != PENT_OK) return st;
   return solve_launch(p, f, x, max_refine);
@@ -868,6 +882,7 @@ pent_status pent_solve_batch(pent_plan* p, const double* f, double* x, int max_r
 
 pent_status pent_solve_host_batch(pent_plan* p, const double* h_f, double* h_x, double* d_f, double* d_x,
                                   int nchunks, int max_refine) {
+  const Range range("pent_solve_host_batch");
   if (!p || !h_f || !h_x || nchunks < 1) return PENT_EINVAL;
   pent_status st = check_solve(p, d_f, d_x, max_refine);
   if (st != PENT_OK) return st;
@@ -919,6 +934,7 @@ pent_status pent_solve_host_batch(pent_plan* p, const double* h_f, double* h_x, 
 }
 
 pent_status pent_solve_steps(pent_plan* p, double* x, int64_t nsteps, int max_refine) {
+  const Range range("pent_solve_steps");
   pent_status st = check_solve(p, x, x, max_refine);
   if (st != PENT_OK) return st;
   if (nsteps < 0) return PENT_EINVAL;
@@ -959,6 +975,7 @@ static pent_status step_launch(pent_plan* p, const double* mu, const double* nu,
 
 pent_status pent_step_batch(pent_plan* p, const double* mu, const double* nu, double* C, int64_t nsteps,
                             int max_refine) {
+  const Range range("pent_step_batch");
   pent_status st = check_solve(p, C, C, max_refine);
   if (st != PENT_OK) return st;
   if (nsteps < 0) return PENT_EINVAL;
@@ -983,6 +1000,7 @@ pent_status pent_step_batch(pent_plan* p, const double* mu, const double* nu, do
 }
 
 pent_status pent_refactor_solve_hyperdiff(pent_plan* p, const double* d_sigma, const double* f, double* x) {
+  const Range range("pent_refactor_solve_hyperdiff");
   if (!p || !d_sigma) return PENT_EINVAL;
   if (!p->bound) return PENT_ENOTBOUND;
   if (!f || !x || (((uintptr_t)f) | ((uintptr_t)x) | ((uintptr_t)d_sigma)) % sizeof(double)) return PENT_EINVAL;
@@ -1008,6 +1026,7 @@ pent_status pent_refactor_solve_hyperdiff(pent_plan* p, const double* d_sigma, c
 }
 
 pent_status pent_adjoint_solve_batch(pent_plan* p, const double* f, double* x, int max_refine) {
+  const Range range("pent_adjoint_solve_batch");
   pent_status st = check_solve(p, f, x, max_refine);
   if (st != PENT_OK) return st;
   if (p->periodic) return PENT_EINVAL;
@@ -1092,6 +1111,7 @@ static pent_status adi_launch(pent_plan* px, pent_plan* py, double* C, int64_t n
 
 pent_status adi_step_2d(pent_plan* px, pent_plan* py, double* C, int64_t nx, int64_t ny, double gamma, double dt,
                         double dx, int max_refine) {
+  const Range range("adi_step_2d");
   pent_status st = adi_check(px, py, C, nx, ny, gamma, dt, dx, max_refine);
   if (st != PENT_OK) return st;
   return adi_launch(px, py, C, nx, ny, gamma, dt, dx);
@@ -1099,6 +1119,7 @@ pent_status adi_step_2d(pent_plan* px, pent_plan* py, double* C, int64_t nx, int
 
 pent_status adi_steps_2d(pent_plan* px, pent_plan* py, double* C, int64_t nx, int64_t ny, double gamma, double dt,
                          double dx, int max_refine, int64_t nsteps) {
+  const Range range("adi_steps_2d");
   pent_status st = adi_check(px, py, C, nx, ny, gamma, dt, dx, max_refine);
   if (st != PENT_OK) return st;
   if (nsteps < 0) return PENT_EINVAL;
