@@ -151,6 +151,23 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(ms: float, world: int, device=None) -> float:
+    """The slowest rank's time: every rank runs its own replica of the batch, and the
+    whole job's throughput is all ranks' rows over this time (weak scaling)."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(rows_per_rank: int, steps: int, world: int, ms: float) -> float:
+    """Row-solves per second of the whole job: every rank's rows over the slowest rank's time."""
+    return world * rows_per_rank * steps / (ms / 1e3)
+
+
 # ----------------------------------------------------------------------------- CPU baseline (oracle)
 
 def cpu_baseline(w, budget_s=15.0, gpu_results=None):
@@ -241,13 +258,9 @@ def run_own(args):
             ev1.record(stream)
             torch.cuda.synchronize(dev)
         barrier()
-        ms = ev0.elapsed_time(ev1)
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
         ms_step = ms / args.steps
-        value = world * rows * args.steps / (ms / 1e3)
+        value = job_throughput(rows, args.steps, world, ms)
         achieved = ALG_BYTES[name] * rows / (ms_step / 1e3) / 1e9
         tr = traffic_per_row(name)
         variants[name] = {
@@ -292,12 +305,8 @@ def run_own(args):
         ev1.record(stream)
         torch.cuda.synchronize(dev)
         barrier()
-        ms = ev0.elapsed_time(ev1)
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
-        e2e = {"value": world * rows * e2e_steps / (ms / 1e3), "unit": UNIT,
+        ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
+        e2e = {"value": job_throughput(rows, e2e_steps, world, ms), "unit": UNIT,
                "h2d_bytes_per_step": int(fh.numel() * 8), "d2h_bytes_per_step": int(xh.numel() * 8),
                "steps": e2e_steps, "precision": head}
         del plan
