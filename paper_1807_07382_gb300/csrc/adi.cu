@@ -47,13 +47,15 @@ constexpr int kChunk = kAdiChunk;
 constexpr int kRowsPerThr = 4;  // block is 32 x 8 threads
 
 // rhs = mu L(C^3 - C) - sigma L(L C) on a 32 x 32 tile, written transposed:
-// rhsT[x * ny + y].  C is staged with a two-cell mirrored halo; u = C^3 - C and
-// L C are formed on the tile plus a one-cell halo, then both outer Laplacians.
+// rhsT[x * ny + y].  L is linear, so this is L w with w = mu (C^3 - C) - sigma L C:
+// C is staged with a two-cell mirrored halo, w is formed on the tile plus a
+// one-cell halo (the even reflection commutes with L, so w's halo is the
+// reflection of w), then one outer Laplacian -- a quarter fewer FP64 operations
+// than two outer Laplacians, on a kernel bound by the FP64 pipe.
 __global__ void __launch_bounds__(256) k_adi_rhs_T(const double* __restrict__ C, double* __restrict__ rhsT, int nx,
                                                   int ny, double mu, double sigma) {
   __shared__ double sC[kTile + 4][kTile + 4 + 1];
-  __shared__ double sU[kTile + 2][kTile + 2 + 1];
-  __shared__ double sL[kTile + 2][kTile + 2 + 1];
+  __shared__ double sW[kTile + 2][kTile + 2 + 1];
   __shared__ double sO[kTile][kTile + 1];
   const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
@@ -66,15 +68,13 @@ __global__ void __launch_bounds__(256) k_adi_rhs_T(const double* __restrict__ C,
   for (int yy = ty; yy < kTile + 2; yy += 8)
     for (int xx = tx; xx < kTile + 2; xx += 32) {
       const double c = sC[yy + 1][xx + 1];
-      sU[yy][xx] = fma(c * c, c, -c);
-      sL[yy][xx] = (sC[yy + 1][xx] + sC[yy + 1][xx + 2]) + (sC[yy][xx + 1] + sC[yy + 2][xx + 1]) - 4.0 * c;
+      const double lc = (sC[yy + 1][xx] + sC[yy + 1][xx + 2]) + (sC[yy][xx + 1] + sC[yy + 2][xx + 1]) - 4.0 * c;
+      sW[yy][xx] = fma(mu, fma(c * c, c, -c), -sigma * lc);
     }
   __syncthreads();
   for (int r = 0; r < kRowsPerThr; ++r) {
     const int yy = ty + 8 * r, xx = tx;
-    const double lu = (sU[yy + 1][xx] + sU[yy + 1][xx + 2]) + (sU[yy][xx + 1] + sU[yy + 2][xx + 1]) - 4.0 * sU[yy + 1][xx + 1];
-    const double ll = (sL[yy + 1][xx] + sL[yy + 1][xx + 2]) + (sL[yy][xx + 1] + sL[yy + 2][xx + 1]) - 4.0 * sL[yy + 1][xx + 1];
-    sO[xx][yy] = fma(mu, lu, -sigma * ll);
+    sO[xx][yy] = (sW[yy + 1][xx] + sW[yy + 1][xx + 2]) + (sW[yy][xx + 1] + sW[yy + 2][xx + 1]) - 4.0 * sW[yy + 1][xx + 1];
   }
   __syncthreads();
   for (int r = 0; r < kRowsPerThr; ++r) {
