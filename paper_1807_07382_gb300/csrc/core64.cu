@@ -396,10 +396,14 @@ __global__ void __launch_bounds__(128) k_solve64_pair(DevPlan P, F64Factors F, c
 
 // f of rows base+2 and base+3 from v[k] = C_{base+k}, k = 0..5.
 __device__ __forceinline__ void step_rhs_pair(const double (&v)[6], double mu, double nu, double& fa, double& fb) {
-  const double d4a = fma(6.0, v[2], fma(-4.0, v[1] + v[3], v[0] + v[4]));
-  const double d4b = fma(6.0, v[3], fma(-4.0, v[2] + v[4], v[1] + v[5]));
-  fa = fma(-nu, d4a, v[2]);
-  fb = fma(-nu, d4b, v[3]);
+  fa = v[2];
+  fb = v[3];
+  if (nu != 0.0) {  // skipped for Cahn-Hilliard steps: the FP64 pipe is what bounds this kernel
+    const double d4a = fma(6.0, v[2], fma(-4.0, v[1] + v[3], v[0] + v[4]));
+    const double d4b = fma(6.0, v[3], fma(-4.0, v[2] + v[4], v[1] + v[5]));
+    fa = fma(-nu, d4a, fa);
+    fb = fma(-nu, d4b, fb);
+  }
   if (mu != 0.0) {
     const double u1 = fma(v[1] * v[1], v[1], -v[1]), u2 = fma(v[2] * v[2], v[2], -v[2]);
     const double u3 = fma(v[3] * v[3], v[3], -v[3]), u4 = fma(v[4] * v[4], v[4], -v[4]);
@@ -576,8 +580,8 @@ __global__ void __launch_bounds__(256) k_step_rhs(DevPlan P, const double* __res
       while (j < 0 || j >= n) j = (j < 0) ? (-1 - j) : (2 * n - 1 - j);
       v[k] = C[o + j];
     }
-    const double d4 = fma(6.0, v[2], fma(-4.0, v[1] + v[3], v[0] + v[4]));
-    double fi = fma(-nu, d4, v[2]);
+    double fi = v[2];
+    if (nu != 0.0) fi = fma(-nu, fma(6.0, v[2], fma(-4.0, v[1] + v[3], v[0] + v[4])), fi);
     if (mu != 0.0) {
       const double u1 = fma(v[1] * v[1], v[1], -v[1]), u2 = fma(v[2] * v[2], v[2], -v[2]);
       const double u3 = fma(v[3] * v[3], v[3], -v[3]);

@@ -204,8 +204,8 @@ __global__ void k_factor_periodic(PerArgs A, const double* __restrict__ a, const
 // Eq. temporal: nu = 0, mu = D dt / dx^2).
 __device__ __forceinline__ double rhs_row(double cm2, double cm1, double c0, double cp1, double cp2, double mu,
                                           double nu) {
-  const double d4 = fma(6.0, c0, fma(-4.0, cm1 + cp1, cm2 + cp2));
-  double f = fma(-nu, d4, c0);
+  double f = c0;
+  if (nu != 0.0) f = fma(-nu, fma(6.0, c0, fma(-4.0, cm1 + cp1, cm2 + cp2)), f);
   if (mu != 0.0) {
     const double um1 = fma(cm1 * cm1, cm1, -cm1), u0 = fma(c0 * c0, c0, -c0), up1 = fma(cp1 * cp1, cp1, -cp1);
     f = fma(mu, fma(-2.0, u0, um1 + up1), f);
