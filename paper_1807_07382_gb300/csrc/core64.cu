@@ -75,7 +75,13 @@ __global__ void k_factor64(DevPlan P, const double* __restrict__ a, const double
     double gam2 = 0.0, del2 = 0.0, gam1 = 0.0, del1 = 0.0;  // gamma/delta of rows r-2, r-1
     for (; r < n; ++r) {
       double ar, br, cr, dr, er;
-      if (sigma) {
+      if (sigma && r >= 2 && r + 2 < n) {  // interior rows of I + sigma D4: [1, -4, 6, -4, 1]
+        ar = sg;
+        br = -4.0 * sg;
+        cr = 1.0 + sg * 6.0;
+        dr = br;
+        er = sg;
+      } else if (sigma) {
         double w[5];
         d4_weights(r, n, w);
         ar = sg * w[0];
@@ -615,6 +621,7 @@ __global__ void __launch_bounds__(128) k_refactor_solve64(DevPlan P, F64Factors 
   const bool fvec = ((L.fo & 1) == 0) && ((((uintptr_t)f) & 15) == 0);
   const bool xvec = ((L.fo & 1) == 0) && ((((uintptr_t)x) & 15) == 0);
   const double sg = (L.s >= 0) ? sigma[L.s] : 0.0;
+  const double m4sg = -4.0 * sg, c6sg = 1.0 + sg * 6.0;
   if (L.s >= 0) sig[L.s] = sg;  // the plan's copy of sigma (epsilon of the records)
 
   // ---- factor + forward: L g = f ----
@@ -638,13 +645,16 @@ __global__ void __launch_bounds__(128) k_refactor_solve64(DevPlan P, F64Factors 
       const int64_t r = r0 + h;
       ia[h] = bt[h] = ga[h] = de[h] = 0.0;  // padding rows and rows after a failed pivot: g = x = 0
       if (r < L.n && !failed) {
-        double w[5];
-        d4_weights(r, L.n, w);
-        const double ar = (r >= 2) ? sg * w[0] : 0.0;
-        const double br = (r >= 1) ? sg * w[1] : 0.0;
-        const double cr = 1.0 + sg * w[2];
-        const double dr = (r + 1 < L.n) ? sg * w[3] : 0.0;
-        const double er = (r + 2 < L.n) ? sg * w[4] : 0.0;
+        double ar = sg, br = m4sg, cr = c6sg, dr = m4sg, er = sg;  // interior rows: [1, -4, 6, -4, 1]
+        if (r < 2 || r + 2 >= L.n) {                              // the two rows at each wall
+          double w[5];
+          d4_weights(r, L.n, w);
+          ar = (r >= 2) ? sg * w[0] : 0.0;
+          br = (r >= 1) ? sg * w[1] : 0.0;
+          cr = 1.0 + sg * w[2];
+          dr = (r + 1 < L.n) ? sg * w[3] : 0.0;
+          er = (r + 2 < L.n) ? sg * w[4] : 0.0;
+        }
         const double beta = br - ar * gam2;
         const double alpha = cr - ar * del2 - beta * gam1;
         if (!(alpha != 0.0) || !isfinite(alpha)) {

@@ -1130,13 +1130,16 @@ __global__ void k_factor32(F32Tables T, int64_t nsys, const int32_t* __restrict_
   for (int i = 0; i < rows; ++i) {
     float ainv = 0.f, bt = 0.f;  // padding rows and rows after a failed pivot: g = x = 0
     if (i < n && !failed) {
-      float w[5];
-      d4_weights_f(i, n, w);
-      const double ar = (i >= 2) ? sg * w[0] : 0.0;
-      const double br = (i >= 1) ? sg * w[1] : 0.0;
-      const double cr = 1.0 + sg * w[2];
-      const double dr = (i + 1 < n) ? sg * w[3] : 0.0;
-      const double er = (i + 2 < n) ? sg * w[4] : 0.0;
+      double ar = sg, br = -4.0 * sg, cr = 1.0 + sg * 6.0, dr = -4.0 * sg, er = sg;  // interior rows
+      if (i < 2 || i + 2 >= n) {  // the two rows at each wall
+        float w[5];
+        d4_weights_f(i, n, w);
+        ar = (i >= 2) ? sg * w[0] : 0.0;
+        br = (i >= 1) ? sg * w[1] : 0.0;
+        cr = 1.0 + sg * w[2];
+        dr = (i + 1 < n) ? sg * w[3] : 0.0;
+        er = (i + 2 < n) ? sg * w[4] : 0.0;
+      }
       const double beta = br - ar * gam2;
       const double alpha = cr - ar * del2 - beta * gam1;
       if (!(alpha != 0.0) || !isfinite(alpha)) {
