@@ -1006,13 +1006,21 @@ __global__ void k_sigma_grad(DevPlan P, const double* __restrict__ mu, const dou
   const int64_t o = P.shared ? s * P.n_shared : P.off[s];
   double acc = 0.0;
   for (int64_t i = lane; i < n; i += kWarp) {
-    double w[5];
-    d4_weights(i, n, w);
     double d4x = 0.0;
+    if (i >= 2 && i + 2 < n) {  // interior rows: [1, -4, 6, -4, 1], accumulated in the same order as below
+      const double* xi = x + o + i;
+      d4x = fma(-4.0, xi[-1], xi[-2]);
+      d4x = fma(6.0, xi[0], d4x);
+      d4x = fma(-4.0, xi[1], d4x);
+      d4x = d4x + xi[2];
+    } else {
+      double w[5];
+      d4_weights(i, n, w);
 #pragma unroll
-    for (int k = 0; k < 5; ++k) {
-      const int64_t j = i + k - 2;
-      if (j >= 0 && j < n && w[k] != 0.0) d4x = fma(w[k], x[o + j], d4x);
+      for (int k = 0; k < 5; ++k) {
+        const int64_t j = i + k - 2;
+        if (j >= 0 && j < n && w[k] != 0.0) d4x = fma(w[k], x[o + j], d4x);
+      }
     }
     acc = fma(mu[o + i], d4x, acc);
   }
