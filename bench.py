@@ -397,7 +397,7 @@ def run_workloads(names, args):
             ms, ck = _time_device(stream, lambda: plan.solve_steps(x, w.steps), w.steps, dev)
             err = _sys_err(x.cpu().numpy().reshape(w.batch, n), ref.reshape(w.batch, n))
             _line(name, "64 systems x N=256, shared sigma=0.5, 4 cosine modes + noise, 100 implicit steps (1 graph)",
-                  w.rows, w.steps, ms, 16, "k_solve64<shared>", err, clocks=ck,
+                  w.rows, w.steps, ms, 16, "k_solve64_pair<shared>", err, clocks=ck,
                   extra={"note": "shared factors broadcast; latency bound (16,384 rows per step)"})
         elif name == "uneven":
             w = synth.uneven()
@@ -526,8 +526,32 @@ def run_workloads(names, args):
                       extra={"note": note + "; the right-hand side C + mu D2(C^3 - C) is assembled in the kernel",
                              "err_sample": f"{len(pick)} systems, one step"})
                 del plan
+        elif name == "shared":
+            # the paper's benchmark configuration (Sec. 3): every system has the same matrix
+            w = synth.hyperdiff_parametric(batch=args.batch or 65536, steps=200)
+            n = int(w.n[0])
+            sig1 = np.array([1.0])
+            f0 = torch.from_numpy(w.field0).to(dev)
+            pick = np.arange(0, w.batch, max(1, w.batch // 128))
+            ref = oracle.hyperdiff_steps(np.full(len(pick), n), np.full(len(pick), 1.0),
+                                         w.field0.reshape(w.batch, n)[pick].reshape(-1), 1)
+            for prec, pname, alg, kern in ((pb.PENT_F64, "f64", 16, "k_solve64_pair<shared>"),
+                                           (pb.PENT_F32_REFINE, "f32_refine", 16, "k_solve32r (shared block)")):
+                plan = pb.Plan(n, batch=w.batch, shared=True, stream=stream, precision=prec)
+                plan.factor_hyperdiff(torch.from_numpy(sig1).to(dev))
+                one = plan.solve(f0, max_refine=1).cpu().numpy().reshape(w.batch, n)
+                err = _sys_err(one[pick], ref.reshape(len(pick), n))
+                x = f0.clone()
+                plan.solve_steps(x, w.steps, max_refine=1)
+                ms, ck = _time_device(stream, lambda: plan.solve_steps(x, w.steps, max_refine=1), w.steps, dev)
+                _line(f"{name}_{pname}", f"one matrix for the batch (the paper's identical systems, Sec. 3): {w.batch:,} "
+                      f"systems x N={n}, sigma = 1, C0 U[-1,1], {w.steps} implicit steps (1 graph)", w.rows, w.steps, ms,
+                      alg, kern, err, clocks=ck, dtype="f64" if prec == pb.PENT_F64 else "f32",
+                      extra={"note": "16 B/row: f read, x written; the factors are one broadcast block",
+                             "err_sample": f"{len(pick)} systems, one step"})
+                del plan
         elif name == "rewrite":
-            w = synth.hyperdiff_parametric(batch=args.batch or 65536)
+            w = synth.hyperdiff_parametric(batch=args.batch or 65536, steps=200)
             n = int(w.n[0])
             K = 20
             plan = pb.Plan(n, batch=w.batch, stream=stream)
@@ -616,13 +640,13 @@ def main():
                     help="systems (default: the full workload; smaller for profiling, also for --workload "
                          "periodic_cn, ch1d and rewrite)")
     ap.add_argument("--workload", default=None,
-                    help="comma-separated other workloads: cosines, uneven, adi, adjoint, periodic_cn, ch1d, rewrite, "
+                    help="comma-separated other workloads: cosines, uneven, adi, adjoint, periodic_cn, ch1d, rewrite, shared, "
                          "or all (one JSON line each; the default run is the parametric headline line)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.workload:
-        names = ["cosines", "uneven", "adi", "adjoint", "periodic_cn", "ch1d", "rewrite"] \
+        names = ["cosines", "uneven", "adi", "adjoint", "periodic_cn", "ch1d", "rewrite", "shared"] \
             if args.workload == "all" else args.workload.split(",")
         run_workloads(names, args)
         return

@@ -273,13 +273,18 @@ __global__ void __launch_bounds__(256) k_solve64(DevPlan P, F64Factors F, const 
 // buffering).  HYP: hyperdiffusion records, g_i = (1/alpha_i)(f_i - beta_i
 // g_{i-1} - sigma g_{i-2}) with sigma in a register -- one factor plane (8 bytes
 // per row) less to read than the general form, for the same FP64 operations.
-template <int U2, bool HYP>
+// SHARED: one matrix for the whole batch (general records fwd[r*3 + p], bwd[r*2 + p],
+// loaded as broadcasts; the system length must be even so that row pairs do not
+// straddle systems); f, x and g still move in row pairs.
+template <int U2, bool HYP, bool SHARED = false>
 __global__ void __launch_bounds__(128) k_solve64_pair(DevPlan P, F64Factors F, const double* f, double* x,
                                                       double* __restrict__ gscr, int64_t kbeg, int64_t kend) {
   const int64_t k = kbeg + (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kWarp;
   if (k >= kend) return;
   const int lane = threadIdx.x & (kWarp - 1);
-  const Lane L = lane_setup<false>(P, k, lane);
+  const Lane L = lane_setup<SHARED>(P, k, lane);
+  const double* __restrict__ fwd1 = F.fwd;
+  const double* __restrict__ bwd1 = F.bwd;
   const double2* __restrict__ fwd = reinterpret_cast<const double2*>(F.fwd);
   const double2* __restrict__ bwd = reinterpret_cast<const double2*>(F.bwd);
   double2* __restrict__ g2s = reinterpret_cast<double2*>(gscr);
@@ -298,10 +303,17 @@ __global__ void __launch_bounds__(128) k_solve64_pair(DevPlan P, F64Factors F, c
     for (int u = 0; u < U2; ++u) {
       const int64_t q = q0 + u;
       if (q < np) {
-        const double2* rec = fwd + ((P0 + q) * NP) * kWarp + lane;
-        A[u] = __ldg(rec);
-        B[u] = __ldg(rec + kWarp);
-        if (!HYP) E[u] = __ldg(rec + 2 * kWarp);
+        if (SHARED) {
+          const double* ra = fwd1 + (2 * q) * 3;
+          A[u] = make_double2(__ldg(ra), __ldg(ra + 3));
+          B[u] = make_double2(__ldg(ra + 1), __ldg(ra + 4));
+          E[u] = make_double2(__ldg(ra + 2), __ldg(ra + 5));
+        } else {
+          const double2* rec = fwd + ((P0 + q) * NP) * kWarp + lane;
+          A[u] = __ldg(rec);
+          B[u] = __ldg(rec + kWarp);
+          if (!HYP) E[u] = __ldg(rec + 2 * kWarp);
+        }
         const int64_t r = 2 * q;
         if (fvec && r + 1 < L.n) {
           Fv[u] = *reinterpret_cast<const double2*>(f + L.fo + r);
@@ -350,9 +362,15 @@ __global__ void __launch_bounds__(128) k_solve64_pair(DevPlan P, F64Factors F, c
     for (int u = 0; u < U2; ++u) {
       const int64_t q = q0 - u;
       if (q >= 0) {
-        const double2* rec = bwd + ((P0 + q) * 2) * kWarp + lane;
-        Ga[u] = __ldg(rec);
-        De[u] = __ldg(rec + kWarp);
+        if (SHARED) {
+          const double* rb = bwd1 + (2 * q) * 2;
+          Ga[u] = make_double2(__ldg(rb), __ldg(rb + 2));
+          De[u] = make_double2(__ldg(rb + 1), __ldg(rb + 3));
+        } else {
+          const double2* rec = bwd + ((P0 + q) * 2) * kWarp + lane;
+          Ga[u] = __ldg(rec);
+          De[u] = __ldg(rec + kWarp);
+        }
         Gv[u] = g2s[(P0 + q) * kWarp + lane];
       }
     }
@@ -1046,6 +1064,16 @@ cudaError_t launch_solve64(const DevPlan& P, F64Factors F, const double* f, doub
   if (g1 <= g0) return cudaSuccess;
   const int block = kWarp * block_warps;
   const int grid = grid_for((g1 - g0) * kWarp, block);
+  if (P.shared && (P.n_shared & 1) == 0) {  // row pairs of a shared matrix (even length)
+#define PENT_U2S(U_, U2_)                                                               \
+  if (unroll == U_) {                                                                   \
+    k_solve64_pair<U2_, false, true><<<grid, block, 0, st>>>(P, F, f, x, gscr, g0, g1); \
+    return cudaGetLastError();                                                          \
+  }
+    PENT_U2S(2, 1) PENT_U2S(4, 2) PENT_U2S(8, 4)
+#undef PENT_U2S
+    return cudaErrorInvalidValue;
+  }
   if (P.shared) {
 #define PENT_U(U_)                                                   \
   if (unroll == U_) {                                                \

@@ -279,10 +279,11 @@ __global__ void __launch_bounds__(128) k_solve_periodic(PerArgs A, const double*
     fa = fs[n - 2];
     fb = fs[n - 1];
   }
-  const double4 si = *reinterpret_cast<const double4*>(A.sinv + 4 * sr);
+  const double2 s01 = *reinterpret_cast<const double2*>(A.sinv + 4 * sr);
+  const double2 s23 = *reinterpret_cast<const double2*>(A.sinv + 4 * sr + 2);
   const double t0 = fa - acc0, t1 = fb - acc1;
-  const double xa = fma(si.x, t0, si.y * t1);
-  const double xb = fma(si.z, t0, si.w * t1);
+  const double xa = fma(s01.x, t0, s01.y * t1);
+  const double xb = fma(s23.x, t0, s23.y * t1);
   // ---- back: R X = g - W t ----
   double x1 = 0.0, x2 = 0.0;
   for (int64_t i = m - 1; i >= 0; --i) {
