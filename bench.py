@@ -194,6 +194,19 @@ def cpu_baseline(w, budget_s=15.0, gpu_results=None):
     out = {"value": sample * n * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
            "sample": f"{sample} of {w.batch} systems (every {w.batch // sample}th) x N={n}, {steps} implicit steps, "
                      f"factored untimed; OpenMP over systems"}
+    # the paper's serial C arm (Sec. 3.3): one thread, the first 512 sampled systems, about 3 s
+    ns = min(512, sample)
+    fs = x1[:ns * n].copy()
+    facs = [v[:ns * n] for v in fac]
+    t0 = time.perf_counter()
+    oracle.solve_batch(np.full(ns, n), facs, fs, nthreads=1)
+    t1 = time.perf_counter() - t0
+    reps = max(1, int(min(3.0, budget_s / 5) / max(t1, 1e-6)))
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        fs = oracle.solve_batch(np.full(ns, n), facs, fs, nthreads=1)
+    out["serial_1_core"] = {"value": ns * n * reps / (time.perf_counter() - t0), "unit": UNIT,
+                            "sample": f"{ns} sampled systems x N={n}, {reps} implicit steps, one thread"}
     errs = {}
     if gpu_results:
         ref = x1.reshape(sample, n)

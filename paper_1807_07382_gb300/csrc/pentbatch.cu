@@ -318,7 +318,10 @@ void build_f64_runs(pent_plan* p) {
     return len > 1024 ? std::make_pair(8, 1) : std::make_pair(4, 2);
   };
   if (p->shared) {
-    const auto kb = knobs(p->n_uniform);
+    // one broadcast record block: a row's only per-lane loads are f and g, and one-warp CTAs spread
+    // the batch over the most SMs (65,536 x 1024 on GB300: unroll 4 one warp 0.65 ms a step,
+    // two to four warps 0.70-0.77 ms, unroll 8 0.98 ms)
+    const auto kb = p->f64_explicit ? std::make_pair(p->unroll, p->block_warps) : std::make_pair(4, 1);
     p->runs.push_back({0, p->ngroups, kb.first, kb.second, false, 0, 0});
     return;
   }
