@@ -203,9 +203,29 @@ pent_status pent_solve_batch(pent_plan* plan, const double* f, double* x, int ma
  * partitioned groups); other plans run as one slice.  Asynchronous on the
  * plan's stream, which waits for every slice; h_f must stay unchanged and h_x
  * unread until the stream reaches that point.  Not capture-safe (host memory).
+ *
+ * Direct form (d_f = d_x = NULL, PENT_F32_REFINE plans): no staging and no
+ * copies.  The FP32 solve kernels read each f row once from h_f and write each
+ * x row once to h_x over the host link (NVLink-C2C on Grace-Blackwell nodes),
+ * as pent_solve_batch would in device memory; h_x may alias h_f; nchunks is
+ * ignored.  h_f and h_x must each lie, for all sum(n_s) doubles, inside one
+ * page-locked allocation the device maps (cudaHostAlloc, pinned tensors); the
+ * library checks this through the driver's pointer attributes before any
+ * launch and returns PENT_EINVAL otherwise (pageable or device memory, a range
+ * that runs past its allocation).  PENT_F64 plans: PENT_EINVAL (their
+ * one-thread-per-system loads would cross the link 16 bytes at a time).
  */
 pent_status pent_solve_host_batch(pent_plan* plan, const double* h_f, double* h_x, double* d_f, double* d_x,
                                   int nchunks, int max_refine);
+
+/*
+ * The check the direct form of pent_solve_host_batch makes on each of h_f and
+ * h_x: PENT_OK when [h, h + bytes) lies inside one page-locked host allocation
+ * that the device maps, PENT_EINVAL otherwise (NULL, bytes = 0, pageable or
+ * device memory, a range past its allocation).  A host-side driver query: no
+ * launch, no synchronisation, no plan needed.
+ */
+pent_status pent_host_range_mapped(const void* h, size_t bytes);
 
 /*
  * `nsteps` implicit steps in place: x <- A^{-1} x, repeated.  The sequence is

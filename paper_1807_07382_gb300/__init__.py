@@ -174,17 +174,29 @@ class Plan:
                                        int(max_refine)), "pent_solve_batch")
         return x
 
-    def solve_host(self, f_host, x_host, f_dev=None, x_dev=None, max_refine: int = 2, chunks: int = 16):
+    def solve_host(self, f_host, x_host, f_dev=None, x_dev=None, max_refine: int = 2, chunks: int = 16,
+                   direct: bool = False):
         """Solve for right-hand sides held in pinned host memory: the library copies f to the
         device staging buffer, solves and copies x back, in `chunks` slices whose copies and
         solves overlap (pent_solve_host_batch); asynchronous on the plan's stream.  f_dev / x_dev
-        are device staging buffers (allocated here if not given; x_dev may be f_dev)."""
+        are device staging buffers (allocated here if not given; x_dev may be f_dev).
+        direct=True (FP32+refine plans): no staging; the solve kernels read f_host and write
+        x_host in place over the host link (x_host may be f_host); both must be pinned."""
         torch = _torch()
         if f_host.is_cuda or x_host.is_cuda:
             raise ValueError("solve_host takes host tensors")
         for t, name in ((f_host, "f_host"), (x_host, "x_host")):
             if t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != self.rows:
                 raise ValueError(f"{name} must be a contiguous float64 tensor of {self.rows} elements")
+        if direct:
+            if f_dev is not None or x_dev is not None:
+                raise ValueError("direct solves take no staging buffers")
+            if not (f_host.is_pinned() and x_host.is_pinned()):
+                raise ValueError("direct solves need pinned host tensors")
+            self._host_refs = (f_host, x_host)
+            check(self._L.pent_solve_host_batch(self._h, f_host.data_ptr(), x_host.data_ptr(), None, None,
+                                                int(chunks), int(max_refine)), "pent_solve_host_batch")
+            return x_host
         fd = f_dev if f_dev is not None else torch.empty(self.rows, dtype=torch.float64, device=self.device)
         xd = x_dev if x_dev is not None else torch.empty_like(fd)
         self._host_refs = (f_host, x_host, fd, xd)

@@ -52,6 +52,7 @@ SIGNATURES = {
     "pent_solve_batch": (_int, [_vp, _vp, _vp, _int]),
     "pent_solve_steps": (_int, [_vp, _vp, _i64, _int]),
     "pent_solve_host_batch": (_int, [_vp, _vp, _vp, _vp, _vp, _int, _int]),
+    "pent_host_range_mapped": (_int, [_vp, ctypes.c_size_t]),
     "pent_step_batch": (_int, [_vp, _vp, _vp, _vp, _i64, _int]),
     "pent_refactor_solve_hyperdiff": (_int, [_vp, _vp, _vp, _vp]),
     "pent_adjoint_solve_batch": (_int, [_vp, _vp, _vp, _int]),

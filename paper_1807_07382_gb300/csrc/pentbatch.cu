@@ -12,6 +12,7 @@
 #include <tuple>
 #include <vector>
 
+#include <cuda.h>  // CUpointer_attribute / CUmemorytype; the driver function comes through the runtime
 #include <nvtx3/nvToolsExt.h>
 
 #include "../../include/pentbatch.h"
@@ -883,10 +884,57 @@ pent_status pent_solve_batch(pent_plan* p, const double* f, double* x, int max_r
   return solve_launch(p, f, x, max_refine);
 }
 
+}  // extern "C"
+
+// The device address of [h, h + bytes) when the whole range lies inside one
+// page-locked host allocation that the GPU addresses directly (cudaHostAlloc,
+// pinned tensors); nullptr for anything else (pageable memory, device memory,
+// a range that runs past its allocation, a driver without the query).
+static void* mapped_host_range(const void* h, size_t bytes) {
+  using GetAttr = CUresult (*)(void*, CUpointer_attribute, CUdeviceptr);
+  static const GetAttr get = []() -> GetAttr {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<GetAttr>(fn);
+  }();
+  if (!get || !h || bytes == 0) return nullptr;
+  const CUdeviceptr hp = (CUdeviceptr)(uintptr_t)h;
+  unsigned int type = 0;
+  CUdeviceptr d = 0, start = 0;
+  size_t size = 0;
+  if (get(&type, CU_POINTER_ATTRIBUTE_MEMORY_TYPE, hp) != CUDA_SUCCESS || type != CU_MEMORYTYPE_HOST) return nullptr;
+  if (get(&d, CU_POINTER_ATTRIBUTE_DEVICE_POINTER, hp) != CUDA_SUCCESS || d == 0) return nullptr;
+  if (get(&start, CU_POINTER_ATTRIBUTE_RANGE_START_ADDR, d) != CUDA_SUCCESS ||
+      get(&size, CU_POINTER_ATTRIBUTE_RANGE_SIZE, d) != CUDA_SUCCESS)
+    return nullptr;
+  if (d < start || d - start > size || bytes > size - (size_t)(d - start)) return nullptr;
+  return reinterpret_cast<void*>((uintptr_t)d);
+}
+
+extern "C" {
+
+pent_status pent_host_range_mapped(const void* h, size_t bytes) {
+  return mapped_host_range(h, bytes) ? PENT_OK : PENT_EINVAL;
+}
+
 pent_status pent_solve_host_batch(pent_plan* p, const double* h_f, double* h_x, double* d_f, double* d_x,
                                   int nchunks, int max_refine) {
   const Range range("pent_solve_host_batch");
   if (!p || !h_f || !h_x || nchunks < 1) return PENT_EINVAL;
+  if (!d_f && !d_x) {  // direct: the kernels read h_f and write h_x where they lie, over the host link
+    if (p->precision != PENT_F32_REFINE || max_refine < 0) return PENT_EINVAL;
+    if (!p->bound) return PENT_ENOTBOUND;
+    if (!p->factored) return PENT_ENOTFACTORED;
+    if ((((uintptr_t)h_f) | ((uintptr_t)h_x)) % sizeof(double)) return PENT_EINVAL;
+    const size_t bytes = (size_t)p->rows * sizeof(double);
+    const double* df = static_cast<const double*>(mapped_host_range(h_f, bytes));
+    double* dx = static_cast<double*>(mapped_host_range(h_x, bytes));
+    if (!df || !dx) return PENT_EINVAL;
+    return solve_launch(p, df, dx, max_refine);
+  }
   pent_status st = check_solve(p, d_f, d_x, max_refine);
   if (st != PENT_OK) return st;
   if ((((uintptr_t)h_f) | ((uintptr_t)h_x)) % sizeof(double)) return PENT_EINVAL;

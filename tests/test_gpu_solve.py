@@ -352,3 +352,52 @@ def test_solve_host_uneven_plan_runs_as_one_slice():
     plan.solve_host(fh, xh, chunks=4)
     torch.cuda.synchronize()
     assert sys_rel_err(xh.numpy(), ref, ns) <= TOL
+
+
+@pytest.mark.parametrize("case", ["uniform", "uneven", "in_place"])
+def test_solve_host_direct(case):
+    """Direct host solves (no staging): the FP32+refine kernels read f from, and write x to,
+    pinned host memory; equal to the oracle, for a uniform batch, an uneven one (several
+    launch shapes, a cluster-sized system) and x aliasing f."""
+    ns = np.full(700, 384) if case != "uneven" else np.array([100, 3000, 7, 512, 9000] * 7)
+    sig = synth.log_uniform(883, 0, len(ns), 1e-3, 10.0)
+    f = synth.uniform(883, len(ns), int(ns.sum()), -1, 1)
+    ref = oracle.hyperdiff_steps(ns, sig, f, 1)
+    plan = pb.Plan(list(ns), precision=pb.PENT_F32_REFINE)
+    plan.factor_hyperdiff(dev(sig))
+    fh = torch.from_numpy(f.copy()).pin_memory()
+    xh = fh if case == "in_place" else torch.zeros_like(fh).pin_memory()
+    plan.solve_host(fh, xh, max_refine=2, direct=True)
+    torch.cuda.synchronize()
+    assert sys_rel_err(xh.numpy(), ref, ns) <= TOL
+    if case != "in_place":
+        assert np.array_equal(fh.numpy(), f)  # f untouched
+
+
+def test_host_range_check_refuses_unmapped_memory():
+    """The check of the direct form, called on its own (a host-side driver query, nothing is
+    launched): pinned tensors pass for their own length, and pageable memory, device memory, a
+    range running past its pinned allocation, NULL and zero bytes are refused; an FP64 plan
+    refuses the direct form before looking at the pointers."""
+    from paper_1807_07382_gb300._lib import PENT_EINVAL
+    n, batch = 256, 64
+    rows = n * batch
+    L = pb.Plan(n, batch=batch)._L
+    pinned = torch.zeros(rows, dtype=torch.float64).pin_memory()
+    pageable = torch.zeros(rows, dtype=torch.float64)
+    dbuf = torch.zeros(rows, dtype=torch.float64, device="cuda")
+    big = torch.zeros(1 << 20, dtype=torch.float64).pin_memory()
+    assert L.pent_host_range_mapped(pinned.data_ptr(), rows * 8) == pb.PENT_OK
+    assert L.pent_host_range_mapped(big.data_ptr(), big.numel() * 8) == pb.PENT_OK
+    assert L.pent_host_range_mapped(pageable.data_ptr(), rows * 8) == PENT_EINVAL
+    assert L.pent_host_range_mapped(dbuf.data_ptr(), rows * 8) == PENT_EINVAL
+    assert L.pent_host_range_mapped(None, rows * 8) == PENT_EINVAL
+    assert L.pent_host_range_mapped(pinned.data_ptr(), 0) == PENT_EINVAL
+    # the last half-row block of `big`, asked for twice its length, and far past the end
+    tail = big.data_ptr() + big.numel() * 8 - rows * 4
+    assert L.pent_host_range_mapped(tail, rows * 4) == pb.PENT_OK
+    assert L.pent_host_range_mapped(tail, 1 << 40) == PENT_EINVAL
+    p64 = pb.Plan(n, batch=batch)
+    p64.factor_hyperdiff(dev(np.full(batch, 0.5)))
+    assert p64._L.pent_solve_host_batch(p64._h, pinned.data_ptr(), pinned.data_ptr(), None, None, 1, 1) \
+        == PENT_EINVAL
