@@ -331,11 +331,23 @@ def run_own(args):
             xh.zero_()
             modes["direct"] = timed(lambda: plan.solve_host(fh, xh, max_refine=args.max_refine, direct=True))
             match = bool(torch.equal(staged_x, xh))
+        # the host link's floor: the step's two copies alone, both directions at once
+        side = torch.cuda.Stream(dev)
+
+        def copies():
+            side.wait_stream(stream)
+            fd.copy_(fh, non_blocking=True)
+            with torch.cuda.stream(side):
+                xh.copy_(xd, non_blocking=True)
+            stream.wait_stream(side)
+
+        link_ms = timed(copies)
         best = min(modes, key=modes.get)
         e2e = {"value": job_throughput(rows, e2e_steps, world, modes[best]), "unit": UNIT,
                "h2d_bytes_per_step": int(fh.numel() * 8), "d2h_bytes_per_step": int(xh.numel() * 8),
                "steps": e2e_steps, "precision": head, "mode": best,
-               "ms_per_step": {k: v / e2e_steps for k, v in modes.items()}}
+               "ms_per_step": {k: v / e2e_steps for k, v in modes.items()},
+               "link_floor_ms_per_step": link_ms / e2e_steps, "frac_of_link_floor": link_ms / modes[best]}
         if match is not None:
             e2e["direct_equals_staged"] = match
         del plan
