@@ -1066,6 +1066,7 @@ pent_status pent_refactor_solve_hyperdiff(pent_plan* p, const double* d_sigma, c
   const DevPlan P = p->dev();
   F64Factors F = p->f64();
   F.sig = p->at<double>(p->r_sigma);
+  if (p->factored != 2) p->drop_graphs();  // graphs cached for another record form
   double* gscr = p->at<double>(p->r_scr);
   const cudaError_t err = fork_join(p, p->runs.size(), [&](size_t i, cudaStream_t s) {
     const auto& r = p->runs[i];

@@ -200,6 +200,47 @@ def test_full_size_parametric_sampled():
         torch.cuda.empty_cache()
 
 
+@pytest.mark.parametrize("precision", [pb.PENT_F64, pb.PENT_F32_REFINE])
+def test_full_size_uneven_sampled(precision):
+    """The uneven workload at full size (20,000 systems, N log-uniform in [64, 16384],
+    sum N = 59.1 M) with the GB300 tune cache, as the benchmark launches it: one solve,
+    every 97th system checked against the oracle, plus the longest system."""
+    import os
+    w = synth.uneven()
+    off = w.offsets
+    pick = np.unique(np.append(np.arange(0, w.batch, 97), int(np.argmax(w.n))))
+    sub_f = np.concatenate([w.field0[off[s]:off[s + 1]] for s in pick])
+    ref = oracle.hyperdiff_steps(w.n[pick], w.sigma[pick], sub_f, 1)
+    tune = os.path.join(os.path.dirname(pb.__file__), "tune_gb300.txt")
+    plan = pb.Plan(list(w.n), precision=precision, tune_cache=tune)
+    plan.factor_hyperdiff(dev(w.sigma))
+    x = host(plan.solve(dev(w.field0), max_refine=2))
+    got = np.concatenate([x[off[s]:off[s + 1]] for s in pick])
+    assert plan.info()[0] == pb.PENT_OK
+    assert sys_rel_err(got, ref, w.n[pick]) <= TOL
+    del plan
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("precision", [pb.PENT_F64, pb.PENT_F32_REFINE])
+def test_full_size_shared_matrix_sampled(precision):
+    """One matrix for 65,536 systems of N=1024 (the paper's identical systems), solved
+    through the broadcast-record kernels; 64 sampled systems against the oracle."""
+    w = synth.hyperdiff_parametric(steps=1)
+    n = 1024
+    idx = np.unique(np.linspace(0, w.batch - 1, 64).astype(int))
+    sub_f = np.concatenate([w.field0[s * n:(s + 1) * n] for s in idx])
+    ref = oracle.hyperdiff_steps(np.full(len(idx), n), np.full(len(idx), 1.0), sub_f, 1)
+    plan = pb.Plan(n, batch=w.batch, shared=True, precision=precision)
+    plan.factor_hyperdiff(dev(np.array([1.0])))
+    x = plan.solve(dev(w.field0), max_refine=2)
+    xs = host(x.view(w.batch, n)[torch.as_tensor(idx, device=x.device)]).reshape(-1)
+    assert plan.info()[0] == pb.PENT_OK
+    assert sys_rel_err(xs, ref, np.full(len(idx), n)) <= TOL
+    del plan, x
+    torch.cuda.empty_cache()
+
+
 # ----------------------------------------------------------------------------- FP32 shapes and uneven batches
 
 @pytest.mark.parametrize("tps", [128, 256, 512, 1024, 2048])
@@ -401,3 +442,24 @@ def test_host_range_check_refuses_unmapped_memory():
     p64.factor_hyperdiff(dev(np.full(batch, 0.5)))
     assert p64._L.pent_solve_host_batch(p64._h, pinned.data_ptr(), pinned.data_ptr(), None, None, 1, 1) \
         == PENT_EINVAL
+
+
+
+def test_refactor_after_general_factorisation_drops_cached_graphs():
+    """A plan factored from general bands caches its step graph with the general-record kernel;
+    a later one-pass refactorisation writes hyperdiffusion records, so a replay under the same
+    graph key must run the hyperdiffusion kernel."""
+    ns = np.array([256] * 40 + [4, 5, 300, 301] * 3)
+    sig = synth.log_uniform(886, 0, len(ns), 1e-3, 10.0)
+    f = synth.uniform(886, len(ns), int(ns.sum()), -1, 1)
+    bands = oracle.band_hyperdiff_batch(ns, sig)
+    plan = pb.Plan(list(ns))
+    plan.factor(*[dev(b) for b in bands])
+    X = dev(f)
+    plan.solve_steps(X, 2)  # cached under (X, 2 steps)
+    X2 = dev(f)
+    plan.refactor_solve(dev(2.0 * sig), X2, X2)
+    X.copy_(dev(f))
+    plan.solve_steps(X, 2)
+    ref = oracle.hyperdiff_steps(ns, 2.0 * sig, f, 2)
+    assert sys_rel_err(host(X), ref, ns) <= TOL
