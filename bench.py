@@ -441,7 +441,7 @@ def run_workloads(names, args):
                   w.rows, w.steps, ms, 16, "k_solve64_pair<shared>", err, clocks=ck,
                   extra={"note": "shared factors broadcast; latency bound (16,384 rows per step)"})
         elif name == "uneven":
-            w = synth.uneven()
+            w = synth.uneven(steps=args.workload_steps or 200)
             f0 = torch.from_numpy(w.field0).to(dev)
             sig = torch.from_numpy(w.sigma).to(dev)
             off = w.offsets
@@ -461,7 +461,7 @@ def run_workloads(names, args):
                 plan.solve_steps(x, w.steps, max_refine=1)
                 ms, ck = _time_device(stream, lambda: plan.solve_steps(x, w.steps, max_refine=1), w.steps, dev)
                 _line(f"{name}_{pname}", "20,000 systems, N log-U[64,16384] (sum 59.1 M rows), sigma log-U[1e-2,10], "
-                      "200 implicit steps (1 graph), tuned launch settings", w.rows, w.steps, ms, alg, kern, err,
+                      f"{w.steps} implicit steps (1 graph), tuned launch settings", w.rows, w.steps, ms, alg, kern, err,
                       dtype="f64" if prec == pb.PENT_F64 else "f32", clocks=ck,
                       extra={"max_refine": 1 if prec == pb.PENT_F32_REFINE else 0,
                              "err_sample": f"{len(pick)} systems, one step"})
@@ -680,6 +680,8 @@ def main():
     ap.add_argument("--batch", type=int, default=None,
                     help="systems (default: the full workload; smaller for profiling, also for --workload "
                          "periodic_cn, ch1d and rewrite)")
+    ap.add_argument("--workload-steps", type=int, default=None,
+                    help="steps of the uneven workload's timed graph (default 200; fewer for profiling)")
     ap.add_argument("--workload", default=None,
                     help="comma-separated other workloads: cosines, uneven, adi, adjoint, periodic_cn, ch1d, rewrite, shared, "
                          "or all (one JSON line each; the default run is the parametric headline line)")
