@@ -134,7 +134,7 @@ enum {
                                       scans, instead of one serial walk per system; 0 never, -1 automatic
                                       (the default: where a walk would outlast the whole batch's streaming
                                       time, and at least 2048 rows).  Before pent_plan_bind. */
-  PENT_OPT_PERIODIC = 8            /* 1: the systems are cyclic (Sec. 2.3, Eq. matrix_sys1): row i reads
+  PENT_OPT_PERIODIC = 8,           /* 1: the systems are cyclic (Sec. 2.3, Eq. matrix_sys1): row i reads
                                       x_{i-2} .. x_{i+2} with column indices modulo n, so the first two rows
                                       reach the last two columns and vice versa.  Plans of uniform n >= 5
                                       only, before pent_plan_bind.  PENT_F32_REFINE periodic plans take the
@@ -150,6 +150,12 @@ enum {
                                       the cyclic band; pent_factor_hyperdiff builds Eq. (matrix_sys) with
                                       sigma_x = sigma.  Adjoint, sigma-gradient and ADI calls return
                                       PENT_EINVAL for periodic plans. */
+  PENT_OPT_CLUSTER_WARPS = 9       /* PENT_F32_REFINE: systems that need more than 512 threads run in a
+                                      thread-block cluster of up to 8 CTAs of exactly this many warps: 8
+                                      (the default) or 4, which keep several CTAs resident per SM, or 16
+                                      (CTAs of up to 16 warps, one per SM); systems longer than 8 such CTAs
+                                      take the 16-warp form.  Systems of up to 512 threads run in one CTA
+                                      whatever the value.  Before pent_plan_bind. */
 };
 pent_status pent_plan_set_option(pent_plan* plan, int key, int64_t value);
 pent_status pent_plan_get_option(const pent_plan* plan, int key, int64_t* value);

@@ -1295,7 +1295,14 @@ template <int L, bool RES64, bool STEP>
 cudaError_t dispatch_bucket(const F32Tables& T, const int32_t* sys, const F32Bucket& b, int shared, const double* f,
                             double* x, int max_refine, int tol_log2, const double* mu, const double* nu,
                             cudaStream_t st) {
-  if (b.C > 1) return launch_bucket<L, 0, true, RES64, STEP>(T, sys, b, shared, f, x, max_refine, tol_log2, mu, nu, st);
+  if (b.C > 1) {
+    // clusters of 4- or 8-warp CTAs compiled for that width (several CTAs per SM), else any width
+    if (!RES64 && b.W == 4)
+      return launch_bucket<L, 4, true, RES64, STEP>(T, sys, b, shared, f, x, max_refine, tol_log2, mu, nu, st);
+    if (!RES64 && b.W == 8)
+      return launch_bucket<L, 8, true, RES64, STEP>(T, sys, b, shared, f, x, max_refine, tol_log2, mu, nu, st);
+    return launch_bucket<L, 0, true, RES64, STEP>(T, sys, b, shared, f, x, max_refine, tol_log2, mu, nu, st);
+  }
   if (!RES64) {
     switch (b.W) {
       case 1: return launch_bucket<L, 1, false, RES64, STEP>(T, sys, b, shared, f, x, max_refine, tol_log2, mu, nu, st);

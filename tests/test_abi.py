@@ -146,3 +146,31 @@ def test_new_entry_points_check_arguments_on_the_host(L):
     assert L.pent_refactor_solve_hyperdiff(h, ctypes.c_void_p(16), ctypes.c_void_p(16),
                                            ctypes.c_void_p(16)) == _lib.PENT_ENOTBOUND
     L.pent_plan_destroy(h)
+
+
+def test_cluster_warps_option_shapes(L):
+    # FP32+refine only, 4 / 8 / 16, before binding; long systems become clusters of whole cw-warp CTAs
+    st, h = _create(L, batch=3, n=[5000, 1000, 30000], prec=1)
+    assert st == 0
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    v = ctypes.c_int64()
+    assert L.pent_plan_get_option(h, _lib.PENT_OPT_CLUSTER_WARPS, ctypes.byref(v)) == 0 and v.value == 8
+    assert L.pent_plan_system_config(h, 0, ctypes.byref(a), ctypes.byref(b)) == 0
+    assert (a.value, b.value) == (8, 768)  # 625 threads: three CTAs of 8 warps
+    assert L.pent_plan_set_option(h, _lib.PENT_OPT_CLUSTER_WARPS, 16) == 0
+    assert L.pent_plan_system_config(h, 0, ctypes.byref(a), ctypes.byref(b)) == 0
+    assert (a.value, b.value) == (8, 640)  # two CTAs of 10 warps under the 16-warp rule
+    for cw, tps0 in ((8, 768), (4, 640)):
+        assert L.pent_plan_set_option(h, _lib.PENT_OPT_CLUSTER_WARPS, cw) == 0
+        assert L.pent_plan_system_config(h, 0, ctypes.byref(a), ctypes.byref(b)) == 0
+        assert (a.value, b.value) == (8, tps0)  # ceil(625 / (32 cw)) CTAs of cw warps
+        assert L.pent_plan_system_config(h, 1, ctypes.byref(a), ctypes.byref(b)) == 0
+        assert b.value == 128  # 125 threads: one CTA of 4 warps
+        assert L.pent_plan_system_config(h, 2, ctypes.byref(a), ctypes.byref(b)) == 0
+        assert a.value * b.value >= 30000  # beyond 8 CTAs of cw warps: the 16-warp rule
+    for bad in (0, 2, 12, 32):
+        assert L.pent_plan_set_option(h, _lib.PENT_OPT_CLUSTER_WARPS, bad) == _lib.PENT_EINVAL
+    L.pent_plan_destroy(h)
+    st, h = _create(L, batch=2, n_uniform=64)  # FP64
+    assert L.pent_plan_set_option(h, _lib.PENT_OPT_CLUSTER_WARPS, 8) == _lib.PENT_EINVAL
+    L.pent_plan_destroy(h)

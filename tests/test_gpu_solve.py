@@ -277,6 +277,27 @@ def test_f32_refine_long_systems_in_clusters(n, batch):
     assert sys_rel_err(host(x), ref, w.n) <= TOL
 
 
+@pytest.mark.parametrize("cw", [4, 8, 16])
+def test_f32_refine_cluster_widths(cw):
+    """PENT_OPT_CLUSTER_WARPS: systems that need more than 512 threads run in clusters of CTAs
+    of that many warps (4 and 8: compiled for the width; beyond 8 CTAs, the 16-warp rule):
+    lengths on both sides of every switch, refined to the oracle."""
+    ns = np.array([100, 129, 1024, 1025, 2048, 2049, 3000, 4096, 4097, 8192, 8193, 16384, 20000])
+    sig = synth.log_uniform(887, 0, len(ns), 1e-2, 10.0)
+    f = synth.uniform(887, len(ns), int(ns.sum()), -1, 1)
+    ref = oracle.hyperdiff_steps(ns, sig, f, 1)
+    plan = pb.Plan(list(ns), precision=pb.PENT_F32_REFINE, options={pb.PENT_OPT_CLUSTER_WARPS: cw})
+    plan.factor_hyperdiff(dev(sig))
+    x = plan.solve(dev(f), max_refine=2)
+    assert plan.info()[0] == pb.PENT_OK
+    assert sys_rel_err(host(x), ref, ns) <= TOL
+    for s_, m in enumerate(ns):
+        rpt, tps = plan.system_config(s_)
+        assert rpt * tps >= m
+        if cw < 16 and tps > 512 and tps <= 8 * 32 * cw:
+            assert tps % (32 * cw) == 0  # whole cw-warp CTAs
+
+
 def test_f32_refine_uneven_batch():
     """Log-uniform lengths in [64, 16384] (the uneven workload's distribution),
     many shape buckets launched over the plan's side streams, plus a CUDA graph."""

@@ -45,7 +45,7 @@ def test_f32_rules_pick_each_systems_shape(L, tmp_path):
         assert config(L, h, 1) == (4, 64)
         assert config(L, h, 2) == (8, 512)       # explicit threads per system
         assert config(L, h, 3) == (8, 512)
-        assert config(L, h, 4) == (8, 640)       # 625 threads -> cluster of 2 CTAs x 10 warps
+        assert config(L, h, 4) == (8, 768)       # 625 threads -> cluster of 3 CTAs x 8 warps
         assert config(L, h, 5) == (8, 3840)      # 3750 threads -> 8 CTAs x 15 warps
     finally:
         L.pent_plan_destroy(h)
