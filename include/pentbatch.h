@@ -203,8 +203,9 @@ pent_status pent_solve_batch(pent_plan* plan, const double* f, double* x, int ma
  * copied to the device staging array d_f, solved into d_x (as
  * pent_solve_batch; d_x may alias d_f) and copied back to h_x.  The batch is cut
  * into `nchunks` slices of whole systems that flow through three streams of
- * the plan, so that the copy of one slice to the device, the solve of the
- * next and the copy of a third back overlap.  Slicing needs plans of one
+ * the plan -- copies in, solves, copies out, handed on slice by slice with
+ * events -- so that the copy of one slice to the device, the solve of another
+ * and the copy of a third back overlap.  Slicing needs plans of one
  * system length solved by one launch shape (uniform batches, not periodic, no
  * partitioned groups); other plans run as one slice.  Asynchronous on the
  * plan's stream, which waits for every slice; h_f must stay unchanged and h_x

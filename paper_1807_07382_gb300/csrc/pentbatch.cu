@@ -103,6 +103,7 @@ struct pent_plan {
   std::vector<cudaEvent_t> ev;    // fork/join events
   std::vector<cudaStream_t> pipe; // slices of pent_solve_host_batch (copy in, solve, copy out)
   std::vector<cudaEvent_t> pev;   // their fork/join events
+  std::vector<cudaEvent_t> sev;   // per-slice hand-over events (copied in, solved)
   // workspace regions
   Region r_info, r_perm, r_off, r_n, r_goff, r_glen, r_sigma, r_fwd, r_bwd, r_scr, r_fac32, r_sig32, r_foff, r_shape,
       r_sys32, r_adi, r_cmap, r_swU, r_swE, r_pck, r_pcc, r_pcbase, r_pcnum, r_pcmap, r_pU, r_pE, r_per, r_psinv,
@@ -184,10 +185,12 @@ struct pent_plan {
     for (auto e : ev) cudaEventDestroy(e);
     for (auto st : side) cudaStreamDestroy(st);
     for (auto e : pev) cudaEventDestroy(e);
+    for (auto e : sev) cudaEventDestroy(e);
     for (auto st : pipe) cudaStreamDestroy(st);
     ev.clear();
     side.clear();
     pev.clear();
+    sev.clear();
     pipe.clear();
   }
 };
@@ -978,6 +981,12 @@ pent_status pent_solve_host_batch(pent_plan* p, const double* h_f, double* h_x, 
     return e != cudaSuccess ? PENT_ECUDA : st;
   }
   const int np = (int)p->pipe.size();
+  while ((int)p->sev.size() < 2 * K && e == cudaSuccess) {  // per-slice hand-over events, kept by the plan
+    cudaEvent_t ee;
+    e = cudaEventCreateWithFlags(&ee, cudaEventDisableTiming);
+    if (e == cudaSuccess) p->sev.push_back(ee);
+  }
+  if (e != cudaSuccess) return PENT_ECUDA;
   e = cudaEventRecord(p->pev[0], p->stream);
   for (int k = 0; k < np && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(p->pipe[k], p->pev[0], 0);
   const int64_t n = p->n_uniform;
@@ -985,9 +994,13 @@ pent_status pent_solve_host_batch(pent_plan* p, const double* h_f, double* h_x, 
     const int64_t u0 = units * c / K, u1 = units * (c + 1) / K;
     const int64_t s0 = sys_of(u0), s1 = sys_of(u1);
     if (s1 <= s0) continue;
-    cudaStream_t ss = p->pipe[c % np];
+    // one stream per role: copies in, solves, copies out, each slice handed on by events, so
+    // that neither copy direction waits behind the other in a stream's order
+    cudaStream_t s_in = p->pipe[0], ss = p->pipe[1], s_out = p->pipe[2];
     const size_t off = (size_t)(s0 * n), bytes = (size_t)((s1 - s0) * n) * sizeof(double);
-    e = cudaMemcpyAsync(d_f + off, h_f + off, bytes, cudaMemcpyHostToDevice, ss);
+    e = cudaMemcpyAsync(d_f + off, h_f + off, bytes, cudaMemcpyHostToDevice, s_in);
+    if (e == cudaSuccess) e = cudaEventRecord(p->sev[2 * c], s_in);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ss, p->sev[2 * c], 0);
     if (e != cudaSuccess) break;
     if (f32_one) {
       F32Bucket b = p->buckets[0];
@@ -999,7 +1012,9 @@ pent_status pent_solve_host_batch(pent_plan* p, const double* h_f, double* h_x, 
       const auto& r = p->runs[0];
       e = launch_solve64(p->dev(), p->f64(), d_f, d_x, p->at<double>(p->r_scr), r.bw, r.unroll, u0, u1, ss);
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h_x + off, d_x + off, bytes, cudaMemcpyDeviceToHost, ss);
+    if (e == cudaSuccess) e = cudaEventRecord(p->sev[2 * c + 1], ss);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s_out, p->sev[2 * c + 1], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_x + off, d_x + off, bytes, cudaMemcpyDeviceToHost, s_out);
   }
   for (int k = 0; k < np && e == cudaSuccess; ++k) {
     e = cudaEventRecord(p->pev[1 + k], p->pipe[k]);
