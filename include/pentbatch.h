@@ -79,7 +79,9 @@ typedef struct pent_plan pent_plan;
  *                 the built-in choices.
  * The plan is a host object; it records shapes and choices only.
  * Errors: PENT_EINVAL for batch < 1, a row count < 1, shared_matrix with
- * uneven sizes, or a NULL `plan`.
+ * uneven sizes, or a NULL `plan`; for PENT_F32_REFINE also a system longer
+ * than 32,768 rows (one system is at most a cluster of 8 CTAs of 512
+ * threads holding 8 rows each; PENT_F64 plans take any length).
  */
 pent_status pent_plan_create(pent_plan** plan, int64_t batch, const int64_t* n_per_system, int64_t n_uniform,
                              int shared_matrix, pent_precision precision, const char* tune_cache);

@@ -174,3 +174,15 @@ def test_cluster_warps_option_shapes(L):
     st, h = _create(L, batch=2, n_uniform=64)  # FP64
     assert L.pent_plan_set_option(h, _lib.PENT_OPT_CLUSTER_WARPS, 8) == _lib.PENT_EINVAL
     L.pent_plan_destroy(h)
+
+
+def test_f32_refine_length_limit(L):
+    # FP32+refine systems are at most a cluster of 8 CTAs x 512 threads x 8 rows; FP64 takes any length
+    for n, want32 in ((32768, 0), (32769, _lib.PENT_EINVAL), (100000, _lib.PENT_EINVAL)):
+        st, h = _create(L, batch=1, n=[n], prec=1)
+        assert st == want32
+        if st == 0:
+            L.pent_plan_destroy(h)
+        st, h = _create(L, batch=1, n=[n])
+        assert st == 0
+        L.pent_plan_destroy(h)
