@@ -69,6 +69,42 @@ def source_sha(path):
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
+def profile_entry(variant):
+    """The ncu figures of profiles/traffic.json for this variant's kernel, or None once the
+    kernel source has changed since they were taken."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        e = json.load(fh).get(variant)
+    if not e or e.get("source_sha") != source_sha(KERNEL_SRC[variant]):
+        return None
+    return e
+
+
+# GB300: 152 SMs of 4 schedulers, each issuing at most one warp instruction per clock;
+# FP64 at 1/64 of the FP32 rate, 1.25 TFLOP/s nominal (the FP64 solve does 4 FMA + 1 MUL
+# = 9 flops per row: g = (1/alpha)(f - beta g1 - sigma g2), x = g - gamma x1 - delta x2)
+SMS, SCHEDULERS, FP64_TFLOPS, F64_FLOPS_PER_ROW = 152, 4, 1.25, 9
+
+
+def compute_roofline(variant, rows, ms_step, sm_mhz):
+    """The compute side of the solve: warp-instruction issue for FP32+refine (instructions
+    per row from the ncu capture), the FP64 pipe for the FP64 solve."""
+    if variant == "f64":
+        achieved = F64_FLOPS_PER_ROW * rows / (ms_step / 1e3) / 1e12
+        return {"bound": "fp64", "achieved": achieved, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_TFLOPS, "peak_kind": "nominal (GB300 FP64)"}
+    e = profile_entry(variant)
+    if not e or "warp_inst_per_row" not in e or not sm_mhz:
+        return None
+    achieved = e["warp_inst_per_row"] * rows / (ms_step / 1e3)
+    peak = SMS * SCHEDULERS * sm_mhz * 1e6
+    return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "warp instructions/s",
+            "frac": achieved / peak, "peak_kind": "152 SMs x 4 schedulers x 1 per clock at the sampled SM clock",
+            "warp_inst_per_row": e["warp_inst_per_row"]}
+
+
 def traffic_per_row(variant):
     """DRAM bytes per row from a committed ncu summary, if it was taken on the current kernel source."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
@@ -284,6 +320,8 @@ def run_own(args):
                          "peak_kind": peak_kind},
             "clocks": cs.summary(),
         }
+        variants[name]["compute_roofline"] = compute_roofline(name, rows, ms_step,
+                                                              variants[name]["clocks"].get("sm_mhz"))
         if name == "f32_refine":
             variants[name]["max_refine"] = args.max_refine
             variants[name]["refine_steps_used"] = plan.info()[3]
@@ -369,7 +407,8 @@ def run_own(args):
                        "max_refine": args.max_refine if head == "f32_refine" else 0,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "working set (factors + field) >= 1.9 GB, larger than L2; no flush"},
-            "roofline": hv["roofline"], "cpu_baseline": base, "e2e": e2e, "gpu_launches": args.steps,
+            "roofline": hv["roofline"], "compute_roofline": hv["compute_roofline"], "cpu_baseline": base,
+            "e2e": e2e, "gpu_launches": args.steps,
             "clocks": clocks, "variants": variants,
         }
         if errs:
