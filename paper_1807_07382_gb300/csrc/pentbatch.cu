@@ -201,11 +201,10 @@ pent_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PENT_OK : PEN
 
 using Shape = pent_plan::Shape;
 
-// FP32 CTA shape for n rows with L rows per thread: the fewest warps that cover
-// n in one CTA of at most 16 warps, and beyond that a cluster of C CTAs (at
-// most 8) with as few warps each as cover n.
-// Up to 512 threads: one CTA.  Beyond: a cluster of up to 8 CTAs of exactly cw
-// warps (4 or 8), else of up to 16 warps each.  On GB300, 8-warp clusters solve
+// FP32 CTA shape for n rows with L rows per thread.  Up to 512 threads: one CTA
+// of the fewest warps that cover n.  Beyond: a cluster of up to 8 CTAs of
+// exactly cw warps (4 or 8), else of up to 8 CTAs with as few warps each (at
+// most 16) as cover n.  On GB300, 8-warp clusters solve
 // 6,144-16,384-row systems in 0.020-0.024 ms per million rows against 0.028-0.030
 // for 16-warp ones (three CTAs resident per SM instead of one); up to 4,096 rows
 // one CTA of up to 16 warps beats a cluster (0.018 against 0.024).
