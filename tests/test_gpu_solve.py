@@ -349,6 +349,21 @@ def test_f64_partitioned_general_bands(part_rows):
     assert sys_rel_err(host(fx), ref, ns) <= TOL
 
 
+def test_f64_very_long_systems():
+    """Systems of a million rows and more (odd lengths) beside short ones: the long group runs
+    as 256-row chunks joined by scans; two implicit steps against the oracle."""
+    ns = np.array([1_000_003, 5, 1_048_576, 300, 2_000_001])
+    sig = synth.log_uniform(889, 0, len(ns), 1e-2, 10.0)
+    f = synth.uniform(889, len(ns), int(ns.sum()), -1, 1)
+    ref = oracle.hyperdiff_steps(ns, sig, f, 2)
+    plan = pb.Plan(list(ns))
+    plan.factor_hyperdiff(dev(sig))
+    x = dev(f)
+    plan.solve_steps(x, 2)
+    assert plan.info()[0] == pb.PENT_OK
+    assert sys_rel_err(host(x), ref, ns) <= TOL
+
+
 def test_f64_partitioned_hyperdiff_uneven_steps_and_graph():
     w = synth.uneven(batch=200, steps=3)
     ref = oracle.hyperdiff_steps(w.n, w.sigma, w.field0, w.steps)
