@@ -965,7 +965,7 @@ __global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, min_blocks(L, WT, STEP
     float muh = 0.f, mul = 0.f, nuh = 0.f, nul = 0.f;
     if (mu_s) split_scaled(mu_s[ms], 0, muh, mul);
     if (nu_s) split_scaled(nu_s[ms], 0, nuh, nul);
-    if (emax > 1023 + 40 && t == 0) atomicOr(T.info + 2, 1ull);  // field outside the FP32 path's range
+    if (emax >= 1023 + 40 && t == 0) atomicOr(T.info + 2, 1ull);  // |C| >= 2^40: outside the FP32 path's range
     step_rhs_ff<L, PER>(fv, muh, mul, nuh, nul, muh != 0.f, nuh != 0.f, twice, fh, fl, n, tg, cx, sm);
   } else {
 #pragma unroll

@@ -499,3 +499,25 @@ def test_refactor_after_general_factorisation_drops_cached_graphs():
     plan.solve_steps(X, 2)
     ref = oracle.hyperdiff_steps(ns, 2.0 * sig, f, 2)
     assert sys_rel_err(host(X), ref, ns) <= TOL
+
+
+def test_f32_refine_reports_non_convergence():
+    """Refinement that stops contracting sets the non-convergence flag: FP32 factors of
+    I + sigma D4 at sigma = 1e8 (condition number ~1.6e9, far beyond 1/u of FP32) cannot
+    contract the error, and pent_get_info returns PENT_ENOCONV; after pent_clear_info a
+    well-conditioned solve reads back PENT_OK.  A step whose field exceeds the FP32 path's
+    range (|C| >= 2^40) is flagged the same way."""
+    from paper_1807_07382_gb300._lib import PENT_ENOCONV
+    n, batch = 1024, 8
+    f = synth.uniform(890, 0, batch * n, -1, 1)
+    plan = pb.Plan(n, batch=batch, precision=pb.PENT_F32_REFINE)
+    plan.factor_hyperdiff(dev(np.full(batch, 1e8)))
+    plan.solve(dev(f), max_refine=6)
+    assert plan.info()[0] == PENT_ENOCONV
+    plan.clear_info()
+    plan.factor_hyperdiff(dev(np.full(batch, 1.0)))
+    plan.solve(dev(f), max_refine=2)
+    assert plan.info()[0] == pb.PENT_OK
+    C = dev(f * 2.0 ** 41)
+    plan.step(C, mu=dev(np.full(batch, 1e-3)), nsteps=1, max_refine=2)
+    assert plan.info()[0] == PENT_ENOCONV
