@@ -207,7 +207,8 @@ pent_status pent_solve_batch(pent_plan* plan, const double* f, double* x, int ma
  * into `nchunks` slices of whole systems that flow through three streams of
  * the plan -- copies in, solves, copies out, handed on slice by slice with
  * events -- so that the copy of one slice to the device, the solve of another
- * and the copy of a third back overlap.  Slicing needs plans of one
+ * and the copy of a third back overlap (at most 256 slices; nchunks beyond
+ * that, or beyond the number of systems, is clamped).  Slicing needs plans of one
  * system length solved by one launch shape (uniform batches, not periodic, no
  * partitioned groups); other plans run as one slice.  Asynchronous on the
  * plan's stream, which waits for every slice; h_f must stay unchanged and h_x

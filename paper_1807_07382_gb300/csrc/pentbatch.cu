@@ -912,6 +912,10 @@ pent_status pent_solve_batch(pent_plan* p, const double* f, double* x, int max_r
 
 }  // extern "C"
 
+// Slices of one pent_solve_host_batch call at most (two hand-over events each; on
+// GB300 the pipeline gains nothing beyond 16-24 slices).
+constexpr int64_t kMaxSlices = 256;
+
 // The device address of [h, h + bytes) when the whole range lies inside one
 // page-locked host allocation that the GPU addresses directly (cudaHostAlloc,
 // pinned tensors); nullptr for anything else (pageable memory, device memory,
@@ -969,7 +973,7 @@ pent_status pent_solve_host_batch(pent_plan* p, const double* h_f, double* h_x, 
   const bool f64_one = p->precision == PENT_F64 && !p->periodic && p->runs.size() == 1 && !p->runs[0].part &&
                        p->uniform;
   int64_t units = f32_one ? p->batch : (f64_one ? p->ngroups : 1);  // slice granularity: systems or groups of 32
-  const int K = (int)std::min<int64_t>(nchunks, units);
+  const int K = (int)std::min<int64_t>(std::min<int64_t>(nchunks, units), kMaxSlices);
   auto sys_of = [&](int64_t u) { return f64_one ? std::min<int64_t>(u * kWarp, p->batch) : u; };
   cudaError_t e = cudaSuccess;
   if (K <= 1 || (!f32_one && !f64_one)) {  // one slice: copy in, solve, copy out on the plan's stream

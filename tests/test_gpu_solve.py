@@ -400,7 +400,7 @@ def test_adjoint_of_sigma_built_matrices_matches_transposed_oracle(prec):
 
 
 @pytest.mark.parametrize("prec", [pb.PENT_F64, pb.PENT_F32_REFINE])
-@pytest.mark.parametrize("chunks", [1, 3, 8])
+@pytest.mark.parametrize("chunks", [1, 3, 8, 100000])
 def test_solve_host_pipeline(prec, chunks):
     """Right-hand sides in pinned host memory, solved in slices whose copies overlap the solves
     (pent_solve_host_batch): equal to the oracle, for a batch that the slices do not divide evenly."""
