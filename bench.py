@@ -539,29 +539,33 @@ def run_workloads(names, args):
             sig = torch.from_numpy(w.sigma).to(dev).requires_grad_(True)
             target = pag.hyperdiff_steps(c0.detach(), sig.detach() * (1 + w.extra["perturb"]), w.steps)
 
-            def grad():
-                xT = pag.hyperdiff_steps(c0, sig, w.steps, 10)
-                loss = ((xT - target) ** 2).sum()
-                return torch.autograd.grad(loss, (c0, sig))
-            gc, gs = grad()
             pick = np.arange(0, w.batch, 128)
             _, rgc, rgs = oracle.hyperdiff_loss_grad(w.sigma[pick], w.steps, w.field0.reshape(w.batch, n)[pick],
                                                      target.detach().cpu().numpy()[pick])
-            err_s = float(np.max(np.abs(gs.cpu().numpy()[pick] - rgs) / np.abs(rgs)))
-            torch.cuda.synchronize(dev)
-            t0 = time.perf_counter()
-            reps = 3
-            for _ in range(reps):
-                grad()
-            torch.cuda.synchronize(dev)
-            ms = (time.perf_counter() - t0) * 1e3 / reps
-            solves = 3 * w.steps  # forward, recompute from checkpoints, adjoint
-            _line(name, "4,096 systems x N=1024, loss over T=50 implicit steps, gradient w.r.t. C0 and sigma "
-                  "(checkpoints every 10 steps)", w.batch * n * solves, 1, ms, 56,
-                  "k_solve64_pair + k_adjoint64 + k_sigma_grad", err_s,
-                  extra={"ms_per_gradient": ms, "err_metric": "relative error of dL/dsigma vs the oracle adjoint "
-                                                              f"({len(pick)} systems)",
-                         "timing": "host wall clock around torch.autograd (3 gradients)"})
+            for prec, pname, mr, kern in ((pb.PENT_F64, "", 0, "k_solve64_pair + k_adjoint64 + k_sigma_grad"),
+                                          (pb.PENT_F32_REFINE, "_f32_refine", 2, "k_solve32r + k_sigma_grad")):
+                def grad():
+                    xT = pag.hyperdiff_steps(c0, sig, w.steps, 10, precision=prec, max_refine=mr)
+                    loss = ((xT - target) ** 2).sum()
+                    return torch.autograd.grad(loss, (c0, sig))
+                gc, gs = grad()
+                err_s = float(np.max(np.abs(gs.cpu().numpy()[pick] - rgs) / np.abs(rgs)))
+                err_c = float(np.max(np.abs(gc.cpu().numpy()[pick] - rgc)) / np.max(np.abs(rgc)))
+                torch.cuda.synchronize(dev)
+                t0 = time.perf_counter()
+                reps = 3
+                for _ in range(reps):
+                    grad()
+                torch.cuda.synchronize(dev)
+                ms = (time.perf_counter() - t0) * 1e3 / reps
+                solves = 3 * w.steps  # forward, recompute from checkpoints, adjoint
+                _line(name + pname, "4,096 systems x N=1024, loss over T=50 implicit steps, gradient w.r.t. C0 and "
+                      "sigma (checkpoints every 10 steps)", w.batch * n * solves, 1, ms, 56 if not pname else 36,
+                      kern, err_s, dtype="f64" if not pname else "f32",
+                      extra={"ms_per_gradient": ms, "max_refine": mr,
+                             "err_metric": "relative error of dL/dsigma vs the oracle adjoint "
+                                           f"({len(pick)} systems)",
+                             "err_dC0": err_c, "timing": "host wall clock around torch.autograd (3 gradients)"})
         elif name == "periodic_cn":
             w = synth.periodic_cn(batch=args.batch or 65536)
             n = int(w.n[0])

@@ -303,8 +303,9 @@ pent_status pent_adjoint_solve_batch(pent_plan* plan, const double* f, double* x
 
 /*
  * dL/dsigma_s contribution of one implicit step: g_sigma[s] -= mu_s . (D4 x_s)
- * for every system, with mu and x device arrays laid out like f.  Used by the
- * differentiable time stepper (from A x^k = x^{k-1} and dA/dsigma = D4).
+ * for every system, with mu and x device arrays laid out like f (FP64
+ * arithmetic, plans of either precision; periodic plans: PENT_EINVAL).  Used by
+ * the differentiable time stepper (from A x^k = x^{k-1} and dA/dsigma = D4).
  */
 pent_status pent_hyperdiff_sigma_grad(pent_plan* plan, const double* mu, const double* x, double* g_sigma);
 

@@ -19,12 +19,12 @@ from __future__ import annotations
 
 import torch
 
-from . import PENT_F64, Plan
+from . import PENT_F32_REFINE, PENT_F64, Plan
 
 
 class _Steps(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, c0, sigma, T: int, checkpoint_every: int):
+    def forward(ctx, c0, sigma, T: int, checkpoint_every: int, precision: int, max_refine: int):
         if c0.dtype != torch.float64 or sigma.dtype != torch.float64:
             raise TypeError("c0 and sigma must be float64")
         if not (c0.is_cuda and sigma.is_cuda):
@@ -33,16 +33,19 @@ class _Steps(torch.autograd.Function):
         if sigma.shape != (batch,):
             raise ValueError("sigma must have shape (batch,)")
         k = max(1, int(checkpoint_every))
-        plan = Plan(n, batch=batch, precision=PENT_F64, device=c0.device)
+        if precision not in (PENT_F64, PENT_F32_REFINE):
+            raise ValueError("precision must be PENT_F64 or PENT_F32_REFINE")
+        plan = Plan(n, batch=batch, precision=precision, device=c0.device)
         sig = sigma.detach().contiguous()
         plan.factor_hyperdiff(sig)
         x = c0.detach().contiguous().clone()
         checkpoints = [x.clone()]
         for step in range(1, T + 1):
-            plan.solve(x, x)
+            plan.solve(x, x, max_refine=max_refine)
             if step % k == 0 and step < T:
                 checkpoints.append(x.clone())
         ctx.plan = plan
+        ctx.max_refine = max_refine
         ctx.sig = sig
         ctx.T = T
         ctx.k = k
@@ -62,17 +65,20 @@ class _Steps(torch.autograd.Function):
             states = [ctx.checkpoints[j]]
             x = ctx.checkpoints[j].clone()
             for _ in range(s0, s1):
-                plan.solve(x, x)
+                plan.solve(x, x, max_refine=ctx.max_refine)
                 states.append(x.clone())
             for step in range(s1, s0, -1):
-                plan.adjoint_solve(lam, mu)
+                plan.adjoint_solve(lam, mu, max_refine=ctx.max_refine)
                 plan.sigma_grad(mu, states[step - s0], gsig)
                 lam, mu = mu, lam
         ctx.checkpoints = None
-        return lam, gsig, None, None
+        return lam, gsig, None, None, None, None
 
 
-def hyperdiff_steps(c0, sigma, T: int, checkpoint_every: int = 10):
+def hyperdiff_steps(c0, sigma, T: int, checkpoint_every: int = 10, precision: int = PENT_F64, max_refine: int = 2):
     """x^T after T implicit hyperdiffusion steps from c0 (batch x n) with per-system
-    sigma (batch,), differentiable w.r.t. c0 and sigma."""
-    return _Steps.apply(c0, sigma, int(T), int(checkpoint_every))
+    sigma (batch,), differentiable w.r.t. c0 and sigma.  precision: PENT_F64, or
+    PENT_F32_REFINE (FP32 solves refined against the float-float residual, up to
+    max_refine steps each; A = I + sigma D4 is symmetric, so the adjoint solves run
+    through the same kernel)."""
+    return _Steps.apply(c0, sigma, int(T), int(checkpoint_every), int(precision), int(max_refine))

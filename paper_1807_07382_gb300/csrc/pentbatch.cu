@@ -1136,7 +1136,7 @@ pent_status pent_adjoint_solve_batch(pent_plan* p, const double* f, double* x, i
 pent_status pent_hyperdiff_sigma_grad(pent_plan* p, const double* mu, const double* x, double* g_sigma) {
   if (!p || !mu || !x || !g_sigma) return PENT_EINVAL;
   if (!p->bound) return PENT_ENOTBOUND;
-  if (p->periodic || p->precision != PENT_F64) return PENT_EINVAL;
+  if (p->periodic) return PENT_EINVAL;  // the reduction reads only the plan's offsets: either precision
   return cuda_status(launch_sigma_grad(p->dev(), mu, x, g_sigma, p->stream));
 }
 

@@ -115,3 +115,36 @@ def test_full_size_differentiation_workload():
     assert abs(loss_g - loss_o) <= 1e-11 * loss_o
     assert np.max(np.abs(gc_g - gc_o)) <= max(1e-11 * np.max(np.abs(gc_o)), 2.0 * 2.0 * dx)
     assert nrel(gs_g, gs_o) <= 1e-11
+
+
+@pytest.mark.parametrize("batch,n,T,k", [(37, 64, 7, 3), (33, 1024, 20, 10)])
+def test_f32_refine_gradients(batch, n, T, k):
+    """The same gradients with FP32+refine solves (max_refine = 2); A = I + sigma D4 is
+    symmetric, so the adjoint solves run through the FP32 kernel too.  Bars from the
+    per-solve parity bar eps = 1e-12 (every FP32+refine solve meets it) and ||A^{-1}|| <= 1,
+    so solve errors add over the steps: x^T within T eps; the vector-Jacobian product for the
+    oracle's cotangent within 2 T eps (T adjoint solves on T recomputed states); the loss
+    gradient within (amp + 2) T eps, where amp = max|x^T| / max|x^T - target| (~250 here) is
+    how much the cotangent 2 (x^T - target) magnifies the error of x^T."""
+    from paper_1807_07382_gb300 import PENT_F32_REFINE
+    eps = 1e-12
+    w, c0, target = make_case(batch, n, T)
+    xT_o = oracle.hyperdiff_steps(w.n, w.sigma, w.field0, T).reshape(batch, n)
+    lam = 2.0 * (xT_o - target)
+    c = torch.from_numpy(c0).cuda().requires_grad_(True)
+    s = torch.from_numpy(w.sigma).cuda().requires_grad_(True)
+    x = hyperdiff_steps(c, s, T, checkpoint_every=k, precision=PENT_F32_REFINE, max_refine=2)
+    assert nrel(x.detach().cpu().numpy(), xT_o) <= T * eps
+    x.backward(torch.from_numpy(lam).cuda())
+    vc_o, vs_o = oracle.hyperdiff_vjp(w.sigma, T, c0, lam)
+    assert nrel(c.grad.cpu().numpy(), vc_o) <= 2 * T * eps
+    assert nrel(s.grad.cpu().numpy(), vs_o) <= 2 * T * eps
+    amp = float(np.max(np.abs(xT_o)) / np.max(np.abs(xT_o - target)))
+    _, gc_o, gs_o = oracle.hyperdiff_loss_grad(w.sigma, T, c0, target)
+    c2 = torch.from_numpy(c0).cuda().requires_grad_(True)
+    s2 = torch.from_numpy(w.sigma).cuda().requires_grad_(True)
+    x2 = hyperdiff_steps(c2, s2, T, checkpoint_every=k, precision=PENT_F32_REFINE, max_refine=2)
+    gc, gs = torch.autograd.grad(((x2 - torch.from_numpy(target).cuda()) ** 2).sum(), (c2, s2))
+    print("f32 loss gradient: dC0", nrel(gc.cpu().numpy(), gc_o), "dsigma", nrel(gs.cpu().numpy(), gs_o), "amp", amp)
+    assert nrel(gc.cpu().numpy(), gc_o) <= (amp + 2) * T * eps
+    assert nrel(gs.cpu().numpy(), gs_o) <= (amp + 2) * T * eps
