@@ -106,14 +106,17 @@ __global__ void k_factor64(DevPlan P, const double* __restrict__ a, const double
         report_bad_pivot(P.info, s, r);
         break;
       }
-      const double gamma = (dr - beta * del1) / alpha;
-      const double delta = er / alpha;
-      fwd_at(r, 0) = 1.0 / alpha;
+      // one reciprocal per row, then products (each FP64 division is several operations on the
+      // 1/64-rate FP64 pipe)
+      const double ia = 1.0 / alpha;
+      const double gamma = (dr - beta * del1) * ia;
+      const double delta = er * ia;
+      fwd_at(r, 0) = ia;
       if (hyp) {
         fwd_at(r, 1) = beta;
       } else {
-        fwd_at(r, 1) = beta / alpha;
-        fwd_at(r, 2) = ar / alpha;
+        fwd_at(r, 1) = beta * ia;
+        fwd_at(r, 2) = ar * ia;
       }
       bwd_at(r, 0) = gamma;
       bwd_at(r, 1) = delta;
