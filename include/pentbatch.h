@@ -152,6 +152,15 @@ enum {
                                       the cyclic band; pent_factor_hyperdiff builds Eq. (matrix_sys) with
                                       sigma_x = sigma.  Adjoint, sigma-gradient and ADI calls return
                                       PENT_EINVAL for periodic plans. */
+  PENT_OPT_FP32_KERNEL = 10,       /* PENT_F32_REFINE, not periodic: 0 (the default) solves with at most one
+                                      refinement step and the float-float residual on the interior-constant
+                                      kernel wherever the system's CTA shape allows it (one CTA of 1, 2, 4, 8
+                                      or 16 warps of 8 rows a thread, or one warp of 4): away from the walls
+                                      the FP32 factors of I + sigma D4 settle on one pair of constants, which
+                                      that kernel uses without loading them and whose chunk-map powers the
+                                      factorisation stores; 1 solves every system with the general kernel that
+                                      loads every row's factors.  Any time; results agree to the refinement's
+                                      accuracy, not bit for bit. */
   PENT_OPT_CLUSTER_WARPS = 9       /* PENT_F32_REFINE: systems that need more than 512 threads run in a
                                       thread-block cluster of up to 8 CTAs of exactly this many warps: 8
                                       (the default) or 4, which keep several CTAs resident per SM, or 16
@@ -242,6 +251,12 @@ pent_status pent_host_range_mapped(const void* h, size_t bytes);
  * captured once into a CUDA graph (keyed by x and nsteps) and replayed on
  * later calls; the factors stay resident.  The first call for a given key is
  * therefore not capture-safe; later calls are single graph launches.
+ * PENT_F32_REFINE plans solved by the interior-constant kernel
+ * (PENT_OPT_FP32_KERNEL 0, max_refine <= 1) keep each system's field in x as
+ * a float pair per row (its high and low parts, scaled by a power of two held
+ * in the workspace) between the steps of one call, so that only the first
+ * step converts from FP64 and only the last back: x holds those pairs while
+ * the call runs and FP64 values again once it has completed.
  */
 pent_status pent_solve_steps(pent_plan* plan, double* x, int64_t nsteps, int max_refine);
 

@@ -32,6 +32,7 @@ PENT_OPT_ROWS_PER_THREAD = 6
 PENT_OPT_PARTITION_ROWS = 7
 PENT_OPT_PERIODIC = 8
 PENT_OPT_CLUSTER_WARPS = 9
+PENT_OPT_FP32_KERNEL = 10
 
 # every symbol the header declares, with (restype, argtypes)
 _vp = ctypes.c_void_p

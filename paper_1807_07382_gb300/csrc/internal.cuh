@@ -128,6 +128,19 @@ cudaError_t launch_solve32r(const F32Tables& T, const int32_t* sys, const F32Buc
                             double* x, int max_refine, int residual_f64, int tol_log2, cudaStream_t st,
                             const double* mu = nullptr, const double* nu = nullptr, bool step = false,
                             bool periodic = false);
+// FP32 hyperdiffusion plans, interior-constant kernel (csrc/f32u.cu).  Per factor block a record of
+// kURecFloat4 float4: (1/alpha, beta of the interior, K = first row of the interior, scan levels and
+// flags), then the powers M^(2^l) (l = 0..5) and M^k (k = 0..31) of the forward and of the back
+// chunk map.  kscale: per system, the power of two by which a field kept as float pairs is scaled.
+constexpr int kURecFloat4 = 77;
+cudaError_t launch_uplan32(const F32Tables& T, const int32_t* shape, int64_t nfac, float4* urec, cudaStream_t st);
+// True if the bucket's CTA shape has an instantiation of the interior-constant kernel.
+bool solve32u_supported(const F32Bucket& b);
+// in_ff / out_ff: f / x hold float pairs (h, l) per row scaled by 2^-kscale[s] instead of FP64
+// values (x may alias f); max_refine 0 or 1.
+cudaError_t launch_solve32u(const F32Tables& T, const float4* urec, int32_t* kscale, const int32_t* sys,
+                            const F32Bucket& b, int shared, const double* f, double* x, int max_refine, int in_ff,
+                            int out_ff, cudaStream_t st);
 // Periodic FP32 plans: factors of E, the columns of Z = E^{-1} k and S^{-1} (k_factor32_periodic).
 cudaError_t launch_factor32_periodic(const F32Tables& T, const int32_t* shape, int64_t nsys, const double* sigma,
                                      cudaStream_t st);

@@ -99,6 +99,7 @@ struct pent_plan {
   std::vector<F32Bucket> buckets;
   int64_t tps_override = 0;       // PENT_OPT_THREADS_PER_SYSTEM for FP32 (0: automatic)
   int cluster_warps = 8;          // PENT_OPT_CLUSTER_WARPS
+  int f32_kernel = 0;             // PENT_OPT_FP32_KERNEL: 0 interior-constant kernel where it applies, 1 general
   std::vector<cudaStream_t> side; // extra streams so that bucket launches overlap
   std::vector<cudaEvent_t> ev;    // fork/join events
   std::vector<cudaStream_t> pipe; // slices of pent_solve_host_batch (copy in, solve, copy out)
@@ -107,7 +108,7 @@ struct pent_plan {
   // workspace regions
   Region r_info, r_perm, r_off, r_n, r_goff, r_glen, r_sigma, r_fwd, r_bwd, r_scr, r_fac32, r_sig32, r_foff, r_shape,
       r_sys32, r_adi, r_cmap, r_swU, r_swE, r_pck, r_pcc, r_pcbase, r_pcnum, r_pcmap, r_pU, r_pE, r_per, r_psinv,
-      r_pg, r_rhs, r_psinv32;
+      r_pg, r_rhs, r_psinv32, r_urec, r_kscale;
   size_t ws_bytes = 0;
   // binding / state
   unsigned char* ws = nullptr;
@@ -450,6 +451,10 @@ void layout(pent_plan* p) {
     take(p->r_shape, (size_t)nfac * sizeof(int32_t));
     take(p->r_sys32, (size_t)p->batch * sizeof(int32_t));
     if (p->periodic) take(p->r_psinv32, (size_t)nfac * 4 * sizeof(float));
+    if (!p->periodic) {  // interior-constant kernel: per factor block record, per system field scale
+      take(p->r_urec, (size_t)nfac * kURecFloat4 * sizeof(float4));
+      take(p->r_kscale, (size_t)p->batch * sizeof(int32_t));
+    }
   }
   // ADI scratch, for shared-matrix plans whose batch is the number of columns of
   // a sweep: a full field (rows doubles), the partial sums of the sweep
@@ -704,6 +709,8 @@ pent_status pent_plan_set_option(pent_plan* p, int key, int64_t value) {
     case PENT_OPT_RESIDUAL:
       if (value != PENT_RESIDUAL_FF && value != PENT_RESIDUAL_F64) return PENT_EINVAL;
       p->residual = (int)value;
+      ++p->cfg_version;  // the kernels a step graph launches depend on it
+      p->drop_graphs();
       return PENT_OK;
     case PENT_OPT_BLOCK_WARPS:
       if (value < 1 || value > 8) return PENT_EINVAL;
@@ -718,6 +725,12 @@ pent_status pent_plan_set_option(pent_plan* p, int key, int64_t value) {
       p->unroll = (int)value;
       p->f64_explicit = true;
       build_f64_runs(p);
+      ++p->cfg_version;
+      p->drop_graphs();
+      return PENT_OK;
+    case PENT_OPT_FP32_KERNEL:
+      if (p->precision != PENT_F32_REFINE || (value != 0 && value != 1)) return PENT_EINVAL;
+      p->f32_kernel = (int)value;
       ++p->cfg_version;
       p->drop_graphs();
       return PENT_OK;
@@ -743,6 +756,7 @@ pent_status pent_plan_get_option(const pent_plan* p, int key, int64_t* value) {
     case PENT_OPT_PARTITION_ROWS: *value = p->part_rows; return PENT_OK;
     case PENT_OPT_PERIODIC: *value = p->periodic ? 1 : 0; return PENT_OK;
     case PENT_OPT_CLUSTER_WARPS: *value = p->cluster_warps; return PENT_OK;
+    case PENT_OPT_FP32_KERNEL: *value = p->f32_kernel; return PENT_OK;
   }
   return PENT_EINVAL;
 }
@@ -813,8 +827,12 @@ static pent_status factor_common(pent_plan* p, const double* a, const double* b,
   }
   else if (p->periodic)
     err = launch_factor32_periodic(p->f32(), p->at<int32_t>(p->r_shape), p->shared ? 1 : p->batch, sg, p->stream);
-  else
+  else {
     err = launch_factor32(p->f32(), p->at<int32_t>(p->r_shape), p->shared ? 1 : p->batch, sg, p->stream);
+    if (err == cudaSuccess)
+      err = launch_uplan32(p->f32(), p->at<int32_t>(p->r_shape), p->shared ? 1 : p->batch, p->at<float4>(p->r_urec),
+                           p->stream);
+  }
   if (err != cudaSuccess) return PENT_ECUDA;
   p->factored = sigma ? 2 : 1;
   return PENT_OK;
@@ -834,7 +852,28 @@ pent_status pent_factor_hyperdiff(pent_plan* p, const double* d_sigma) {
   return factor_common(p, nullptr, nullptr, nullptr, nullptr, nullptr, d_sigma);
 }
 
-static pent_status solve_launch(pent_plan* p, const double* f, double* x, int max_refine) {
+// True if bucket b of an FP32 plan is solved by the interior-constant kernel (csrc/f32u.cu).
+static bool use_u(const pent_plan* p, const F32Bucket& b, int max_refine) {
+  return p->precision == PENT_F32_REFINE && !p->periodic && p->residual == PENT_RESIDUAL_FF && p->f32_kernel == 0 &&
+         max_refine <= 1 && solve32u_supported(b);
+}
+
+// One FP32 solve of bucket b (systems [b.first, b.first + b.count) of the bucket order).  in_ff /
+// out_ff: f / x of the bucket's systems hold scaled float pairs (interior-constant kernel only).
+static cudaError_t f32_bucket(pent_plan* p, const F32Bucket& b, const double* f, double* x, int max_refine, int in_ff,
+                              int out_ff, cudaStream_t st) {
+  const F32Tables T = p->f32();
+  const int32_t* sys = p->at<int32_t>(p->r_sys32);
+  if (use_u(p, b, max_refine))
+    return launch_solve32u(T, p->at<float4>(p->r_urec), p->at<int32_t>(p->r_kscale), sys, b, p->shared, f, x,
+                           max_refine, in_ff, out_ff, st);
+  if (in_ff || out_ff) return cudaErrorInvalidValue;
+  return launch_solve32r(T, sys, b, p->shared, f, x, max_refine, p->residual == PENT_RESIDUAL_F64, p->tol_log2, st,
+                         nullptr, nullptr, false, p->periodic);
+}
+
+static pent_status solve_launch(pent_plan* p, const double* f, double* x, int max_refine, int in_ff = 0,
+                                int out_ff = 0) {
   cudaError_t err;
   if (p->periodic && p->precision == PENT_F64) {
     err = launch_solve_periodic(p->per(), f, x, nullptr, nullptr, false, p->stream);
@@ -849,13 +888,11 @@ static pent_status solve_launch(pent_plan* p, const double* f, double* x, int ma
       return launch_solve64(P, F, f, x, gscr, r.bw, r.unroll, r.g0, r.g1, st);
     });
   } else {
-    const F32Tables T = p->f32();
-    const int32_t* sys = p->at<int32_t>(p->r_sys32);
-    const int rf = p->residual == PENT_RESIDUAL_F64;
-    if (p->periodic && rf) return PENT_EINVAL;  // periodic FP32 plans refine against the float-float residual
+    if (p->periodic && p->residual == PENT_RESIDUAL_F64) return PENT_EINVAL;  // periodic: float-float residual
     err = fork_join(p, p->buckets.size(), [&](size_t i, cudaStream_t st) {
-      return launch_solve32r(T, sys, p->buckets[i], p->shared, f, x, max_refine, rf, p->tol_log2, st, nullptr,
-                             nullptr, false, p->periodic);
+      const F32Bucket& b = p->buckets[i];
+      const bool u = use_u(p, b, max_refine);
+      return f32_bucket(p, b, f, x, max_refine, u && in_ff, u && out_ff, st);
     });
   }
   return cuda_status(err);
@@ -1009,8 +1046,7 @@ pent_status pent_solve_host_batch(pent_plan* p, const double* h_f, double* h_x, 
       F32Bucket b = p->buckets[0];
       b.first += s0;
       b.count = s1 - s0;
-      e = launch_solve32r(p->f32(), p->at<int32_t>(p->r_sys32), b, p->shared, d_f, d_x, max_refine,
-                          p->residual == PENT_RESIDUAL_F64, p->tol_log2, ss);
+      e = f32_bucket(p, b, d_f, d_x, max_refine, 0, 0, ss);
     } else {
       const auto& r = p->runs[0];
       e = launch_solve64(p->dev(), p->f64(), d_f, d_x, p->at<double>(p->r_scr), r.bw, r.unroll, u0, u1, ss);
@@ -1033,7 +1069,14 @@ pent_status pent_solve_steps(pent_plan* p, double* x, int64_t nsteps, int max_re
   if (nsteps < 0) return PENT_EINVAL;
   if (nsteps == 0) return PENT_OK;
   const auto key = std::make_tuple((const void*)x, nsteps, max_refine, p->cfg_version);
-  return run_steps(p, key, nsteps, [&]() { return solve_launch(p, x, x, max_refine); });
+  // FP32 plans on the interior-constant kernel keep the field as scaled float pairs between steps:
+  // the first step reads FP64, the last writes FP64
+  int64_t k = 0;
+  return run_steps(p, key, nsteps, [&]() {
+    const int in_ff = k > 0, out_ff = k + 1 < nsteps;
+    ++k;
+    return solve_launch(p, x, x, max_refine, in_ff, out_ff);
+  });
 }
 
 // One pent_step_batch step on a no-flux FP64 plan: the fused right-hand side

@@ -119,9 +119,8 @@ def test_periodic_option_host_checks(L):
     L.pent_plan_destroy(h)
     # FP32+refine periodic plans keep four FP32 planes per row (1/alpha, beta and the two columns of Z)
     st, h = _create(L, batch=4, n_uniform=64, prec=1)
-    base32 = L.pent_plan_workspace_bytes(h)
     assert L.pent_plan_set_option(h, _lib.PENT_OPT_PERIODIC, 1) == 0
-    assert L.pent_plan_workspace_bytes(h) >= base32 + 4 * 64 * 2 * 4
+    assert L.pent_plan_workspace_bytes(h) >= 4 * 64 * 4 * 4  # systems x rows x planes x 4 B
     L.pent_plan_destroy(h)
     st, h = _create(L, batch=2, n=[64, 65])
     assert L.pent_plan_set_option(h, _lib.PENT_OPT_PERIODIC, 1) == _lib.PENT_EINVAL
@@ -186,3 +185,19 @@ def test_f32_refine_length_limit(L):
         st, h = _create(L, batch=1, n=[n])
         assert st == 0
         L.pent_plan_destroy(h)
+
+
+def test_fp32_kernel_option(L):
+    """PENT_OPT_FP32_KERNEL: 0 (interior-constant kernel where it applies) or 1 (general
+    kernel), FP32 plans only; settable at any time, readable back."""
+    st, h = _create(L, batch=4, n_uniform=64, prec=1)
+    assert st == 0
+    v = ctypes.c_int64()
+    assert L.pent_plan_get_option(h, _lib.PENT_OPT_FP32_KERNEL, ctypes.byref(v)) == 0 and v.value == 0
+    assert L.pent_plan_set_option(h, _lib.PENT_OPT_FP32_KERNEL, 2) == _lib.PENT_EINVAL
+    assert L.pent_plan_set_option(h, _lib.PENT_OPT_FP32_KERNEL, 1) == 0
+    assert L.pent_plan_get_option(h, _lib.PENT_OPT_FP32_KERNEL, ctypes.byref(v)) == 0 and v.value == 1
+    L.pent_plan_destroy(h)
+    st, h = _create(L, batch=4, n_uniform=64, prec=0)
+    assert L.pent_plan_set_option(h, _lib.PENT_OPT_FP32_KERNEL, 1) == _lib.PENT_EINVAL  # FP64 plan
+    L.pent_plan_destroy(h)
