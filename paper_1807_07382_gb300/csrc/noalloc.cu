@@ -31,24 +31,57 @@ constexpr int kMaxDevices = 64;
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[kMaxDevices] = {};
+struct ScratchAddr {
+  void* ctx = nullptr;  // the context the address belongs to
+  void* ptr = nullptr;
+};
+ScratchAddr g_noalloc_addr[kMaxDevices];
 
-// Device address of the scratch array for the current device.  In host code
-// g_noalloc_scratch names a host-side shadow, not device memory, so the
-// address comes from cudaGetSymbolAddress, once per device.
-cudaError_t noalloc_scratch(void** out) {
+// The current context (driver entry point through the runtime: the library links no
+// driver library), or nullptr if the query is unavailable.
+void* current_context() {
+  using GetCtx = int (*)(void**);
+  static const GetCtx get = []() -> GetCtx {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<GetCtx>(fn);
+  }();
+  void* ctx = nullptr;
+  if (!get || get(&ctx) != 0) return nullptr;
+  return ctx;
+}
+
+// Device address of the scratch array in the current context.  In host code
+// g_noalloc_scratch names a host-side shadow, not device memory, so the address
+// comes from cudaGetSymbolAddress.  It is looked up again on every call whose
+// stream is not being captured (a context that was torn down and created again
+// loads the module afresh, possibly elsewhere); during a capture the address
+// found by an earlier call in the same context is used, and a capture with no
+// such call fails with an error instead of using a stale address.
+cudaError_t noalloc_scratch(cudaStream_t st, void** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(st, &cs);
+  if (e != cudaSuccess) return e;
+  void* ctx = current_context();
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
+  ScratchAddr& c = g_noalloc_addr[dev];
+  if (cs == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    g_noalloc_ptr[dev] = p;
+    c.ctx = ctx;
+    c.ptr = p;
+  } else if (!c.ptr || !ctx || c.ctx != ctx) {
+    return cudaErrorStreamCaptureUnsupported;
   }
-  *out = g_noalloc_ptr[dev];
+  *out = c.ptr;
   return cudaSuccess;
 }
 
@@ -125,9 +158,9 @@ extern "C" pent_status pent_gbsv_batch_noalloc(int64_t batch, int64_t n, const d
   if (n > (int64_t)(kNoAllocScratchBytes / (3 * kWarp * sizeof(double))) ||
       groups > (int64_t)(kNoAllocScratchBytes / (3 * kWarp * sizeof(double))) / n)
     return PENT_EINVAL;  // beyond the fixed scratch: ceil(batch/32) * 32 * n * 24 bytes must fit in 32 MiB
-  void* scratch = nullptr;
-  if (noalloc_scratch(&scratch) != cudaSuccess) return PENT_ECUDA;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  void* scratch = nullptr;
+  if (noalloc_scratch(st, &scratch) != cudaSuccess) return PENT_ECUDA;
   if (d_info && cudaMemsetAsync(d_info, 0x7f, sizeof(unsigned long long), st) != cudaSuccess) return PENT_ECUDA;
   const int block = 128;
   const int64_t grid = (batch + block - 1) / block;
