@@ -120,6 +120,12 @@ pent_status pent_plan_bind(pent_plan* plan, void* d_workspace, void* cuda_stream
  * and the workspace size, so it is accepted only before pent_plan_bind (query
  * pent_plan_workspace_bytes after setting it).
  */
+/* pent_solve_steps, pent_step_batch and adi_steps_2d keep the CUDA graphs they capture,
+ * keyed by the field pointer, the step count and the settings, at most this many per plan;
+ * beyond it the least recently launched graph is destroyed (one still running is freed
+ * by the runtime when it completes) and a later call with its key captures it anew. */
+#define PENT_MAX_CACHED_GRAPHS 16
+
 enum {
   PENT_OPT_THREADS_PER_SYSTEM = 1, /* PENT_F64: 1 (one thread per system).  PENT_F32_REFINE: threads per
                                       system, 32 W with W <= 16 (one CTA) or 512 C with C <= 8 (a cluster of C
@@ -152,6 +158,8 @@ enum {
                                       the cyclic band; pent_factor_hyperdiff builds Eq. (matrix_sys) with
                                       sigma_x = sigma.  Adjoint, sigma-gradient and ADI calls return
                                       PENT_EINVAL for periodic plans. */
+  PENT_OPT_CACHED_GRAPHS = 11,     /* read only (pent_plan_get_option): step graphs the plan holds now, at
+                                      most PENT_MAX_CACHED_GRAPHS */
   PENT_OPT_FP32_KERNEL = 10,       /* PENT_F32_REFINE, not periodic: 0 (the default) solves with at most one
                                       refinement step and the float-float residual on the interior-constant
                                       kernel wherever the system's CTA shape allows it (one CTA of 1, 2, 4, 8
@@ -334,18 +342,32 @@ pent_status pent_hyperdiff_sigma_grad(pent_plan* plan, const double* mu, const d
  * the Douglas delta form of its semi-implicit step (Sec. 2.1).  Exact dC has
  * zero mean; removing the mean of the computed dC keeps the total mass to
  * rounding of C itself.
- * px: a PENT_F64 shared-matrix plan of ny systems of n = nx, factored by
- *     pent_factor_hyperdiff with the same sigma; it also holds the step's
- *     scratch (two fields and one accumulator).
- * py: a PENT_F64 shared-matrix plan of nx systems of n = ny, factored likewise.
- * Both must be bound to the same stream.  max_refine must be 0: the sweeps run
+ * px: a PENT_F64 shared-matrix plan of ny systems of n = nx; it also holds
+ *     the step's scratch (two fields and one accumulator).
+ * py: a PENT_F64 shared-matrix plan of nx systems of n = ny.
+ * Both must be bound to the same stream and factored by adi_plans_factor for
+ * exactly this (gamma, dt, dx): the explicit part and the two sweeps then use
+ * one sigma, and any other (gamma, dt, dx), or plans factored otherwise or
+ * since, return PENT_EINVAL before anything is launched.  max_refine must be 0: the sweeps run
  * in FP64 (at sigma ~ 1e5 the FP32 factorisation would contract the error by
  * only ~0.2 per refinement step, and the field stays in L2, so there are no
  * HBM bytes for FP32 streaming to save).  Errors: PENT_EINVAL for mismatched
- * shapes or plans, PENT_ENOTFACTORED if either plan is not factored from sigma.
+ * shapes, plans or parameters, PENT_ENOTFACTORED if either plan is not factored.
  */
 pent_status adi_step_2d(pent_plan* px, pent_plan* py, double* C, int64_t nx, int64_t ny, double gamma, double dt,
                         double dx, int max_refine);
+
+/*
+ * Factor the two plans of an ADI step for (gamma, dt, dx): both take
+ * A = I + sigma D4 with sigma = gamma dt / dx^4 (Sec. 2.1, the coefficient of
+ * the implicit fourth-order term; D4 as in pent_factor_hyperdiff), computed
+ * here once, and remember the three parameters for adi_step_2d / adi_steps_2d.
+ * px, py as for adi_step_2d (shapes checked against each other: px has
+ * py's n systems of py's batch rows).  Asynchronous and capture-safe (sigma
+ * reaches the device as a kernel argument).  PENT_EINVAL for non-positive or
+ * non-finite parameters or mismatched plans.
+ */
+pent_status adi_plans_factor(pent_plan* px, pent_plan* py, double gamma, double dt, double dx);
 
 /* `nsteps` ADI steps, captured once into a CUDA graph and replayed. */
 pent_status adi_steps_2d(pent_plan* px, pent_plan* py, double* C, int64_t nx, int64_t ny, double gamma, double dt,
@@ -374,10 +396,13 @@ pent_status pent_clear_info(pent_plan* plan);
  * (system << 32 | row) of a zero or non-finite pivot, or 0x7f7f7f7f7f7f7f7f.
  * Scratch: a fixed 32 MiB array owned by the library in every device's
  * memory, held from the moment a device loads the library until the process
- * exits; ceil(batch/32) * 32 * n * 24 bytes must fit in it (for example 1,365
- * systems of 1,024 rows), otherwise PENT_EINVAL and nothing is launched.  The
- * first call on each device looks up the array's device address; make that
- * first call before any stream capture.  Every call uses the same array, so
+ * exits; ceil(batch/32) * 32 * n * 24 bytes must fit in it (at most 1,344
+ * systems of 1,024 rows: 42 warps of 32), otherwise PENT_EINVAL and nothing is
+ * launched.  Every call whose stream is not being captured looks up the
+ * array's device address in the current context; a call during a capture uses
+ * the address an earlier call found in the same context, so make one call
+ * before any stream capture (a capture without one returns PENT_ECUDA).  Every
+ * call uses the same array, so
  * calls whose kernels may overlap on the GPU (unordered streams) race; order
  * them on one stream.  Asynchronous on cuda_stream; no cudaMalloc, cudaFree
  * or other allocating call is made.

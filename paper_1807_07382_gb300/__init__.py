@@ -24,7 +24,7 @@ from ._lib import (PENT_ENOCONV, PENT_ESINGULAR, PENT_F32_REFINE, PENT_F64, PENT
                    PENT_RESIDUAL_FF, PentError, check)
 
 __all__ = ["Plan", "PentError", "PENT_F64", "PENT_F32_REFINE", "PENT_RESIDUAL_FF", "PENT_RESIDUAL_F64",
-           "library_path", "load_library", "adi_step_2d", "adi_steps_2d", "ADI2D"]
+           "library_path", "load_library", "adi_plans_factor", "adi_step_2d", "adi_steps_2d", "ADI2D"]
 
 __version__ = "0.1.0"
 
@@ -267,6 +267,11 @@ def adi_step_2d(px: Plan, py: Plan, C, gamma: float, dt: float, dx: float, max_r
     return C
 
 
+def adi_plans_factor(px: Plan, py: Plan, gamma: float, dt: float, dx: float):
+    """Factor both plans of an ADI step for (gamma, dt, dx) (see adi_step_2d)."""
+    check(_lib.load().adi_plans_factor(px._h, py._h, float(gamma), float(dt), float(dx)), "adi_plans_factor")
+
+
 def adi_steps_2d(px: Plan, py: Plan, C, gamma: float, dt: float, dx: float, nsteps: int, max_refine: int = 0):
     torch = _torch()
     ny, nx = C.shape
@@ -278,22 +283,18 @@ def adi_steps_2d(px: Plan, py: Plan, C, gamma: float, dt: float, dx: float, nste
 class ADI2D:
     """Alternating-direction Cahn-Hilliard stepper on an ny x nx no-flux grid.
 
-    Builds and factors the two shared matrices I + sigma D4 (n = nx for the
-    row sweeps, n = ny for the column sweeps), sigma = gamma dt / dx^4, once;
-    `step` advances a device field C (ny x nx, float64, in place).
+    Two shared-matrix plans (n = nx for the row sweeps, n = ny for the column
+    sweeps), factored once by adi_plans_factor for (gamma, dt, dx), which also
+    derives the scheme's coefficients; `step` advances a device field C
+    (ny x nx, float64, in place).
     """
 
     def __init__(self, nx: int, ny: int, gamma: float, dt: float, dx: float, device=None, stream=None):
-        torch = _torch()
         self.nx, self.ny = int(nx), int(ny)
         self.gamma, self.dt, self.dx = float(gamma), float(dt), float(dx)
-        self.sigma = self.gamma * self.dt / self.dx ** 4
-        self.mu = self.dt / self.dx ** 2
         self.px = Plan(self.nx, batch=self.ny, shared=True, device=device, stream=stream)
         self.py = Plan(self.ny, batch=self.nx, shared=True, device=self.px.device, stream=self.px.stream)
-        sig = torch.full((1,), self.sigma, dtype=torch.float64, device=self.px.device)
-        self.px.factor_hyperdiff(sig)
-        self.py.factor_hyperdiff(sig)
+        check(_lib.load().adi_plans_factor(self.px._h, self.py._h, self.gamma, self.dt, self.dx), "adi_plans_factor")
 
     def step(self, C, nsteps: int = 1):
         if tuple(C.shape) != (self.ny, self.nx):

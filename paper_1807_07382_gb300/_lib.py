@@ -33,6 +33,8 @@ PENT_OPT_PARTITION_ROWS = 7
 PENT_OPT_PERIODIC = 8
 PENT_OPT_CLUSTER_WARPS = 9
 PENT_OPT_FP32_KERNEL = 10
+PENT_OPT_CACHED_GRAPHS = 11
+PENT_MAX_CACHED_GRAPHS = 16
 
 # every symbol the header declares, with (restype, argtypes)
 _vp = ctypes.c_void_p
@@ -60,6 +62,7 @@ SIGNATURES = {
     "pent_adjoint_solve_batch": (_int, [_vp, _vp, _vp, _int]),
     "pent_hyperdiff_sigma_grad": (_int, [_vp, _vp, _vp, _vp]),
     "adi_step_2d": (_int, [_vp, _vp, _vp, _i64, _i64, _dbl, _dbl, _dbl, _int]),
+    "adi_plans_factor": (_int, [_vp, _vp, _dbl, _dbl, _dbl]),
     "adi_steps_2d": (_int, [_vp, _vp, _vp, _i64, _i64, _dbl, _dbl, _dbl, _int, _i64]),
     "pent_get_info": (_int, [_vp, _i64p, _i64p, _intp]),
     "pent_clear_info": (_int, [_vp]),

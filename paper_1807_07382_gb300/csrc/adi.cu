@@ -327,4 +327,16 @@ cudaError_t launch_adi_step(const AdiArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// dst[0 .. count) = v (a kernel argument: asynchronous and capture-safe, unlike a copy from host memory).
+__global__ void k_fill(double* dst, double v, int64_t count) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < count) dst[i] = v;
+}
+
+cudaError_t launch_fill(double* dst, double v, int64_t count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  k_fill<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(dst, v, count);
+  return cudaGetLastError();
+}
+
 }  // namespace pent

@@ -175,6 +175,8 @@ struct AdiArgs {
   SweepArgs sy;  // y sweep: n = ny, nx columns
 };
 cudaError_t launch_adi_step(const AdiArgs& a, cudaStream_t st);
+// dst[0 .. count) = v on stream st.
+cudaError_t launch_fill(double* dst, double v, int64_t count, cudaStream_t st);
 // Chunk maps of a shared FP64 factorisation with n rows (once per factorisation).
 cudaError_t launch_chunk_maps(F64Factors F, int n, double* cmap, cudaStream_t st);
 

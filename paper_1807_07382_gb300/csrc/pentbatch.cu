@@ -115,8 +115,35 @@ struct pent_plan {
   cudaStream_t stream = nullptr;
   bool bound = false;
   int factored = 0;  // 0 none, 1 general band, 2 hyperdiffusion
-  // graph cache: (x, nsteps, max_refine, settings version) -> exec
-  std::map<std::tuple<const void*, int64_t, int, int64_t>, cudaGraphExec_t> graphs;
+  // step-graph cache: (x, nsteps, max_refine, settings version) -> exec, at most kMaxGraphs
+  // entries; the least recently launched is destroyed to make room (an exec still running
+  // is freed by the runtime once it completes)
+  using GraphKey = std::tuple<const void*, int64_t, int, int64_t>;
+  struct GraphEntry {
+    cudaGraphExec_t exec;
+    uint64_t used;
+  };
+  std::map<GraphKey, GraphEntry> graphs;
+  uint64_t graph_clock = 0;
+  // ADI: the parameters this (shared-matrix) plan was factored for by adi_plans_factor
+  bool adi_ready = false;
+  double adi_gamma = 0.0, adi_dt = 0.0, adi_dx = 0.0, adi_sigma = 0.0;
+  cudaGraphExec_t find_graph(const GraphKey& k) {
+    auto it = graphs.find(k);
+    if (it == graphs.end()) return nullptr;
+    it->second.used = ++graph_clock;
+    return it->second.exec;
+  }
+  void add_graph(const GraphKey& k, cudaGraphExec_t exec) {
+    while (graphs.size() >= (size_t)PENT_MAX_CACHED_GRAPHS) {
+      auto lru = graphs.begin();
+      for (auto it = graphs.begin(); it != graphs.end(); ++it)
+        if (it->second.used < lru->second.used) lru = it;
+      cudaGraphExecDestroy(lru->second.exec);
+      graphs.erase(lru);
+    }
+    graphs[k] = GraphEntry{exec, ++graph_clock};
+  }
 
   template <class T>
   T* at(const Region& r) const {
@@ -179,7 +206,7 @@ struct pent_plan {
     return T;
   }
   void drop_graphs() {
-    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second.exec);
     graphs.clear();
   }
   void drop_streams() {
@@ -757,6 +784,7 @@ pent_status pent_plan_get_option(const pent_plan* p, int key, int64_t* value) {
     case PENT_OPT_PERIODIC: *value = p->periodic ? 1 : 0; return PENT_OK;
     case PENT_OPT_CLUSTER_WARPS: *value = p->cluster_warps; return PENT_OK;
     case PENT_OPT_FP32_KERNEL: *value = p->f32_kernel; return PENT_OK;
+    case PENT_OPT_CACHED_GRAPHS: *value = (int64_t)p->graphs.size(); return PENT_OK;
   }
   return PENT_EINVAL;
 }
@@ -803,11 +831,12 @@ static pent_status factor_common(pent_plan* p, const double* a, const double* b,
   if (!p) return PENT_EINVAL;
   if (!p->bound) return PENT_ENOTBOUND;
   p->drop_graphs();
+  p->adi_ready = false;
   pent_status st = reset_info(p);
   if (st != PENT_OK) return st;
   const DevPlan P = p->dev();
   const int64_t nsig = p->shared ? 1 : p->batch;
-  if (sigma) {
+  if (sigma && sigma != p->at<double>(p->r_sigma)) {
     cudaError_t err = cudaMemcpyAsync(p->at<double>(p->r_sigma), sigma, (size_t)nsig * sizeof(double),
                                       cudaMemcpyDeviceToDevice, p->stream);
     if (err != cudaSuccess) return PENT_ECUDA;
@@ -911,8 +940,8 @@ static pent_status run_steps(pent_plan* p, const std::tuple<const void*, int64_t
     for (int64_t k = 0; k < nsteps && st == PENT_OK; ++k) st = launch();
     return st;
   }
-  auto it = p->graphs.find(key);
-  if (it == p->graphs.end()) {
+  cudaGraphExec_t exec = p->find_graph(key);
+  if (!exec) {
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return PENT_ECUDA;
     for (int64_t k = 0; k < nsteps && st == PENT_OK; ++k) st = launch();
@@ -921,13 +950,12 @@ static pent_status run_steps(pent_plan* p, const std::tuple<const void*, int64_t
       if (g) cudaGraphDestroy(g);
       return st != PENT_OK ? st : PENT_ECUDA;
     }
-    cudaGraphExec_t exec = nullptr;
     e = cudaGraphInstantiate(&exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return PENT_ECUDA;
-    it = p->graphs.emplace(key, exec).first;
+    p->add_graph(key, exec);
   }
-  return cuda_status(cudaGraphLaunch(it->second, p->stream));
+  return cuda_status(cudaGraphLaunch(exec, p->stream));
 }
 
 extern "C" {
@@ -1225,6 +1253,10 @@ static pent_status adi_check(pent_plan* px, pent_plan* py, double* C, int64_t nx
   if (px->batch != ny || px->n_uniform != nx || py->batch != nx || py->n_uniform != ny) return PENT_EINVAL;
   if (px->stream != py->stream) return PENT_EINVAL;
   if (((uintptr_t)C) % sizeof(double)) return PENT_EINVAL;
+  // the step's explicit part and its sweeps must use one scheme: both plans factored by
+  // adi_plans_factor for exactly these (gamma, dt, dx)
+  for (const pent_plan* q : {px, py})
+    if (!q->adi_ready || q->adi_gamma != gamma || q->adi_dt != dt || q->adi_dx != dx) return PENT_EINVAL;
   return PENT_OK;
 }
 
@@ -1240,10 +1272,36 @@ static pent_status adi_launch(pent_plan* px, pent_plan* py, double* C, int64_t n
   a.nx = (int)nx;
   a.ny = (int)ny;
   a.mu = dt / (dx * dx);
-  a.sigma = gamma * dt / (dx * dx * dx * dx);
+  a.sigma = px->adi_sigma;  // the sigma both plans were factored with
   a.sx = SweepArgs{px->f64(), px->at<double>(px->r_cmap), px->at<double2>(px->r_swU), px->at<double2>(px->r_swE)};
   a.sy = SweepArgs{py->f64(), py->at<double>(py->r_cmap), py->at<double2>(py->r_swU), py->at<double2>(py->r_swE)};
   return cuda_status(launch_adi_step(a, px->stream));
+}
+
+pent_status adi_plans_factor(pent_plan* px, pent_plan* py, double gamma, double dt, double dx) {
+  const Range range("adi_plans_factor");
+  if (!px || !py || px == py) return PENT_EINVAL;
+  if (!(gamma > 0.0) || !(dt > 0.0) || !(dx > 0.0)) return PENT_EINVAL;
+  for (const pent_plan* q : {px, py}) {
+    if (!q->bound) return PENT_ENOTBOUND;
+    if (q->precision != PENT_F64 || !q->shared || q->periodic) return PENT_EINVAL;
+  }
+  if (px->batch != py->n_uniform || py->batch != px->n_uniform || px->stream != py->stream) return PENT_EINVAL;
+  const double sigma = gamma * dt / (dx * dx * dx * dx);  // Sec. 2.1: the fourth-order term's coefficient
+  if (!std::isfinite(sigma) || !(sigma > 0.0)) return PENT_EINVAL;
+  for (pent_plan* q : {px, py}) {
+    // sigma into the plan's own slot by a kernel argument (asynchronous, capture-safe), then factor from it
+    double* slot = q->at<double>(q->r_sigma);
+    if (launch_fill(slot, sigma, 1, q->stream) != cudaSuccess) return PENT_ECUDA;
+    const pent_status st = factor_common(q, nullptr, nullptr, nullptr, nullptr, nullptr, slot);
+    if (st != PENT_OK) return st;
+    q->adi_ready = true;
+    q->adi_gamma = gamma;
+    q->adi_dt = dt;
+    q->adi_dx = dx;
+    q->adi_sigma = sigma;
+  }
+  return PENT_OK;
 }
 
 pent_status adi_step_2d(pent_plan* px, pent_plan* py, double* C, int64_t nx, int64_t ny, double gamma, double dt,
@@ -1274,8 +1332,8 @@ pent_status adi_steps_2d(pent_plan* px, pent_plan* py, double* C, int64_t nx, in
   }
   h ^= (uint64_t)(uintptr_t)py;
   const auto key = std::make_tuple((const void*)C, nsteps, -1, (int64_t)(h & 0x7fffffffffffffffull));
-  auto it = px->graphs.find(key);
-  if (it == px->graphs.end()) {
+  cudaGraphExec_t exec = px->find_graph(key);
+  if (!exec) {
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(px->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return PENT_ECUDA;
     for (int64_t k = 0; k < nsteps && st == PENT_OK; ++k) st = adi_launch(px, py, C, nx, ny, gamma, dt, dx);
@@ -1284,13 +1342,12 @@ pent_status adi_steps_2d(pent_plan* px, pent_plan* py, double* C, int64_t nx, in
       if (g) cudaGraphDestroy(g);
       return st != PENT_OK ? st : PENT_ECUDA;
     }
-    cudaGraphExec_t exec = nullptr;
     e = cudaGraphInstantiate(&exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return PENT_ECUDA;
-    it = px->graphs.emplace(key, exec).first;
+    px->add_graph(key, exec);
   }
-  return cuda_status(cudaGraphLaunch(it->second, px->stream));
+  return cuda_status(cudaGraphLaunch(exec, px->stream));
 }
 
 }  // extern "C"

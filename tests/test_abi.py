@@ -201,3 +201,19 @@ def test_fp32_kernel_option(L):
     st, h = _create(L, batch=4, n_uniform=64, prec=0)
     assert L.pent_plan_set_option(h, _lib.PENT_OPT_FP32_KERNEL, 1) == _lib.PENT_EINVAL  # FP64 plan
     L.pent_plan_destroy(h)
+
+
+def test_adi_plans_factor_and_graph_cache_query_check_arguments_on_the_host(L):
+    st, px = _create(L, batch=8, n_uniform=16, shared=1)
+    st2, py = _create(L, batch=16, n_uniform=8, shared=1)
+    assert st == 0 and st2 == 0
+    assert L.adi_plans_factor(None, py, 0.01, 1e-6, 1 / 16) == _lib.PENT_EINVAL
+    assert L.adi_plans_factor(px, px, 0.01, 1e-6, 1 / 16) == _lib.PENT_EINVAL
+    assert L.adi_plans_factor(px, py, -0.01, 1e-6, 1 / 16) == _lib.PENT_EINVAL
+    assert L.adi_plans_factor(px, py, 0.01, 0.0, 1 / 16) == _lib.PENT_EINVAL
+    assert L.adi_plans_factor(px, py, 0.01, 1e-6, 1 / 16) == _lib.PENT_ENOTBOUND  # nothing launched
+    v = ctypes.c_int64(-1)
+    assert L.pent_plan_get_option(px, _lib.PENT_OPT_CACHED_GRAPHS, ctypes.byref(v)) == 0 and v.value == 0
+    assert L.pent_plan_set_option(px, _lib.PENT_OPT_CACHED_GRAPHS, 3) == _lib.PENT_EINVAL  # read only
+    L.pent_plan_destroy(px)
+    L.pent_plan_destroy(py)

@@ -116,10 +116,39 @@ def test_adi_rejects_bad_plans():
     C = torch.zeros(8, 16, dtype=torch.float64, device="cuda")
     with pytest.raises(pb.PentError):
         pb.adi_step_2d(px, py, C, 0.01, 1e-6, 1 / 16)       # not factored
-    sig = torch.ones(1, dtype=torch.float64, device="cuda")
-    px.factor_hyperdiff(sig)
-    py.factor_hyperdiff(sig)
+    pb.adi_plans_factor(px, py, 0.01, 1e-6, 1 / 16)
     with pytest.raises(pb.PentError):
         pb.adi_step_2d(py, px, C, 0.01, 1e-6, 1 / 16)       # swapped plans
     with pytest.raises(pb.PentError):
         pb.adi_step_2d(px, py, C, 0.01, 1e-6, 1 / 16, max_refine=1)
+
+
+def test_adi_refuses_parameters_the_plans_were_not_factored_for():
+    """adi_step_2d runs only on plans factored by adi_plans_factor for its exact (gamma, dt, dx):
+    another dt (a different sigma than the sweeps were factored with), plans factored by
+    pent_factor_hyperdiff, or plans refactored since, return PENT_EINVAL and leave C untouched."""
+    nx, ny, gamma, dt, dx = 16, 8, 0.01, 1e-6, 1.0 / 16
+    L = pb._lib.load()
+    px = pb.Plan(nx, batch=ny, shared=True)
+    py = pb.Plan(ny, batch=nx, shared=True)
+    C = torch.from_numpy(synth.uniform(9, 0, nx * ny, -0.1, 0.1).reshape(ny, nx)).cuda()
+    C0 = C.clone()
+
+    def step(g, t, h):
+        return L.adi_step_2d(px._h, py._h, C.data_ptr(), nx, ny, g, t, h, 0)
+
+    sig = torch.full((1,), gamma * dt / dx ** 4, dtype=torch.float64, device="cuda")
+    px.factor_hyperdiff(sig)
+    py.factor_hyperdiff(sig)
+    assert step(gamma, dt, dx) == pb._lib.PENT_EINVAL     # factored, but not for an ADI step
+    pb.adi_plans_factor(px, py, gamma, dt, dx)
+    assert step(gamma, 2 * dt, dx) == pb._lib.PENT_EINVAL
+    assert step(gamma, dt, dx * (1 + 1e-15)) == pb._lib.PENT_EINVAL
+    assert step(2 * gamma, dt, dx) == pb._lib.PENT_EINVAL
+    torch.cuda.synchronize()
+    assert torch.equal(C, C0)
+    assert step(gamma, dt, dx) == pb._lib.PENT_OK
+    torch.cuda.synchronize()
+    assert not torch.equal(C, C0)
+    px.factor_hyperdiff(sig)                               # refactored otherwise: the record is gone
+    assert step(gamma, dt, dx) == pb._lib.PENT_EINVAL

@@ -521,3 +521,57 @@ def test_f32_refine_reports_non_convergence():
     C = dev(f * 2.0 ** 41)
     plan.step(C, mu=dev(np.full(batch, 1e-3)), nsteps=1, max_refine=2)
     assert plan.info()[0] == PENT_ENOCONV
+
+
+def test_step_graph_cache_is_bounded():
+    """More distinct fields than the step-graph cache holds: every result stays right, the
+    plan never holds more than PENT_MAX_CACHED_GRAPHS graphs, and an evicted key is
+    captured anew when it comes back."""
+    n, batch, limit = 256, 40, pb._lib.PENT_MAX_CACHED_GRAPHS
+    w = synth.hyperdiff_parametric(batch=batch, n=n, steps=2)
+    ref = oracle.hyperdiff_steps(w.n, w.sigma, w.field0, 2)
+    side = torch.cuda.Stream()  # graphs are captured on a non-default stream
+    with torch.cuda.stream(side):
+        plan = pb.Plan(n, batch=batch, stream=side)
+        plan.factor_hyperdiff(dev(w.sigma))
+        fields = [dev(w.field0) for _ in range(limit + 5)]
+        for x in fields + fields[:3]:
+            if x is fields[0] or x is fields[1] or x is fields[2]:
+                x.copy_(dev(w.field0))
+            plan.solve_steps(x, 2)
+            assert plan.get_option(pb._lib.PENT_OPT_CACHED_GRAPHS) <= limit
+        torch.cuda.synchronize()
+    assert plan.get_option(pb._lib.PENT_OPT_CACHED_GRAPHS) == limit
+    for x in fields:
+        assert sys_rel_err(host(x), ref, w.n) <= TOL
+
+
+@pytest.mark.parametrize("n,batch", [(1, 37), (2, 37), (5, 37), (33, 37), (64, 37), (100, 37), (255, 37), (512, 37),
+                                     (1000, 37), (1024, 300), (4097, 6), (8192, 4)])
+def test_f32_refine_fp64_residual(n, batch):
+    """PENT_RESIDUAL_F64: the refinement residual f - A x formed in native FP64 from the band
+    rebuilt from sigma (x accumulated in FP64), the FP32 solves unchanged; lengths from one
+    row to clusters of CTAs, against the oracle at the 1e-12 bar."""
+    w = synth.hyperdiff_parametric(batch=batch, n=n, steps=1, sigma_range=(1e-3, 10.0))
+    ref = oracle.hyperdiff_steps(w.n, w.sigma, w.field0, 1)
+    plan = pb.Plan(n, batch=w.batch, precision=pb.PENT_F32_REFINE,
+                   options={pb.PENT_OPT_RESIDUAL: pb.PENT_RESIDUAL_F64})
+    plan.factor_hyperdiff(dev(w.sigma))
+    x = plan.solve(dev(w.field0), max_refine=3)
+    st, _, _, used = plan.info()
+    assert st == pb.PENT_OK and used >= 1
+    assert sys_rel_err(host(x), ref, w.n) <= TOL
+
+
+def test_f32_refine_fp64_residual_steps_and_one_refinement():
+    """The FP64-residual form in a step graph (three steps, bar 3 x 1e-12), and with one
+    refinement step (the benchmark's setting), where it meets the per-solve bar."""
+    w = synth.hyperdiff_parametric(batch=200, n=1024, steps=3)
+    plan = pb.Plan(1024, batch=w.batch, precision=pb.PENT_F32_REFINE,
+                   options={pb.PENT_OPT_RESIDUAL: pb.PENT_RESIDUAL_F64})
+    plan.factor_hyperdiff(dev(w.sigma))
+    x = dev(w.field0)
+    plan.solve_steps(x, w.steps, max_refine=2)
+    assert sys_rel_err(host(x), oracle.hyperdiff_steps(w.n, w.sigma, w.field0, w.steps), w.n) <= w.steps * TOL
+    x1 = plan.solve(dev(w.field0), max_refine=1)
+    assert sys_rel_err(host(x1), oracle.hyperdiff_steps(w.n, w.sigma, w.field0, 1), w.n) <= TOL
