@@ -48,9 +48,18 @@ WORKLOAD = ("hyperdiffusion parametric batch: 65,536 systems x N=1024, sigma_i l
 # The FP32 kernel itself needs only 24 B/row (it stores 1/alpha and beta and rebuilds the
 # other three factors of the symmetric band from sigma), so its fraction of the HBM
 # roofline on the 36 B/row basis can exceed what its DRAM traffic alone would allow.
-ALG_BYTES = {"f64": 56, "f32_refine": 36}
-KERNEL = {"f64": "k_solve64_pair", "f32_refine": "k_solve32r"}
-KERNEL_SRC = {"f64": "paper_1807_07382_gb300/csrc/core64.cu", "f32_refine": "paper_1807_07382_gb300/csrc/f32r.cu"}
+ALG_BYTES = {"f64": 56, "f32_refine": 36, "f32_refine_general": 36, "f32_refine_res64": 36}
+# the headline variants: FP64; FP32 + one refinement step on the interior-constant kernel (the
+# default), on the general kernel that loads every row's factors, and with the residual in native FP64
+KERNEL = {"f64": "k_solve64_pair", "f32_refine": "k_solve32u", "f32_refine_general": "k_solve32r",
+          "f32_refine_res64": "k_solve32r (FP64 residual)"}
+_CS = "paper_1807_07382_gb300/csrc/"
+# the sources a kernel is compiled from (its file and the headers it includes): the ncu table's gate
+KERNEL_SRC = {"f64": [_CS + "core64.cu", _CS + "internal.cuh"],
+              "f32_refine": [_CS + "f32u.cu", _CS + "ff.cuh", _CS + "internal.cuh"],
+              "f32_refine_general": [_CS + "f32r.cu", _CS + "ff.cuh", _CS + "internal.cuh"],
+              "f32_refine_res64": [_CS + "f32r.cu", _CS + "ff.cuh", _CS + "internal.cuh"],
+              "adi": [_CS + "adi.cu", _CS + "internal.cuh"]}
 
 
 # ----------------------------------------------------------------------------- helpers
@@ -64,9 +73,13 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def source_sha(path):
-    with open(os.path.join(ROOT, path), "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+def source_sha(paths):
+    """sha256 prefix of a source file, or of several concatenated in order."""
+    h = hashlib.sha256()
+    for path in ([paths] if isinstance(paths, str) else paths):
+        with open(os.path.join(ROOT, path), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def profile_entry(variant):
@@ -82,27 +95,76 @@ def profile_entry(variant):
     return e
 
 
-# GB300: 152 SMs of 4 schedulers, each issuing at most one warp instruction per clock;
-# FP64 at 1/64 of the FP32 rate, 1.25 TFLOP/s nominal (the FP64 solve does 4 FMA + 1 MUL
-# = 9 flops per row: g = (1/alpha)(f - beta g1 - sigma g2), x = g - gamma x1 - delta x2)
-SMS, SCHEDULERS, FP64_TFLOPS, F64_FLOPS_PER_ROW = 152, 4, 1.25, 9
+# Each SM has 4 schedulers, each issuing at most one warp instruction per clock.  The FP64
+# solve does 4 FMA + 1 MUL per row (9 flops, 5 operations of the FP64 pipe, which takes a
+# multiply as long as an FMA): g = (1/alpha)(f - beta g1 - sigma g2), x = g - gamma x1 - delta x2.
+# The pipe's rate is measured on the GPU at hand (pent_probe_fp64_fma, see measure_fp64_peak).
+SCHEDULERS, F64_FLOPS_PER_ROW, F64_OPS_PER_ROW = 4, 9, 5
 
 
-def compute_roofline(variant, rows, ms_step, sm_mhz):
-    """The compute side of the solve: warp-instruction issue for FP32+refine (instructions
-    per row from the ncu capture), the FP64 pipe for the FP64 solve."""
+def compute_roofline(variant, rows, ms_step, sm_mhz, sms, fp64=None):
+    """The compute side of the solve: the FP64 pipe for the FP64 solve (against the measured
+    FMA rate), warp-instruction issue for FP32+refine (instructions per row from the ncu
+    capture, against sms x 4 schedulers x the sampled SM clock)."""
     if variant == "f64":
-        achieved = F64_FLOPS_PER_ROW * rows / (ms_step / 1e3) / 1e12
-        return {"bound": "fp64", "achieved": achieved, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_TFLOPS, "peak_kind": "nominal (GB300 FP64)"}
+        if not fp64:
+            return None
+        return fp64_roofline(F64_OPS_PER_ROW, F64_FLOPS_PER_ROW, rows, ms_step, fp64, "row")
     e = profile_entry(variant)
     if not e or "warp_inst_per_row" not in e or not sm_mhz:
         return None
     achieved = e["warp_inst_per_row"] * rows / (ms_step / 1e3)
-    peak = SMS * SCHEDULERS * sm_mhz * 1e6
+    peak = sms * SCHEDULERS * sm_mhz * 1e6
     return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "warp instructions/s",
-            "frac": achieved / peak, "peak_kind": "152 SMs x 4 schedulers x 1 per clock at the sampled SM clock",
+            "frac": achieved / peak,
+            "peak_kind": f"{sms} SMs (device query) x 4 schedulers x 1 per clock at the sampled SM clock",
             "warp_inst_per_row": e["warp_inst_per_row"]}
+
+
+def fp64_roofline(ops_per_unit, flops_per_unit, units, ms_step, fp64, unit_name):
+    """FP64-pipe roofline: pipe operations (FMA, add, multiply: one each) per second against the
+    measured FMA rate; the flop rate beside it."""
+    t = ms_step / 1e3
+    peak_ops = fp64["tflops"] * 1e12 / 2  # FMA per second
+    achieved = ops_per_unit * units / t
+    return {"bound": "fp64", "achieved": achieved, "peak": peak_ops, "unit": "FP64 pipe operations/s",
+            "frac": achieved / peak_ops, "peak_kind": "measured (pent_probe_fp64_fma, this run)",
+            f"ops_per_{unit_name}": ops_per_unit, "tflops": flops_per_unit * units / t / 1e12,
+            f"flops_per_{unit_name}": flops_per_unit}
+
+
+def measure_fp64_peak(pb, dev, stream, sms):
+    """FP64 FMA rate of this GPU: pent_probe_fp64_fma over 8 CTAs of 256 threads per SM (eight
+    independent FMA chains a thread), CUDA events on the launching stream, best of 5 launches
+    of ~0.1 s after one warm-up launch, SM clocks sampled meanwhile."""
+    import ctypes
+    import torch
+    L = pb._lib.load()
+    sink = torch.zeros(1, dtype=torch.float64, device=dev)
+    flops = ctypes.c_double()
+    blocks, iters = 8 * sms, 1500
+    st = ctypes.c_void_p(stream.cuda_stream)
+
+    def launch():
+        r = L.pent_probe_fp64_fma(blocks, iters, ctypes.c_void_p(sink.data_ptr()), st, ctypes.byref(flops))
+        if r != 0:
+            raise RuntimeError(f"pent_probe_fp64_fma: status {r}")
+    launch()
+    torch.cuda.synchronize(dev)
+    times = []
+    with ClockSampler(dev.index or 0) as cs:
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            launch()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            times.append(e0.elapsed_time(e1))
+    ms = min(times)
+    return {"tflops": flops.value / (ms / 1e3) / 1e12, "ms": ms, "flops_per_launch": flops.value,
+            "launch": f"{blocks} CTAs x 256 threads, 8 FMA chains x {16 * iters} steps a thread",
+            "clocks": cs.summary()}
 
 
 def traffic_per_row(variant):
@@ -254,6 +316,11 @@ def cpu_baseline(w, budget_s=15.0, gpu_results=None):
 
 # ----------------------------------------------------------------------------- own arm
 
+def _variant_options(pb, name):
+    return {"f64": {}, "f32_refine": {}, "f32_refine_general": {pb.PENT_OPT_FP32_KERNEL: 1},
+            "f32_refine_res64": {pb.PENT_OPT_RESIDUAL: pb.PENT_RESIDUAL_F64}}[name]
+
+
 def run_own(args):
     import torch
     import paper_1807_07382_gb300 as pb
@@ -266,7 +333,10 @@ def run_own(args):
     torch.cuda.set_device(local)
     pbuild.build()
     dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev)
+    # a stream of its own: step graphs are captured on it (the legacy stream cannot be captured)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
 
     BATCH = args.batch
     w = synth.hyperdiff_parametric(batch=BATCH, n=N, steps=args.steps)
@@ -274,6 +344,7 @@ def run_own(args):
     sigma = torch.from_numpy(w.sigma).to(dev)
     rows = BATCH * N
     peak, peak_kind = measured_peaks()
+    fp64 = measure_fp64_peak(pb, dev, stream, sms)
 
     def barrier():
         if world > 1:
@@ -281,11 +352,13 @@ def run_own(args):
 
     variants = {}
     one_step = {}
-    order = ["f64", "f32_refine"] if args.precision == "both" else [args.precision]
+    order = {"both": ["f64", "f32_refine", "f32_refine_general", "f32_refine_res64"],
+             "f64": ["f64"], "f32_refine": ["f32_refine"]}[args.precision]
     clocks = None
     for name in order:
         prec = pb.PENT_F64 if name == "f64" else pb.PENT_F32_REFINE
-        plan = pb.Plan(N, batch=BATCH, precision=prec, device=dev, stream=stream)
+        plan = pb.Plan(N, batch=BATCH, precision=prec, device=dev, stream=stream,
+                       options=_variant_options(pb, name))
         plan.factor_hyperdiff(sigma)
         x = f0.clone()
         # one step from C0 for the accuracy check against the oracle
@@ -321,10 +394,13 @@ def run_own(args):
             "clocks": cs.summary(),
         }
         variants[name]["compute_roofline"] = compute_roofline(name, rows, ms_step,
-                                                              variants[name]["clocks"].get("sm_mhz"))
-        if name == "f32_refine":
+                                                              variants[name]["clocks"].get("sm_mhz"), sms, fp64)
+        if name != "f64":
             variants[name]["max_refine"] = args.max_refine
             variants[name]["refine_steps_used"] = plan.info()[3]
+        if name == "f32_refine":
+            variants[name]["note"] = ("interior-constant kernel: factors loaded only near the walls; the field "
+                                      "stays as scaled float pairs between graph steps")
         clocks = variants[name]["clocks"]
         del plan
         torch.cuda.empty_cache()
@@ -401,6 +477,13 @@ def run_own(args):
         del plan
         torch.cuda.empty_cache()
 
+    # the other workloads of the method (uneven batch, 2D ADI), each timed on its own graph after the
+    # headline's timed region; one GPU only
+    if world == 1 and not args.no_workloads:
+        for k, v in measure_uneven(pb, dev, stream, fp64, sms, steps=args.workload_steps or 200).items():
+            variants[k] = v
+        variants["adi"] = measure_adi(pb, dev, stream, fp64)
+
     base, errs = (None, {})
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base, errs = cpu_baseline(w, budget_s=args.cpu_budget, gpu_results=one_step)
@@ -414,18 +497,105 @@ def run_own(args):
             "vs_baseline": None, "dtype": hv["dtype"], "data": "synthetic",
             "config": {"workload": WORKLOAD if BATCH == 65536 else WORKLOAD.replace("65,536", f"{BATCH:,}"),
                        "batch": BATCH, "n": N, "precision": head,
-                       "max_refine": args.max_refine if head == "f32_refine" else 0,
+                       "max_refine": args.max_refine if head != "f64" else 0,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "working set (factors + field) >= 1.9 GB, larger than L2; no flush"},
             "roofline": hv["roofline"], "compute_roofline": hv["compute_roofline"], "cpu_baseline": base,
             "e2e": e2e, "gpu_launches": args.steps,
-            "clocks": clocks, "variants": variants,
+            "clocks": clocks, "fp64_peak": fp64, "sms": sms, "variants": variants,
         }
         if errs:
             line["max_rel_err_vs_oracle"] = errs.get(head)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def measure_uneven(pb, dev, stream, fp64, sms, steps=200):
+    """The uneven batch (20,000 systems, N log-uniform in [64, 16384], sum N = 59.1 M) with the GB300
+    tune cache, both precisions, one refinement step: ms per graph step, error of one solve against
+    the oracle on every 97th system, HBM roofline on the algorithmic bytes."""
+    import torch
+    import oracle
+    w = synth.uneven(steps=steps)
+    f0 = torch.from_numpy(w.field0).to(dev)
+    sig = torch.from_numpy(w.sigma).to(dev)
+    off = w.offsets
+    pick = np.arange(0, w.batch, 97)
+    ref = oracle.hyperdiff_steps(w.n[pick], w.sigma[pick], np.concatenate([w.field0[off[s]:off[s + 1]] for s in pick]),
+                                 1)
+    roff = oracle.offsets(w.n[pick])
+    tune = os.path.join(ROOT, "paper_1807_07382_gb300", "tune_gb300.txt")
+    peak, peak_kind = measured_peaks()
+    out = {}
+    for prec, pname, alg, kern in ((pb.PENT_F64, "f64", 56, "k_solve64_pair + partitioned"),
+                                   (pb.PENT_F32_REFINE, "f32_refine", 36, "k_solve32u + k_solve32r (clusters)")):
+        plan = pb.Plan(list(w.n), precision=prec, stream=stream, device=dev, tune_cache=tune)
+        plan.factor_hyperdiff(sig)
+        one = plan.solve(f0, max_refine=1).cpu().numpy()
+        got = np.concatenate([one[off[s]:off[s + 1]] for s in pick])
+        err = max(float(np.max(np.abs(got[roff[k]:roff[k + 1]] - ref[roff[k]:roff[k + 1]])) /
+                        np.max(np.abs(ref[roff[k]:roff[k + 1]]))) for k in range(len(pick)))
+        x = f0.clone()
+        plan.solve_steps(x, steps, max_refine=1)
+        ms, ck = _time_device(stream, lambda: plan.solve_steps(x, steps, max_refine=1), steps, dev)
+        ms_step = ms / steps
+        achieved = alg * w.rows / (ms_step / 1e3) / 1e9
+        out[f"uneven_{pname}"] = {
+            "value": w.rows * steps / (ms / 1e3), "ms_per_step": ms_step, "dtype": pname.split("_")[0],
+            "workload": "20,000 systems, N log-U[64,16384] (sum 59.1 M rows), sigma log-U[1e-2,10], "
+                        f"{steps} implicit steps (1 graph), tuned launch settings",
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "kernel": kern, "alg_bytes_per_row": alg, "peak_kind": peak_kind},
+            "max_rel_err_vs_oracle": err, "err_sample": f"{len(pick)} systems, one solve",
+            "max_refine": 1 if prec == pb.PENT_F32_REFINE else 0, "clocks": ck}
+        del plan
+        torch.cuda.empty_cache()
+    return out
+
+
+def adi_fp64_counts():
+    """FP64 pipe operations and flops per cell of one ADI step from a committed ncu count
+    (profiles/traffic.json), or None once the ADI kernels' sources have changed since."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        e = json.load(fh).get("adi")
+    if not e or e.get("source_sha") != source_sha(KERNEL_SRC["adi"]):
+        return None
+    return float(e["fp64_ops_per_cell"]), float(e["fp64_flops_per_cell"])
+
+
+def measure_adi(pb, dev, stream, fp64, steps=500):
+    """The 2D Cahn-Hilliard ADI step on 2048^2 (gamma = 0.01, dt = 1e-6, dx = 1/2048): ms per step in a
+    500-step graph, the step's change against the oracle's, mass drift, and the FP64-pipe roofline
+    (the step is bound by FP64 arithmetic, its 33.5 MB field staying in L2)."""
+    import torch
+    import oracle
+    w = synth.ch_adi(steps=steps)
+    adi = pb.ADI2D(w.nx, w.ny, w.gamma, w.dt, w.dx, device=dev, stream=stream)
+    C = torch.from_numpy(w.field0).to(dev)
+    one = adi.step(C.clone()).cpu().numpy()
+    ref = oracle.adi_step(w.field0, w.gamma, w.dt, w.dx)
+    # the exact dC is O(sigma) times the field's rounding: compare the step's change, normwise
+    err = float(np.max(np.abs(one - ref)) / np.max(np.abs(ref - w.field0)))
+    m0 = float(C.sum())
+    adi.step(C.clone(), nsteps=steps)
+    ms, ck = _time_device(stream, lambda: adi.step(C, nsteps=steps), steps, dev)
+    drift = abs(float(C.sum()) - m0) / float(np.abs(w.field0).sum())
+    ms_step = ms / steps
+    cells = w.nx * w.ny
+    counts = adi_fp64_counts()
+    comp = fp64_roofline(counts[0], counts[1], cells, ms_step, fp64, "cell") if counts and fp64 else None
+    return {"value": 2 * cells * steps / (ms / 1e3), "ms_per_step": ms_step, "dtype": "f64",
+            "workload": "2048 x 2048 Cahn-Hilliard ADI (Douglas), gamma=0.01, dt=1e-6, dx=1/2048, "
+                        f"{steps} steps (1 graph); rows = both sweeps",
+            "compute_roofline": comp,
+            "memory": "about 40 B per cell and step of algorithmic traffic (C read with its halo, the "
+                      "intermediates, C written); the 33.5 MB field and the sweeps' scratch stay in the 129 MB L2",
+            "max_rel_err_vs_oracle": err, "err_metric": "max|dC - dC_ref| / max|dC_ref| after one step",
+            "mass_drift_rel": drift, "clocks": ck}
 
 
 # ----------------------------------------------------------------------------- other workloads
@@ -473,7 +643,8 @@ def run_workloads(names, args):
     pbuild.build()
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    stream = torch.cuda.current_stream(dev)
+    stream = torch.cuda.Stream(dev)  # a stream of its own: step graphs are captured on it
+    torch.cuda.set_stream(stream)
     tune = os.path.join(ROOT, "paper_1807_07382_gb300", "tune_gb300.txt")
     for name in names:
         if name == "cosines":
@@ -490,48 +661,13 @@ def run_workloads(names, args):
                   w.rows, w.steps, ms, 16, "k_solve64_pair<shared>", err, clocks=ck,
                   extra={"note": "shared factors broadcast; latency bound (16,384 rows per step)"})
         elif name == "uneven":
-            w = synth.uneven(steps=args.workload_steps or 200)
-            f0 = torch.from_numpy(w.field0).to(dev)
-            sig = torch.from_numpy(w.sigma).to(dev)
-            off = w.offsets
-            pick = np.arange(0, w.batch, 97)
-            ref = oracle.hyperdiff_steps(w.n[pick], w.sigma[pick],
-                                         np.concatenate([w.field0[off[s]:off[s + 1]] for s in pick]), 1)
-            for prec, pname, alg, kern in ((pb.PENT_F64, "f64", 56, "k_solve64_pair + partitioned"),
-                                           (pb.PENT_F32_REFINE, "f32_refine", 36, "k_solve32r")):
-                plan = pb.Plan(list(w.n), precision=prec, stream=stream, tune_cache=tune)
-                plan.factor_hyperdiff(sig)
-                one = plan.solve(f0, max_refine=1).cpu().numpy()
-                got = np.concatenate([one[off[s]:off[s + 1]] for s in pick])
-                roff = oracle.offsets(w.n[pick])
-                err = max(float(np.max(np.abs(got[roff[k]:roff[k + 1]] - ref[roff[k]:roff[k + 1]])) /
-                                np.max(np.abs(ref[roff[k]:roff[k + 1]]))) for k in range(len(pick)))
-                x = f0.clone()
-                plan.solve_steps(x, w.steps, max_refine=1)
-                ms, ck = _time_device(stream, lambda: plan.solve_steps(x, w.steps, max_refine=1), w.steps, dev)
-                _line(f"{name}_{pname}", "20,000 systems, N log-U[64,16384] (sum 59.1 M rows), sigma log-U[1e-2,10], "
-                      f"{w.steps} implicit steps (1 graph), tuned launch settings", w.rows, w.steps, ms, alg, kern, err,
-                      dtype="f64" if prec == pb.PENT_F64 else "f32", clocks=ck,
-                      extra={"max_refine": 1 if prec == pb.PENT_F32_REFINE else 0,
-                             "err_sample": f"{len(pick)} systems, one step"})
-                del plan
+            for k, v in measure_uneven(pb, dev, stream, None, 0, steps=args.workload_steps or 200).items():
+                print(json.dumps({"workload_name": k, "metric": METRIC, "unit": UNIT, "n_gpus": 1,
+                                  "higher_is_better": True, "data": "synthetic", **v}), flush=True)
         elif name == "adi":
-            w = synth.ch_adi()
-            adi = pb.ADI2D(w.nx, w.ny, w.gamma, w.dt, w.dx, device=dev, stream=stream)
-            C = torch.from_numpy(w.field0).to(dev)
-            one = adi.step(C.clone()).cpu().numpy()
-            ref = oracle.adi_step(w.field0, w.gamma, w.dt, w.dx)
-            # the exact dC is O(sigma) times the field's rounding: compare the step's change, normwise
-            err = float(np.max(np.abs(one - ref)) / np.max(np.abs(ref - w.field0)))
-            m0 = float(C.sum())
-            adi.step(C.clone(), nsteps=w.steps)
-            ms, ck = _time_device(stream, lambda: adi.step(C, nsteps=w.steps), w.steps, dev)
-            drift = abs(float(C.sum()) - m0) / float(np.abs(w.field0).sum())
-            _line(name, "2048 x 2048 Cahn-Hilliard ADI (Douglas), gamma=0.01, dt=1e-6, dx=1/2048, 500 steps (1 graph)",
-                  2 * w.nx * w.ny, w.steps, ms, 8, "k_adi_rhs_T + partitioned column sweeps", err, clocks=ck,
-                  extra={"mass_drift_rel": drift, "err_metric": "max|dC - dC_ref| / max|dC_ref| after one step",
-                         "note": "rows = both sweeps; 8 B per swept row (C read and written once per step); "
-                                 "the 33.5 MB field stays in L2"})
+            v = measure_adi(pb, dev, stream, None)
+            print(json.dumps({"workload_name": name, "metric": METRIC, "unit": UNIT, "n_gpus": 1,
+                              "higher_is_better": True, "data": "synthetic", **v}), flush=True)
         elif name == "adjoint":
             w = synth.adjoint_batch()
             n = int(w.n[0])
@@ -733,6 +869,8 @@ def main():
     ap.add_argument("--batch", type=int, default=None,
                     help="systems (default: the full workload; smaller for profiling, also for --workload "
                          "periodic_cn, ch1d and rewrite)")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the uneven and ADI workloads that the default line carries under variants")
     ap.add_argument("--workload-steps", type=int, default=None,
                     help="steps of the uneven workload's timed graph (default 200; fewer for profiling)")
     ap.add_argument("--workload", default=None,

@@ -162,8 +162,8 @@ enum {
                                       most PENT_MAX_CACHED_GRAPHS */
   PENT_OPT_FP32_KERNEL = 10,       /* PENT_F32_REFINE, not periodic: 0 (the default) solves with at most one
                                       refinement step and the float-float residual on the interior-constant
-                                      kernel wherever the system's CTA shape allows it (one CTA of 1, 2, 4, 8
-                                      or 16 warps of 8 rows a thread, or one warp of 4): away from the walls
+                                      kernel wherever the system's CTA shape allows it (one CTA of 1 to 16
+                                      warps of 8 rows a thread, or one warp of 4): away from the walls
                                       the FP32 factors of I + sigma D4 settle on one pair of constants, which
                                       that kernel uses without loading them and whose chunk-map powers the
                                       factorisation stores; 1 solves every system with the general kernel that
@@ -410,6 +410,18 @@ pent_status pent_clear_info(pent_plan* plan);
 pent_status pent_gbsv_batch_noalloc(int64_t batch, int64_t n, const double* a, const double* b, const double* c,
                                     const double* d, const double* e, const double* f, double* x,
                                     unsigned long long* d_info, void* cuda_stream);
+
+/*
+ * Measurement probe (the paper has no counterpart): launch `blocks` CTAs of 256
+ * threads, each thread running eight independent FP64 fused multiply-add
+ * chains of 16 * iters steps, on cuda_stream (asynchronous).  *flops receives
+ * the floating-point operations the launch performs (2 per FMA); time the
+ * launch with events on the same stream to obtain the FP64 rate that bounds
+ * the FP64 solves.  d_sink: one device double, written only in a case that
+ * never occurs (it keeps the arithmetic from being removed).  PENT_EINVAL for
+ * non-positive sizes or a misaligned or NULL pointer.
+ */
+pent_status pent_probe_fp64_fma(int64_t blocks, int64_t iters, double* d_sink, void* cuda_stream, double* flops);
 
 /* Destroy a plan (host memory only; the workspace is the caller's). NULL is a no-op. */
 void pent_plan_destroy(pent_plan* plan);

@@ -67,6 +67,7 @@ SIGNATURES = {
     "pent_get_info": (_int, [_vp, _i64p, _i64p, _intp]),
     "pent_clear_info": (_int, [_vp]),
     "pent_gbsv_batch_noalloc": (_int, [_i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "pent_probe_fp64_fma": (_int, [_i64, _i64, _vp, _vp, ctypes.POINTER(_dbl)]),
     "pent_plan_destroy": (None, [_vp]),
     "pent_status_string": (ctypes.c_char_p, [_int]),
     "pent_version": (ctypes.c_char_p, []),

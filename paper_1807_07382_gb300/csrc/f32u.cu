@@ -402,12 +402,16 @@ __device__ __forceinline__ int fexp(float h) { return (int)((__float_as_uint(h) 
 #define PENT_U_WARPS_PER_SM 40
 #endif
 
+// CTAs per SM the launch bound asks for: PENT_U_WARPS_PER_SM warps, or for the runtime-width
+// kernel two CTAs of up to 16 warps (64 registers a thread).
+constexpr int u_min_blocks(int WT) { return WT > 0 ? PENT_U_WARPS_PER_SM / WT : 2; }
+
 template <int L, int WT, int REF, int IN, int OUT>
-__global__ void __launch_bounds__(32 * WT, PENT_U_WARPS_PER_SM / WT)
+__global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, u_min_blocks(WT))
     k_solve32u(F32Tables T, const float4* __restrict__ urec, int32_t* __restrict__ kscale,
-               const int32_t* __restrict__ sys, int shared, const double* f, double* x, int vec_io) {
+               const int32_t* __restrict__ sys, int shared, const double* f, double* x, int vec_io, int Wrt) {
   static_assert(L % 4 == 0, "rows per thread must be a multiple of 4");
-  constexpr int W = WT, P = 32 * W;
+  const int W = WT > 0 ? WT : Wrt, P = 32 * W;  // WT = 0: the warp count is a launch parameter
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4* rec_sm = reinterpret_cast<float4*>(smem_raw);        // [kURecFloat4]
   float4* edge = rec_sm + kURecFloat4;                         // [P]
@@ -692,9 +696,10 @@ template <int L, int WT, int REF, int IN, int OUT>
 cudaError_t launch_u(const F32Tables& T, const float4* urec, int32_t* kscale, const int32_t* sys, const F32Bucket& b,
                      int shared, const double* f, double* x, cudaStream_t st) {
   const int vec = ((((uintptr_t)f) | ((uintptr_t)x)) % 16 == 0) && b.even_offsets;
-  const size_t smem = usmem_bytes(WT, L);
-  k_solve32u<L, WT, REF, IN, OUT><<<(unsigned)b.count, 32 * WT, smem, st>>>(T, urec, kscale, sys + b.first, shared, f,
-                                                                           x, vec);
+  const int W = WT > 0 ? WT : b.W;
+  const size_t smem = usmem_bytes(W, L);
+  k_solve32u<L, WT, REF, IN, OUT><<<(unsigned)b.count, 32 * W, smem, st>>>(T, urec, kscale, sys + b.first, shared, f,
+                                                                          x, vec, W);
   return cudaGetLastError();
 }
 
@@ -719,7 +724,7 @@ cudaError_t dispatch_modes(const F32Tables& T, const float4* urec, int32_t* ksca
 
 bool solve32u_supported(const F32Bucket& b) {
   if (b.C != 1) return false;
-  if (b.L == 8) return b.W == 1 || b.W == 2 || b.W == 4 || b.W == 8 || b.W == 16;
+  if (b.L == 8) return b.W >= 1 && b.W <= 16;
   if (b.L == 4) return b.W == 1;
   return false;
 }
@@ -741,7 +746,9 @@ cudaError_t launch_solve32u(const F32Tables& T, const float4* urec, int32_t* ksc
     case 2: return dispatch_modes<8, 2>(T, urec, kscale, sys, b, shared, f, x, max_refine, in_ff, out_ff, st);
     case 4: return dispatch_modes<8, 4>(T, urec, kscale, sys, b, shared, f, x, max_refine, in_ff, out_ff, st);
     case 8: return dispatch_modes<8, 8>(T, urec, kscale, sys, b, shared, f, x, max_refine, in_ff, out_ff, st);
-    default: return dispatch_modes<8, 16>(T, urec, kscale, sys, b, shared, f, x, max_refine, in_ff, out_ff, st);
+    case 16: return dispatch_modes<8, 16>(T, urec, kscale, sys, b, shared, f, x, max_refine, in_ff, out_ff, st);
+    default:  // the other widths (3, 5-7, 9-15 warps): one kernel for all, compiled for up to 512 threads
+      return dispatch_modes<8, 0>(T, urec, kscale, sys, b, shared, f, x, max_refine, in_ff, out_ff, st);
   }
 }
 
