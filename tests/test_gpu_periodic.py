@@ -269,3 +269,28 @@ def test_full_size_periodic_crank_nicolson_sampled(prec):
     got = C.cpu().numpy().reshape(w.batch, n)[pick].reshape(-1)
     tol = max(TOL, 6 * (1 + 16 * w.sigma[0]) * 2.0 ** -53 * np.max(np.abs(f0)) / np.max(np.abs(ref)))
     assert sys_err(got, ref, n) <= tol
+
+
+@pytest.mark.parametrize("n", [64, 128])
+@pytest.mark.parametrize("prec", [pb.PENT_F64, pb.PENT_F32_REFINE])
+def test_periodic_crank_nicolson_against_the_exact_step(prec, n):
+    """One periodic Crank-Nicolson step at the workload's sigma_x = 343.6, both GPU paths against
+    the step computed in exact rational arithmetic (oracle/exact.py: the scheme's right-hand side
+    and Navon's reduction in Fractions, the inputs taken as the rationals the doubles are).  The
+    exact step has no rounding: both paths are within 1e-12 of it, element by element, although the
+    FP64 oracle's own rounding bound at this sigma (the right-hand side's cancellation) is ~4e-12."""
+    from oracle import exact as ex
+    sigma = 1e-8 / (2 * (1.0 / 512) ** 4)
+    batch = 6
+    f0 = synth.uniform(4400 + n, 0, batch * n, -1, 1)
+    ref = np.concatenate([np.array([float(v) for v in ex.periodic_cn_step(sigma, f0[s * n:(s + 1) * n])])
+                          for s in range(batch)])
+    plan = pb.Plan(n, batch=batch, shared=True, periodic=True, precision=prec)
+    s = dev(np.array([sigma]))
+    plan.factor_hyperdiff(s)
+    C = dev(f0)
+    plan.step(C, nu=s, max_refine=3)
+    assert plan.info()[0] == pb.PENT_OK
+    err = sys_err(C.cpu().numpy(), ref, n)
+    print(f"periodic CN n={n} precision={prec}: GPU vs exact step {err:.2e}")
+    assert err <= TOL
