@@ -352,8 +352,8 @@ def run_own(args):
 
     variants = {}
     one_step = {}
-    order = {"both": ["f64", "f32_refine", "f32_refine_general", "f32_refine_res64"],
-             "f64": ["f64"], "f32_refine": ["f32_refine"]}[args.precision]
+    order = ["f64", "f32_refine", "f32_refine_general", "f32_refine_res64"] if args.precision == "both" \
+        else [args.precision]
     clocks = None
     for name in order:
         prec = pb.PENT_F64 if name == "f64" else pb.PENT_F32_REFINE
@@ -860,7 +860,8 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["own", "reference"], default="own")
-    ap.add_argument("--precision", choices=["both", "f64", "f32_refine"], default="both")
+    ap.add_argument("--precision", choices=["both", "f64", "f32_refine", "f32_refine_general", "f32_refine_res64"],
+                    default="both", help="headline variants to time (both: all four)")
     ap.add_argument("--max-refine", type=int, default=1,
                     help="FP32 refinement steps (one reaches the 1e-12 bar on this workload; the error is measured)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
