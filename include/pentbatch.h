@@ -169,15 +169,44 @@ enum {
                                       factorisation stores; 1 solves every system with the general kernel that
                                       loads every row's factors.  Any time; results agree to the refinement's
                                       accuracy, not bit for bit. */
-  PENT_OPT_CLUSTER_WARPS = 9       /* PENT_F32_REFINE: systems that need more than 512 threads run in a
+  PENT_OPT_CLUSTER_WARPS = 9,      /* PENT_F32_REFINE: systems that need more than 512 threads run in a
                                       thread-block cluster of up to 8 CTAs of exactly this many warps: 8
                                       (the default) or 4, which keep several CTAs resident per SM, or 16
                                       (CTAs of up to 16 warps, one per SM); systems longer than 8 such CTAs
                                       take the 16-warp form.  Systems of up to 512 threads run in one CTA
                                       whatever the value.  Before pent_plan_bind. */
+  PENT_OPT_WINDOW_WARPS = 12,      /* PENT_F32_REFINE, not periodic: systems longer than R = 256 W rows (W
+                                      this value: 4, the default, 8 or 16; 0 turns windows off) are solved,
+                                      when a solve takes the interior-constant kernel, in windows of R rows,
+                                      one CTA of W warps each, side by side in one launch.  A window starts
+                                      and ends with zero states where it cuts the system and keeps only
+                                      the rows at least O from a cut, O the overlap the factorisation finds
+                                      per system: the fewest multiple of 8 rows over which both interior
+                                      chunk maps of 8 rows shrink to 2^-56 (their powers bound how far a
+                                      cut reaches: the rows kept equal the whole system's to far below
+                                      FP64 rounding).  Systems whose overlap exceeds R / 8, or whose head
+                                      of wall-dependent factors reaches the second window, keep their
+                                      one-CTA or cluster shape.  Windows are laid out at factor time, which
+                                      then reads the overlaps back and so waits for the plan's stream (a
+                                      factorisation under a stream capture lays out none).  Before
+                                      pent_plan_bind (the workspace reserves R / 8 overlap rows a side). */
+  PENT_OPT_WINDOWS = 13            /* read only: windows of the current factorisation (0: none) */
 };
 pent_status pent_plan_set_option(pent_plan* plan, int key, int64_t value);
 pent_status pent_plan_get_option(const pent_plan* plan, int key, int64_t* value);
+
+/*
+ * Host only: the windows (PENT_OPT_WINDOW_WARPS) of an n-row system cut into windows of
+ * `window_rows` rows with `overlap` rows of overlap (both multiples of 8, 4 overlap <=
+ * window_rows).  The first window covers rows [0, window_rows) and keeps [0, window_rows -
+ * overlap); each next one starts `overlap` rows before the first row not yet kept and keeps
+ * window_rows - 2 overlap rows; the last ends at row n and keeps the rest, so the kept rows
+ * tile [0, n) once.  Writes, while `cap` lasts, four int32 per window into h_out4 (host memory,
+ * may be NULL): first row, rows, then the first and the end of the kept rows relative to the
+ * window; returns the number of windows, 0 when n <= window_rows (one CTA solves the system)
+ * or the sizes do not qualify.
+ */
+int64_t pent_window_layout(int64_t n, int window_rows, int overlap, int32_t* h_out4, int64_t cap);
 
 /*
  * The settings that solve system `system` (0 <= system < batch), as chosen by

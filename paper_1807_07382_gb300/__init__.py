@@ -17,14 +17,14 @@ from typing import Optional, Sequence
 
 from . import _lib
 from ._lib import (PENT_ENOCONV, PENT_ESINGULAR, PENT_F32_REFINE, PENT_F64, PENT_OK, PENT_OPT_BLOCK_WARPS,
-                   PENT_OPT_CLUSTER_WARPS, PENT_OPT_FP32_KERNEL,
+                   PENT_OPT_CLUSTER_WARPS, PENT_OPT_FP32_KERNEL, PENT_OPT_WINDOW_WARPS, PENT_OPT_WINDOWS,
                    PENT_OPT_PARTITION_ROWS, PENT_OPT_PERIODIC, PENT_OPT_REFINE_TOL_LOG2, PENT_OPT_RESIDUAL, PENT_OPT_ROWS_PER_THREAD,
                    PENT_OPT_THREADS_PER_SYSTEM,
                    PENT_OPT_UNROLL, PENT_RESIDUAL_F64,
                    PENT_RESIDUAL_FF, PentError, check)
 
 __all__ = ["Plan", "PentError", "PENT_F64", "PENT_F32_REFINE", "PENT_RESIDUAL_FF", "PENT_RESIDUAL_F64",
-           "library_path", "load_library", "adi_plans_factor", "adi_step_2d", "adi_steps_2d", "ADI2D"]
+           "library_path", "load_library", "window_layout", "adi_plans_factor", "adi_step_2d", "adi_steps_2d", "ADI2D"]
 
 __version__ = "0.1.0"
 
@@ -265,6 +265,18 @@ def adi_step_2d(px: Plan, py: Plan, C, gamma: float, dt: float, dx: float, max_r
     check(_lib.load().adi_step_2d(px._h, py._h, _dev_ptr(C, "C", torch.float64), nx, ny, float(gamma), float(dt),
                                   float(dx), int(max_refine)), "adi_step_2d")
     return C
+
+
+def window_layout(n: int, window_rows: int, overlap: int):
+    """The windows of an n-row system (pent_window_layout): an int32 array of rows (first row,
+    rows, first kept, end kept), the kept rows relative to the window; empty when n fits one CTA."""
+    import numpy as np
+    L = _lib.load()
+    cnt = int(L.pent_window_layout(int(n), int(window_rows), int(overlap), None, 0))
+    out = np.zeros((max(cnt, 0), 4), dtype=np.int32)
+    if cnt > 0:
+        L.pent_window_layout(int(n), int(window_rows), int(overlap), out.ctypes.data_as(ctypes.c_void_p), cnt)
+    return out
 
 
 def adi_plans_factor(px: Plan, py: Plan, gamma: float, dt: float, dx: float):

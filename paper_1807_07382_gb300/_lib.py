@@ -34,6 +34,8 @@ PENT_OPT_PERIODIC = 8
 PENT_OPT_CLUSTER_WARPS = 9
 PENT_OPT_FP32_KERNEL = 10
 PENT_OPT_CACHED_GRAPHS = 11
+PENT_OPT_WINDOW_WARPS = 12
+PENT_OPT_WINDOWS = 13
 PENT_MAX_CACHED_GRAPHS = 16
 
 # every symbol the header declares, with (restype, argtypes)
@@ -68,6 +70,7 @@ SIGNATURES = {
     "pent_clear_info": (_int, [_vp]),
     "pent_gbsv_batch_noalloc": (_int, [_i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "pent_probe_fp64_fma": (_int, [_i64, _i64, _vp, _vp, ctypes.POINTER(_dbl)]),
+    "pent_window_layout": (_i64, [_i64, _int, _int, _vp, _i64]),
     "pent_plan_destroy": (None, [_vp]),
     "pent_status_string": (ctypes.c_char_p, [_int]),
     "pent_version": (ctypes.c_char_p, []),

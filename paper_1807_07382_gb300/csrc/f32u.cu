@@ -85,6 +85,8 @@ struct UCtx {
   float4* fsl;        // chain factor slots (shared memory)
   const float4* gq;   // the system's factor block (k_factor32 layout)
   int PT;            // threads of the factor block
+  int tg0;           // factor-block thread of this CTA's lane 0 (a window's first row / L)
+  bool lw, rw;       // the CTA's first / last row is the system's wall (else a window's cut)
   int phase;
   float2* tot;   // [4][W] warp totals of one scan (rotating)
   float2* hand;  // [8] chain hand-over slots across warps
@@ -95,12 +97,13 @@ template <int L>
 __device__ __forceinline__ void load_own(const UCtx& cx, float (&A)[L], float (&B)[L], float& bnext) {
 #pragma unroll
   for (int jq = 0; jq < L / 4; ++jq) {
-    const float4 qa = __ldg(cx.gq + (int64_t)(jq * 2 + 0) * cx.PT + cx.t),
-                 qb = __ldg(cx.gq + (int64_t)(jq * 2 + 1) * cx.PT + cx.t);
+    const float4 qa = __ldg(cx.gq + (int64_t)(jq * 2 + 0) * cx.PT + cx.tg0 + cx.t),
+                 qb = __ldg(cx.gq + (int64_t)(jq * 2 + 1) * cx.PT + cx.tg0 + cx.t);
     A[4 * jq] = qa.x; A[4 * jq + 1] = qa.y; A[4 * jq + 2] = qa.z; A[4 * jq + 3] = qa.w;
     B[4 * jq] = qb.x; B[4 * jq + 1] = qb.y; B[4 * jq + 2] = qb.z; B[4 * jq + 3] = qb.w;
   }
-  bnext = (cx.t + 1 < cx.PT) ? __ldg(reinterpret_cast<const float*>(cx.gq + (int64_t)cx.PT + (cx.t + 1))) : 0.f;
+  const int tn = cx.tg0 + cx.t + 1;
+  bnext = (tn < cx.PT) ? __ldg(reinterpret_cast<const float*>(cx.gq + (int64_t)cx.PT + tn)) : 0.f;
 }
 
 // Shared-memory factor slot of a chain lane, or -1 (then the factors come from global memory).
@@ -332,10 +335,12 @@ __device__ __forceinline__ void solve_u(float (&v)[L], UCtx& cx, int W) {
 // Replace the ghost entries of the neighbour window w[0 .. L+3] (rows tg L - 2 ..
 // tg L + L + 1 of a system of n >= 4 rows) by the rows the cell-centred walls
 // reflect them to: rows -2, -1 are rows 1, 0; rows n, n+1 are rows n-1, n-2.
-// Written as selects on fixed positions, so the window stays in registers.
+// lw = false: row 0 is not the wall (nothing reflects there); n may lie beyond
+// every row of the window (no right wall).  Written as selects on fixed
+// positions, so the window stays in registers.
 template <int L>
-__device__ __forceinline__ void ghosts_u(float (&w)[L + 4], int tg, int n) {
-  if (tg == 0) {
+__device__ __forceinline__ void ghosts_u(float (&w)[L + 4], int tg, int n, bool lw) {
+  if (lw && tg == 0) {
     w[0] = w[3];
     w[1] = w[2];
   }
@@ -352,7 +357,8 @@ __device__ __forceinline__ float pick3(const float (&x)[L], int g) {
 
 // Float-float residual r = f - (I + sigma D4) xh of this thread's rows (xh in
 // FP32: the first refinement step), with the rows of the neighbouring threads
-// exchanged through shared memory and the walls' reflected ghosts.
+// exchanged through shared memory and the walls' reflected ghosts; beyond a
+// window's cut the rows count as zero (the window's own truncated system).
 template <int L>
 __device__ __forceinline__ void residual_u(const float4* fsm, const float (&xh)[L], float (&r)[L], float sgh,
                                            float sgl, const UCtx& cx, float4* edge, int P) {
@@ -377,7 +383,7 @@ __device__ __forceinline__ void residual_u(const float4* fsm, const float (&xh)[
 #pragma unroll
   for (int j = 0; j < L; ++j) wh[j + 2] = xh[j];
   if (n >= 4) {
-    ghosts_u<L>(wh, t, n);
+    ghosts_u<L>(wh, t, cx.rw ? n : (1 << 29), cx.lw);
   } else {  // one thread holds the whole system: every stencil column reflects into rows 0 .. n-1
 #pragma unroll
     for (int q = 0; q < L + 4; ++q) wh[q] = pick3<L>(xh, reflect_row(q - 2, n));
@@ -406,11 +412,25 @@ __device__ __forceinline__ int fexp(float h) { return (int)((__float_as_uint(h) 
 // kernel two CTAs of up to 16 warps (64 registers a thread).
 constexpr int u_min_blocks(int WT) { return WT > 0 ? PENT_U_WARPS_PER_SM / WT : 2; }
 
-template <int L, int WT, int REF, int IN, int OUT>
+// WIN = 1: CTA b solves window win[b] = (system, first row w0, rows m | overlap rows O << 16)
+// of a long system: rows w0 .. w0 + m - 1 as one system of m rows whose cuts (a first row
+// other than 0, a last one other than n - 1) enter and leave with zero states, writing out
+// only the rows at least O from a cut.  halo: the overlap rows of every window copied out
+// before an in-place solve ([window][left, right][omax]), or nullptr (read from f).
+struct UWinArgs {
+  const int4* win;
+  const int32_t* fshape;  // [nfac] threads | L << 16 of each factor block
+  const double* halo;
+  int omax;
+};
+
+template <int L, int WT, int REF, int IN, int OUT, int WIN>
 __global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, u_min_blocks(WT))
     k_solve32u(F32Tables T, const float4* __restrict__ urec, int32_t* __restrict__ kscale,
-               const int32_t* __restrict__ sys, int shared, const double* f, double* x, int vec_io, int Wrt) {
+               const int32_t* __restrict__ sys, int shared, const double* f, double* x, int vec_io, int Wrt,
+               UWinArgs wa) {
   static_assert(L % 4 == 0, "rows per thread must be a multiple of 4");
+  static_assert(!WIN || (IN == 0 && OUT == 0), "windows read and write FP64");
   const int W = WT > 0 ? WT : Wrt, P = 32 * W;  // WT = 0: the warp count is a launch parameter
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4* rec_sm = reinterpret_cast<float4*>(smem_raw);        // [kURecFloat4]
@@ -428,9 +448,24 @@ __global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, u_min_blocks(WT))
   cx.phase = 0;
   cx.tot = tot;
   cx.hand = hand;
-  const int64_t s = sys[blockIdx.x];
+  int64_t s;
+  int n, w0 = 0, O = 0;  // rows of the CTA's system (or window), its first row, its overlap
+  cx.tg0 = 0;
+  cx.lw = cx.rw = true;
+  if (WIN) {
+    const int4 d = wa.win[blockIdx.x];
+    s = d.x;
+    w0 = d.y;
+    n = d.z & 0xffff;
+    O = d.z >> 16;
+    cx.lw = w0 == 0;
+    cx.rw = w0 + n == T.n[s];
+    cx.tg0 = w0 / L;
+  } else {
+    s = sys[blockIdx.x];
+    n = T.n[s];
+  }
   const int64_t ms = shared ? 0 : s;
-  const int n = T.n[s];
   cx.n = n;
   const float4* grec = urec + ms * kURecFloat4;
   for (int k = t; k < kURecFloat4; k += P) rec_sm[k] = __ldg(grec + k);
@@ -447,10 +482,10 @@ __global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, u_min_blocks(WT))
   const float2 sgp = __ldg(T.sig2 + ms);
   cx.sg = sgp.x;
   cx.gq = reinterpret_cast<const float4*>(T.fac) + T.foff[ms];
-  cx.PT = P;
+  cx.PT = WIN ? (wa.fshape[ms] & 0xffff) : P;
   cx.T1 = (n - 1) / L;
-  cx.H = min((K + L - 1) / L, cx.T1 + 1);
-  cx.T0 = max(n >= 3 ? (n - 3) / L : 0, cx.H);
+  cx.H = cx.lw ? min((K + L - 1) / L, cx.T1 + 1) : 0;             // a cut: no head chain
+  cx.T0 = cx.rw ? max(n >= 3 ? (n - 3) / L : 0, cx.H) : cx.T1 + 1;  // a cut: no tail chain
   const int i0 = t * L;
   {  // the chain lanes' factors, loaded once for all four sweeps
     const int k = fslot(cx, t);
@@ -473,18 +508,24 @@ __global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, u_min_blocks(WT))
   int kshift;
   bool store_k = false;
   if (IN == 0) {
-    const double* fs = f + T.off[s];
+    const double* src = f + T.off[s] + w0 + i0;  // this thread's first row
+    if (WIN && wa.halo) {  // overlap rows (whole threads: O and the cuts are multiples of L)
+      const bool lh = !cx.lw && i0 < O, rh = !cx.rw && i0 >= n - O;
+      const double* hb = wa.halo + (int64_t)blockIdx.x * 2 * wa.omax;
+      if (lh) src = hb + i0;
+      if (rh) src = hb + wa.omax + (i0 - (n - O));
+    }
     double fv[L];
     if (vec_io && i0 + L <= n) {
 #pragma unroll
       for (int j = 0; j < L; j += 2) {
-        const double2 q = *reinterpret_cast<const double2*>(fs + i0 + j);
+        const double2 q = *reinterpret_cast<const double2*>(src + j);
         fv[j] = q.x;
         fv[j + 1] = q.y;
       }
     } else {
 #pragma unroll
-      for (int j = 0; j < L; ++j) fv[j] = (i0 + j < n) ? fs[i0 + j] : 0.0;
+      for (int j = 0; j < L; ++j) fv[j] = (i0 + j < n) ? src[j] : 0.0;
     }
     int emax = 0;
 #pragma unroll
@@ -585,17 +626,18 @@ __global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, u_min_blocks(WT))
 
   // ---- store ----
   if (OUT == 0) {
-    double* xs = x + T.off[s];
+    double* xs = x + T.off[s] + w0;
+    const int o0 = cx.lw ? 0 : O, o1 = cx.rw ? n : n - O;  // rows written out (a window: its own rows)
     double xv[L];
 #pragma unroll
     for (int j = 0; j < L; ++j) xv[j] = ff_to_double_shift(xh[j], xl[j], kshift);
-    if (vec_io && i0 + L <= n) {
+    if (vec_io && i0 >= o0 && i0 + L <= o1) {
 #pragma unroll
       for (int j = 0; j < L; j += 2) *reinterpret_cast<double2*>(xs + i0 + j) = make_double2(xv[j], xv[j + 1]);
     } else {
 #pragma unroll
       for (int j = 0; j < L; ++j)
-        if (i0 + j < n) xs[i0 + j] = xv[j];
+        if (i0 + j >= o0 && i0 + j < o1) xs[i0 + j] = xv[j];
     }
   } else {
     float* xs = reinterpret_cast<float*>(x + T.off[s]);
@@ -632,7 +674,17 @@ __device__ __forceinline__ double norm2(const M2& m) {
 // pairs that ends at row n - 3), the interior pair, and the powers of the
 // interior chunk maps of L rows -- forward on (g_{i-2}, g_{i-1}), back on
 // (x_{i+1}, x_{i+2}), the recurrences of pass_own with constant factors.
-__global__ void k_uplan32(F32Tables T, int64_t nfac, const int32_t* __restrict__ shape, float4* __restrict__ urec) {
+// uwin (if set): (K, O) per factor block, O the overlap rows a window of the system needs: the
+// fewest whole chunks k L with |M^k| <= 2^-56 for both chunk maps (largest entry), 0 if more
+// than kUWinChunks chunks or no interior.  A window's cut enters as a zero state; the error it
+// leaves decays as the chunk maps' powers (their spectral radius is the decay rate of the
+// inverse's entries), so the rows at least O from a cut differ from the whole system's by
+// well below FP64 rounding.
+constexpr int kUWinChunks = 64;
+constexpr double kUWinTol = 1.3877787807814457e-17;  // 2^-56
+
+__global__ void k_uplan32(F32Tables T, int64_t nfac, const int32_t* __restrict__ shape, float4* __restrict__ urec,
+                          int2* __restrict__ uwin) {
   const int64_t s = blockIdx.x * (int64_t)(blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (s >= nfac) return;
@@ -690,6 +742,21 @@ __global__ void k_uplan32(F32Tables T, int64_t nfac, const int32_t* __restrict__
   }
   const int flags = nl[0] | (nl[1] << 8) | ((int)small[0] << 16) | ((int)small[1] << 17);
   R[0] = make_float4(ia, bi, __int_as_float(K), __int_as_float(flags));
+  if (uwin) {
+    int O = 0;
+    if (K <= n - 3) {
+      M2 qf = Mf, qb = Mb;
+      for (int k = 1; k <= kUWinChunks; ++k) {
+        if (fmax(norm2(qf), norm2(qb)) <= kUWinTol) {
+          O = k * L;
+          break;
+        }
+        qf = mul2(Mf, qf);
+        qb = mul2(Mb, qb);
+      }
+    }
+    uwin[s] = make_int2(K, O);
+  }
 }
 
 template <int L, int WT, int REF, int IN, int OUT>
@@ -698,9 +765,39 @@ cudaError_t launch_u(const F32Tables& T, const float4* urec, int32_t* kscale, co
   const int vec = ((((uintptr_t)f) | ((uintptr_t)x)) % 16 == 0) && b.even_offsets;
   const int W = WT > 0 ? WT : b.W;
   const size_t smem = usmem_bytes(W, L);
-  k_solve32u<L, WT, REF, IN, OUT><<<(unsigned)b.count, 32 * W, smem, st>>>(T, urec, kscale, sys + b.first, shared, f,
-                                                                          x, vec, W);
+  k_solve32u<L, WT, REF, IN, OUT, 0><<<(unsigned)b.count, 32 * W, smem, st>>>(T, urec, kscale, sys + b.first, shared,
+                                                                             f, x, vec, W, UWinArgs{});
   return cudaGetLastError();
+}
+
+template <int WT>
+cudaError_t launch_w(const F32Tables& T, const float4* urec, const UWinArgs& wa, int64_t nwin, int shared,
+                     int even_offsets, const double* f, double* x, int max_refine, cudaStream_t st) {
+  const int vec = ((((uintptr_t)f) | ((uintptr_t)x)) % 16 == 0) && even_offsets;
+  const size_t smem = usmem_bytes(WT, 8);
+  if (max_refine > 0)
+    k_solve32u<8, WT, 1, 0, 0, 1><<<(unsigned)nwin, 32 * WT, smem, st>>>(T, urec, nullptr, nullptr, shared, f, x, vec,
+                                                                         WT, wa);
+  else
+    k_solve32u<8, WT, 0, 0, 0, 1><<<(unsigned)nwin, 32 * WT, smem, st>>>(T, urec, nullptr, nullptr, shared, f, x, vec,
+                                                                         WT, wa);
+  return cudaGetLastError();
+}
+
+// Copy the overlap rows of every window out of f (before an in-place windowed solve):
+// one CTA per window, halo[w][0][0 .. O) = rows w0 .. w0 + O - 1 (after a cut at w0),
+// halo[w][1][0 .. O) = the last O rows (before a cut at the window's end).
+__global__ void k_uwin_halo(F32Tables T, const int4* __restrict__ win, int omax, const double* __restrict__ f,
+                            double* __restrict__ halo) {
+  const int4 d = win[blockIdx.x];
+  const int n = T.n[d.x], m = d.z & 0xffff, O = d.z >> 16;
+  const double* fs = f + T.off[d.x] + d.y;
+  double* hb = halo + (int64_t)blockIdx.x * 2 * omax;
+  for (int i = threadIdx.x; i < 2 * O; i += blockDim.x) {
+    const bool right = i >= O;
+    if (!right && d.y > 0) hb[i] = fs[i];
+    if (right && d.y + m < n) hb[omax + (i - O)] = fs[m - O + (i - O)];
+  }
 }
 
 template <int L, int WT>
@@ -729,10 +826,32 @@ bool solve32u_supported(const F32Bucket& b) {
   return false;
 }
 
-cudaError_t launch_uplan32(const F32Tables& T, const int32_t* shape, int64_t nfac, float4* urec, cudaStream_t st) {
+cudaError_t launch_uplan32(const F32Tables& T, const int32_t* shape, int64_t nfac, float4* urec, int2* uwin,
+                           cudaStream_t st) {
   const int warps = 4;
-  k_uplan32<<<(unsigned)((nfac + warps - 1) / warps), 32 * warps, 0, st>>>(T, nfac, shape, urec);
+  k_uplan32<<<(unsigned)((nfac + warps - 1) / warps), 32 * warps, 0, st>>>(T, nfac, shape, urec, uwin);
   return cudaGetLastError();
+}
+
+bool solve32w_supported(int W) { return W == 4 || W == 8 || W == 16; }
+
+cudaError_t launch_solve32w(const F32Tables& T, const float4* urec, const int32_t* fshape, const int4* win,
+                            int64_t nwin, int W, int omax, int shared, int even_offsets, const double* f, double* x,
+                            double* halo, int max_refine, cudaStream_t st) {
+  if (nwin == 0) return cudaSuccess;
+  if (max_refine > 1 || !solve32w_supported(W) || omax <= 0 || omax % 8) return cudaErrorInvalidValue;
+  const bool in_place = f == x;
+  if (in_place) {
+    k_uwin_halo<<<(unsigned)nwin, 128, 0, st>>>(T, win, omax, f, halo);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  const UWinArgs wa{win, fshape, in_place ? halo : nullptr, omax};
+  switch (W) {
+    case 4: return launch_w<4>(T, urec, wa, nwin, shared, even_offsets, f, x, max_refine, st);
+    case 8: return launch_w<8>(T, urec, wa, nwin, shared, even_offsets, f, x, max_refine, st);
+    default: return launch_w<16>(T, urec, wa, nwin, shared, even_offsets, f, x, max_refine, st);
+  }
 }
 
 cudaError_t launch_solve32u(const F32Tables& T, const float4* urec, int32_t* kscale, const int32_t* sys,

@@ -133,7 +133,10 @@ cudaError_t launch_solve32r(const F32Tables& T, const int32_t* sys, const F32Buc
 // flags), then the powers M^(2^l) (l = 0..5) and M^k (k = 0..31) of the forward and of the back
 // chunk map.  kscale: per system, the power of two by which a field kept as float pairs is scaled.
 constexpr int kURecFloat4 = 77;
-cudaError_t launch_uplan32(const F32Tables& T, const int32_t* shape, int64_t nfac, float4* urec, cudaStream_t st);
+// uwin (or nullptr): per factor block (K, O), O the overlap rows of a window of the system (0: none
+// keeps the windowed solve within FP64 rounding of the whole system's).
+cudaError_t launch_uplan32(const F32Tables& T, const int32_t* shape, int64_t nfac, float4* urec, int2* uwin,
+                           cudaStream_t st);
 // True if the bucket's CTA shape has an instantiation of the interior-constant kernel.
 bool solve32u_supported(const F32Bucket& b);
 // in_ff / out_ff: f / x hold float pairs (h, l) per row scaled by 2^-kscale[s] instead of FP64
@@ -141,6 +144,14 @@ bool solve32u_supported(const F32Bucket& b);
 cudaError_t launch_solve32u(const F32Tables& T, const float4* urec, int32_t* kscale, const int32_t* sys,
                             const F32Bucket& b, int shared, const double* f, double* x, int max_refine, int in_ff,
                             int out_ff, cudaStream_t st);
+// Windowed solve of long systems (csrc/f32u.cu): CTA k of W warps (8 rows a thread) solves window
+// win[k] = (system, first row, rows | overlap rows << 16) and writes the rows at least the overlap
+// from its cuts; fshape: each factor block's threads | L << 16.  An in-place solve (f == x) first
+// copies the overlap rows into halo ([nwin][2][omax] doubles).  max_refine 0 or 1.
+bool solve32w_supported(int W);
+cudaError_t launch_solve32w(const F32Tables& T, const float4* urec, const int32_t* fshape, const int4* win,
+                            int64_t nwin, int W, int omax, int shared, int even_offsets, const double* f, double* x,
+                            double* halo, int max_refine, cudaStream_t st);
 // Periodic FP32 plans: factors of E, the columns of Z = E^{-1} k and S^{-1} (k_factor32_periodic).
 cudaError_t launch_factor32_periodic(const F32Tables& T, const int32_t* shape, int64_t nsys, const double* sigma,
                                      cudaStream_t st);

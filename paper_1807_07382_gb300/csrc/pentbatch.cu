@@ -100,6 +100,16 @@ struct pent_plan {
   int64_t tps_override = 0;       // PENT_OPT_THREADS_PER_SYSTEM for FP32 (0: automatic)
   int cluster_warps = 8;          // PENT_OPT_CLUSTER_WARPS
   int f32_kernel = 0;             // PENT_OPT_FP32_KERNEL: 0 interior-constant kernel where it applies, 1 general
+  // windowed solve of long systems (csrc/f32u.cu): CTAs of win_warps warps, 8 rows a thread, each
+  // solving one window of a system longer than one CTA; built at factor time from each system's
+  // overlap (k_uplan32)
+  int win_warps = 4;              // PENT_OPT_WINDOW_WARPS (0: off)
+  int win_omax = 0;               // overlap rows reserved per window side (window rows / 8)
+  int64_t win_cap = 0;            // windows the workspace holds
+  int64_t nwin = 0;               // windows of the current factorisation (0: none)
+  int win_even = 1;               // every windowed system starts at an even row
+  std::vector<int32_t> wsys32;    // the other systems, bucket order
+  std::vector<F32Bucket> wbuckets;
   std::vector<cudaStream_t> side; // extra streams so that bucket launches overlap
   std::vector<cudaEvent_t> ev;    // fork/join events
   std::vector<cudaStream_t> pipe; // slices of pent_solve_host_batch (copy in, solve, copy out)
@@ -108,7 +118,7 @@ struct pent_plan {
   // workspace regions
   Region r_info, r_perm, r_off, r_n, r_goff, r_glen, r_sigma, r_fwd, r_bwd, r_scr, r_fac32, r_sig32, r_foff, r_shape,
       r_sys32, r_adi, r_cmap, r_swU, r_swE, r_pck, r_pcc, r_pcbase, r_pcnum, r_pcmap, r_pU, r_pE, r_per, r_psinv,
-      r_pg, r_rhs, r_psinv32, r_urec, r_kscale;
+      r_pg, r_rhs, r_psinv32, r_urec, r_kscale, r_uwin, r_win, r_whalo, r_wsys32;
   size_t ws_bytes = 0;
   // binding / state
   unsigned char* ws = nullptr;
@@ -391,6 +401,33 @@ void build_f64_runs(pent_plan* p) {
   }
 }
 
+// Windows of an n-row system, R rows each with O overlap rows (multiples of 8, 4 O <= R): the
+// first covers rows [0, R) and keeps [0, R - O); each next one starts O rows before the first
+// row not yet kept and keeps R - 2 O rows; the last ends at row n and keeps the rest.  Writes
+// (first row, rows, first kept, end kept) relative to the window per window while cap lasts
+// and returns the count; 0 if n <= R (one CTA solves the system) or the sizes do not qualify.
+int64_t window_layout(int64_t n, int R, int O, int32_t* out4, int64_t cap) {
+  if (n <= R || R <= 0 || R % 8 || O <= 0 || O % 8 || 4 * O > R) return 0;
+  int64_t k = 0;
+  auto emit = [&](int64_t w0, int64_t m, int64_t o0, int64_t o1) {
+    if (out4 && k < cap) {
+      out4[4 * k] = (int32_t)w0;
+      out4[4 * k + 1] = (int32_t)m;
+      out4[4 * k + 2] = (int32_t)o0;
+      out4[4 * k + 3] = (int32_t)o1;
+    }
+    ++k;
+  };
+  emit(0, R, 0, R - O);
+  int64_t a = R - O;  // first row not yet kept
+  while (n - a > R - O) {
+    emit(a - O, R, O, R - O);
+    a += R - 2 * O;
+  }
+  emit(a - O, n - a + O, O, n - a + O);
+  return k;
+}
+
 bool build_f32_shapes(pent_plan* p) {
   const int64_t nfac = p->shared ? 1 : p->batch;
   p->shape.assign(nfac, Shape{0, 0, 0});
@@ -481,6 +518,18 @@ void layout(pent_plan* p) {
     if (!p->periodic) {  // interior-constant kernel: per factor block record, per system field scale
       take(p->r_urec, (size_t)nfac * kURecFloat4 * sizeof(float4));
       take(p->r_kscale, (size_t)p->batch * sizeof(int32_t));
+      // windows: as many as the largest overlap could need (the count grows with the overlap)
+      p->win_cap = 0;
+      p->win_omax = 0;
+      if (p->win_warps > 0) {
+        const int R = 256 * p->win_warps;
+        p->win_omax = R / 8;
+        for (int64_t s = 0; s < p->batch; ++s) p->win_cap += window_layout(p->n[s], R, p->win_omax, nullptr, 0);
+      }
+      take(p->r_uwin, (size_t)nfac * sizeof(int2));
+      take(p->r_win, (size_t)p->win_cap * sizeof(int4));
+      take(p->r_whalo, (size_t)p->win_cap * 2 * p->win_omax * sizeof(double));
+      take(p->r_wsys32, (size_t)(p->win_cap > 0 ? p->batch : 0) * sizeof(int32_t));
     }
   }
   // ADI scratch, for shared-matrix plans whose batch is the number of columns of
@@ -606,6 +655,10 @@ pent_status pent_plan_create(pent_plan** out, int64_t batch, const int64_t* n_pe
 
 size_t pent_plan_workspace_bytes(const pent_plan* p) { return p ? p->ws_bytes : 0; }
 
+int64_t pent_window_layout(int64_t n, int window_rows, int overlap, int32_t* h_out4, int64_t cap) {
+  return window_layout(n, window_rows, overlap, h_out4, cap < 0 ? 0 : cap);
+}
+
 pent_status pent_plan_bind(pent_plan* p, void* ws, void* stream) {
   if (!p || !ws) return PENT_EINVAL;
   if (((uintptr_t)ws) % kAlign) return PENT_EINVAL;
@@ -641,7 +694,7 @@ pent_status pent_plan_bind(pent_plan* p, void* ws, void* stream) {
   }
   // side streams (and fork/join events) so that several launches of one solve overlap
   p->drop_streams();
-  const size_t nlaunch = p->precision == PENT_F64 ? p->runs.size() : p->buckets.size();
+  const size_t nlaunch = p->precision == PENT_F64 ? p->runs.size() : p->buckets.size() + (p->win_cap > 0 ? 1 : 0);
   const int nside = (int)std::min<size_t>(3, nlaunch > 1 ? nlaunch - 1 : 0);
   for (int k = 0; k < nside && e == cudaSuccess; ++k) {
     cudaStream_t ss;
@@ -668,6 +721,7 @@ pent_status pent_plan_bind(pent_plan* p, void* ws, void* stream) {
   if (e != cudaSuccess) return PENT_ECUDA;
   p->bound = true;
   p->factored = 0;
+  p->nwin = 0;
   return PENT_OK;
 }
 
@@ -755,6 +809,13 @@ pent_status pent_plan_set_option(pent_plan* p, int key, int64_t value) {
       ++p->cfg_version;
       p->drop_graphs();
       return PENT_OK;
+    case PENT_OPT_WINDOW_WARPS:
+      // changes the workspace size: only before binding
+      if (p->bound || p->precision != PENT_F32_REFINE || p->periodic) return PENT_EINVAL;
+      if (value != 0 && !solve32w_supported((int)value)) return PENT_EINVAL;
+      p->win_warps = (int)value;
+      layout(p);
+      return PENT_OK;
     case PENT_OPT_FP32_KERNEL:
       if (p->precision != PENT_F32_REFINE || (value != 0 && value != 1)) return PENT_EINVAL;
       p->f32_kernel = (int)value;
@@ -785,6 +846,8 @@ pent_status pent_plan_get_option(const pent_plan* p, int key, int64_t* value) {
     case PENT_OPT_CLUSTER_WARPS: *value = p->cluster_warps; return PENT_OK;
     case PENT_OPT_FP32_KERNEL: *value = p->f32_kernel; return PENT_OK;
     case PENT_OPT_CACHED_GRAPHS: *value = (int64_t)p->graphs.size(); return PENT_OK;
+    case PENT_OPT_WINDOW_WARPS: *value = p->win_warps; return PENT_OK;
+    case PENT_OPT_WINDOWS: *value = p->nwin; return PENT_OK;
   }
   return PENT_EINVAL;
 }
@@ -826,6 +889,79 @@ static pent_status reset_info(pent_plan* p) {
   return cuda_status(e);
 }
 
+// Windows for the current factorisation: every system longer than one window CTA whose overlap
+// (from k_uplan32) fits the reserved room, and whose head of non-constant factors ends before its
+// second window starts, is cut into windows; the others keep their buckets.  The overlaps are
+// read back, which waits for the plan's stream; under a stream capture no windows are built.
+static cudaError_t build_windows(pent_plan* p) {
+  const int64_t nprev = p->nwin;
+  p->nwin = 0;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(p->stream, &cs);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusNone) {
+    if (nprev) ++p->cfg_version;
+    return cudaSuccess;
+  }
+  const int64_t nfac = p->shared ? 1 : p->batch;
+  std::vector<int2> kw((size_t)nfac);
+  e = cudaMemcpyAsync(kw.data(), p->at<int2>(p->r_uwin), (size_t)nfac * sizeof(int2), cudaMemcpyDeviceToHost,
+                      p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);  // also: no solve still reads the old windows
+  if (e != cudaSuccess) return e;
+  const int R = 256 * p->win_warps;
+  std::vector<int32_t> win, geo;  // four int32 per window
+  std::vector<char> windowed((size_t)p->batch, 0);
+  int even = 1;
+  for (int64_t s = 0; s < p->batch; ++s) {
+    const int64_t n = p->n[s];
+    if (n <= R) continue;
+    const int64_t ms = p->shared ? 0 : s;
+    const int K = kw[ms].x, O = kw[ms].y;
+    if (p->shape[ms].L != 8 || O <= 0 || O > p->win_omax || K > R - 2 * O) continue;
+    const int64_t cnt = window_layout(n, R, O, nullptr, 0);
+    geo.resize((size_t)(4 * cnt));
+    window_layout(n, R, O, geo.data(), cnt);
+    for (int64_t k = 0; k < cnt; ++k) {
+      win.push_back((int32_t)s);
+      win.push_back(geo[4 * k]);
+      win.push_back(geo[4 * k + 1] | (O << 16));
+      win.push_back(0);
+    }
+    windowed[s] = 1;
+    if (p->off[s] & 1) even = 0;
+  }
+  const int64_t nw = (int64_t)win.size() / 4;
+  if (nw > p->win_cap) return cudaErrorInvalidValue;  // not reached: the room is sized for the largest overlap
+  p->wsys32.clear();
+  p->wbuckets.clear();
+  for (const F32Bucket& b : p->buckets) {
+    F32Bucket q = b;
+    q.first = (int64_t)p->wsys32.size();
+    q.count = 0;
+    q.even_offsets = 1;
+    for (int64_t i = b.first; i < b.first + b.count; ++i) {
+      const int32_t sy = p->sys32[i];
+      if (windowed[sy]) continue;
+      p->wsys32.push_back(sy);
+      ++q.count;
+      if (p->off[sy] & 1) q.even_offsets = 0;
+    }
+    if (q.count) p->wbuckets.push_back(q);
+  }
+  if (nw > 0) {
+    e = cudaMemcpy(p->at<int4>(p->r_win), win.data(), (size_t)nw * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !p->wsys32.empty())
+      e = cudaMemcpy(p->at<int32_t>(p->r_wsys32), p->wsys32.data(), p->wsys32.size() * sizeof(int32_t),
+                     cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+  }
+  p->nwin = nw;
+  p->win_even = even;
+  if (nw || nprev) ++p->cfg_version;  // step graphs hold the launches of the old layout
+  return cudaSuccess;
+}
+
 static pent_status factor_common(pent_plan* p, const double* a, const double* b, const double* c, const double* d,
                                  const double* e, const double* sigma) {
   if (!p) return PENT_EINVAL;
@@ -860,7 +996,8 @@ static pent_status factor_common(pent_plan* p, const double* a, const double* b,
     err = launch_factor32(p->f32(), p->at<int32_t>(p->r_shape), p->shared ? 1 : p->batch, sg, p->stream);
     if (err == cudaSuccess)
       err = launch_uplan32(p->f32(), p->at<int32_t>(p->r_shape), p->shared ? 1 : p->batch, p->at<float4>(p->r_urec),
-                           p->stream);
+                           p->at<int2>(p->r_uwin), p->stream);
+    if (err == cudaSuccess && p->win_cap > 0) err = build_windows(p);
   }
   if (err != cudaSuccess) return PENT_ECUDA;
   p->factored = sigma ? 2 : 1;
@@ -881,18 +1018,28 @@ pent_status pent_factor_hyperdiff(pent_plan* p, const double* d_sigma) {
   return factor_common(p, nullptr, nullptr, nullptr, nullptr, nullptr, d_sigma);
 }
 
-// True if bucket b of an FP32 plan is solved by the interior-constant kernel (csrc/f32u.cu).
-static bool use_u(const pent_plan* p, const F32Bucket& b, int max_refine) {
+// True if the plan's FP32 solves with max_refine steps may take the interior-constant kernel
+// (csrc/f32u.cu), single-CTA systems and windows alike.
+static bool u_path(const pent_plan* p, int max_refine) {
   return p->precision == PENT_F32_REFINE && !p->periodic && p->residual == PENT_RESIDUAL_FF && p->f32_kernel == 0 &&
-         max_refine <= 1 && solve32u_supported(b);
+         max_refine <= 1;
 }
 
-// One FP32 solve of bucket b (systems [b.first, b.first + b.count) of the bucket order).  in_ff /
-// out_ff: f / x of the bucket's systems hold scaled float pairs (interior-constant kernel only).
+// True if bucket b of an FP32 plan is solved by the interior-constant kernel.
+static bool use_u(const pent_plan* p, const F32Bucket& b, int max_refine) {
+  return u_path(p, max_refine) && solve32u_supported(b);
+}
+
+// True if the solve runs the long systems' windows (and the other systems' buckets).
+static bool use_windows(const pent_plan* p, int max_refine) { return p->nwin > 0 && u_path(p, max_refine); }
+
+// One FP32 solve of bucket b (systems [b.first, b.first + b.count) of the bucket order `sys`,
+// the plan's order by default).  in_ff / out_ff: f / x of the bucket's systems hold scaled
+// float pairs (interior-constant kernel only).
 static cudaError_t f32_bucket(pent_plan* p, const F32Bucket& b, const double* f, double* x, int max_refine, int in_ff,
-                              int out_ff, cudaStream_t st) {
+                              int out_ff, cudaStream_t st, const int32_t* sys = nullptr) {
   const F32Tables T = p->f32();
-  const int32_t* sys = p->at<int32_t>(p->r_sys32);
+  if (!sys) sys = p->at<int32_t>(p->r_sys32);
   if (use_u(p, b, max_refine))
     return launch_solve32u(T, p->at<float4>(p->r_urec), p->at<int32_t>(p->r_kscale), sys, b, p->shared, f, x,
                            max_refine, in_ff, out_ff, st);
@@ -918,10 +1065,20 @@ static pent_status solve_launch(pent_plan* p, const double* f, double* x, int ma
     });
   } else {
     if (p->periodic && p->residual == PENT_RESIDUAL_F64) return PENT_EINVAL;  // periodic: float-float residual
-    err = fork_join(p, p->buckets.size(), [&](size_t i, cudaStream_t st) {
-      const F32Bucket& b = p->buckets[i];
+    // windows of the long systems (FP64 in and out: a window reads its neighbours' rows) and the
+    // other systems' buckets, each launch on its own branch
+    const bool w = use_windows(p, max_refine);
+    const std::vector<F32Bucket>& bk = w ? p->wbuckets : p->buckets;
+    const int32_t* sys = p->at<int32_t>(w ? p->r_wsys32 : p->r_sys32);
+    const size_t nw = w ? 1 : 0;
+    err = fork_join(p, bk.size() + nw, [&](size_t i, cudaStream_t st) {
+      if (i < nw)
+        return launch_solve32w(p->f32(), p->at<float4>(p->r_urec), p->at<int32_t>(p->r_shape), p->at<int4>(p->r_win),
+                               p->nwin, p->win_warps, p->win_omax, p->shared, p->win_even, f, x,
+                               p->at<double>(p->r_whalo), max_refine, st);
+      const F32Bucket& b = bk[i - nw];
       const bool u = use_u(p, b, max_refine);
-      return f32_bucket(p, b, f, x, max_refine, u && in_ff, u && out_ff, st);
+      return f32_bucket(p, b, f, x, max_refine, u && in_ff, u && out_ff, st, sys);
     });
   }
   return cuda_status(err);

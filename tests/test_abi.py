@@ -5,6 +5,7 @@ import ctypes
 import re
 from pathlib import Path
 
+import numpy as np
 import pytest
 
 import paper_1807_07382_gb300 as pb
@@ -23,7 +24,7 @@ def L():
 def declared_functions():
     text = HEADER.read_text()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"^\s*(?:const\s+)?[a-z_]+\s*\*?\s*([a-z_0-9]+)\s*\(", text, flags=re.M)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_][a-z_0-9]*\s*\*?\s*([a-z_0-9]+)\s*\(", text, flags=re.M)
     return sorted(set(names))
 
 
@@ -217,3 +218,58 @@ def test_adi_plans_factor_and_graph_cache_query_check_arguments_on_the_host(L):
     assert L.pent_plan_set_option(px, _lib.PENT_OPT_CACHED_GRAPHS, 3) == _lib.PENT_EINVAL  # read only
     L.pent_plan_destroy(px)
     L.pent_plan_destroy(py)
+
+
+@pytest.mark.parametrize("R", [1024, 2048, 4096])
+def test_window_layout_tiles_every_length(L, R):
+    """pent_window_layout: the kept rows of the windows tile [0, n) once, every window has at
+    most R rows and lies inside the system, each cut is at least the overlap away from the
+    rows a window keeps, and windows start on multiples of 8 rows."""
+    for O in (8, 16, 96, R // 8, R // 4):
+        for n in list(range(R + 1, R + 40)) + [2 * R - 2 * O, 2 * R - 2 * O + 1, 3 * R, 5 * R + 7, 16384, 65536 + 3]:
+            w = pb.window_layout(n, R, O)
+            assert len(w) >= 2
+            kept = np.concatenate([np.arange(a + k0, a + k1) for a, m, k0, k1 in w])
+            assert np.array_equal(kept, np.arange(n))
+            for i, (a, m, k0, k1) in enumerate(w):
+                assert a % 8 == 0 and 0 < m <= R and a + m <= n
+                assert (a == 0) == (i == 0) and (a + m == n) == (i == len(w) - 1)
+                assert k0 == (0 if a == 0 else O) and k1 == (m if a + m == n else m - O)
+                assert k1 > k0
+            # the count never falls as the overlap grows (the workspace is sized for the largest)
+            if O < R // 4:
+                assert len(w) <= len(pb.window_layout(n, R, R // 4))
+    for n, R2, O in ((R, R, 8), (100, R, 8), (5 * R, R, 0), (5 * R, R, 12), (5 * R, R, R // 4 + 8), (5 * R, 1004, 8)):
+        assert len(pb.window_layout(n, R2, O)) == 0
+
+
+def test_window_warps_option_host_checks(L):
+    """PENT_OPT_WINDOW_WARPS: FP32+refine, non-periodic, before binding, 0 / 4 / 8 / 16; it
+    resizes the workspace by the windows' overlap room.  PENT_OPT_WINDOWS is read only (0
+    before any factorisation)."""
+    st, h = _create(L, batch=3, n=[16384, 1000, 5000], prec=1)
+    assert st == 0
+    v = ctypes.c_int64()
+    assert L.pent_plan_get_option(h, _lib.PENT_OPT_WINDOW_WARPS, ctypes.byref(v)) == 0 and v.value == 4
+    assert L.pent_plan_get_option(h, _lib.PENT_OPT_WINDOWS, ctypes.byref(v)) == 0 and v.value == 0
+    assert L.pent_plan_set_option(h, _lib.PENT_OPT_WINDOWS, 1) == _lib.PENT_EINVAL
+    sizes = {}
+    for w in (0, 4, 8, 16):
+        assert L.pent_plan_set_option(h, _lib.PENT_OPT_WINDOW_WARPS, w) == 0
+        sizes[w] = L.pent_plan_workspace_bytes(h)
+    # the reserve: per window 2 (R / 8) doubles of overlap rows and one int4, per system an int32
+    for w in (4, 8, 16):
+        R = 256 * w
+        nwin = sum(len(pb.window_layout(n, R, R // 8)) for n in (16384, 1000, 5000))
+        assert sizes[w] - sizes[0] >= nwin * 2 * (R // 8) * 8 - 3 * 256  # 256-byte aligned regions
+        assert sizes[w] - sizes[0] <= nwin * (2 * (R // 8) * 8 + 16) + 3 * 4 + 4096
+    for bad in (1, 2, 12, 32, -1):
+        assert L.pent_plan_set_option(h, _lib.PENT_OPT_WINDOW_WARPS, bad) == _lib.PENT_EINVAL
+    L.pent_plan_destroy(h)
+    st, h = _create(L, batch=2, n_uniform=8192)  # FP64
+    assert L.pent_plan_set_option(h, _lib.PENT_OPT_WINDOW_WARPS, 4) == _lib.PENT_EINVAL
+    L.pent_plan_destroy(h)
+    st, h = _create(L, batch=2, n_uniform=8192, prec=1)
+    assert L.pent_plan_set_option(h, _lib.PENT_OPT_PERIODIC, 1) == 0
+    assert L.pent_plan_set_option(h, _lib.PENT_OPT_WINDOW_WARPS, 4) == _lib.PENT_EINVAL  # periodic
+    L.pent_plan_destroy(h)

@@ -1,0 +1,183 @@
+"""GPU parity of the windowed FP32 solve of long systems (csrc/f32u.cu, k_solve32u with
+windows) against the CPU oracle.
+
+A system longer than one CTA of W warps x 8 rows (R = 256 W rows) is solved as windows of R
+rows, one CTA each, that overlap by O rows: a window enters and leaves its cuts with zero
+states and keeps only the rows at least O from a cut.  O is the fewest multiple of 8 rows
+over which both interior chunk maps shrink to 2^-56, so the rows kept agree with the whole
+system's direct solve far below FP64 rounding; the results are held to the same bar as every
+FP32+refine solve: 1e-12 relative (per system, max |x - x_ref| / max |x_ref|) after one
+refinement step for sigma in [1e-3, 10], and 1e-4 for the plain FP32 solve.  Systems whose
+decay is too slow for the window (the overlap above R / 8) keep the cluster path."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1807_07382_gb300 as pb  # noqa: E402
+from paper_1807_07382_gb300 import build  # noqa: E402
+
+TOL = 1e-12
+TOL_FP32 = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def sys_rel_err(x, ref, n_per_system):
+    off = oracle.offsets(n_per_system)
+    worst = 0.0
+    for s in range(len(off) - 1):
+        r = ref[off[s]:off[s + 1]]
+        d = np.max(np.abs(x[off[s]:off[s + 1]] - r))
+        worst = max(worst, d / max(np.max(np.abs(r)), 1e-300))
+    return worst
+
+
+def plan_for(ns, sigma, window_warps=None, kernel=0, shared=False):
+    opts = {pb.PENT_OPT_FP32_KERNEL: kernel}
+    if window_warps is not None:
+        opts[pb.PENT_OPT_WINDOW_WARPS] = window_warps
+    if shared:
+        plan = pb.Plan(int(ns[0]), batch=len(ns), shared=True, precision=pb.PENT_F32_REFINE, options=opts)
+    else:
+        plan = pb.Plan(list(ns), precision=pb.PENT_F32_REFINE, options=opts)
+    plan.factor_hyperdiff(dev(sigma))
+    return plan
+
+
+def workload(n, batch, seed_index, sigma_range=(1e-3, 10.0)):
+    return synth.hyperdiff_parametric(batch=batch, n=n, steps=1, seed_index=seed_index, sigma_range=sigma_range)
+
+
+@pytest.mark.parametrize("n", [1025, 1100, 2047, 2048, 2049, 3000, 4097, 8192, 12345, 16384])
+def test_windows_meet_the_bar(n):
+    """Lengths from just above one window (two windows, the last a sliver) to 16 windows,
+    out of place and in place (the overlap rows copied out first)."""
+    w = workload(n, 12, 40 + n % 7)
+    ref = oracle.hyperdiff_steps(w.n, w.sigma, w.field0, 1)
+    plan = plan_for(w.n, w.sigma)
+    assert plan.get_option(pb.PENT_OPT_WINDOWS) >= 2 * len(w.n)
+    x = plan.solve(dev(w.field0), max_refine=1)
+    st, _, _, used = plan.info()
+    assert st == pb.PENT_OK and used == 1
+    assert sys_rel_err(host(x), ref, w.n) <= TOL
+    x0 = plan.solve(dev(w.field0), max_refine=0)
+    assert sys_rel_err(host(x0), ref, w.n) <= TOL_FP32
+    xi = dev(w.field0)
+    plan.solve(xi, xi, max_refine=1)
+    assert sys_rel_err(host(xi), ref, w.n) <= TOL
+
+
+@pytest.mark.parametrize("window_warps", [4, 8, 16])
+def test_window_widths(window_warps):
+    """Every window width on the longest FP32 systems (30,000 rows) and ragged lengths."""
+    ns = np.array([30000, 9999, 4100, 20001])
+    sig = np.array([10.0, 1e-3, 0.5, 3.0])
+    f = synth.uniform(777, 0, int(ns.sum()), -1, 1)
+    ref = oracle.hyperdiff_steps(ns, sig, f, 1)
+    plan = plan_for(ns, sig, window_warps=window_warps)
+    R = 256 * window_warps
+    assert plan.get_option(pb.PENT_OPT_WINDOWS) >= sum(len(pb.window_layout(int(n), R, 8)) for n in ns)
+    x = dev(f)
+    plan.solve(x, x, max_refine=1)
+    assert sys_rel_err(host(x), ref, ns) <= TOL
+
+
+@pytest.mark.parametrize("steps", [1, 3, 8])
+def test_windowed_graph_steps_in_place(steps):
+    """pent_solve_steps runs in place: every step copies the overlap rows out before its
+    windows overwrite them.  Bar: steps x 1e-12 (each solve within 1e-12, carried forward),
+    and no worse than the same plan with windows off (clusters)."""
+    ns = np.array([16384, 5000, 700, 12000, 1024, 9000])
+    sig = synth.log_uniform(91, 0, len(ns), 1e-3, 10.0)
+    f = synth.uniform(92, 0, int(ns.sum()), -1, 1)
+    ref = oracle.hyperdiff_steps(ns, sig, f, steps)
+    errs = []
+    for ww in (4, 0):
+        plan = plan_for(ns, sig, window_warps=ww)
+        assert (plan.get_option(pb.PENT_OPT_WINDOWS) > 0) == (ww > 0)
+        x = dev(f)
+        plan.solve_steps(x, steps, max_refine=1)
+        assert plan.info()[0] == pb.PENT_OK
+        errs.append(sys_rel_err(host(x), ref, ns))
+    print("errors (windows, clusters):", errs)
+    assert errs[0] <= steps * TOL
+    assert errs[0] <= 1.5 * errs[1] + 1e-13
+
+
+def test_slow_decay_systems_keep_their_clusters():
+    """sigma = 300 needs an overlap above R / 8 = 128 rows for 4-warp windows: that system keeps
+    its cluster and is solved exactly as with windows off (bitwise), while its neighbours run in
+    windows and meet the bar."""
+    ns = np.array([8192, 8192, 6000])
+    sig = np.array([300.0, 0.01, 5.0])
+    f = synth.uniform(55, 0, int(ns.sum()), -1, 1)
+    plan = plan_for(ns, sig)
+    off = plan_for(ns, sig, window_warps=0)
+    nwin = plan.get_option(pb.PENT_OPT_WINDOWS)
+    assert 0 < nwin <= len(pb.window_layout(8192, 1024, 128)) + len(pb.window_layout(6000, 1024, 128))
+    assert off.get_option(pb.PENT_OPT_WINDOWS) == 0
+    a = host(plan.solve(dev(f), max_refine=1))
+    b = host(off.solve(dev(f), max_refine=1))
+    assert np.array_equal(a[:8192], b[:8192])
+    ref = oracle.hyperdiff_steps(ns[1:], sig[1:], f[8192:], 1)
+    assert sys_rel_err(a[8192:], ref, ns[1:]) <= TOL
+
+
+def test_shared_matrix_in_windows():
+    n, batch = 9000, 6
+    f = synth.uniform(4102, 0, n * batch, -1, 1)
+    ns = np.full(batch, n)
+    ref = oracle.hyperdiff_steps(ns, np.full(batch, 2.5), f, 2)
+    plan = plan_for(ns, np.array([2.5]), shared=True)
+    assert plan.get_option(pb.PENT_OPT_WINDOWS) >= 10 * batch
+    x = dev(f)
+    plan.solve_steps(x, 2, max_refine=1)
+    assert sys_rel_err(host(x), ref, ns) <= 2 * TOL
+
+
+def test_more_refinement_steps_and_the_general_kernel_bypass_windows():
+    """max_refine = 2 and PENT_OPT_FP32_KERNEL = 1 take the bucket path (clusters for the long
+    systems): the same results within the bar."""
+    w = workload(7000, 6, 47)
+    ref = oracle.hyperdiff_steps(w.n, w.sigma, w.field0, 1)
+    plan = plan_for(w.n, w.sigma)
+    assert plan.get_option(pb.PENT_OPT_WINDOWS) > 0
+    x = plan.solve(dev(w.field0), max_refine=2)
+    assert plan.info()[0] == pb.PENT_OK
+    assert sys_rel_err(host(x), ref, w.n) <= TOL
+    gen = plan_for(w.n, w.sigma, kernel=1)
+    assert sys_rel_err(host(gen.solve(dev(w.field0), max_refine=1)), ref, w.n) <= TOL
+
+
+def test_refactor_rebuilds_the_windows():
+    """A second factorisation with other sigmas lays the windows out anew (the overlap grows
+    with sigma) and the step graphs captured for the first one are not reused."""
+    ns = np.full(4, 12000)
+    f = synth.uniform(61, 0, int(ns.sum()), -1, 1)
+    plan = plan_for(ns, np.full(4, 1e-3))
+    n_small = plan.get_option(pb.PENT_OPT_WINDOWS)
+    x = dev(f)
+    plan.solve_steps(x, 2, max_refine=1)
+    assert sys_rel_err(host(x), oracle.hyperdiff_steps(ns, np.full(4, 1e-3), f, 2), ns) <= 2 * TOL
+    plan.factor_hyperdiff(dev(np.full(4, 10.0)))
+    assert plan.get_option(pb.PENT_OPT_WINDOWS) > n_small
+    x = dev(f)
+    plan.solve_steps(x, 2, max_refine=1)
+    assert sys_rel_err(host(x), oracle.hyperdiff_steps(ns, np.full(4, 10.0), f, 2), ns) <= 2 * TOL
