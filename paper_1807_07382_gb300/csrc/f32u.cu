@@ -408,9 +408,18 @@ __device__ __forceinline__ int fexp(float h) { return (int)((__float_as_uint(h) 
 #define PENT_U_WARPS_PER_SM 40
 #endif
 
-// CTAs per SM the launch bound asks for: PENT_U_WARPS_PER_SM warps, or for the runtime-width
-// kernel two CTAs of up to 16 warps (64 registers a thread).
-constexpr int u_min_blocks(int WT) { return WT > 0 ? PENT_U_WARPS_PER_SM / WT : 2; }
+// Warps per SM for the windows of long systems (FP64 in and out): 32 (64 registers a thread, no
+// spills; on GB300 the uneven batch with 4-warp windows takes 0.700 ms a step against 0.713 at 40
+// and 0.777 at 48).
+#ifndef PENT_U_WIN_WARPS_PER_SM
+#define PENT_U_WIN_WARPS_PER_SM 32
+#endif
+
+// CTAs per SM the launch bound asks for: PENT_U_WARPS_PER_SM (windows: PENT_U_WIN_WARPS_PER_SM)
+// warps, or for the runtime-width kernel two CTAs of up to 16 warps (64 registers a thread).
+constexpr int u_min_blocks(int WT, int WIN) {
+  return WT > 0 ? (WIN ? PENT_U_WIN_WARPS_PER_SM : PENT_U_WARPS_PER_SM) / WT : 2;
+}
 
 // WIN = 1: CTA b solves window win[b] = (system, first row w0, rows m | overlap rows O << 16)
 // of a long system: rows w0 .. w0 + m - 1 as one system of m rows whose cuts (a first row
@@ -425,7 +434,7 @@ struct UWinArgs {
 };
 
 template <int L, int WT, int REF, int IN, int OUT, int WIN>
-__global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, u_min_blocks(WT))
+__global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, u_min_blocks(WT, WIN))
     k_solve32u(F32Tables T, const float4* __restrict__ urec, int32_t* __restrict__ kscale,
                const int32_t* __restrict__ sys, int shared, const double* f, double* x, int vec_io, int Wrt,
                UWinArgs wa) {
@@ -784,19 +793,30 @@ cudaError_t launch_w(const F32Tables& T, const float4* urec, const UWinArgs& wa,
   return cudaGetLastError();
 }
 
-// Copy the overlap rows of every window out of f (before an in-place windowed solve):
-// one CTA per window, halo[w][0][0 .. O) = rows w0 .. w0 + O - 1 (after a cut at w0),
-// halo[w][1][0 .. O) = the last O rows (before a cut at the window's end).
-__global__ void k_uwin_halo(F32Tables T, const int4* __restrict__ win, int omax, const double* __restrict__ f,
-                            double* __restrict__ halo) {
-  const int4 d = win[blockIdx.x];
+// Copy the overlap rows of every window out of f (before an in-place windowed solve): one warp
+// per window, halo[w][0][0 .. O) = rows w0 .. w0 + O - 1 (after a cut at w0), halo[w][1][0 .. O)
+// = the window's last O rows (before a cut at its end); row pairs when every windowed system
+// starts at an even row (O and the window's first row are multiples of 8).
+__global__ void k_uwin_halo(F32Tables T, const int4* __restrict__ win, int64_t nwin, int omax, int pairs,
+                            const double* __restrict__ f, double* __restrict__ halo) {
+  const int64_t w = blockIdx.x * (int64_t)(blockDim.x / 32) + threadIdx.x / 32;
+  if (w >= nwin) return;
+  const int lane = threadIdx.x & 31;
+  const int4 d = win[w];
   const int n = T.n[d.x], m = d.z & 0xffff, O = d.z >> 16;
   const double* fs = f + T.off[d.x] + d.y;
-  double* hb = halo + (int64_t)blockIdx.x * 2 * omax;
-  for (int i = threadIdx.x; i < 2 * O; i += blockDim.x) {
-    const bool right = i >= O;
-    if (!right && d.y > 0) hb[i] = fs[i];
-    if (right && d.y + m < n) hb[omax + (i - O)] = fs[m - O + (i - O)];
+  double* hb = halo + w * 2 * omax;
+  const bool left = d.y > 0, right = d.y + m < n;
+  if (pairs) {
+    for (int i = lane; i < O / 2; i += 32) {
+      if (left) reinterpret_cast<double2*>(hb)[i] = reinterpret_cast<const double2*>(fs)[i];
+      if (right) reinterpret_cast<double2*>(hb + omax)[i] = reinterpret_cast<const double2*>(fs + m - O)[i];
+    }
+  } else {
+    for (int i = lane; i < O; i += 32) {
+      if (left) hb[i] = fs[i];
+      if (right) hb[omax + i] = fs[m - O + i];
+    }
   }
 }
 
@@ -842,7 +862,9 @@ cudaError_t launch_solve32w(const F32Tables& T, const float4* urec, const int32_
   if (max_refine > 1 || !solve32w_supported(W) || omax <= 0 || omax % 8) return cudaErrorInvalidValue;
   const bool in_place = f == x;
   if (in_place) {
-    k_uwin_halo<<<(unsigned)nwin, 128, 0, st>>>(T, win, omax, f, halo);
+    const int wpb = 4;  // windows (warps) per CTA
+    const int pairs = even_offsets && ((uintptr_t)f) % 16 == 0;
+    k_uwin_halo<<<(unsigned)((nwin + wpb - 1) / wpb), 32 * wpb, 0, st>>>(T, win, nwin, omax, pairs, f, halo);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
