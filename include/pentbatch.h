@@ -190,7 +190,24 @@ enum {
                                       then reads the overlaps back and so waits for the plan's stream (a
                                       factorisation under a stream capture lays out none).  Before
                                       pent_plan_bind (the workspace reserves R / 8 overlap rows a side). */
-  PENT_OPT_WINDOWS = 13            /* read only: windows of the current factorisation (0: none) */
+  PENT_OPT_WINDOWS = 13,           /* read only: windows of the current factorisation (0: none; FP32 plans
+                                      the PENT_OPT_WINDOW_WARPS windows, FP64 those of PENT_OPT_WINDOW_ROWS) */
+  PENT_OPT_WINDOW_ROWS = 14        /* PENT_F64, per-system matrices factored by pent_factor_hyperdiff: a
+                                      group of 32 length-sorted systems (one warp walks one system per
+                                      lane) whose padded length exceeds this many rows (1024, the default;
+                                      a multiple of 64 in 256 .. 16384; 0 turns windows off) is walked as
+                                      windows of that many rows, one warp each, side by side in one launch:
+                                      a window enters each sweep with a zero state where it cuts the group
+                                      and writes x only for the rows at least O from a cut, O the fewest
+                                      multiple of 8 rows over which the interior row maps of every system
+                                      of the group shrink to 2^-56.  The groups of a launch setting (a run
+                                      of equal unroll, CTA width and partitioning) take windows only if
+                                      each of their long groups has an overlap within 1/8 of the window;
+                                      the others, and general bands (pent_factor_batch), keep their walks
+                                      or partitioned solves.  The factorisation reads the overlaps back
+                                      and so waits for the plan's stream (under a stream capture it lays
+                                      out no windows).  Before pent_plan_bind (the workspace reserves the
+                                      windows' overlap rows). */
 };
 pent_status pent_plan_set_option(pent_plan* plan, int key, int64_t value);
 pent_status pent_plan_get_option(const pent_plan* plan, int key, int64_t* value);

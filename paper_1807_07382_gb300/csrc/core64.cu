@@ -1052,6 +1052,202 @@ __global__ void k_sigma_grad(DevPlan P, const double* __restrict__ mu, const dou
 
 inline int grid_for(int64_t threads, int block) { return (int)((threads + block - 1) / block); }
 
+// ---- windowed walks of groups of long hyperdiffusion systems ----
+//
+// A group whose rows are many times one window is walked as windows of its rows, one warp each,
+// side by side: window (group k, first row w0, rows m, overlap O) runs the group's forward and
+// back substitutions over rows w0 .. w0 + m - 1 only, entering each sweep with a zero state where
+// it cuts the group (w0 > 0 for the forward sweep, w0 + m < Lg for the back sweep), and writes x
+// only for the rows at least O from a cut.  The error a cut leaves decays as the powers of the
+// interior row maps (forward (g_{i-2}, g_{i-1}) -> (g_{i-1}, g_i), back (x_{i+1}, x_{i+2}) ->
+// (x_i, x_{i+1}), Sec. 2.4's recurrences with the interior factors); O is the fewest multiple of 8
+// rows over which both shrink to 2^-56 for every system of the group, so the rows kept agree with
+// the whole walk far below FP64 rounding.
+
+constexpr double kWinTol64 = 1.3877787807814457e-17;  // 2^-56
+
+// Overlap rows per group (k_overlap64): the group's largest over its systems of at least 8 rows,
+// from the records of row n - 3 (interior), or 0x7fff if a system needs more than omax rows.
+__global__ void k_overlap64(DevPlan P, F64Factors F, int omax, int32_t* __restrict__ gover) {
+  const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kWarp;
+  if (k >= P.ngroups) return;
+  const int lane = threadIdx.x & (kWarp - 1);
+  const Lane L = lane_setup<false>(P, k, lane);
+  int O = 0;
+  if (L.s >= 0 && L.n >= 8) {
+    const int64_t r = L.n - 3;
+    const double ia = F.fwd[fwd_idx<false, 2>(L, r, 0, lane)], be = F.fwd[fwd_idx<false, 2>(L, r, 1, lane)];
+    const double ga = F.bwd[bwd_idx<false>(L, r, 0, lane)], de = F.bwd[bwd_idx<false>(L, r, 1, lane)];
+    const double sg = F.sig[L.s];
+    // P_f = M_f^j, P_b = M_b^j, one row at a time
+    double fa = 1, fb = 0, fc = 0, fd = 1, ba = 1, bb = 0, bc = 0, bd = 1;
+    O = 0x7fff;
+    for (int j = 1; j <= omax; ++j) {
+      const double na = fc, nb = fd, nc = -ia * (sg * fa + be * fc), nd = -ia * (sg * fb + be * fd);
+      fa = na; fb = nb; fc = nc; fd = nd;
+      const double ma = -ga * ba - de * bc, mb = -ga * bb - de * bd;
+      bc = ba; bd = bb; ba = ma; bb = mb;
+      const double nf = fmax(fmax(fabs(fa), fabs(fb)), fmax(fabs(fc), fabs(fd)));
+      const double nbk = fmax(fmax(fabs(ba), fabs(bb)), fmax(fabs(bc), fabs(bd)));
+      if (fmax(nf, nbk) <= kWinTol64) {
+        O = (j + 7) / 8 * 8;
+        break;
+      }
+    }
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) O = max(O, __shfl_xor_sync(0xffffffffu, O, d));
+  if (lane == 0) gover[k] = O;
+}
+
+// Overlap rows of f copied out before an in-place windowed walk: halo[w][side][pair][lane]
+// (side 0: the O rows after a cut at w0, side 1: the O rows before a cut at w0 + m; rows past a
+// system's end are zero), omax / 2 pairs a side.
+__global__ void k_win64_halo(DevPlan P, const int4* __restrict__ win, int64_t nwin, int omax,
+                             const double* __restrict__ f, double2* __restrict__ halo) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kWarp;
+  if (w >= nwin) return;
+  const int lane = threadIdx.x & (kWarp - 1);
+  const int4 d = win[w];
+  const Lane L = lane_setup<false>(P, d.x, lane);
+  const int w0 = d.y, m = d.z & 0xffff, O = d.z >> 16;
+  const int hp = omax / 2;
+  for (int side = 0; side < 2; ++side) {
+    if (side == 0 ? w0 == 0 : w0 + m >= L.Lg) continue;
+    const int64_t r0 = side == 0 ? w0 : w0 + m - O;
+    double2* h = halo + ((w * 2 + side) * hp) * kWarp + lane;
+    for (int q = 0; q < O / 2; ++q) {
+      const int64_t r = r0 + 2 * q;
+      h[q * kWarp] = make_double2(r < L.n ? f[L.fo + r] : 0.0, r + 1 < L.n ? f[L.fo + r + 1] : 0.0);
+    }
+  }
+}
+
+// The walk of one window (hyperdiffusion records, row pairs, U2 pairs of loads ahead), as
+// k_solve64_pair.  g of the kept rows goes to the group's scratch rows (no other window keeps
+// them), g of the O rows after them to the window's side scratch (side[w][pair][lane], omax / 2
+// pairs), the rows before them need none.  halo: the overlap rows of f, or nullptr (read f).
+template <int U2>
+__global__ void __launch_bounds__(128) k_solve64w(DevPlan P, F64Factors F, const int4* __restrict__ win, int64_t nwin,
+                                                  int omax, const double* f, double* x, double* __restrict__ gscr,
+                                                  double2* __restrict__ side, const double2* __restrict__ halo) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kWarp;
+  if (w >= nwin) return;
+  const int lane = threadIdx.x & (kWarp - 1);
+  const int4 d = win[w];
+  const Lane L = lane_setup<false>(P, d.x, lane);
+  const int w0 = d.y, m = d.z & 0xffff, O = d.z >> 16;
+  const bool lcut = w0 > 0, rcut = w0 + m < L.Lg;
+  const int hp = omax / 2, oh = O / 2;
+  const int64_t q0 = w0 >> 1, q1 = (w0 + m) >> 1;                                    // pairs walked
+  const int64_t k0 = (w0 + (lcut ? O : 0)) >> 1, k1 = (w0 + m - (rcut ? O : 0)) >> 1;  // pairs kept
+  const double2* __restrict__ fwd = reinterpret_cast<const double2*>(F.fwd);
+  const double2* __restrict__ bwd = reinterpret_cast<const double2*>(F.bwd);
+  double2* __restrict__ g2s = reinterpret_cast<double2*>(gscr);
+  double2* __restrict__ gside = side + (w * hp) * kWarp + lane;
+  const double2* hl = halo ? halo + ((w * 2 + 0) * hp) * kWarp + lane : nullptr;
+  const double2* hr = halo ? halo + ((w * 2 + 1) * hp) * kWarp + lane : nullptr;
+  const int64_t P0 = L.R0 >> 1;
+  const bool fvec = ((L.fo & 1) == 0) && ((((uintptr_t)f) & 15) == 0);
+  const bool xvec = ((L.fo & 1) == 0) && ((((uintptr_t)x) & 15) == 0);
+  const double sg = L.s >= 0 ? F.sig[L.s] : 0.0;
+
+  // ---- forward: L g = f over the window's pairs ----
+  double2 ca[U2], cb[U2], cf[U2], na[U2], nb[U2], nf[U2];
+  auto load_f = [&](int64_t qb, double2* A, double2* B, double2* Fv) {
+#pragma unroll
+    for (int u = 0; u < U2; ++u) {
+      const int64_t q = qb + u;
+      if (q < q1) {
+        const double2* rec = fwd + ((P0 + q) * 2) * kWarp + lane;
+        A[u] = __ldg(rec);
+        B[u] = __ldg(rec + kWarp);
+        const int64_t r = 2 * q;
+        if (hl && lcut && q < q0 + oh) {
+          Fv[u] = hl[(q - q0) * kWarp];
+        } else if (hr && rcut && q >= q1 - oh) {
+          Fv[u] = hr[(q - (q1 - oh)) * kWarp];
+        } else if (fvec && r + 1 < L.n) {
+          Fv[u] = *reinterpret_cast<const double2*>(f + L.fo + r);
+        } else {
+          Fv[u].x = (r < L.n) ? f[L.fo + r] : 0.0;
+          Fv[u].y = (r + 1 < L.n) ? f[L.fo + r + 1] : 0.0;
+        }
+      }
+    }
+  };
+  double g1 = 0.0, g2 = 0.0;
+  load_f(q0, ca, cb, cf);
+  for (int64_t qb = q0; qb < q1; qb += U2) {
+    if (qb + U2 < q1) load_f(qb + U2, na, nb, nf);
+#pragma unroll
+    for (int u = 0; u < U2; ++u) {
+      const int64_t q = qb + u;
+      if (q < q1) {
+        const double ga = ca[u].x * fma(-cb[u].x, g1, fma(-sg, g2, cf[u].x));
+        const double gb = ca[u].y * fma(-cb[u].y, ga, fma(-sg, g1, cf[u].y));
+        if (q >= k1)
+          gside[(q - k1) * kWarp] = make_double2(ga, gb);
+        else if (q >= k0)
+          g2s[(P0 + q) * kWarp + lane] = make_double2(ga, gb);
+        g2 = ga;
+        g1 = gb;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U2; ++u) {
+      ca[u] = na[u];
+      cb[u] = nb[u];
+      cf[u] = nf[u];
+    }
+  }
+
+  // ---- back: R x = g from the window's end down to its first kept pair ----
+  double2 cg[U2], cd[U2], cG[U2], ng[U2], nd[U2], nG[U2];
+  auto load_b = [&](int64_t qb, double2* Ga, double2* De, double2* Gv) {
+#pragma unroll
+    for (int u = 0; u < U2; ++u) {
+      const int64_t q = qb - u;
+      if (q >= k0) {
+        const double2* rec = bwd + ((P0 + q) * 2) * kWarp + lane;
+        Ga[u] = __ldg(rec);
+        De[u] = __ldg(rec + kWarp);
+        Gv[u] = q >= k1 ? gside[(q - k1) * kWarp] : g2s[(P0 + q) * kWarp + lane];
+      }
+    }
+  };
+  double x1 = 0.0, x2 = 0.0;
+  load_b(q1 - 1, cg, cd, cG);
+  for (int64_t qb = q1 - 1; qb >= k0; qb -= U2) {
+    if (qb - U2 >= k0) load_b(qb - U2, ng, nd, nG);
+#pragma unroll
+    for (int u = 0; u < U2; ++u) {
+      const int64_t q = qb - u;
+      if (q >= k0) {
+        const double xb = fma(-cg[u].y, x1, fma(-cd[u].y, x2, cG[u].y));
+        const double xa = fma(-cg[u].x, xb, fma(-cd[u].x, x1, cG[u].x));
+        if (q < k1) {
+          const int64_t r = 2 * q;
+          if (xvec && r + 1 < L.n) {
+            *reinterpret_cast<double2*>(x + L.fo + r) = make_double2(xa, xb);
+          } else {
+            if (r < L.n) x[L.fo + r] = xa;
+            if (r + 1 < L.n) x[L.fo + r + 1] = xb;
+          }
+        }
+        x2 = xb;
+        x1 = xa;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U2; ++u) {
+      cg[u] = ng[u];
+      cd[u] = nd[u];
+      cG[u] = nG[u];
+    }
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_factor64(const DevPlan& P, const double* a, const double* b, const double* c, const double* d,
@@ -1183,6 +1379,38 @@ cudaError_t launch_adjoint64(const DevPlan& P, F64Factors F, const double* f, do
 cudaError_t launch_sigma_grad(const DevPlan& P, const double* mu, const double* x, double* g_sigma, cudaStream_t st) {
   const int block = 256;
   k_sigma_grad<<<grid_for(P.batch * kWarp, block), block, 0, st>>>(P, mu, x, g_sigma);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_overlap64(const DevPlan& P, F64Factors F, int omax, int32_t* gover, cudaStream_t st) {
+  if (P.ngroups == 0 || P.shared || !F.sig) return cudaErrorInvalidValue;
+  k_overlap64<<<grid_for(P.ngroups * kWarp, 128), 128, 0, st>>>(P, F, omax, gover);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_solve64w(const DevPlan& P, F64Factors F, const int4* win, int64_t nwin, int omax, int unroll,
+                            int block_warps, const double* f, double* x, double* gscr, double* side, double* halo,
+                            cudaStream_t st) {
+  if (nwin == 0) return cudaSuccess;
+  if (P.shared || !F.sig || omax <= 0 || omax % 8 || block_warps < 1 || block_warps > 4) return cudaErrorInvalidValue;
+  const int block = kWarp * block_warps;
+  const int grid = grid_for(nwin * kWarp, block);
+  double2* h = nullptr;
+  if (f == x) {  // in place: the overlap rows are overwritten by the neighbouring windows
+    h = reinterpret_cast<double2*>(halo);
+    k_win64_halo<<<grid, block, 0, st>>>(P, win, nwin, omax, f, h);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  double2* sd = reinterpret_cast<double2*>(side);
+  if (unroll == 8)
+    k_solve64w<4><<<grid, block, 0, st>>>(P, F, win, nwin, omax, f, x, gscr, sd, h);
+  else if (unroll == 4)
+    k_solve64w<2><<<grid, block, 0, st>>>(P, F, win, nwin, omax, f, x, gscr, sd, h);
+  else if (unroll == 2)
+    k_solve64w<1><<<grid, block, 0, st>>>(P, F, win, nwin, omax, f, x, gscr, sd, h);
+  else
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 

@@ -120,6 +120,14 @@ cudaError_t launch_step_rhs(const DevPlan& P, const double* mu, const double* nu
 // A_s x = f in one pass per system, groups [g0, g1).
 cudaError_t launch_refactor_solve64(const DevPlan& P, F64Factors F, const double* sigma, const double* f, double* x,
                                     double* gscr, int block_warps, int64_t g0, int64_t g1, cudaStream_t st);
+// Windowed walks of groups of long hyperdiffusion systems (csrc/core64.cu).  gover: per group the
+// overlap rows a window needs (a multiple of 8; 0x7fff: more than omax).  win: per window (group,
+// first row, rows | overlap << 16); side: [nwin][omax / 2][32] double2 of g after the kept rows;
+// halo: [nwin][2][omax / 2][32] double2 of overlap rows, filled first when f == x.
+cudaError_t launch_overlap64(const DevPlan& P, F64Factors F, int omax, int32_t* gover, cudaStream_t st);
+cudaError_t launch_solve64w(const DevPlan& P, F64Factors F, const int4* win, int64_t nwin, int omax, int unroll,
+                            int block_warps, const double* f, double* x, double* gscr, double* side, double* halo,
+                            cudaStream_t st);
 cudaError_t launch_adjoint64(const DevPlan& P, F64Factors F, const double* f, double* x, double* gscr,
                              int block_warps, cudaStream_t st);
 // step: f is the field C and the kernel assembles the right-hand side C + mu D2(C^3 - C) - nu D4 C

@@ -72,6 +72,13 @@ struct pent_plan {
     int64_t c0, c1;
   };
   std::vector<F64Run> runs;
+  // windowed walks of groups of long hyperdiffusion systems (csrc/core64.cu): windows of
+  // win64_rows rows, one warp each, built at factor time from each group's overlap
+  int win64_rows = 1024;          // PENT_OPT_WINDOW_ROWS (0: off)
+  int win64_omax = 0;             // overlap rows reserved per window side (window rows / 8)
+  int64_t win64_cap = 0;          // windows the workspace holds
+  int64_t nwin64 = 0;             // windows of the current factorisation (0: none)
+  std::vector<F64Run> wruns;      // the runs of the other groups
   int64_t part_rows = -1;  // PENT_OPT_PARTITION_ROWS (-1: automatic)
   bool periodic = false;   // PENT_OPT_PERIODIC: cyclic systems (Navon's reduction)
   // partitioned groups: chunk list and per-group chunk ranges
@@ -118,7 +125,8 @@ struct pent_plan {
   // workspace regions
   Region r_info, r_perm, r_off, r_n, r_goff, r_glen, r_sigma, r_fwd, r_bwd, r_scr, r_fac32, r_sig32, r_foff, r_shape,
       r_sys32, r_adi, r_cmap, r_swU, r_swE, r_pck, r_pcc, r_pcbase, r_pcnum, r_pcmap, r_pU, r_pE, r_per, r_psinv,
-      r_pg, r_rhs, r_psinv32, r_urec, r_kscale, r_uwin, r_win, r_whalo, r_wsys32;
+      r_pg, r_rhs, r_psinv32, r_urec, r_kscale, r_uwin, r_win, r_whalo, r_wsys32, r_gover, r_win64, r_side64,
+      r_halo64;
   size_t ws_bytes = 0;
   // binding / state
   unsigned char* ws = nullptr;
@@ -508,6 +516,19 @@ void layout(pent_plan* p) {
     take(p->r_pE, (size_t)p->pchunks * kWarp * 2 * sizeof(double));
     // right-hand sides of pent_step_batch for the partitioned groups (their chunked solve reads f)
     take(p->r_rhs, (size_t)(p->pchunks > 0 ? p->rows : 0) * sizeof(double));
+    // windows of long groups (hyperdiffusion factorisations): as many as the largest overlap needs
+    p->win64_cap = 0;
+    p->win64_omax = 0;
+    if (!p->shared && p->win64_rows > 0) {
+      p->win64_omax = p->win64_rows / 8;
+      for (int64_t k = 0; k < p->ngroups; ++k)
+        p->win64_cap += window_layout(p->glen[k], p->win64_rows, p->win64_omax, nullptr, 0);
+    }
+    const size_t wpairs = (size_t)p->win64_cap * (p->win64_omax / 2) * kWarp;  // double2 per window side
+    take(p->r_gover, (size_t)(p->win64_cap > 0 ? p->ngroups : 0) * sizeof(int32_t));
+    take(p->r_win64, (size_t)p->win64_cap * sizeof(int4));
+    take(p->r_side64, wpairs * 2 * sizeof(double));
+    take(p->r_halo64, wpairs * 4 * sizeof(double));
   } else {
     take(p->r_fac32, (size_t)p->fac_float4 * 4 * sizeof(float));
     take(p->r_sig32, (size_t)nfac * 2 * sizeof(float));
@@ -694,7 +715,8 @@ pent_status pent_plan_bind(pent_plan* p, void* ws, void* stream) {
   }
   // side streams (and fork/join events) so that several launches of one solve overlap
   p->drop_streams();
-  const size_t nlaunch = p->precision == PENT_F64 ? p->runs.size() : p->buckets.size() + (p->win_cap > 0 ? 1 : 0);
+  const size_t nlaunch = p->precision == PENT_F64 ? p->runs.size() + (p->win64_cap > 0 ? 1 : 0)
+                                                 : p->buckets.size() + (p->win_cap > 0 ? 1 : 0);
   const int nside = (int)std::min<size_t>(3, nlaunch > 1 ? nlaunch - 1 : 0);
   for (int k = 0; k < nside && e == cudaSuccess; ++k) {
     cudaStream_t ss;
@@ -722,6 +744,7 @@ pent_status pent_plan_bind(pent_plan* p, void* ws, void* stream) {
   p->bound = true;
   p->factored = 0;
   p->nwin = 0;
+  p->nwin64 = 0;
   return PENT_OK;
 }
 
@@ -809,6 +832,13 @@ pent_status pent_plan_set_option(pent_plan* p, int key, int64_t value) {
       ++p->cfg_version;
       p->drop_graphs();
       return PENT_OK;
+    case PENT_OPT_WINDOW_ROWS:
+      // changes the workspace size: only before binding
+      if (p->bound || p->precision != PENT_F64 || p->periodic || p->shared) return PENT_EINVAL;
+      if (value != 0 && (value < 256 || value > 16384 || value % 64)) return PENT_EINVAL;
+      p->win64_rows = (int)value;
+      layout(p);
+      return PENT_OK;
     case PENT_OPT_WINDOW_WARPS:
       // changes the workspace size: only before binding
       if (p->bound || p->precision != PENT_F32_REFINE || p->periodic) return PENT_EINVAL;
@@ -847,7 +877,8 @@ pent_status pent_plan_get_option(const pent_plan* p, int key, int64_t* value) {
     case PENT_OPT_FP32_KERNEL: *value = p->f32_kernel; return PENT_OK;
     case PENT_OPT_CACHED_GRAPHS: *value = (int64_t)p->graphs.size(); return PENT_OK;
     case PENT_OPT_WINDOW_WARPS: *value = p->win_warps; return PENT_OK;
-    case PENT_OPT_WINDOWS: *value = p->nwin; return PENT_OK;
+    case PENT_OPT_WINDOWS: *value = p->precision == PENT_F64 ? p->nwin64 : p->nwin; return PENT_OK;
+    case PENT_OPT_WINDOW_ROWS: *value = p->win64_rows; return PENT_OK;
   }
   return PENT_EINVAL;
 }
@@ -962,6 +993,95 @@ static cudaError_t build_windows(pent_plan* p) {
   return cudaSuccess;
 }
 
+// Launch settings (unroll, warps per CTA) of the FP64 windows: those a group of one window's rows
+// takes (options, then the tune cache, then the built-in rule of build_f64_runs).
+static std::pair<int, int> win64_knobs(const pent_plan* p) {
+  const int R = p->win64_rows;
+  if (p->f64_explicit) return {p->unroll, std::min(p->block_warps, 4)};
+  if (const pent_plan::Rule* rl = find_rule(p, PENT_F64, R)) return {rl->a, std::min(rl->b, 4)};
+  return R > 1024 ? std::make_pair(8, 1) : std::make_pair(4, 2);
+}
+
+// Windows of long groups for an FP64 hyperdiffusion factorisation: the groups longer than one
+// window of every run whose such groups all have an overlap (k_overlap64) within the reserved
+// room are walked in windows; the rest of each run is kept (a partitioned run keeps the chunks
+// of its remaining groups).  The overlaps are read back, which waits for the plan's stream; under
+// a stream capture no windows are built.
+static cudaError_t build_windows64(pent_plan* p) {
+  const int64_t nprev = p->nwin64;
+  p->nwin64 = 0;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(p->stream, &cs);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusNone) {
+    if (nprev) ++p->cfg_version;
+    return cudaSuccess;
+  }
+  F64Factors F = p->f64();
+  F.sig = p->at<double>(p->r_sigma);
+  e = launch_overlap64(p->dev(), F, p->win64_omax, p->at<int32_t>(p->r_gover), p->stream);
+  std::vector<int32_t> gover((size_t)p->ngroups);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(gover.data(), p->at<int32_t>(p->r_gover), gover.size() * sizeof(int32_t),
+                        cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);  // also: no solve still reads the old windows
+  if (e != cudaSuccess) return e;
+  const int R = p->win64_rows;
+  std::vector<int32_t> win, geo;
+  // per run: its groups longer than one window are walked in windows only if every one of them
+  // decays fast enough (so each run splits once at most: its groups are sorted longest first)
+  std::vector<char> windowed((size_t)p->ngroups, 0);
+  for (const auto& r : p->runs) {
+    bool ok = true;
+    for (int64_t k = r.g0; k < r.g1 && ok; ++k)
+      if (p->glen[k] > R && (gover[k] <= 0 || gover[k] > p->win64_omax)) ok = false;
+    for (int64_t k = r.g0; k < r.g1 && ok; ++k) windowed[k] = p->glen[k] > R;
+  }
+  for (int64_t k = 0; k < p->ngroups; ++k) {
+    const int O = gover[k];
+    if (!windowed[k]) continue;
+    const int64_t cnt = window_layout(p->glen[k], R, O, nullptr, 0);
+    geo.resize((size_t)(4 * cnt));
+    window_layout(p->glen[k], R, O, geo.data(), cnt);
+    for (int64_t j = 0; j < cnt; ++j) {
+      win.push_back((int32_t)k);
+      win.push_back(geo[4 * j]);
+      win.push_back(geo[4 * j + 1] | (O << 16));
+      win.push_back(0);
+    }
+    windowed[k] = 1;
+  }
+  const int64_t nw = (int64_t)win.size() / 4;
+  if (nw > p->win64_cap) return cudaErrorInvalidValue;  // not reached: the room is sized for the largest overlap
+  p->wruns.clear();
+  for (const auto& r : p->runs) {
+    for (int64_t g = r.g0; g < r.g1;) {
+      if (windowed[g]) {
+        ++g;
+        continue;
+      }
+      int64_t h = g;
+      while (h < r.g1 && !windowed[h]) ++h;
+      pent_plan::F64Run q = r;
+      q.g0 = g;
+      q.g1 = h;
+      if (r.part) {
+        q.c0 = p->pcbase[g];
+        q.c1 = p->pcbase[h - 1] + p->pcnum[h - 1];
+      }
+      p->wruns.push_back(q);
+      g = h;
+    }
+  }
+  if (nw > 0) {
+    e = cudaMemcpy(p->at<int4>(p->r_win64), win.data(), (size_t)nw * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+  }
+  p->nwin64 = nw;
+  if (nw || nprev) ++p->cfg_version;  // step graphs hold the launches of the old layout
+  return cudaSuccess;
+}
+
 static pent_status factor_common(pent_plan* p, const double* a, const double* b, const double* c, const double* d,
                                  const double* e, const double* sigma) {
   if (!p) return PENT_EINVAL;
@@ -989,6 +1109,15 @@ static pent_status factor_common(pent_plan* p, const double* a, const double* b,
     if (err == cudaSuccess && p->shared) err = launch_chunk_maps(F, (int)p->n_uniform, p->at<double>(p->r_cmap), p->stream);
     // chunk maps of the partitioned groups
     if (err == cudaSuccess && p->pchunks > 0) err = launch_chunk_maps64(P, F, p->part(), 0, p->pchunks, p->stream);
+    // windows of the long groups (hyperdiffusion records); a general band keeps the runs
+    if (err == cudaSuccess && p->win64_cap > 0) {
+      if (sigma) {
+        err = build_windows64(p);
+      } else if (p->nwin64) {
+        p->nwin64 = 0;
+        ++p->cfg_version;
+      }
+    }
   }
   else if (p->periodic)
     err = launch_factor32_periodic(p->f32(), p->at<int32_t>(p->r_shape), p->shared ? 1 : p->batch, sg, p->stream);
@@ -1058,8 +1187,15 @@ static pent_status solve_launch(pent_plan* p, const double* f, double* x, int ma
     const F64Factors F = p->f64();
     double* gscr = p->at<double>(p->r_scr);
     const F64Part X = p->part();
-    err = fork_join(p, p->runs.size(), [&](size_t i, cudaStream_t st) {
-      const auto& r = p->runs[i];
+    // windows of the long groups and the other groups' runs, each launch on its own branch
+    const size_t nw = p->nwin64 > 0 ? 1 : 0;
+    const std::vector<pent_plan::F64Run>& runs = nw ? p->wruns : p->runs;
+    err = fork_join(p, runs.size() + nw, [&](size_t i, cudaStream_t st) {
+      if (i < nw)
+        return launch_solve64w(P, F, p->at<int4>(p->r_win64), p->nwin64, p->win64_omax, win64_knobs(p).first,
+                               win64_knobs(p).second, f, x, gscr, p->at<double>(p->r_side64),
+                               p->at<double>(p->r_halo64), st);
+      const auto& r = runs[i - nw];
       if (r.part) return launch_solve64_part(P, F, X, f, x, gscr, r.g0, r.g1, r.c0, r.c1, st);
       return launch_solve64(P, F, f, x, gscr, r.bw, r.unroll, r.g0, r.g1, st);
     });

@@ -273,3 +273,28 @@ def test_window_warps_option_host_checks(L):
     assert L.pent_plan_set_option(h, _lib.PENT_OPT_PERIODIC, 1) == 0
     assert L.pent_plan_set_option(h, _lib.PENT_OPT_WINDOW_WARPS, 4) == _lib.PENT_EINVAL  # periodic
     L.pent_plan_destroy(h)
+
+
+def test_window_rows_option_host_checks(L):
+    """PENT_OPT_WINDOW_ROWS: FP64 per-system plans, before binding, 0 or a multiple of 64 in
+    256 .. 16384 (default 1024); the workspace grows by the windows' side scratch and overlap
+    rows (three times omax / 2 row pairs of 32 lanes a window) when a group is longer than one window."""
+    st, h = _create(L, batch=64, n=[5000] * 32 + [300] * 32)
+    assert st == 0
+    v = ctypes.c_int64()
+    assert L.pent_plan_get_option(h, _lib.PENT_OPT_WINDOW_ROWS, ctypes.byref(v)) == 0 and v.value == 1024
+    base = L.pent_plan_workspace_bytes(h)
+    assert L.pent_plan_set_option(h, _lib.PENT_OPT_WINDOW_ROWS, 0) == 0
+    off = L.pent_plan_workspace_bytes(h)
+    nwin = len(pb.window_layout(5000, 1024, 128))
+    assert base - off >= nwin * 3 * 64 * 32 * 16 - 4 * 256
+    for bad in (100, 255, 1000, 16448, -4):
+        assert L.pent_plan_set_option(h, _lib.PENT_OPT_WINDOW_ROWS, bad) == _lib.PENT_EINVAL
+    for good in (256, 512, 2048, 16384):
+        assert L.pent_plan_set_option(h, _lib.PENT_OPT_WINDOW_ROWS, good) == 0
+    L.pent_plan_destroy(h)
+    for kw in (dict(n_uniform=5000, shared=1), dict(n_uniform=5000, prec=1)):  # shared; FP32
+        st, h = _create(L, batch=8, **kw)
+        assert st == 0
+        assert L.pent_plan_set_option(h, _lib.PENT_OPT_WINDOW_ROWS, 1024) == _lib.PENT_EINVAL
+        L.pent_plan_destroy(h)

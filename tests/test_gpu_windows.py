@@ -8,7 +8,11 @@ over which both interior chunk maps shrink to 2^-56, so the rows kept agree with
 system's direct solve far below FP64 rounding; the results are held to the same bar as every
 FP32+refine solve: 1e-12 relative (per system, max |x - x_ref| / max |x_ref|) after one
 refinement step for sigma in [1e-3, 10], and 1e-4 for the plain FP32 solve.  Systems whose
-decay is too slow for the window (the overlap above R / 8) keep the cluster path."""
+decay is too slow for the window (the overlap above R / 8) keep the cluster path.
+
+FP64 per-system hyperdiffusion plans cut groups of 32 length-sorted systems (one warp, one
+system per lane) into windows of 1024 rows the same way, one warp each, with the group's
+largest overlap: against the oracle at 1e-12 and within 1e-14 of the whole-group walk."""
 import numpy as np
 import pytest
 
@@ -181,3 +185,94 @@ def test_refactor_rebuilds_the_windows():
     x = dev(f)
     plan.solve_steps(x, 2, max_refine=1)
     assert sys_rel_err(host(x), oracle.hyperdiff_steps(ns, np.full(4, 10.0), f, 2), ns) <= 2 * TOL
+
+
+# ----------------------------------------------------------------------------- FP64 windows
+
+def plan64(ns, sigma, window_rows=None):
+    opts = {} if window_rows is None else {pb.PENT_OPT_WINDOW_ROWS: window_rows}
+    plan = pb.Plan(list(ns), precision=pb.PENT_F64, options=opts)
+    plan.factor_hyperdiff(dev(sigma))
+    return plan
+
+
+@pytest.mark.parametrize("n", [1025, 2049, 4097, 8192, 16384, 40000])
+def test_f64_windows_meet_the_bar(n):
+    """Groups of 32 systems longer than one window (1024 rows) walked in windows: against the
+    oracle at 1e-12 and within 1e-14 of the same plan walking whole groups (windows off), out of
+    place and in place."""
+    batch = 40 if n <= 8192 else 33
+    w = workload(n, batch, 60 + n % 5)
+    ref = oracle.hyperdiff_steps(w.n, w.sigma, w.field0, 1)
+    plan = plan64(w.n, w.sigma)
+    assert plan.get_option(pb.PENT_OPT_WINDOWS) >= 2 * ((batch + 31) // 32)
+    x = host(plan.solve(dev(w.field0)))
+    assert sys_rel_err(x, ref, w.n) <= TOL
+    whole = host(plan64(w.n, w.sigma, window_rows=0).solve(dev(w.field0)))
+    assert sys_rel_err(x, whole, w.n) <= 1e-14
+    xi = dev(w.field0)
+    plan.solve(xi, xi)
+    assert np.array_equal(host(xi), x)
+
+
+def test_f64_windows_of_uneven_groups_and_steps_in_place():
+    """Systems of one group end at different rows (lengths 3,000 .. 9,000, sorted into groups),
+    so windows cut some lanes inside their systems and run others through padding; several steps
+    in place in one graph, against the oracle (bar: steps x 1e-12) and the whole-group walks."""
+    ns = np.floor(synth.log_uniform(71, 0, 80, 3000.0, 9000.0)).astype(np.int64)
+    sig = synth.log_uniform(72, 0, len(ns), 1e-2, 10.0)
+    f = synth.uniform(73, 0, int(ns.sum()), -1, 1)
+    steps = 3
+    ref = oracle.hyperdiff_steps(ns, sig, f, steps)
+    got = []
+    for wr in (1024, 0):
+        plan = plan64(ns, sig, window_rows=wr)
+        assert (plan.get_option(pb.PENT_OPT_WINDOWS) > 0) == (wr > 0)
+        x = dev(f)
+        plan.solve_steps(x, steps)
+        got.append(host(x))
+    assert sys_rel_err(got[0], ref, ns) <= steps * TOL
+    assert sys_rel_err(got[0], got[1], ns) <= 1e-14
+
+
+@pytest.mark.parametrize("window_rows,sigma_hi", [(256, 0.05), (512, 1.0), (2048, 10.0)])
+def test_f64_window_sizes(window_rows, sigma_hi):
+    """Other window lengths (the overlap room is 1/8 of the window: smaller windows take the
+    faster-decaying systems)."""
+    ns = np.array([20000] * 20 + [3000] * 20 + [700] * 20)
+    sig = synth.log_uniform(74, 0, len(ns), 1e-3, sigma_hi)
+    f = synth.uniform(75, 0, int(ns.sum()), -1, 1)
+    ref = oracle.hyperdiff_steps(ns, sig, f, 1)
+    plan = plan64(ns, sig, window_rows=window_rows)
+    assert plan.get_option(pb.PENT_OPT_WINDOWS) > 0
+    x = dev(f)
+    plan.solve(x, x)
+    assert sys_rel_err(host(x), ref, ns) <= TOL
+
+
+def test_f64_slow_decay_and_general_bands_keep_their_walks():
+    """A run of groups one of which decays too slowly for the window (sigma = 1e4: an overlap
+    above 128 rows) keeps its solves, bitwise as with windows off, while the run of another
+    launch setting takes windows (here the 6,000-row groups are partitioned, PENT_OPT_PARTITION_ROWS
+    = 5,000, and the 1,500-row group is walked); a general band (pent_factor_batch) lays out no
+    windows at all."""
+    ns = np.array([6000] * 32 + [6000] * 32 + [1500] * 32)
+    sig = np.concatenate([np.full(32, 1e4), np.full(32, 0.5), np.full(32, 2.0)])
+    f = synth.uniform(76, 0, int(ns.sum()), -1, 1)
+    runs = []
+    for wr in (1024, 0):
+        plan = pb.Plan(list(ns), precision=pb.PENT_F64,
+                       options={pb.PENT_OPT_PARTITION_ROWS: 5000, pb.PENT_OPT_WINDOW_ROWS: wr})
+        plan.factor_hyperdiff(dev(sig))
+        runs.append((plan.get_option(pb.PENT_OPT_WINDOWS), host(plan.solve(dev(f)))))
+    (nw, a), (nw0, b) = runs
+    assert nw0 == 0 and 2 <= nw <= len(pb.window_layout(1500, 1024, 128))
+    assert np.array_equal(a[:64 * 6000], b[:64 * 6000])
+    ref = oracle.hyperdiff_steps(ns[32:], sig[32:], f[32 * 6000:], 1)
+    assert sys_rel_err(a[32 * 6000:], ref, ns[32:]) <= TOL
+    band = oracle.band_hyperdiff_batch(ns, sig)
+    gen = pb.Plan(list(ns), precision=pb.PENT_F64)
+    gen.factor(*[dev(v) for v in band])
+    assert gen.get_option(pb.PENT_OPT_WINDOWS) == 0
+    g = host(gen.solve(dev(f)))
+    assert sys_rel_err(g[32 * 6000:], ref, ns[32:]) <= TOL  # (sigma = 1e4 is left out: kappa ~ 1.6e5)
