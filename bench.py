@@ -528,8 +528,9 @@ def measure_uneven(pb, dev, stream, fp64, sms, steps=200):
     tune = os.path.join(ROOT, "paper_1807_07382_gb300", "tune_gb300.txt")
     peak, peak_kind = measured_peaks()
     out = {}
-    for prec, pname, alg, kern in ((pb.PENT_F64, "f64", 56, "k_solve64_pair + partitioned"),
-                                   (pb.PENT_F32_REFINE, "f32_refine", 36, "k_solve32u + k_solve32r (clusters)")):
+    for prec, pname, alg, kern in ((pb.PENT_F64, "f64", 56, "k_solve64w (windows of 1024 rows) + k_solve64_pair"),
+                                   (pb.PENT_F32_REFINE, "f32_refine", 36,
+                                    "k_solve32u (windows of 1024 rows, single CTAs)")):
         plan = pb.Plan(list(w.n), precision=prec, stream=stream, device=dev, tune_cache=tune)
         plan.factor_hyperdiff(sig)
         one = plan.solve(f0, max_refine=1).cpu().numpy()
@@ -548,6 +549,7 @@ def measure_uneven(pb, dev, stream, fp64, sms, steps=200):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "kernel": kern, "alg_bytes_per_row": alg, "peak_kind": peak_kind},
             "max_rel_err_vs_oracle": err, "err_sample": f"{len(pick)} systems, one solve",
+            "windows": plan.get_option(pb.PENT_OPT_WINDOWS),
             "max_refine": 1 if prec == pb.PENT_F32_REFINE else 0, "clocks": ck}
         del plan
         torch.cuda.empty_cache()

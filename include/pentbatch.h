@@ -192,7 +192,7 @@ enum {
                                       pent_plan_bind (the workspace reserves R / 8 overlap rows a side). */
   PENT_OPT_WINDOWS = 13,           /* read only: windows of the current factorisation (0: none; FP32 plans
                                       the PENT_OPT_WINDOW_WARPS windows, FP64 those of PENT_OPT_WINDOW_ROWS) */
-  PENT_OPT_WINDOW_ROWS = 14        /* PENT_F64, per-system matrices factored by pent_factor_hyperdiff: a
+  PENT_OPT_WINDOW_ROWS = 14,       /* PENT_F64, per-system matrices factored by pent_factor_hyperdiff: a
                                       group of 32 length-sorted systems (one warp walks one system per
                                       lane) whose padded length exceeds this many rows (1024, the default;
                                       a multiple of 64 in 256 .. 16384; 0 turns windows off) is walked as
@@ -208,6 +208,11 @@ enum {
                                       and so waits for the plan's stream (under a stream capture it lays
                                       out no windows).  Before pent_plan_bind (the workspace reserves the
                                       windows' overlap rows). */
+  PENT_OPT_PERSISTENT = 15         /* not periodic: 1 launches the windows (PENT_OPT_WINDOW_WARPS,
+                                      PENT_OPT_WINDOW_ROWS) as a persistent grid, as many CTAs as stay
+                                      resident, each taking windows in turn (bounded by the window count,
+                                      no waits between CTAs); 0 (the default) one CTA (FP32) or warp (FP64)
+                                      per window.  The same results either way. */
 };
 pent_status pent_plan_set_option(pent_plan* plan, int key, int64_t value);
 pent_status pent_plan_get_option(const pent_plan* plan, int key, int64_t* value);

@@ -11,6 +11,7 @@
 // one-thread-per-system layout of the paper (Sec. 2.6), applied per group of
 // 32 systems (which keeps uneven lengths cheap to pad) and with row pairs (which
 // halves the number of memory instructions per row).
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 
@@ -1127,123 +1128,126 @@ __global__ void k_win64_halo(DevPlan P, const int4* __restrict__ win, int64_t nw
 // k_solve64_pair.  g of the kept rows goes to the group's scratch rows (no other window keeps
 // them), g of the O rows after them to the window's side scratch (side[w][pair][lane], omax / 2
 // pairs), the rows before them need none.  halo: the overlap rows of f, or nullptr (read f).
-template <int U2>
+// PERS: the persistent form, a resident grid whose warps take the windows in turn (else one
+// warp per window).
+template <int U2, bool PERS>
 __global__ void __launch_bounds__(128) k_solve64w(DevPlan P, F64Factors F, const int4* __restrict__ win, int64_t nwin,
                                                   int omax, const double* f, double* x, double* __restrict__ gscr,
                                                   double2* __restrict__ side, const double2* __restrict__ halo) {
-  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kWarp;
-  if (w >= nwin) return;
+  const int64_t nwarps = PERS ? (int64_t)gridDim.x * blockDim.x / kWarp : nwin;
   const int lane = threadIdx.x & (kWarp - 1);
-  const int4 d = win[w];
-  const Lane L = lane_setup<false>(P, d.x, lane);
-  const int w0 = d.y, m = d.z & 0xffff, O = d.z >> 16;
-  const bool lcut = w0 > 0, rcut = w0 + m < L.Lg;
-  const int hp = omax / 2, oh = O / 2;
-  const int64_t q0 = w0 >> 1, q1 = (w0 + m) >> 1;                                    // pairs walked
-  const int64_t k0 = (w0 + (lcut ? O : 0)) >> 1, k1 = (w0 + m - (rcut ? O : 0)) >> 1;  // pairs kept
-  const double2* __restrict__ fwd = reinterpret_cast<const double2*>(F.fwd);
-  const double2* __restrict__ bwd = reinterpret_cast<const double2*>(F.bwd);
-  double2* __restrict__ g2s = reinterpret_cast<double2*>(gscr);
-  double2* __restrict__ gside = side + (w * hp) * kWarp + lane;
-  const double2* hl = halo ? halo + ((w * 2 + 0) * hp) * kWarp + lane : nullptr;
-  const double2* hr = halo ? halo + ((w * 2 + 1) * hp) * kWarp + lane : nullptr;
-  const int64_t P0 = L.R0 >> 1;
-  const bool fvec = ((L.fo & 1) == 0) && ((((uintptr_t)f) & 15) == 0);
-  const bool xvec = ((L.fo & 1) == 0) && ((((uintptr_t)x) & 15) == 0);
-  const double sg = L.s >= 0 ? F.sig[L.s] : 0.0;
+  for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kWarp; w < nwin; w += nwarps) {
+    const int4 d = win[w];
+    const Lane L = lane_setup<false>(P, d.x, lane);
+    const int w0 = d.y, m = d.z & 0xffff, O = d.z >> 16;
+    const bool lcut = w0 > 0, rcut = w0 + m < L.Lg;
+    const int hp = omax / 2, oh = O / 2;
+    const int64_t q0 = w0 >> 1, q1 = (w0 + m) >> 1;                                    // pairs walked
+    const int64_t k0 = (w0 + (lcut ? O : 0)) >> 1, k1 = (w0 + m - (rcut ? O : 0)) >> 1;  // pairs kept
+    const double2* __restrict__ fwd = reinterpret_cast<const double2*>(F.fwd);
+    const double2* __restrict__ bwd = reinterpret_cast<const double2*>(F.bwd);
+    double2* __restrict__ g2s = reinterpret_cast<double2*>(gscr);
+    double2* __restrict__ gside = side + (w * hp) * kWarp + lane;
+    const double2* hl = halo ? halo + ((w * 2 + 0) * hp) * kWarp + lane : nullptr;
+    const double2* hr = halo ? halo + ((w * 2 + 1) * hp) * kWarp + lane : nullptr;
+    const int64_t P0 = L.R0 >> 1;
+    const bool fvec = ((L.fo & 1) == 0) && ((((uintptr_t)f) & 15) == 0);
+    const bool xvec = ((L.fo & 1) == 0) && ((((uintptr_t)x) & 15) == 0);
+    const double sg = L.s >= 0 ? F.sig[L.s] : 0.0;
 
-  // ---- forward: L g = f over the window's pairs ----
-  double2 ca[U2], cb[U2], cf[U2], na[U2], nb[U2], nf[U2];
-  auto load_f = [&](int64_t qb, double2* A, double2* B, double2* Fv) {
+    // ---- forward: L g = f over the window's pairs ----
+    double2 ca[U2], cb[U2], cf[U2], na[U2], nb[U2], nf[U2];
+    auto load_f = [&](int64_t qb, double2* A, double2* B, double2* Fv) {
 #pragma unroll
-    for (int u = 0; u < U2; ++u) {
-      const int64_t q = qb + u;
-      if (q < q1) {
-        const double2* rec = fwd + ((P0 + q) * 2) * kWarp + lane;
-        A[u] = __ldg(rec);
-        B[u] = __ldg(rec + kWarp);
-        const int64_t r = 2 * q;
-        if (hl && lcut && q < q0 + oh) {
-          Fv[u] = hl[(q - q0) * kWarp];
-        } else if (hr && rcut && q >= q1 - oh) {
-          Fv[u] = hr[(q - (q1 - oh)) * kWarp];
-        } else if (fvec && r + 1 < L.n) {
-          Fv[u] = *reinterpret_cast<const double2*>(f + L.fo + r);
-        } else {
-          Fv[u].x = (r < L.n) ? f[L.fo + r] : 0.0;
-          Fv[u].y = (r + 1 < L.n) ? f[L.fo + r + 1] : 0.0;
-        }
-      }
-    }
-  };
-  double g1 = 0.0, g2 = 0.0;
-  load_f(q0, ca, cb, cf);
-  for (int64_t qb = q0; qb < q1; qb += U2) {
-    if (qb + U2 < q1) load_f(qb + U2, na, nb, nf);
-#pragma unroll
-    for (int u = 0; u < U2; ++u) {
-      const int64_t q = qb + u;
-      if (q < q1) {
-        const double ga = ca[u].x * fma(-cb[u].x, g1, fma(-sg, g2, cf[u].x));
-        const double gb = ca[u].y * fma(-cb[u].y, ga, fma(-sg, g1, cf[u].y));
-        if (q >= k1)
-          gside[(q - k1) * kWarp] = make_double2(ga, gb);
-        else if (q >= k0)
-          g2s[(P0 + q) * kWarp + lane] = make_double2(ga, gb);
-        g2 = ga;
-        g1 = gb;
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < U2; ++u) {
-      ca[u] = na[u];
-      cb[u] = nb[u];
-      cf[u] = nf[u];
-    }
-  }
-
-  // ---- back: R x = g from the window's end down to its first kept pair ----
-  double2 cg[U2], cd[U2], cG[U2], ng[U2], nd[U2], nG[U2];
-  auto load_b = [&](int64_t qb, double2* Ga, double2* De, double2* Gv) {
-#pragma unroll
-    for (int u = 0; u < U2; ++u) {
-      const int64_t q = qb - u;
-      if (q >= k0) {
-        const double2* rec = bwd + ((P0 + q) * 2) * kWarp + lane;
-        Ga[u] = __ldg(rec);
-        De[u] = __ldg(rec + kWarp);
-        Gv[u] = q >= k1 ? gside[(q - k1) * kWarp] : g2s[(P0 + q) * kWarp + lane];
-      }
-    }
-  };
-  double x1 = 0.0, x2 = 0.0;
-  load_b(q1 - 1, cg, cd, cG);
-  for (int64_t qb = q1 - 1; qb >= k0; qb -= U2) {
-    if (qb - U2 >= k0) load_b(qb - U2, ng, nd, nG);
-#pragma unroll
-    for (int u = 0; u < U2; ++u) {
-      const int64_t q = qb - u;
-      if (q >= k0) {
-        const double xb = fma(-cg[u].y, x1, fma(-cd[u].y, x2, cG[u].y));
-        const double xa = fma(-cg[u].x, xb, fma(-cd[u].x, x1, cG[u].x));
-        if (q < k1) {
+      for (int u = 0; u < U2; ++u) {
+        const int64_t q = qb + u;
+        if (q < q1) {
+          const double2* rec = fwd + ((P0 + q) * 2) * kWarp + lane;
+          A[u] = __ldg(rec);
+          B[u] = __ldg(rec + kWarp);
           const int64_t r = 2 * q;
-          if (xvec && r + 1 < L.n) {
-            *reinterpret_cast<double2*>(x + L.fo + r) = make_double2(xa, xb);
+          if (hl && lcut && q < q0 + oh) {
+            Fv[u] = hl[(q - q0) * kWarp];
+          } else if (hr && rcut && q >= q1 - oh) {
+            Fv[u] = hr[(q - (q1 - oh)) * kWarp];
+          } else if (fvec && r + 1 < L.n) {
+            Fv[u] = *reinterpret_cast<const double2*>(f + L.fo + r);
           } else {
-            if (r < L.n) x[L.fo + r] = xa;
-            if (r + 1 < L.n) x[L.fo + r + 1] = xb;
+            Fv[u].x = (r < L.n) ? f[L.fo + r] : 0.0;
+            Fv[u].y = (r + 1 < L.n) ? f[L.fo + r + 1] : 0.0;
           }
         }
-        x2 = xb;
-        x1 = xa;
+      }
+    };
+    double g1 = 0.0, g2 = 0.0;
+    load_f(q0, ca, cb, cf);
+    for (int64_t qb = q0; qb < q1; qb += U2) {
+      if (qb + U2 < q1) load_f(qb + U2, na, nb, nf);
+#pragma unroll
+      for (int u = 0; u < U2; ++u) {
+        const int64_t q = qb + u;
+        if (q < q1) {
+          const double ga = ca[u].x * fma(-cb[u].x, g1, fma(-sg, g2, cf[u].x));
+          const double gb = ca[u].y * fma(-cb[u].y, ga, fma(-sg, g1, cf[u].y));
+          if (q >= k1)
+            gside[(q - k1) * kWarp] = make_double2(ga, gb);
+          else if (q >= k0)
+            g2s[(P0 + q) * kWarp + lane] = make_double2(ga, gb);
+          g2 = ga;
+          g1 = gb;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U2; ++u) {
+        ca[u] = na[u];
+        cb[u] = nb[u];
+        cf[u] = nf[u];
       }
     }
+
+    // ---- back: R x = g from the window's end down to its first kept pair ----
+    double2 cg[U2], cd[U2], cG[U2], ng[U2], nd[U2], nG[U2];
+    auto load_b = [&](int64_t qb, double2* Ga, double2* De, double2* Gv) {
 #pragma unroll
-    for (int u = 0; u < U2; ++u) {
-      cg[u] = ng[u];
-      cd[u] = nd[u];
-      cG[u] = nG[u];
+      for (int u = 0; u < U2; ++u) {
+        const int64_t q = qb - u;
+        if (q >= k0) {
+          const double2* rec = bwd + ((P0 + q) * 2) * kWarp + lane;
+          Ga[u] = __ldg(rec);
+          De[u] = __ldg(rec + kWarp);
+          Gv[u] = q >= k1 ? gside[(q - k1) * kWarp] : g2s[(P0 + q) * kWarp + lane];
+        }
+      }
+    };
+    double x1 = 0.0, x2 = 0.0;
+    load_b(q1 - 1, cg, cd, cG);
+    for (int64_t qb = q1 - 1; qb >= k0; qb -= U2) {
+      if (qb - U2 >= k0) load_b(qb - U2, ng, nd, nG);
+#pragma unroll
+      for (int u = 0; u < U2; ++u) {
+        const int64_t q = qb - u;
+        if (q >= k0) {
+          const double xb = fma(-cg[u].y, x1, fma(-cd[u].y, x2, cG[u].y));
+          const double xa = fma(-cg[u].x, xb, fma(-cd[u].x, x1, cG[u].x));
+          if (q < k1) {
+            const int64_t r = 2 * q;
+            if (xvec && r + 1 < L.n) {
+              *reinterpret_cast<double2*>(x + L.fo + r) = make_double2(xa, xb);
+            } else {
+              if (r < L.n) x[L.fo + r] = xa;
+              if (r + 1 < L.n) x[L.fo + r + 1] = xb;
+            }
+          }
+          x2 = xb;
+          x1 = xa;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U2; ++u) {
+        cg[u] = ng[u];
+        cd[u] = nd[u];
+        cG[u] = nG[u];
+      }
     }
   }
 }
@@ -1390,7 +1394,7 @@ cudaError_t launch_overlap64(const DevPlan& P, F64Factors F, int omax, int32_t* 
 
 cudaError_t launch_solve64w(const DevPlan& P, F64Factors F, const int4* win, int64_t nwin, int omax, int unroll,
                             int block_warps, const double* f, double* x, double* gscr, double* side, double* halo,
-                            cudaStream_t st) {
+                            bool persistent, cudaStream_t st) {
   if (nwin == 0) return cudaSuccess;
   if (P.shared || !F.sig || omax <= 0 || omax % 8 || block_warps < 1 || block_warps > 4) return cudaErrorInvalidValue;
   const int block = kWarp * block_warps;
@@ -1403,15 +1407,29 @@ cudaError_t launch_solve64w(const DevPlan& P, F64Factors F, const int4* win, int
     if (e != cudaSuccess) return e;
   }
   double2* sd = reinterpret_cast<double2*>(side);
-  if (unroll == 8)
-    k_solve64w<4><<<grid, block, 0, st>>>(P, F, win, nwin, omax, f, x, gscr, sd, h);
-  else if (unroll == 4)
-    k_solve64w<2><<<grid, block, 0, st>>>(P, F, win, nwin, omax, f, x, gscr, sd, h);
-  else if (unroll == 2)
-    k_solve64w<1><<<grid, block, 0, st>>>(P, F, win, nwin, omax, f, x, gscr, sd, h);
-  else
-    return cudaErrorInvalidValue;
-  return cudaGetLastError();
+  auto go = [&](auto kernel) {
+    int g = grid;
+    if (persistent) {  // as many CTAs as stay resident
+      int dev = 0, sms = 0, per_sm = 0;
+      cudaError_t e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0);
+      if (e != cudaSuccess) return e;
+      g = (int)std::min<int64_t>(grid, (int64_t)std::max(per_sm, 1) * sms);
+    }
+    kernel<<<g, block, 0, st>>>(P, F, win, nwin, omax, f, x, gscr, sd, h);
+    return cudaGetLastError();
+  };
+  if (persistent) {
+    if (unroll == 8) return go(k_solve64w<4, true>);
+    if (unroll == 4) return go(k_solve64w<2, true>);
+    if (unroll == 2) return go(k_solve64w<1, true>);
+  } else {
+    if (unroll == 8) return go(k_solve64w<4, false>);
+    if (unroll == 4) return go(k_solve64w<2, false>);
+    if (unroll == 2) return go(k_solve64w<1, false>);
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace pent

@@ -32,6 +32,7 @@
 // per-system power of two kept in `kscale`): only the first step splits the
 // FP64 input and only the last reassembles FP64, so the steps in between carry
 // no conversion work.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 
@@ -421,23 +422,24 @@ constexpr int u_min_blocks(int WT, int WIN) {
   return WT > 0 ? (WIN ? PENT_U_WIN_WARPS_PER_SM : PENT_U_WARPS_PER_SM) / WT : 2;
 }
 
-// WIN = 1: CTA b solves window win[b] = (system, first row w0, rows m | overlap rows O << 16)
-// of a long system: rows w0 .. w0 + m - 1 as one system of m rows whose cuts (a first row
-// other than 0, a last one other than n - 1) enter and leave with zero states, writing out
-// only the rows at least O from a cut.  halo: the overlap rows of every window copied out
-// before an in-place solve ([window][left, right][omax]), or nullptr (read from f).
+// WIN = 1: the CTA solves window win[b] (b < nwin) = (system, first row w0, rows m | overlap
+// rows O << 16) of a long system: rows w0 .. w0 + m - 1 as one system of m rows whose cuts (a
+// first row other than 0, a last one other than n - 1) enter and leave with zero states,
+// writing out only the rows at least O from a cut.  halo: the overlap rows of every window
+// copied out before an in-place solve ([window][left, right][omax]), or nullptr (read from f).
 struct UWinArgs {
   const int4* win;
+  int64_t nwin;
   const int32_t* fshape;  // [nfac] threads | L << 16 of each factor block
   const double* halo;
   int omax;
 };
 
+// One system (or window) `item` solved by the CTA.
 template <int L, int WT, int REF, int IN, int OUT, int WIN>
-__global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, u_min_blocks(WT, WIN))
-    k_solve32u(F32Tables T, const float4* __restrict__ urec, int32_t* __restrict__ kscale,
-               const int32_t* __restrict__ sys, int shared, const double* f, double* x, int vec_io, int Wrt,
-               UWinArgs wa) {
+__device__ __forceinline__ void u_item(unsigned item, const F32Tables& T, const float4* __restrict__ urec,
+                                       int32_t* __restrict__ kscale, const int32_t* __restrict__ sys, int shared,
+                                       const double* f, double* x, int vec_io, int Wrt, const UWinArgs& wa) {
   static_assert(L % 4 == 0, "rows per thread must be a multiple of 4");
   static_assert(!WIN || (IN == 0 && OUT == 0), "windows read and write FP64");
   const int W = WT > 0 ? WT : Wrt, P = 32 * W;  // WT = 0: the warp count is a launch parameter
@@ -462,7 +464,7 @@ __global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, u_min_blocks(WT, WIN))
   cx.tg0 = 0;
   cx.lw = cx.rw = true;
   if (WIN) {
-    const int4 d = wa.win[blockIdx.x];
+    const int4 d = wa.win[item];
     s = d.x;
     w0 = d.y;
     n = d.z & 0xffff;
@@ -471,7 +473,7 @@ __global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, u_min_blocks(WT, WIN))
     cx.rw = w0 + n == T.n[s];
     cx.tg0 = w0 / L;
   } else {
-    s = sys[blockIdx.x];
+    s = sys[item];
     n = T.n[s];
   }
   const int64_t ms = shared ? 0 : s;
@@ -520,7 +522,7 @@ __global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, u_min_blocks(WT, WIN))
     const double* src = f + T.off[s] + w0 + i0;  // this thread's first row
     if (WIN && wa.halo) {  // overlap rows (whole threads: O and the cuts are multiples of L)
       const bool lh = !cx.lw && i0 < O, rh = !cx.rw && i0 >= n - O;
-      const double* hb = wa.halo + (int64_t)blockIdx.x * 2 * wa.omax;
+      const double* hb = wa.halo + (int64_t)item * 2 * wa.omax;
       if (lh) src = hb + i0;
       if (rh) src = hb + wa.omax + (i0 - (n - O));
     }
@@ -627,7 +629,7 @@ __global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, u_min_blocks(WT, WIN))
       two_sum(xh[j], v[j], sh, se);
       fast_two_sum(sh, se, xh[j], xl[j]);
     }
-    if (blockIdx.x == 0 && t == 0) atomicMax(T.info + 1, (unsigned long long)REF);
+    if (item == 0 && t == 0) atomicMax(T.info + 1, (unsigned long long)REF);
   } else {
 #pragma unroll
     for (int j = 0; j < L; ++j) xl[j] = 0.f;
@@ -660,6 +662,23 @@ __global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, u_min_blocks(WT, WIN))
         if (i0 + j < n) *reinterpret_cast<float2*>(xs + 2 * (i0 + j)) = make_float2(xh[j], xl[j]);
     }
     if (store_k && t == 0) kscale[s] = kshift;
+  }
+}
+
+// A CTA per system (WIN = 0) or window (WIN = 1); WIN = 2 is the persistent form of the windows,
+// a grid of resident CTAs that take the windows in turn.
+template <int L, int WT, int REF, int IN, int OUT, int WIN>
+__global__ void __launch_bounds__(WT > 0 ? 32 * WT : 512, u_min_blocks(WT, WIN))
+    k_solve32u(F32Tables T, const float4* __restrict__ urec, int32_t* __restrict__ kscale,
+               const int32_t* __restrict__ sys, int shared, const double* f, double* x, int vec_io, int Wrt,
+               UWinArgs wa) {
+  if (WIN == 2) {
+    for (unsigned item = blockIdx.x; item < wa.nwin; item += gridDim.x) {
+      u_item<L, WT, REF, IN, OUT, WIN>(item, T, urec, kscale, sys, shared, f, x, vec_io, Wrt, wa);
+      __syncthreads();  // the next window reuses the shared memory
+    }
+  } else {
+    u_item<L, WT, REF, IN, OUT, WIN>(blockIdx.x, T, urec, kscale, sys, shared, f, x, vec_io, Wrt, wa);
   }
 }
 
@@ -779,17 +798,34 @@ cudaError_t launch_u(const F32Tables& T, const float4* urec, int32_t* kscale, co
   return cudaGetLastError();
 }
 
-template <int WT>
-cudaError_t launch_w(const F32Tables& T, const float4* urec, const UWinArgs& wa, int64_t nwin, int shared,
-                     int even_offsets, const double* f, double* x, int max_refine, cudaStream_t st) {
+// Grid of a window launch: one CTA per window, or (persistent) as many as stay resident.
+template <class K>
+cudaError_t window_grid(K kernel, int block, size_t smem, int64_t nwin, bool persistent, unsigned* grid) {
+  *grid = (unsigned)nwin;
+  if (!persistent) return cudaSuccess;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem);
+  if (e != cudaSuccess) return e;
+  *grid = (unsigned)std::min<int64_t>(nwin, (int64_t)std::max(per_sm, 1) * sms);
+  return cudaSuccess;
+}
+
+template <int WT, int REF>
+cudaError_t launch_w(const F32Tables& T, const float4* urec, const UWinArgs& wa, int shared, int even_offsets,
+                     const double* f, double* x, bool persistent, cudaStream_t st) {
   const int vec = ((((uintptr_t)f) | ((uintptr_t)x)) % 16 == 0) && even_offsets;
   const size_t smem = usmem_bytes(WT, 8);
-  if (max_refine > 0)
-    k_solve32u<8, WT, 1, 0, 0, 1><<<(unsigned)nwin, 32 * WT, smem, st>>>(T, urec, nullptr, nullptr, shared, f, x, vec,
-                                                                         WT, wa);
-  else
-    k_solve32u<8, WT, 0, 0, 0, 1><<<(unsigned)nwin, 32 * WT, smem, st>>>(T, urec, nullptr, nullptr, shared, f, x, vec,
-                                                                         WT, wa);
+  if (!persistent) {
+    k_solve32u<8, WT, REF, 0, 0, 1><<<(unsigned)wa.nwin, 32 * WT, smem, st>>>(T, urec, nullptr, nullptr, shared, f, x,
+                                                                              vec, WT, wa);
+    return cudaGetLastError();
+  }
+  unsigned grid;
+  const cudaError_t e = window_grid(k_solve32u<8, WT, REF, 0, 0, 2>, 32 * WT, smem, wa.nwin, true, &grid);
+  if (e != cudaSuccess) return e;
+  k_solve32u<8, WT, REF, 0, 0, 2><<<grid, 32 * WT, smem, st>>>(T, urec, nullptr, nullptr, shared, f, x, vec, WT, wa);
   return cudaGetLastError();
 }
 
@@ -857,7 +893,7 @@ bool solve32w_supported(int W) { return W == 4 || W == 8 || W == 16; }
 
 cudaError_t launch_solve32w(const F32Tables& T, const float4* urec, const int32_t* fshape, const int4* win,
                             int64_t nwin, int W, int omax, int shared, int even_offsets, const double* f, double* x,
-                            double* halo, int max_refine, cudaStream_t st) {
+                            double* halo, int max_refine, bool persistent, cudaStream_t st) {
   if (nwin == 0) return cudaSuccess;
   if (max_refine > 1 || !solve32w_supported(W) || omax <= 0 || omax % 8) return cudaErrorInvalidValue;
   const bool in_place = f == x;
@@ -868,11 +904,18 @@ cudaError_t launch_solve32w(const F32Tables& T, const float4* urec, const int32_
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  const UWinArgs wa{win, fshape, in_place ? halo : nullptr, omax};
+  const UWinArgs wa{win, nwin, fshape, in_place ? halo : nullptr, omax};
+  const bool r = max_refine > 0;
   switch (W) {
-    case 4: return launch_w<4>(T, urec, wa, nwin, shared, even_offsets, f, x, max_refine, st);
-    case 8: return launch_w<8>(T, urec, wa, nwin, shared, even_offsets, f, x, max_refine, st);
-    default: return launch_w<16>(T, urec, wa, nwin, shared, even_offsets, f, x, max_refine, st);
+    case 4:
+      return r ? launch_w<4, 1>(T, urec, wa, shared, even_offsets, f, x, persistent, st)
+               : launch_w<4, 0>(T, urec, wa, shared, even_offsets, f, x, persistent, st);
+    case 8:
+      return r ? launch_w<8, 1>(T, urec, wa, shared, even_offsets, f, x, persistent, st)
+               : launch_w<8, 0>(T, urec, wa, shared, even_offsets, f, x, persistent, st);
+    default:
+      return r ? launch_w<16, 1>(T, urec, wa, shared, even_offsets, f, x, persistent, st)
+               : launch_w<16, 0>(T, urec, wa, shared, even_offsets, f, x, persistent, st);
   }
 }
 

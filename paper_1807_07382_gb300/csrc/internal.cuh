@@ -125,9 +125,10 @@ cudaError_t launch_refactor_solve64(const DevPlan& P, F64Factors F, const double
 // first row, rows | overlap << 16); side: [nwin][omax / 2][32] double2 of g after the kept rows;
 // halo: [nwin][2][omax / 2][32] double2 of overlap rows, filled first when f == x.
 cudaError_t launch_overlap64(const DevPlan& P, F64Factors F, int omax, int32_t* gover, cudaStream_t st);
+// persistent: a grid of as many CTAs as stay resident, whose warps take the windows in turn.
 cudaError_t launch_solve64w(const DevPlan& P, F64Factors F, const int4* win, int64_t nwin, int omax, int unroll,
                             int block_warps, const double* f, double* x, double* gscr, double* side, double* halo,
-                            cudaStream_t st);
+                            bool persistent, cudaStream_t st);
 cudaError_t launch_adjoint64(const DevPlan& P, F64Factors F, const double* f, double* x, double* gscr,
                              int block_warps, cudaStream_t st);
 // step: f is the field C and the kernel assembles the right-hand side C + mu D2(C^3 - C) - nu D4 C
@@ -157,9 +158,10 @@ cudaError_t launch_solve32u(const F32Tables& T, const float4* urec, int32_t* ksc
 // from its cuts; fshape: each factor block's threads | L << 16.  An in-place solve (f == x) first
 // copies the overlap rows into halo ([nwin][2][omax] doubles).  max_refine 0 or 1.
 bool solve32w_supported(int W);
+// persistent: a grid of as many CTAs as stay resident, which take the windows in turn.
 cudaError_t launch_solve32w(const F32Tables& T, const float4* urec, const int32_t* fshape, const int4* win,
                             int64_t nwin, int W, int omax, int shared, int even_offsets, const double* f, double* x,
-                            double* halo, int max_refine, cudaStream_t st);
+                            double* halo, int max_refine, bool persistent, cudaStream_t st);
 // Periodic FP32 plans: factors of E, the columns of Z = E^{-1} k and S^{-1} (k_factor32_periodic).
 cudaError_t launch_factor32_periodic(const F32Tables& T, const int32_t* shape, int64_t nsys, const double* sigma,
                                      cudaStream_t st);

@@ -78,6 +78,7 @@ struct pent_plan {
   int win64_omax = 0;             // overlap rows reserved per window side (window rows / 8)
   int64_t win64_cap = 0;          // windows the workspace holds
   int64_t nwin64 = 0;             // windows of the current factorisation (0: none)
+  bool persistent = false;        // PENT_OPT_PERSISTENT: window launches as resident grids
   std::vector<F64Run> wruns;      // the runs of the other groups
   int64_t part_rows = -1;  // PENT_OPT_PARTITION_ROWS (-1: automatic)
   bool periodic = false;   // PENT_OPT_PERIODIC: cyclic systems (Navon's reduction)
@@ -832,6 +833,12 @@ pent_status pent_plan_set_option(pent_plan* p, int key, int64_t value) {
       ++p->cfg_version;
       p->drop_graphs();
       return PENT_OK;
+    case PENT_OPT_PERSISTENT:
+      if (p->periodic || (value != 0 && value != 1)) return PENT_EINVAL;
+      p->persistent = value == 1;
+      ++p->cfg_version;  // the launches a step graph holds depend on it
+      p->drop_graphs();
+      return PENT_OK;
     case PENT_OPT_WINDOW_ROWS:
       // changes the workspace size: only before binding
       if (p->bound || p->precision != PENT_F64 || p->periodic || p->shared) return PENT_EINVAL;
@@ -879,6 +886,7 @@ pent_status pent_plan_get_option(const pent_plan* p, int key, int64_t* value) {
     case PENT_OPT_WINDOW_WARPS: *value = p->win_warps; return PENT_OK;
     case PENT_OPT_WINDOWS: *value = p->precision == PENT_F64 ? p->nwin64 : p->nwin; return PENT_OK;
     case PENT_OPT_WINDOW_ROWS: *value = p->win64_rows; return PENT_OK;
+    case PENT_OPT_PERSISTENT: *value = p->persistent ? 1 : 0; return PENT_OK;
   }
   return PENT_EINVAL;
 }
@@ -1194,7 +1202,7 @@ static pent_status solve_launch(pent_plan* p, const double* f, double* x, int ma
       if (i < nw)
         return launch_solve64w(P, F, p->at<int4>(p->r_win64), p->nwin64, p->win64_omax, win64_knobs(p).first,
                                win64_knobs(p).second, f, x, gscr, p->at<double>(p->r_side64),
-                               p->at<double>(p->r_halo64), st);
+                               p->at<double>(p->r_halo64), p->persistent, st);
       const auto& r = runs[i - nw];
       if (r.part) return launch_solve64_part(P, F, X, f, x, gscr, r.g0, r.g1, r.c0, r.c1, st);
       return launch_solve64(P, F, f, x, gscr, r.bw, r.unroll, r.g0, r.g1, st);
@@ -1211,7 +1219,7 @@ static pent_status solve_launch(pent_plan* p, const double* f, double* x, int ma
       if (i < nw)
         return launch_solve32w(p->f32(), p->at<float4>(p->r_urec), p->at<int32_t>(p->r_shape), p->at<int4>(p->r_win),
                                p->nwin, p->win_warps, p->win_omax, p->shared, p->win_even, f, x,
-                               p->at<double>(p->r_whalo), max_refine, st);
+                               p->at<double>(p->r_whalo), max_refine, p->persistent, st);
       const F32Bucket& b = bk[i - nw];
       const bool u = use_u(p, b, max_refine);
       return f32_bucket(p, b, f, x, max_refine, u && in_ff, u && out_ff, st, sys);

@@ -298,3 +298,20 @@ def test_window_rows_option_host_checks(L):
         assert st == 0
         assert L.pent_plan_set_option(h, _lib.PENT_OPT_WINDOW_ROWS, 1024) == _lib.PENT_EINVAL
         L.pent_plan_destroy(h)
+
+
+def test_persistent_option_host_checks(L):
+    """PENT_OPT_PERSISTENT: 0 or 1, any precision but periodic plans, at any time; readable back."""
+    for prec in (0, 1):
+        st, h = _create(L, batch=4, n_uniform=5000, prec=prec)
+        assert st == 0
+        v = ctypes.c_int64(-1)
+        assert L.pent_plan_get_option(h, _lib.PENT_OPT_PERSISTENT, ctypes.byref(v)) == 0 and v.value == 0
+        assert L.pent_plan_set_option(h, _lib.PENT_OPT_PERSISTENT, 2) == _lib.PENT_EINVAL
+        assert L.pent_plan_set_option(h, _lib.PENT_OPT_PERSISTENT, 1) == 0
+        assert L.pent_plan_get_option(h, _lib.PENT_OPT_PERSISTENT, ctypes.byref(v)) == 0 and v.value == 1
+        L.pent_plan_destroy(h)
+    st, h = _create(L, batch=4, n_uniform=64)
+    assert L.pent_plan_set_option(h, _lib.PENT_OPT_PERIODIC, 1) == 0
+    assert L.pent_plan_set_option(h, _lib.PENT_OPT_PERSISTENT, 1) == _lib.PENT_EINVAL
+    L.pent_plan_destroy(h)

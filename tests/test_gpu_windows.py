@@ -276,3 +276,28 @@ def test_f64_slow_decay_and_general_bands_keep_their_walks():
     assert gen.get_option(pb.PENT_OPT_WINDOWS) == 0
     g = host(gen.solve(dev(f)))
     assert sys_rel_err(g[32 * 6000:], ref, ns[32:]) <= TOL  # (sigma = 1e4 is left out: kappa ~ 1.6e5)
+
+
+@pytest.mark.parametrize("prec", [pb.PENT_F32_REFINE, pb.PENT_F64])
+def test_persistent_windows_give_the_same_bits(prec):
+    """PENT_OPT_PERSISTENT = 1 launches the windows as a resident grid whose CTAs (FP32) or warps
+    (FP64) take the windows in turn: each window's arithmetic is unchanged, so the results are
+    bitwise those of one CTA or warp per window, out of place, in place and in step graphs."""
+    ns = np.array([16384] * 40 + [3000] * 40 + [500] * 40)
+    sig = synth.log_uniform(81, 0, len(ns), 1e-2, 10.0)
+    f = synth.uniform(82, 0, int(ns.sum()), -1, 1)
+    out = []
+    for pers in (0, 1):
+        plan = pb.Plan(list(ns), precision=prec, options={pb.PENT_OPT_PERSISTENT: pers})
+        plan.factor_hyperdiff(dev(sig))
+        assert plan.get_option(pb.PENT_OPT_WINDOWS) > 0 and plan.get_option(pb.PENT_OPT_PERSISTENT) == pers
+        a = host(plan.solve(dev(f), max_refine=1))
+        x = dev(f)
+        plan.solve(x, x, max_refine=1)
+        y = dev(f)
+        plan.solve_steps(y, 3, max_refine=1)
+        out.append((a, host(x), host(y)))
+    for u, v in zip(*out):
+        assert np.array_equal(u, v)
+    ref = oracle.hyperdiff_steps(ns, sig, f, 1)
+    assert sys_rel_err(out[1][0], ref, ns) <= TOL
