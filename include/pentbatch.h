@@ -208,11 +208,18 @@ enum {
                                       and so waits for the plan's stream (under a stream capture it lays
                                       out no windows).  Before pent_plan_bind (the workspace reserves the
                                       windows' overlap rows). */
-  PENT_OPT_PERSISTENT = 15         /* not periodic: 1 launches the windows (PENT_OPT_WINDOW_WARPS,
+  PENT_OPT_PERSISTENT = 15,        /* not periodic: 1 launches the windows (PENT_OPT_WINDOW_WARPS,
                                       PENT_OPT_WINDOW_ROWS) as a persistent grid, as many CTAs as stay
                                       resident, each taking windows in turn (bounded by the window count,
                                       no waits between CTAs); 0 (the default) one CTA (FP32) or warp (FP64)
                                       per window.  The same results either way. */
+  PENT_OPT_FP64_INTERIOR = 16      /* PENT_F64: 1 (the default) lets the walks of a hyperdiffusion
+                                      factorisation (pent_factor_hyperdiff, per-system matrices) take the
+                                      records of the interior rows from registers: rows 2 .. n - 3 of
+                                      I + sigma D4 share one band row, so once the factorisation's row
+                                      step reaches the record of row n - 3 from two rows holding it, every
+                                      later interior row holds the same bits (found per system at factor
+                                      time); 0 reads every record from memory.  Bitwise the same results. */
 };
 pent_status pent_plan_set_option(pent_plan* plan, int key, int64_t value);
 pent_status pent_plan_get_option(const pent_plan* plan, int key, int64_t* value);

@@ -12,6 +12,7 @@
 // 32 systems (which keeps uneven lengths cheap to pad) and with row pairs (which
 // halves the number of memory instructions per row).
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdint>
 
@@ -179,6 +180,29 @@ __device__ __forceinline__ int64_t scr_idx(const Lane& L, int64_t r, int lane) {
   return SHARED ? (L.R0 + r) * kWarp + lane : (((L.R0 + r) >> 1) * kWarp + lane) * 2 + ((L.R0 + r) & 1);
 }
 
+// The lane's interior records (rows lo .. hi take them from registers; lo > hi: none).
+struct Interior {
+  double ia = 0.0, be = 0.0, ga = 0.0, de = 0.0;
+  int64_t lo = INT64_MAX, hi = -1;
+};
+__device__ __forceinline__ Interior interior_of(const F64Factors& F, const Lane& L, int64_t k, int lane) {
+  Interior I;
+  if (F.ik && L.s >= 0) {
+    const int64_t q = k * kWarp + lane;
+    const int K = F.ik[q];
+    if (K != INT_MAX) {
+      const double4 c = F.icst[q];
+      I.ia = c.x;
+      I.be = c.y;
+      I.ga = c.z;
+      I.de = c.w;
+      I.lo = K;
+      I.hi = L.n - 3;
+    }
+  }
+  return I;
+}
+
 // x = A^{-1} f by the forward substitution L g = f and the back substitution
 // R x = g (Sec. 2.4).  With the stored 1/alpha, beta/alpha, epsilon/alpha:
 //   g_i = (1/alpha_i) f_i - (epsilon_i/alpha_i) g_{i-2} - (beta_i/alpha_i) g_{i-1}
@@ -298,6 +322,7 @@ __global__ void __launch_bounds__(128) k_solve64_pair(DevPlan P, F64Factors F, c
   const bool xvec = ((L.fo & 1) == 0) && ((((uintptr_t)x) & 15) == 0);
   const double sg = (HYP && L.s >= 0) ? F.sig[L.s] : 0.0;
   constexpr int NP = HYP ? 2 : 3;
+  const Interior I = (HYP && !SHARED) ? interior_of(F, L, k, lane) : Interior{};
 
   // ---- forward: L g = f ----
   double2 ca[U2], cb[U2], ce[U2], cf[U2];
@@ -312,6 +337,9 @@ __global__ void __launch_bounds__(128) k_solve64_pair(DevPlan P, F64Factors F, c
           A[u] = make_double2(__ldg(ra), __ldg(ra + 3));
           B[u] = make_double2(__ldg(ra + 1), __ldg(ra + 4));
           E[u] = make_double2(__ldg(ra + 2), __ldg(ra + 5));
+        } else if (HYP && 2 * q >= I.lo && 2 * q + 1 <= I.hi) {  // interior: the records are known
+          A[u] = make_double2(I.ia, I.ia);
+          B[u] = make_double2(I.be, I.be);
         } else {
           const double2* rec = fwd + ((P0 + q) * NP) * kWarp + lane;
           A[u] = __ldg(rec);
@@ -370,6 +398,9 @@ __global__ void __launch_bounds__(128) k_solve64_pair(DevPlan P, F64Factors F, c
           const double* rb = bwd1 + (2 * q) * 2;
           Ga[u] = make_double2(__ldg(rb), __ldg(rb + 2));
           De[u] = make_double2(__ldg(rb + 1), __ldg(rb + 3));
+        } else if (HYP && 2 * q >= I.lo && 2 * q + 1 <= I.hi) {
+          Ga[u] = make_double2(I.ga, I.ga);
+          De[u] = make_double2(I.de, I.de);
         } else {
           const double2* rec = bwd + ((P0 + q) * 2) * kWarp + lane;
           Ga[u] = __ldg(rec);
@@ -1053,6 +1084,50 @@ __global__ void k_sigma_grad(DevPlan P, const double* __restrict__ mu, const dou
 
 inline int grid_for(int64_t threads, int block) { return (int)((threads + block - 1) / block); }
 
+// ---- interior records of hyperdiffusion factorisations ----
+//
+// Rows 2 .. n - 3 of I + sigma D4 share one band row, so the factorisation's row step (Sec. 2.4)
+// maps the (gamma, delta) records of the two rows before a row to that row's records by one fixed
+// function.  Once rows r - 2 and r - 1 hold the (gamma, delta) of row n - 3 and row r holds all of
+// row n - 3's record, every row up to n - 3 holds that record, bit for bit: the walks can take it
+// from registers there instead of memory, with the same arithmetic.  One thread per group lane:
+// ik = the first such row r (INT_MAX if none), icst = the record (1/alpha, beta, gamma, delta).
+__global__ void k_interior64(DevPlan P, F64Factors F, double4* __restrict__ icst, int32_t* __restrict__ ik) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= P.ngroups * kWarp) return;
+  const int lane = (int)(q % kWarp);
+  const Lane L = lane_setup<false>(P, q / kWarp, lane);
+  int K = INT_MAX;
+  double4 c = make_double4(0.0, 0.0, 0.0, 0.0);
+  if (L.s >= 0 && L.n >= 8) {
+    auto bits = [](double v) { return __double_as_longlong(v); };
+    auto rec = [&](int64_t r) {
+      return make_double4(F.fwd[fwd_idx<false, 2>(L, r, 0, lane)], F.fwd[fwd_idx<false, 2>(L, r, 1, lane)],
+                          F.bwd[bwd_idx<false>(L, r, 0, lane)], F.bwd[bwd_idx<false>(L, r, 1, lane)]);
+    };
+    const double4 z = rec(L.n - 3);
+    const long long zg = bits(z.z), zd = bits(z.w);
+    long long g2 = bits(F.bwd[bwd_idx<false>(L, 0, 0, lane)]), d2 = bits(F.bwd[bwd_idx<false>(L, 0, 1, lane)]);
+    long long g1 = bits(F.bwd[bwd_idx<false>(L, 1, 0, lane)]), d1 = bits(F.bwd[bwd_idx<false>(L, 1, 1, lane)]);
+    for (int64_t r = 2; r <= L.n - 3; ++r) {
+      const double4 v = rec(r);
+      if (g2 == zg && d2 == zd && g1 == zg && d1 == zd && bits(v.x) == bits(z.x) && bits(v.y) == bits(z.y) &&
+          bits(v.z) == zg && bits(v.w) == zd) {
+        K = (int)r;
+        c = z;
+        break;
+      }
+      g2 = g1;
+      d2 = d1;
+      g1 = bits(v.z);
+      d1 = bits(v.w);
+    }
+  }
+  icst[q] = c;
+  ik[q] = K;
+}
+
+
 // ---- windowed walks of groups of long hyperdiffusion systems ----
 //
 // A group whose rows are many times one window is walked as windows of its rows, one warp each,
@@ -1154,6 +1229,7 @@ __global__ void __launch_bounds__(128) k_solve64w(DevPlan P, F64Factors F, const
     const bool fvec = ((L.fo & 1) == 0) && ((((uintptr_t)f) & 15) == 0);
     const bool xvec = ((L.fo & 1) == 0) && ((((uintptr_t)x) & 15) == 0);
     const double sg = L.s >= 0 ? F.sig[L.s] : 0.0;
+    const Interior I = interior_of(F, L, d.x, lane);
 
     // ---- forward: L g = f over the window's pairs ----
     double2 ca[U2], cb[U2], cf[U2], na[U2], nb[U2], nf[U2];
@@ -1162,10 +1238,15 @@ __global__ void __launch_bounds__(128) k_solve64w(DevPlan P, F64Factors F, const
       for (int u = 0; u < U2; ++u) {
         const int64_t q = qb + u;
         if (q < q1) {
-          const double2* rec = fwd + ((P0 + q) * 2) * kWarp + lane;
-          A[u] = __ldg(rec);
-          B[u] = __ldg(rec + kWarp);
           const int64_t r = 2 * q;
+          if (r >= I.lo && r + 1 <= I.hi) {  // interior: the records are known
+            A[u] = make_double2(I.ia, I.ia);
+            B[u] = make_double2(I.be, I.be);
+          } else {
+            const double2* rec = fwd + ((P0 + q) * 2) * kWarp + lane;
+            A[u] = __ldg(rec);
+            B[u] = __ldg(rec + kWarp);
+          }
           if (hl && lcut && q < q0 + oh) {
             Fv[u] = hl[(q - q0) * kWarp];
           } else if (hr && rcut && q >= q1 - oh) {
@@ -1212,9 +1293,14 @@ __global__ void __launch_bounds__(128) k_solve64w(DevPlan P, F64Factors F, const
       for (int u = 0; u < U2; ++u) {
         const int64_t q = qb - u;
         if (q >= k0) {
-          const double2* rec = bwd + ((P0 + q) * 2) * kWarp + lane;
-          Ga[u] = __ldg(rec);
-          De[u] = __ldg(rec + kWarp);
+          if (2 * q >= I.lo && 2 * q + 1 <= I.hi) {
+            Ga[u] = make_double2(I.ga, I.ga);
+            De[u] = make_double2(I.de, I.de);
+          } else {
+            const double2* rec = bwd + ((P0 + q) * 2) * kWarp + lane;
+            Ga[u] = __ldg(rec);
+            De[u] = __ldg(rec + kWarp);
+          }
           Gv[u] = q >= k1 ? gside[(q - k1) * kWarp] : g2s[(P0 + q) * kWarp + lane];
         }
       }
@@ -1430,6 +1516,12 @@ cudaError_t launch_solve64w(const DevPlan& P, F64Factors F, const int4* win, int
     if (unroll == 2) return go(k_solve64w<1, false>);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_interior64(const DevPlan& P, F64Factors F, double4* icst, int32_t* ik, cudaStream_t st) {
+  if (P.ngroups == 0 || P.shared || !F.sig) return cudaErrorInvalidValue;
+  k_interior64<<<grid_for(P.ngroups * kWarp, 128), 128, 0, st>>>(P, F, icst, ik);
+  return cudaGetLastError();
 }
 
 }  // namespace pent

@@ -79,6 +79,7 @@ struct pent_plan {
   int64_t win64_cap = 0;          // windows the workspace holds
   int64_t nwin64 = 0;             // windows of the current factorisation (0: none)
   bool persistent = false;        // PENT_OPT_PERSISTENT: window launches as resident grids
+  bool f64_interior = true;       // PENT_OPT_FP64_INTERIOR: hyperdiffusion walks take interior records from registers
   std::vector<F64Run> wruns;      // the runs of the other groups
   int64_t part_rows = -1;  // PENT_OPT_PARTITION_ROWS (-1: automatic)
   bool periodic = false;   // PENT_OPT_PERIODIC: cyclic systems (Navon's reduction)
@@ -127,7 +128,7 @@ struct pent_plan {
   Region r_info, r_perm, r_off, r_n, r_goff, r_glen, r_sigma, r_fwd, r_bwd, r_scr, r_fac32, r_sig32, r_foff, r_shape,
       r_sys32, r_adi, r_cmap, r_swU, r_swE, r_pck, r_pcc, r_pcbase, r_pcnum, r_pcmap, r_pU, r_pE, r_per, r_psinv,
       r_pg, r_rhs, r_psinv32, r_urec, r_kscale, r_uwin, r_win, r_whalo, r_wsys32, r_gover, r_win64, r_side64,
-      r_halo64;
+      r_halo64, r_icst, r_ik;
   size_t ws_bytes = 0;
   // binding / state
   unsigned char* ws = nullptr;
@@ -184,7 +185,12 @@ struct pent_plan {
   }
   // Hyperdiffusion factors of per-system matrices use the constant-epsilon records.
   F64Factors f64() const {
-    return F64Factors{at<double>(r_fwd), at<double>(r_bwd), (factored == 2 && !shared) ? at<double>(r_sigma) : nullptr};
+    F64Factors F{at<double>(r_fwd), at<double>(r_bwd), (factored == 2 && !shared) ? at<double>(r_sigma) : nullptr};
+    if (factored == 2 && !shared && f64_interior && r_ik.bytes > 1) {
+      F.icst = at<double4>(r_icst);
+      F.ik = at<int32_t>(r_ik);
+    }
+    return F;
   }
   F64Part part() const {
     F64Part X;
@@ -526,6 +532,9 @@ void layout(pent_plan* p) {
         p->win64_cap += window_layout(p->glen[k], p->win64_rows, p->win64_omax, nullptr, 0);
     }
     const size_t wpairs = (size_t)p->win64_cap * (p->win64_omax / 2) * kWarp;  // double2 per window side
+    // interior records per group lane (hyperdiffusion factorisations)
+    take(p->r_icst, (size_t)(p->shared ? 0 : p->ngroups * kWarp) * sizeof(double4));
+    take(p->r_ik, (size_t)(p->shared ? 0 : p->ngroups * kWarp) * sizeof(int32_t));
     take(p->r_gover, (size_t)(p->win64_cap > 0 ? p->ngroups : 0) * sizeof(int32_t));
     take(p->r_win64, (size_t)p->win64_cap * sizeof(int4));
     take(p->r_side64, wpairs * 2 * sizeof(double));
@@ -833,6 +842,12 @@ pent_status pent_plan_set_option(pent_plan* p, int key, int64_t value) {
       ++p->cfg_version;
       p->drop_graphs();
       return PENT_OK;
+    case PENT_OPT_FP64_INTERIOR:
+      if (p->precision != PENT_F64 || (value != 0 && value != 1)) return PENT_EINVAL;
+      p->f64_interior = value == 1;
+      ++p->cfg_version;
+      p->drop_graphs();
+      return PENT_OK;
     case PENT_OPT_PERSISTENT:
       if (p->periodic || (value != 0 && value != 1)) return PENT_EINVAL;
       p->persistent = value == 1;
@@ -887,6 +902,7 @@ pent_status pent_plan_get_option(const pent_plan* p, int key, int64_t* value) {
     case PENT_OPT_WINDOWS: *value = p->precision == PENT_F64 ? p->nwin64 : p->nwin; return PENT_OK;
     case PENT_OPT_WINDOW_ROWS: *value = p->win64_rows; return PENT_OK;
     case PENT_OPT_PERSISTENT: *value = p->persistent ? 1 : 0; return PENT_OK;
+    case PENT_OPT_FP64_INTERIOR: *value = p->f64_interior ? 1 : 0; return PENT_OK;
   }
   return PENT_EINVAL;
 }
@@ -1090,8 +1106,10 @@ static cudaError_t build_windows64(pent_plan* p) {
   return cudaSuccess;
 }
 
+// windows = false: lay out no FP64 windows (a refactorisation inside a solve: the layout would wait
+// for the stream on every call), dropping those of an earlier factorisation.
 static pent_status factor_common(pent_plan* p, const double* a, const double* b, const double* c, const double* d,
-                                 const double* e, const double* sigma) {
+                                 const double* e, const double* sigma, bool windows = true) {
   if (!p) return PENT_EINVAL;
   if (!p->bound) return PENT_ENOTBOUND;
   p->drop_graphs();
@@ -1117,9 +1135,12 @@ static pent_status factor_common(pent_plan* p, const double* a, const double* b,
     if (err == cudaSuccess && p->shared) err = launch_chunk_maps(F, (int)p->n_uniform, p->at<double>(p->r_cmap), p->stream);
     // chunk maps of the partitioned groups
     if (err == cudaSuccess && p->pchunks > 0) err = launch_chunk_maps64(P, F, p->part(), 0, p->pchunks, p->stream);
+    // interior records of the hyperdiffusion walks
+    if (err == cudaSuccess && sigma && !p->shared)
+      err = launch_interior64(P, F, p->at<double4>(p->r_icst), p->at<int32_t>(p->r_ik), p->stream);
     // windows of the long groups (hyperdiffusion records); a general band keeps the runs
     if (err == cudaSuccess && p->win64_cap > 0) {
-      if (sigma) {
+      if (sigma && windows) {
         err = build_windows64(p);
       } else if (p->nwin64) {
         p->nwin64 = 0;
@@ -1472,7 +1493,7 @@ pent_status pent_refactor_solve_hyperdiff(pent_plan* p, const double* d_sigma, c
   if (p->precision != PENT_F64 || p->periodic) return PENT_EINVAL;
   if (p->shared || p->pchunks > 0) {
     // one matrix for the batch, or groups solved in chunks: factor, then solve
-    pent_status st = factor_common(p, nullptr, nullptr, nullptr, nullptr, nullptr, d_sigma);
+    pent_status st = factor_common(p, nullptr, nullptr, nullptr, nullptr, nullptr, d_sigma, false);
     return st != PENT_OK ? st : solve_launch(p, f, x, 0);
   }
   pent_status st = reset_info(p);
@@ -1482,11 +1503,17 @@ pent_status pent_refactor_solve_hyperdiff(pent_plan* p, const double* d_sigma, c
   F.sig = p->at<double>(p->r_sigma);
   if (p->factored != 2) p->drop_graphs();  // graphs cached for another record form
   double* gscr = p->at<double>(p->r_scr);
-  const cudaError_t err = fork_join(p, p->runs.size(), [&](size_t i, cudaStream_t s) {
+  cudaError_t err = fork_join(p, p->runs.size(), [&](size_t i, cudaStream_t s) {
     const auto& r = p->runs[i];
     return launch_refactor_solve64(P, F, d_sigma, f, x, gscr, r.bw, r.g0, r.g1, s);
   });
+  // the new records' interior values; the windows' overlaps were those of the old sigma
+  if (err == cudaSuccess) err = launch_interior64(P, F, p->at<double4>(p->r_icst), p->at<int32_t>(p->r_ik), p->stream);
   if (err != cudaSuccess) return PENT_ECUDA;
+  if (p->nwin64) {
+    p->nwin64 = 0;
+    ++p->cfg_version;
+  }
   p->factored = 2;
   return PENT_OK;
 }

@@ -315,3 +315,17 @@ def test_persistent_option_host_checks(L):
     assert L.pent_plan_set_option(h, _lib.PENT_OPT_PERIODIC, 1) == 0
     assert L.pent_plan_set_option(h, _lib.PENT_OPT_PERSISTENT, 1) == _lib.PENT_EINVAL
     L.pent_plan_destroy(h)
+
+
+def test_fp64_interior_option_host_checks(L):
+    """PENT_OPT_FP64_INTERIOR: FP64 plans only, 0 or 1 (default 1), at any time."""
+    st, h = _create(L, batch=4, n_uniform=1024)
+    v = ctypes.c_int64(-1)
+    assert L.pent_plan_get_option(h, _lib.PENT_OPT_FP64_INTERIOR, ctypes.byref(v)) == 0 and v.value == 1
+    assert L.pent_plan_set_option(h, _lib.PENT_OPT_FP64_INTERIOR, 0) == 0
+    assert L.pent_plan_get_option(h, _lib.PENT_OPT_FP64_INTERIOR, ctypes.byref(v)) == 0 and v.value == 0
+    assert L.pent_plan_set_option(h, _lib.PENT_OPT_FP64_INTERIOR, 2) == _lib.PENT_EINVAL
+    L.pent_plan_destroy(h)
+    st, h = _create(L, batch=4, n_uniform=1024, prec=1)
+    assert L.pent_plan_set_option(h, _lib.PENT_OPT_FP64_INTERIOR, 1) == _lib.PENT_EINVAL
+    L.pent_plan_destroy(h)
