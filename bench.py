@@ -856,6 +856,50 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+PROFILE_CASES = ("fp32_steps", "fp64_solve", "fp32_windows", "fp64_windows", "uneven_fp32", "uneven_fp64")
+
+
+def run_profile_case(name):
+    """One small run of a kernel for an ncu capture (never a bench value): the launch to capture
+    is the second of its kind.  fp32_steps: 16,384 x 1024 parametric FP32+refine, a 4-step graph
+    (k_solve32u with float pairs in and out in the middle steps); fp64_solve: 32,768 x 1024 FP64,
+    two solves (k_solve64_pair); fp32_windows: 2,000 x 8,192 FP32+refine, two out-of-place
+    solves (k_solve32u windows); fp64_windows: 4,096 x 8,192 FP64, two in-place solves
+    (k_win64_halo, k_solve64w); uneven_fp32 / uneven_fp64: the uneven batch (20,000 systems),
+    factor and two 2-step graphs (the launch list of its steps)."""
+    import torch
+    import paper_1807_07382_gb300 as pb
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    tune = os.path.join(ROOT, "paper_1807_07382_gb300", "tune_gb300.txt")
+    prec = pb.PENT_F64 if "fp64" in name else pb.PENT_F32_REFINE
+    if name.startswith("uneven"):
+        w = synth.uneven(steps=2)
+    elif name.endswith("windows"):
+        w = synth.hyperdiff_parametric(batch=2000 if prec == pb.PENT_F32_REFINE else 4096, n=8192, steps=1,
+                                       seed_index=3, sigma_range=(1e-2, 10.0))
+    else:
+        w = synth.hyperdiff_parametric(batch=16384 if prec == pb.PENT_F32_REFINE else 32768, n=1024, steps=1)
+    plan = pb.Plan(list(w.n), precision=prec, stream=stream, device=dev, tune_cache=tune)
+    plan.factor_hyperdiff(torch.from_numpy(w.sigma).to(dev))
+    x = torch.from_numpy(w.field0).to(dev)
+    if name == "fp32_steps":
+        plan.solve_steps(x, 4, max_refine=1)
+    elif name.startswith("uneven"):
+        for _ in range(2):
+            plan.solve_steps(x, 2, max_refine=1)
+    elif name == "fp32_windows":
+        y = torch.empty_like(x)
+        for _ in range(2):
+            plan.solve(x, y, max_refine=1)
+    else:
+        for _ in range(2):
+            plan.solve(x, x, max_refine=1)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": name, "rows": int(w.n.sum()), "windows": plan.get_option(pb.PENT_OPT_WINDOWS)}))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -879,7 +923,12 @@ def main():
     ap.add_argument("--workload", default=None,
                     help="comma-separated other workloads: cosines, uneven, adi, adjoint, periodic_cn, ch1d, rewrite, shared, "
                          "or all (one JSON line each; the default run is the parametric headline line)")
+    ap.add_argument("--profile-case", choices=PROFILE_CASES, default=None,
+                    help="run one small case of a kernel for an ncu capture and exit (no timing)")
     args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case(args.profile_case)
+        return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.workload:

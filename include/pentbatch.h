@@ -216,10 +216,11 @@ enum {
   PENT_OPT_FP64_INTERIOR = 16      /* PENT_F64: 1 (the default) lets the walks of a hyperdiffusion
                                       factorisation (pent_factor_hyperdiff, per-system matrices) take the
                                       records of the interior rows from registers: rows 2 .. n - 3 of
-                                      I + sigma D4 share one band row, so once the factorisation's row
-                                      step reaches the record of row n - 3 from two rows holding it, every
-                                      later interior row holds the same bits (found per system at factor
-                                      time); 0 reads every record from memory.  Bitwise the same results. */
+                                      I + sigma D4 share one band row and the factorisation's row step
+                                      settles, so past the first few dozen rows every row pair holds the
+                                      same bits; the run of such pairs is found per system at factor time
+                                      (and after pent_refactor_solve_hyperdiff); 0 reads every record from
+                                      memory.  Bitwise the same results. */
 };
 pent_status pent_plan_set_option(pent_plan* plan, int key, int64_t value);
 pent_status pent_plan_get_option(const pent_plan* plan, int key, int64_t* value);

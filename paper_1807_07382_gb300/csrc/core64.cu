@@ -180,9 +180,9 @@ __device__ __forceinline__ int64_t scr_idx(const Lane& L, int64_t r, int lane) {
   return SHARED ? (L.R0 + r) * kWarp + lane : (((L.R0 + r) >> 1) * kWarp + lane) * 2 + ((L.R0 + r) & 1);
 }
 
-// The lane's interior records (rows lo .. hi take them from registers; lo > hi: none).
+// The lane's interior records: pairs lo .. hi take them from registers (lo > hi: none).
 struct Interior {
-  double ia = 0.0, be = 0.0, ga = 0.0, de = 0.0;
+  double2 ia = {0.0, 0.0}, be = {0.0, 0.0}, ga = {0.0, 0.0}, de = {0.0, 0.0};
   int64_t lo = INT64_MAX, hi = -1;
 };
 __device__ __forceinline__ Interior interior_of(const F64Factors& F, const Lane& L, int64_t k, int lane) {
@@ -191,13 +191,12 @@ __device__ __forceinline__ Interior interior_of(const F64Factors& F, const Lane&
     const int64_t q = k * kWarp + lane;
     const int K = F.ik[q];
     if (K != INT_MAX) {
-      const double4 c = F.icst[q];
-      I.ia = c.x;
-      I.be = c.y;
-      I.ga = c.z;
-      I.de = c.w;
+      I.ia = F.icst[q * 4 + 0];
+      I.be = F.icst[q * 4 + 1];
+      I.ga = F.icst[q * 4 + 2];
+      I.de = F.icst[q * 4 + 3];
       I.lo = K;
-      I.hi = L.n - 3;
+      I.hi = (L.n - 4) / 2;
     }
   }
   return I;
@@ -337,9 +336,9 @@ __global__ void __launch_bounds__(128) k_solve64_pair(DevPlan P, F64Factors F, c
           A[u] = make_double2(__ldg(ra), __ldg(ra + 3));
           B[u] = make_double2(__ldg(ra + 1), __ldg(ra + 4));
           E[u] = make_double2(__ldg(ra + 2), __ldg(ra + 5));
-        } else if (HYP && 2 * q >= I.lo && 2 * q + 1 <= I.hi) {  // interior: the records are known
-          A[u] = make_double2(I.ia, I.ia);
-          B[u] = make_double2(I.be, I.be);
+        } else if (HYP && q >= I.lo && q <= I.hi) {  // interior: the records are known
+          A[u] = I.ia;
+          B[u] = I.be;
         } else {
           const double2* rec = fwd + ((P0 + q) * NP) * kWarp + lane;
           A[u] = __ldg(rec);
@@ -398,9 +397,9 @@ __global__ void __launch_bounds__(128) k_solve64_pair(DevPlan P, F64Factors F, c
           const double* rb = bwd1 + (2 * q) * 2;
           Ga[u] = make_double2(__ldg(rb), __ldg(rb + 2));
           De[u] = make_double2(__ldg(rb + 1), __ldg(rb + 3));
-        } else if (HYP && 2 * q >= I.lo && 2 * q + 1 <= I.hi) {
-          Ga[u] = make_double2(I.ga, I.ga);
-          De[u] = make_double2(I.de, I.de);
+        } else if (HYP && q >= I.lo && q <= I.hi) {
+          Ga[u] = I.ga;
+          De[u] = I.de;
         } else {
           const double2* rec = bwd + ((P0 + q) * 2) * kWarp + lane;
           Ga[u] = __ldg(rec);
@@ -1086,47 +1085,53 @@ inline int grid_for(int64_t threads, int block) { return (int)((threads + block 
 
 // ---- interior records of hyperdiffusion factorisations ----
 //
-// Rows 2 .. n - 3 of I + sigma D4 share one band row, so the factorisation's row step (Sec. 2.4)
-// maps the (gamma, delta) records of the two rows before a row to that row's records by one fixed
-// function.  Once rows r - 2 and r - 1 hold the (gamma, delta) of row n - 3 and row r holds all of
-// row n - 3's record, every row up to n - 3 holds that record, bit for bit: the walks can take it
-// from registers there instead of memory, with the same arithmetic.  One thread per group lane:
-// ik = the first such row r (INT_MAX if none), icst = the record (1/alpha, beta, gamma, delta).
-__global__ void k_interior64(DevPlan P, F64Factors F, double4* __restrict__ icst, int32_t* __restrict__ ik) {
-  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (q >= P.ngroups * kWarp) return;
-  const int lane = (int)(q % kWarp);
-  const Lane L = lane_setup<false>(P, q / kWarp, lane);
+// Rows 2 .. n - 3 of I + sigma D4 share one band row, and the factorisation's row step (Sec. 2.4)
+// settles: past the first few dozen rows every row pair holds the same records bit for bit (a
+// fixed point of the step, or a cycle of two rows, which row pairs also see as fixed).  The walks
+// then take those records from registers instead of memory, with the same arithmetic.  One warp per
+// group lane: ik = the first pair q of the run of pairs equal to pair (n - 4) / 2, the last pair whose
+// rows are both interior (INT_MAX: n < 6), found by scanning back 32 pairs at a time; icst[4 q ..]
+// = that pair's records (1/alpha, beta, gamma, delta), each a double2 of its two rows.
+__global__ void k_interior64(DevPlan P, F64Factors F, double2* __restrict__ icst, int32_t* __restrict__ ik) {
+  const int64_t qg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kWarp;  // group lane
+  if (qg >= P.ngroups * kWarp) return;
+  const int t = threadIdx.x & (kWarp - 1);
+  const int lane = (int)(qg % kWarp);
+  const Lane L = lane_setup<false>(P, qg / kWarp, lane);
+  const double2* __restrict__ fwd = reinterpret_cast<const double2*>(F.fwd);
+  const double2* __restrict__ bwd = reinterpret_cast<const double2*>(F.bwd);
+  const int64_t P0 = L.R0 >> 1;
+  auto same = [](double2 u, double2 v) {
+    return __double_as_longlong(u.x) == __double_as_longlong(v.x) && __double_as_longlong(u.y) == __double_as_longlong(v.y);
+  };
   int K = INT_MAX;
-  double4 c = make_double4(0.0, 0.0, 0.0, 0.0);
-  if (L.s >= 0 && L.n >= 8) {
-    auto bits = [](double v) { return __double_as_longlong(v); };
-    auto rec = [&](int64_t r) {
-      return make_double4(F.fwd[fwd_idx<false, 2>(L, r, 0, lane)], F.fwd[fwd_idx<false, 2>(L, r, 1, lane)],
-                          F.bwd[bwd_idx<false>(L, r, 0, lane)], F.bwd[bwd_idx<false>(L, r, 1, lane)]);
-    };
-    const double4 z = rec(L.n - 3);
-    const long long zg = bits(z.z), zd = bits(z.w);
-    long long g2 = bits(F.bwd[bwd_idx<false>(L, 0, 0, lane)]), d2 = bits(F.bwd[bwd_idx<false>(L, 0, 1, lane)]);
-    long long g1 = bits(F.bwd[bwd_idx<false>(L, 1, 0, lane)]), d1 = bits(F.bwd[bwd_idx<false>(L, 1, 1, lane)]);
-    for (int64_t r = 2; r <= L.n - 3; ++r) {
-      const double4 v = rec(r);
-      if (g2 == zg && d2 == zd && g1 == zg && d1 == zd && bits(v.x) == bits(z.x) && bits(v.y) == bits(z.y) &&
-          bits(v.z) == zg && bits(v.w) == zd) {
-        K = (int)r;
-        c = z;
+  double2 z[4] = {};
+  const int64_t qe = (L.n - 4) / 2;
+  if (L.s >= 0 && L.n >= 6) {
+    z[0] = fwd[((P0 + qe) * 2 + 0) * kWarp + lane];
+    z[1] = fwd[((P0 + qe) * 2 + 1) * kWarp + lane];
+    z[2] = bwd[((P0 + qe) * 2 + 0) * kWarp + lane];
+    z[3] = bwd[((P0 + qe) * 2 + 1) * kWarp + lane];
+    K = 1;  // unless a pair differs
+    for (int64_t base = qe; base >= 1; base -= kWarp) {
+      const int64_t q = base - t;
+      bool diff = false;
+      if (q >= 1) {
+        diff = !same(fwd[((P0 + q) * 2 + 0) * kWarp + lane], z[0]) || !same(fwd[((P0 + q) * 2 + 1) * kWarp + lane], z[1]) ||
+               !same(bwd[((P0 + q) * 2 + 0) * kWarp + lane], z[2]) || !same(bwd[((P0 + q) * 2 + 1) * kWarp + lane], z[3]);
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, diff);
+      if (m) {  // the differing pair nearest the end is the one of the lowest thread with diff set
+        K = (int)(base - (__ffs(m) - 1) + 1);
         break;
       }
-      g2 = g1;
-      d2 = d1;
-      g1 = bits(v.z);
-      d1 = bits(v.w);
     }
   }
-  icst[q] = c;
-  ik[q] = K;
+  if (t == 0) {
+    for (int p = 0; p < 4; ++p) icst[qg * 4 + p] = z[p];
+    ik[qg] = K;
+  }
 }
-
 
 // ---- windowed walks of groups of long hyperdiffusion systems ----
 //
@@ -1239,9 +1244,9 @@ __global__ void __launch_bounds__(128) k_solve64w(DevPlan P, F64Factors F, const
         const int64_t q = qb + u;
         if (q < q1) {
           const int64_t r = 2 * q;
-          if (r >= I.lo && r + 1 <= I.hi) {  // interior: the records are known
-            A[u] = make_double2(I.ia, I.ia);
-            B[u] = make_double2(I.be, I.be);
+          if (q >= I.lo && q <= I.hi) {  // interior: the records are known
+            A[u] = I.ia;
+            B[u] = I.be;
           } else {
             const double2* rec = fwd + ((P0 + q) * 2) * kWarp + lane;
             A[u] = __ldg(rec);
@@ -1293,9 +1298,9 @@ __global__ void __launch_bounds__(128) k_solve64w(DevPlan P, F64Factors F, const
       for (int u = 0; u < U2; ++u) {
         const int64_t q = qb - u;
         if (q >= k0) {
-          if (2 * q >= I.lo && 2 * q + 1 <= I.hi) {
-            Ga[u] = make_double2(I.ga, I.ga);
-            De[u] = make_double2(I.de, I.de);
+          if (q >= I.lo && q <= I.hi) {
+            Ga[u] = I.ga;
+            De[u] = I.de;
           } else {
             const double2* rec = bwd + ((P0 + q) * 2) * kWarp + lane;
             Ga[u] = __ldg(rec);
@@ -1518,9 +1523,9 @@ cudaError_t launch_solve64w(const DevPlan& P, F64Factors F, const int4* win, int
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_interior64(const DevPlan& P, F64Factors F, double4* icst, int32_t* ik, cudaStream_t st) {
+cudaError_t launch_interior64(const DevPlan& P, F64Factors F, double2* icst, int32_t* ik, cudaStream_t st) {
   if (P.ngroups == 0 || P.shared || !F.sig) return cudaErrorInvalidValue;
-  k_interior64<<<grid_for(P.ngroups * kWarp, 128), 128, 0, st>>>(P, F, icst, ik);
+  k_interior64<<<grid_for(P.ngroups * kWarp * kWarp, 128), 128, 0, st>>>(P, F, icst, ik);
   return cudaGetLastError();
 }
 

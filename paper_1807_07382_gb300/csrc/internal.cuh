@@ -41,10 +41,11 @@ struct F64Factors {
   double* fwd;
   double* bwd;
   const double* sig;  // per-system sigma of hyperdiffusion records, nullptr for the general form
-  // Hyperdiffusion records only (or nullptr): per group lane q = 32 k + lane the interior records
-  // (1/alpha, beta, gamma, delta), the same bits on every row ik[q] .. n - 3 of the lane's system
-  // (ik[q] = INT_MAX: none), which the walks then take from registers instead of memory.
-  const double4* icst = nullptr;
+  // Hyperdiffusion records only (or nullptr): per group lane q = 32 k + lane the records of an interior
+  // row pair, icst[4 q + p] for plane p = 1/alpha, beta, gamma, delta (a double2 of the pair's rows),
+  // the same bits on every pair ik[q] .. (n - 4) / 2 of the lane's system (ik[q] = INT_MAX: none),
+  // which the walks then take from registers instead of memory.
+  const double2* icst = nullptr;
   const int32_t* ik = nullptr;
 };
 
@@ -126,7 +127,7 @@ cudaError_t launch_step_rhs(const DevPlan& P, const double* mu, const double* nu
 cudaError_t launch_refactor_solve64(const DevPlan& P, F64Factors F, const double* sigma, const double* f, double* x,
                                     double* gscr, int block_warps, int64_t g0, int64_t g1, cudaStream_t st);
 // Interior records of hyperdiffusion factorisations (F.icst, F.ik; csrc/core64.cu).
-cudaError_t launch_interior64(const DevPlan& P, F64Factors F, double4* icst, int32_t* ik, cudaStream_t st);
+cudaError_t launch_interior64(const DevPlan& P, F64Factors F, double2* icst, int32_t* ik, cudaStream_t st);
 // Windowed walks of groups of long hyperdiffusion systems (csrc/core64.cu).  gover: per group the
 // overlap rows a window needs (a multiple of 8; 0x7fff: more than omax).  win: per window (group,
 // first row, rows | overlap << 16); side: [nwin][omax / 2][32] double2 of g after the kept rows;

@@ -187,7 +187,7 @@ struct pent_plan {
   F64Factors f64() const {
     F64Factors F{at<double>(r_fwd), at<double>(r_bwd), (factored == 2 && !shared) ? at<double>(r_sigma) : nullptr};
     if (factored == 2 && !shared && f64_interior && r_ik.bytes > 1) {
-      F.icst = at<double4>(r_icst);
+      F.icst = at<double2>(r_icst);
       F.ik = at<int32_t>(r_ik);
     }
     return F;
@@ -533,7 +533,7 @@ void layout(pent_plan* p) {
     }
     const size_t wpairs = (size_t)p->win64_cap * (p->win64_omax / 2) * kWarp;  // double2 per window side
     // interior records per group lane (hyperdiffusion factorisations)
-    take(p->r_icst, (size_t)(p->shared ? 0 : p->ngroups * kWarp) * sizeof(double4));
+    take(p->r_icst, (size_t)(p->shared ? 0 : p->ngroups * kWarp) * 4 * sizeof(double2));
     take(p->r_ik, (size_t)(p->shared ? 0 : p->ngroups * kWarp) * sizeof(int32_t));
     take(p->r_gover, (size_t)(p->win64_cap > 0 ? p->ngroups : 0) * sizeof(int32_t));
     take(p->r_win64, (size_t)p->win64_cap * sizeof(int4));
@@ -1137,7 +1137,7 @@ static pent_status factor_common(pent_plan* p, const double* a, const double* b,
     if (err == cudaSuccess && p->pchunks > 0) err = launch_chunk_maps64(P, F, p->part(), 0, p->pchunks, p->stream);
     // interior records of the hyperdiffusion walks
     if (err == cudaSuccess && sigma && !p->shared)
-      err = launch_interior64(P, F, p->at<double4>(p->r_icst), p->at<int32_t>(p->r_ik), p->stream);
+      err = launch_interior64(P, F, p->at<double2>(p->r_icst), p->at<int32_t>(p->r_ik), p->stream);
     // windows of the long groups (hyperdiffusion records); a general band keeps the runs
     if (err == cudaSuccess && p->win64_cap > 0) {
       if (sigma && windows) {
@@ -1508,7 +1508,7 @@ pent_status pent_refactor_solve_hyperdiff(pent_plan* p, const double* d_sigma, c
     return launch_refactor_solve64(P, F, d_sigma, f, x, gscr, r.bw, r.g0, r.g1, s);
   });
   // the new records' interior values; the windows' overlaps were those of the old sigma
-  if (err == cudaSuccess) err = launch_interior64(P, F, p->at<double4>(p->r_icst), p->at<int32_t>(p->r_ik), p->stream);
+  if (err == cudaSuccess) err = launch_interior64(P, F, p->at<double2>(p->r_icst), p->at<int32_t>(p->r_ik), p->stream);
   if (err != cudaSuccess) return PENT_ECUDA;
   if (p->nwin64) {
     p->nwin64 = 0;
