@@ -856,7 +856,8 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-PROFILE_CASES = ("fp32_steps", "fp64_solve", "fp32_windows", "fp64_windows", "uneven_fp32", "uneven_fp64")
+PROFILE_CASES = ("fp32_steps", "fp64_solve", "fp32_windows", "fp64_windows", "uneven_fp32", "uneven_fp64",
+                 "adi_step")
 
 
 def run_profile_case(name):
@@ -866,12 +867,20 @@ def run_profile_case(name):
     two solves (k_solve64_pair); fp32_windows: 2,000 x 8,192 FP32+refine, two out-of-place
     solves (k_solve32u windows); fp64_windows: 4,096 x 8,192 FP64, two in-place solves
     (k_win64_halo, k_solve64w); uneven_fp32 / uneven_fp64: the uneven batch (20,000 systems),
-    factor and two 2-step graphs (the launch list of its steps)."""
+    factor and two 2-step graphs (the launch list of its steps); adi_step: the 2048^2 ADI workload,
+    factor and one step (every kernel of the step once)."""
     import torch
     import paper_1807_07382_gb300 as pb
     dev = torch.device("cuda", 0)
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
+    if name == "adi_step":
+        w = synth.ch_adi(steps=1)
+        adi = pb.ADI2D(w.nx, w.ny, w.gamma, w.dt, w.dx, device=dev, stream=stream)
+        adi.step(torch.from_numpy(w.field0).to(dev))
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": name, "cells": w.nx * w.ny}))
+        return
     tune = os.path.join(ROOT, "paper_1807_07382_gb300", "tune_gb300.txt")
     prec = pb.PENT_F64 if "fp64" in name else pb.PENT_F32_REFINE
     if name.startswith("uneven"):
