@@ -173,3 +173,87 @@ def dense_solve(A, f) -> List[Fraction]:
     for i in range(n - 1, -1, -1):
         x[i] = (M[i][n] - sum(M[i][j] * x[j] for j in range(i + 1, n))) / M[i][i]
     return x
+
+
+# ----------------------------------------------------------------------------- no-flux grids, the ADI step
+
+def noflux_d4_weights(i: int, n: int) -> List[int]:
+    """Sec. 2.2: the centred fourth difference [1, -4, 6, -4, 1] on row i of an n-row cell-centred
+    grid with no-flux walls: a column outside 0..n-1 is mirrored about the wall (-1 -> 0, -2 -> 1,
+    n -> n-1, n+1 -> n-2, again for very short grids) and its weight added there.  Returns the
+    weights of columns i-2 .. i+2 (a weight mirrored outside that window is not possible for n >= 2)."""
+    w = [0] * 5
+    for k, c in enumerate((1, -4, 6, -4, 1)):
+        j = i + k - 2
+        while j < 0 or j >= n:
+            j = -1 - j if j < 0 else 2 * n - 1 - j
+        w[j - i + 2] += c
+    return w
+
+
+def noflux_hyperdiff_band(n: int, sigma) -> tuple:
+    """The band (a, b, c, d, e) of I + sigma D4 on the no-flux grid, exactly: row i holds a_i at
+    column i-2, ..., e_i at column i+2."""
+    s = exact(sigma)
+    a, b, c, d, e = ([Fraction(0)] * n for _ in range(5))
+    for i in range(n):
+        w = noflux_d4_weights(i, n)
+        a[i], b[i], c[i], d[i], e[i] = s * w[0], s * w[1], 1 + s * w[2], s * w[3], s * w[4]
+    return a, b, c, d, e
+
+
+def band_apply(band, x) -> List[Fraction]:
+    """A x for a band (a, b, c, d, e), exactly."""
+    a, b, c, d, e = band
+    n = len(c)
+    x = [exact(v) for v in x]
+    return [sum(coef[i] * x[i + off] for off, coef in ((-2, a), (-1, b), (0, c), (1, d), (2, e)) if 0 <= i + off < n)
+            for i in range(n)]
+
+
+def laplacian_noflux(V) -> List[List[Fraction]]:
+    """The five-point Laplacian in grid units with the no-flux mirror (the ghost beyond a wall equals
+    the cell next to it), on a list of ny rows of nx values, exactly."""
+    ny, nx = len(V), len(V[0])
+    v = [[exact(q) for q in row] for row in V]
+    out = [[Fraction(0)] * nx for _ in range(ny)]
+    for y in range(ny):
+        for x in range(nx):
+            c0 = v[y][x]
+            w = v[y][x - 1] if x > 0 else c0
+            ea = v[y][x + 1] if x + 1 < nx else c0
+            s = v[y - 1][x] if y > 0 else c0
+            nn = v[y + 1][x] if y + 1 < ny else c0
+            out[y][x] = (w - 2 * c0 + ea) + (s - 2 * c0 + nn)
+    return out
+
+
+def ch_rhs(C, mu, sigma) -> List[List[Fraction]]:
+    """The delta form's right-hand side mu L(C^3 - C) - sigma L(L C) (Sec. 2.1's explicit part of the
+    semi-implicit Cahn-Hilliard step with D = 1, the fourth-order term at the old level), exactly."""
+    c = [[exact(q) for q in row] for row in C]
+    u = [[q * q * q - q for q in row] for row in c]
+    lu, llc = laplacian_noflux(u), laplacian_noflux(laplacian_noflux(c))
+    m, s = exact(mu), exact(sigma)
+    return [[m * lu[y][x] - s * llc[y][x] for x in range(len(c[0]))] for y in range(len(c))]
+
+
+def adi_delta(rhs, sigma) -> List[List[Fraction]]:
+    """dC with (I + sigma D4_x)(I + sigma D4_y) dC = rhs: every grid row solved along x, then every
+    column along y, each by the Sec. 2.4 factorisation and substitutions of the shared band."""
+    ny, nx = len(rhs), len(rhs[0])
+    fx = factor(*noflux_hyperdiff_band(nx, sigma))
+    W = [solve(fx, row) for row in rhs]
+    fy = factor(*noflux_hyperdiff_band(ny, sigma))
+    cols = [solve(fy, [W[y][x] for y in range(ny)]) for x in range(nx)]
+    return [[cols[x][y] for x in range(nx)] for y in range(ny)]
+
+
+def adi_step(C, mu, sigma) -> List[List[Fraction]]:
+    """One Douglas ADI step of 2D Cahn-Hilliard in the delta form (the reading of Sec. 4's ADI remark that
+    the library and the oracle share): dC from adi_delta of ch_rhs, its mean removed (zero exactly:
+    L and D4 have zero column sums), C + dC."""
+    dC = adi_delta(ch_rhs(C, mu, sigma), sigma)
+    ny, nx = len(dC), len(dC[0])
+    mean = sum(sum(row) for row in dC) / (nx * ny)
+    return [[exact(C[y][x]) + dC[y][x] - mean for x in range(nx)] for y in range(ny)]

@@ -7,7 +7,9 @@ the implicit factors have condition ~2.8e6 and two independent FP64
 implementations already differ by ~1e-8 relative after one step; there the bar
 is 4x the difference between the oracle and an independent FP64 reference
 (LAPACK's banded solver, scipy.linalg.solve_banded), computed in the test.
-Mass is conserved to 1e-12 of sum|C0| in every case."""
+Mass is conserved to 1e-12 of sum|C0| in every case (the step removes the mean of
+dC, so this holds by construction); the sweeps themselves are pinned on small
+grids to an exact rational step, in which dC sums to zero with no removal."""
 import numpy as np
 import pytest
 
@@ -152,3 +154,24 @@ def test_adi_refuses_parameters_the_plans_were_not_factored_for():
     assert not torch.equal(C, C0)
     px.factor_hyperdiff(sig)                               # refactored otherwise: the record is gone
     assert step(gamma, dt, dx) == pb._lib.PENT_EINVAL
+
+
+@pytest.mark.parametrize("ny,nx,dt,dx,bar", [(20, 24, 1e-4, 1 / 64, 1e-13), (20, 24, 1e-6, 1 / 2048, 2e-9),
+                                             (32, 40, 1e-6, 1 / 2048, 2e-9)])
+def test_adi_step_against_the_exact_step(ny, nx, dt, dx, bar):
+    """The sweeps (and the right-hand side) against one exact rational ADI step (oracle/exact.py: the
+    same doubles taken as rationals, every operation in Fractions), relative to max|dC|: to within
+    rounding at sigma = 16.8, and at the workload's sigma = 1.76e5 (condition ~3e6) within that
+    condition times FP64 rounding, as close as the FP64 oracle comes (printed beside it).  The mean
+    removal changes nothing here: the exact dC sums to zero."""
+    from oracle import exact as ex
+    C0 = synth.uniform(4242, 0, nx * ny, -0.1, 0.1).reshape(ny, nx)
+    gamma = 0.01
+    mu, sigma = dt / (dx * dx), gamma * dt / (dx * dx * dx * dx)
+    E = np.array([[float(v) for v in row] for row in ex.adi_step(C0.tolist(), mu, sigma)])
+    scale = np.max(np.abs(E - C0))
+    got = run_gpu(C0, gamma, dt, dx, 1)
+    orc = oracle.adi_step(C0, gamma, dt, dx)
+    e_gpu, e_orc = np.max(np.abs(got - E)) / scale, np.max(np.abs(orc - E)) / scale
+    print(f"sigma {sigma:.3g}: gpu vs exact {e_gpu:.2e}, oracle vs exact {e_orc:.2e}")
+    assert e_gpu <= bar

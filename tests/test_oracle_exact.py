@@ -66,3 +66,59 @@ def test_fp64_oracle_lies_within_its_forward_error_bound(n):
     err = np.max(np.abs(xo - xe))
     print(f"n={n}: FP64 oracle vs exact {err / np.max(np.abs(xe)):.2e} of max|C'|, bound {bound / np.max(np.abs(xe)):.2e}")
     assert err <= bound
+
+
+# ----------------------------------------------------------------------------- the exact ADI step
+
+def _grid(ny, nx, seed):
+    return synth.uniform(seed, 0, nx * ny, -0.1, 0.1).reshape(ny, nx)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 8, 13])
+@pytest.mark.parametrize("sigma", [0.5, 0.25, 2.0])
+def test_noflux_band_equals_the_oracles(n, sigma):
+    """The exact no-flux band (its mirrored D4 weights written out here) equals the C oracle's band
+    entry by entry where sigma times the weights is exact in FP64 (a power of two)."""
+    e = ex.noflux_hyperdiff_band(n, sigma)
+    o = oracle.band_hyperdiff(n, sigma)
+    inside = [lambda i: i >= 2, lambda i: i >= 1, lambda i: True, lambda i: i + 1 < n, lambda i: i + 2 < n]
+    for k in range(5):
+        for i in range(n):
+            if inside[k](i):
+                assert Fraction(float(o[k][i])) == e[k][i], (k, i)
+    # D4 reflected is symmetric with zero row sums, so I + sigma D4 has unit row and column sums
+    for i in range(n):
+        row = [e[0][i], e[1][i], e[2][i], e[3][i], e[4][i]]
+        assert sum(c for off, c in zip(range(-2, 3), row) if 0 <= i + off < n) == 1
+
+
+@pytest.mark.parametrize("ny,nx,sigma", [(5, 7, 0.7), (9, 6, 343.6), (10, 12, 1.76e5)])
+def test_exact_adi_delta_solves_both_factors_and_keeps_the_mass(ny, nx, sigma):
+    """(I + sigma D4_x)(I + sigma D4_y) dC = rhs holds exactly for the exact dC, whose sum is exactly
+    zero (L has zero column sums and both factors unit ones), so the mean the step removes is zero
+    and the step keeps sum C exactly."""
+    C = _grid(ny, nx, 11)
+    mu = 0.41
+    rhs = ex.ch_rhs(C.tolist(), mu, sigma)
+    assert sum(sum(r) for r in rhs) == 0
+    dC = ex.adi_delta(rhs, sigma)
+    bx, by = ex.noflux_hyperdiff_band(nx, sigma), ex.noflux_hyperdiff_band(ny, sigma)
+    Y = [ex.band_apply(by, [dC[y][x] for y in range(ny)]) for x in range(nx)]  # y factor, per column
+    back = [ex.band_apply(bx, [Y[x][y] for x in range(nx)]) for y in range(ny)]  # then the x factor
+    assert back == rhs
+    assert sum(sum(r) for r in dC) == 0
+    C1 = ex.adi_step(C.tolist(), mu, sigma)
+    assert sum(sum(r) for r in C1) == sum(ex.exact(v) for v in C.ravel())
+
+
+@pytest.mark.parametrize("ny,nx,dt,dx,bar", [(10, 12, 1e-4, 1 / 64, 1e-13), (20, 24, 1e-6, 1 / 2048, 2e-9)])
+def test_fp64_oracle_adi_step_near_the_exact_step(ny, nx, dt, dx, bar):
+    """The FP64 oracle's step against the exact step on the same doubles (relative to max|dC|): at
+    sigma = 16.8 to within rounding; at the workload's sigma = 1.76e5, where the factors'
+    condition is ~3e6, within that condition times FP64 rounding (measured 3e-10)."""
+    C = _grid(ny, nx, 12)
+    gamma = 0.01
+    mu, sigma = dt / (dx * dx), gamma * dt / (dx * dx * dx * dx)
+    E = np.array([[float(v) for v in row] for row in ex.adi_step(C.tolist(), mu, sigma)])
+    O = oracle.adi_step(C, gamma, dt, dx)
+    assert np.max(np.abs(O - E)) <= bar * np.max(np.abs(E - C))
