@@ -24,8 +24,16 @@ Fractions, in the order the paper gives:
     with out-of-range quantities zero.
 
 A dense Gaussian elimination in Fractions (dense_solve) is the independent
-check of the reduction.  Exact results have no rounding to compare with: they
-are the reference that a floating-point step's error is measured against.
+check of the reduction.
+
+Also one step of the 2D Cahn-Hilliard ADI scheme on the no-flux grid, exactly
+(adi_step): the delta form's right-hand side mu L(C^3 - C) - sigma L(L C)
+(Sec. 2.1, the fourth-order term at the old level), then (I + sigma D4_x) and
+(I + sigma D4_y) solved along the rows and the columns by the same Sec. 2.4
+recurrences (the no-flux D4 of Sec. 2.2 with its mirrored weights written out),
+then dC less its mean (zero in exact arithmetic).  Exact results have no
+rounding to compare with: they are the reference that a floating-point step's
+error is measured against.
 """
 from __future__ import annotations
 
