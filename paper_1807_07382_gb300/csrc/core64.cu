@@ -1231,10 +1231,15 @@ __global__ void __launch_bounds__(128) k_solve64w(DevPlan P, F64Factors F, const
     const double2* hl = halo ? halo + ((w * 2 + 0) * hp) * kWarp + lane : nullptr;
     const double2* hr = halo ? halo + ((w * 2 + 1) * hp) * kWarp + lane : nullptr;
     const int64_t P0 = L.R0 >> 1;
-    const bool fvec = ((L.fo & 1) == 0) && ((((uintptr_t)f) & 15) == 0);
-    const bool xvec = ((L.fo & 1) == 0) && ((((uintptr_t)x) & 15) == 0);
+    // 16-byte accesses of f and x: a system starting at an even row reads and writes the pair
+    // (2q, 2q + 1) as one double2; one starting at an odd row the aligned double2 (2q + 1, 2q + 2),
+    // carrying row 2q from the previous one (forward) or row 2q + 2 in the state (back)
+    const bool odd = (L.fo & 1) != 0;
+    const bool fvec = ((((uintptr_t)f) & 15) == 0), xvec = ((((uintptr_t)x) & 15) == 0);
     const double sg = L.s >= 0 ? F.sig[L.s] : 0.0;
     const Interior I = interior_of(F, L, d.x, lane);
+    double fcarry = 0.0;  // odd systems: f of row 2q for the next pair read from f
+    bool cvalid = false;
 
     // ---- forward: L g = f over the window's pairs ----
     double2 ca[U2], cb[U2], cf[U2], na[U2], nb[U2], nf[U2];
@@ -1254,13 +1259,20 @@ __global__ void __launch_bounds__(128) k_solve64w(DevPlan P, F64Factors F, const
           }
           if (hl && lcut && q < q0 + oh) {
             Fv[u] = hl[(q - q0) * kWarp];
+            cvalid = false;
           } else if (hr && rcut && q >= q1 - oh) {
             Fv[u] = hr[(q - (q1 - oh)) * kWarp];
-          } else if (fvec && r + 1 < L.n) {
+          } else if (fvec && !odd && r + 1 < L.n) {
             Fv[u] = *reinterpret_cast<const double2*>(f + L.fo + r);
+          } else if (fvec && odd && r + 2 < L.n) {  // rows r + 1, r + 2 aligned; row r carried
+            const double2 D = *reinterpret_cast<const double2*>(f + L.fo + r + 1);
+            Fv[u] = make_double2(cvalid ? fcarry : f[L.fo + r], D.x);
+            fcarry = D.y;
+            cvalid = true;
           } else {
             Fv[u].x = (r < L.n) ? f[L.fo + r] : 0.0;
             Fv[u].y = (r + 1 < L.n) ? f[L.fo + r + 1] : 0.0;
+            cvalid = false;
           }
         }
       }
@@ -1322,11 +1334,25 @@ __global__ void __launch_bounds__(128) k_solve64w(DevPlan P, F64Factors F, const
           const double xa = fma(-cg[u].x, xb, fma(-cd[u].x, x1, cG[u].x));
           if (q < k1) {
             const int64_t r = 2 * q;
-            if (xvec && r + 1 < L.n) {
-              *reinterpret_cast<double2*>(x + L.fo + r) = make_double2(xa, xb);
-            } else {
+            if (!odd) {
+              if (xvec && r + 1 < L.n) {
+                *reinterpret_cast<double2*>(x + L.fo + r) = make_double2(xa, xb);
+              } else {
+                if (r < L.n) x[L.fo + r] = xa;
+                if (r + 1 < L.n) x[L.fo + r + 1] = xb;
+              }
+            } else if (!xvec) {
               if (r < L.n) x[L.fo + r] = xa;
               if (r + 1 < L.n) x[L.fo + r + 1] = xb;
+            } else {
+              // rows r + 1 (this pair) and r + 2 (x1, the pair above, if kept) as one aligned double2;
+              // row r goes out with the pair below, or alone at the window's first kept pair
+              if (q + 1 < k1 && r + 2 < L.n) {
+                *reinterpret_cast<double2*>(x + L.fo + r + 1) = make_double2(xb, x1);
+              } else if (r + 1 < L.n) {
+                x[L.fo + r + 1] = xb;
+              }
+              if (q == k0 && r < L.n) x[L.fo + r] = xa;
             }
           }
           x2 = xb;

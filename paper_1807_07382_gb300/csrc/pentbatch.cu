@@ -579,9 +579,11 @@ void layout(pent_plan* p) {
 
 // Launch count(i) for i = 0..n-1: on the plan's stream alone, or spread over
 // the plan's side streams (forked from and joined back to the plan's stream
-// with events, which also works inside a stream capture).
+// with events, which also works inside a stream capture).  first_alone: launch
+// 0 (the windows, the bulk of the work) keeps the plan's stream to itself and
+// the others share the side streams, so none waits behind it.
 template <class F>
-cudaError_t fork_join(pent_plan* p, size_t n, F launch) {
+cudaError_t fork_join(pent_plan* p, size_t n, F launch, bool first_alone = false) {
   const int ns = (int)p->side.size();
   cudaError_t e = cudaSuccess;
   if (ns == 0 || n < 2) {
@@ -590,8 +592,11 @@ cudaError_t fork_join(pent_plan* p, size_t n, F launch) {
   }
   e = cudaEventRecord(p->ev[0], p->stream);
   for (int k = 0; k < ns && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(p->side[k], p->ev[0], 0);
-  for (size_t i = 0; i < n && e == cudaSuccess; ++i)
-    e = launch(i, (i % (ns + 1) == 0) ? p->stream : p->side[i % (ns + 1) - 1]);
+  for (size_t i = 0; i < n && e == cudaSuccess; ++i) {
+    cudaStream_t st = (i % (ns + 1) == 0) ? p->stream : p->side[i % (ns + 1) - 1];
+    if (first_alone) st = i == 0 ? p->stream : p->side[(i - 1) % ns];
+    e = launch(i, st);
+  }
   for (int k = 0; k < ns && e == cudaSuccess; ++k) {
     e = cudaEventRecord(p->ev[1 + k], p->side[k]);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(p->stream, p->ev[1 + k], 0);
@@ -727,7 +732,9 @@ pent_status pent_plan_bind(pent_plan* p, void* ws, void* stream) {
   p->drop_streams();
   const size_t nlaunch = p->precision == PENT_F64 ? p->runs.size() + (p->win64_cap > 0 ? 1 : 0)
                                                  : p->buckets.size() + (p->win_cap > 0 ? 1 : 0);
-  const int nside = (int)std::min<size_t>(3, nlaunch > 1 ? nlaunch - 1 : 0);
+  // with windows the other launches share the side streams among themselves (fork_join's first_alone)
+  const size_t maxside = (p->win_cap > 0 || p->win64_cap > 0) ? 6 : 3;
+  const int nside = (int)std::min<size_t>(maxside, nlaunch > 1 ? nlaunch - 1 : 0);
   for (int k = 0; k < nside && e == cudaSuccess; ++k) {
     cudaStream_t ss;
     e = cudaStreamCreateWithFlags(&ss, cudaStreamNonBlocking);
@@ -1227,7 +1234,7 @@ static pent_status solve_launch(pent_plan* p, const double* f, double* x, int ma
       const auto& r = runs[i - nw];
       if (r.part) return launch_solve64_part(P, F, X, f, x, gscr, r.g0, r.g1, r.c0, r.c1, st);
       return launch_solve64(P, F, f, x, gscr, r.bw, r.unroll, r.g0, r.g1, st);
-    });
+    }, nw > 0);
   } else {
     if (p->periodic && p->residual == PENT_RESIDUAL_F64) return PENT_EINVAL;  // periodic: float-float residual
     // windows of the long systems (FP64 in and out: a window reads its neighbours' rows) and the
@@ -1244,7 +1251,7 @@ static pent_status solve_launch(pent_plan* p, const double* f, double* x, int ma
       const F32Bucket& b = bk[i - nw];
       const bool u = use_u(p, b, max_refine);
       return f32_bucket(p, b, f, x, max_refine, u && in_ff, u && out_ff, st, sys);
-    });
+    }, nw > 0);
   }
   return cuda_status(err);
 }

@@ -328,3 +328,28 @@ def test_f64_interior_records_from_registers_give_the_same_bits(case):
     assert np.array_equal(out[0], out[1])
     ref = oracle.hyperdiff_steps(ns, sig, f, steps)
     assert sys_rel_err(out[0], ref, ns) <= steps * TOL
+
+
+@pytest.mark.parametrize("prec", [pb.PENT_F32_REFINE, pb.PENT_F64])
+def test_windows_with_odd_offsets_and_unaligned_vectors(prec):
+    """Systems of odd lengths (so half of them start at odd rows: their pairs are read and written
+    as the aligned pairs one row over) and f / x views one double off a 16-byte boundary (every
+    access scalar): bitwise the results of aligned vectors, and the oracle's."""
+    ns = np.array([3001, 4097, 2049, 5001, 1025, 7777] * 6)
+    sig = synth.log_uniform(87, 0, len(ns), 1e-2, 10.0)
+    f = synth.uniform(88, 0, int(ns.sum()), -1, 1)
+    plan = pb.Plan(list(ns), precision=prec)
+    plan.factor_hyperdiff(dev(sig))
+    assert plan.get_option(pb.PENT_OPT_WINDOWS) > 0
+    a = host(plan.solve(dev(f), max_refine=1))
+    rows = int(ns.sum())
+    fb = torch.zeros(rows + 1, dtype=torch.float64, device="cuda")
+    xb = torch.zeros(rows + 1, dtype=torch.float64, device="cuda")
+    fb[1:] = dev(f)
+    plan.solve(fb[1:], xb[1:], max_refine=1)
+    assert np.array_equal(host(xb[1:]), a)
+    y = dev(f)
+    plan.solve(y, y, max_refine=1)
+    assert np.array_equal(host(y), a)
+    ref = oracle.hyperdiff_steps(ns, sig, f, 1)
+    assert sys_rel_err(a, ref, ns) <= TOL
