@@ -353,3 +353,34 @@ def test_windows_with_odd_offsets_and_unaligned_vectors(prec):
     assert np.array_equal(host(y), a)
     ref = oracle.hyperdiff_steps(ns, sig, f, 1)
     assert sys_rel_err(a, ref, ns) <= TOL
+
+
+def test_f64_refactorisations_drop_stale_windows_and_interior_records():
+    """A plan with windows (hyperdiffusion factorisation) then factored from a general band, or
+    refactored from a new sigma inside a solve, must not keep walking windows or interior records
+    of the old factors: each later solve meets the oracle for the factors it has."""
+    ns = np.array([6000] * 40 + [900] * 24)
+    sig1 = synth.log_uniform(91, 0, len(ns), 1e-2, 10.0)
+    sig2 = synth.log_uniform(92, 0, len(ns), 1e-2, 10.0)
+    f = synth.uniform(93, 0, int(ns.sum()), -1, 1)
+    plan = pb.Plan(list(ns), precision=pb.PENT_F64)
+    plan.factor_hyperdiff(dev(sig1))
+    assert plan.get_option(pb.PENT_OPT_WINDOWS) > 0
+    assert sys_rel_err(host(plan.solve(dev(f))), oracle.hyperdiff_steps(ns, sig1, f, 1), ns) <= TOL
+    # a general band with sigma2's entries: no windows, every record read
+    plan.factor(*[dev(v) for v in oracle.band_hyperdiff_batch(ns, sig2)])
+    assert plan.get_option(pb.PENT_OPT_WINDOWS) == 0
+    ref2 = oracle.hyperdiff_steps(ns, sig2, f, 1)
+    assert sys_rel_err(host(plan.solve(dev(f))), ref2, ns) <= TOL
+    # back to windows, then a refactorisation inside a solve (the new sigma's records and interior)
+    plan.factor_hyperdiff(dev(sig1))
+    assert plan.get_option(pb.PENT_OPT_WINDOWS) > 0
+    x = dev(f)
+    y = torch.empty_like(x)
+    plan.refactor_solve(dev(sig2), x, y)
+    assert sys_rel_err(host(y), ref2, ns) <= TOL
+    assert plan.get_option(pb.PENT_OPT_WINDOWS) == 0
+    assert sys_rel_err(host(plan.solve(dev(f))), ref2, ns) <= TOL
+    xs = dev(f)
+    plan.solve_steps(xs, 2)
+    assert sys_rel_err(host(xs), oracle.hyperdiff_steps(ns, sig2, f, 2), ns) <= 2 * TOL
