@@ -218,9 +218,10 @@ enum {
                                       records of the interior rows from registers: rows 2 .. n - 3 of
                                       I + sigma D4 share one band row and the factorisation's row step
                                       settles, so past the first few dozen rows every row pair holds the
-                                      same bits; the run of such pairs is found per system at factor time
-                                      (and after pent_refactor_solve_hyperdiff); 0 reads every record from
-                                      memory.  Bitwise the same results. */
+                                      same bits; the run of such pairs is found per system by
+                                      pent_factor_hyperdiff (not by pent_refactor_solve_hyperdiff, after
+                                      which the walks read every record until the next factorisation);
+                                      0 reads every record from memory.  Bitwise the same results. */
 };
 pent_status pent_plan_set_option(pent_plan* plan, int key, int64_t value);
 pent_status pent_plan_get_option(const pent_plan* plan, int key, int64_t* value);

@@ -80,6 +80,7 @@ struct pent_plan {
   int64_t nwin64 = 0;             // windows of the current factorisation (0: none)
   bool persistent = false;        // PENT_OPT_PERSISTENT: window launches as resident grids
   bool f64_interior = true;       // PENT_OPT_FP64_INTERIOR: hyperdiffusion walks take interior records from registers
+  bool interior_valid = false;    // the interior records are those of the current factorisation
   std::vector<F64Run> wruns;      // the runs of the other groups
   int64_t part_rows = -1;  // PENT_OPT_PARTITION_ROWS (-1: automatic)
   bool periodic = false;   // PENT_OPT_PERIODIC: cyclic systems (Navon's reduction)
@@ -186,7 +187,7 @@ struct pent_plan {
   // Hyperdiffusion factors of per-system matrices use the constant-epsilon records.
   F64Factors f64() const {
     F64Factors F{at<double>(r_fwd), at<double>(r_bwd), (factored == 2 && !shared) ? at<double>(r_sigma) : nullptr};
-    if (factored == 2 && !shared && f64_interior && r_ik.bytes > 1) {
+    if (factored == 2 && !shared && f64_interior && interior_valid && r_ik.bytes > 1) {
       F.icst = at<double2>(r_icst);
       F.ik = at<int32_t>(r_ik);
     }
@@ -1113,8 +1114,9 @@ static cudaError_t build_windows64(pent_plan* p) {
   return cudaSuccess;
 }
 
-// windows = false: lay out no FP64 windows (a refactorisation inside a solve: the layout would wait
-// for the stream on every call), dropping those of an earlier factorisation.
+// windows = false (a refactorisation inside a solve): lay out no FP64 windows (the layout would wait
+// for the stream on every call), dropping those of an earlier factorisation, and find no interior
+// records (the walks then read every record).
 static pent_status factor_common(pent_plan* p, const double* a, const double* b, const double* c, const double* d,
                                  const double* e, const double* sigma, bool windows = true) {
   if (!p) return PENT_EINVAL;
@@ -1143,8 +1145,11 @@ static pent_status factor_common(pent_plan* p, const double* a, const double* b,
     // chunk maps of the partitioned groups
     if (err == cudaSuccess && p->pchunks > 0) err = launch_chunk_maps64(P, F, p->part(), 0, p->pchunks, p->stream);
     // interior records of the hyperdiffusion walks
-    if (err == cudaSuccess && sigma && !p->shared)
+    p->interior_valid = false;
+    if (err == cudaSuccess && sigma && !p->shared && windows) {
       err = launch_interior64(P, F, p->at<double2>(p->r_icst), p->at<int32_t>(p->r_ik), p->stream);
+      p->interior_valid = err == cudaSuccess;
+    }
     // windows of the long groups (hyperdiffusion records); a general band keeps the runs
     if (err == cudaSuccess && p->win64_cap > 0) {
       if (sigma && windows) {
@@ -1514,8 +1519,10 @@ pent_status pent_refactor_solve_hyperdiff(pent_plan* p, const double* d_sigma, c
     const auto& r = p->runs[i];
     return launch_refactor_solve64(P, F, d_sigma, f, x, gscr, r.bw, r.g0, r.g1, s);
   });
-  // the new records' interior values; the windows' overlaps were those of the old sigma
-  if (err == cudaSuccess) err = launch_interior64(P, F, p->at<double2>(p->r_icst), p->at<int32_t>(p->r_ik), p->stream);
+  // the records are new: their interior is not known (the walks read every record until the next
+  // pent_factor_hyperdiff finds it; finding it here would cost about as much as the solve), and the
+  // windows' overlaps were those of the old sigma
+  p->interior_valid = false;
   if (err != cudaSuccess) return PENT_ECUDA;
   if (p->nwin64) {
     p->nwin64 = 0;
