@@ -10,7 +10,9 @@ Knobs, per bucket of row counts (n_lo, n_hi]:
 Each candidate is timed on a batch of systems of the bucket's largest n,
 hyperdiffusion matrices with sigma log-uniform in [1e-2, 10] and right-hand
 sides uniform in [-1, 1] (seeded), as implicit steps captured in a CUDA graph,
-with CUDA events on the plan's stream.  The fastest candidate wins.
+with CUDA events on the plan's stream.  The fastest candidate wins.  Windows of long systems
+(PENT_OPT_WINDOW_WARPS, PENT_OPT_WINDOW_ROWS) are off while tuning: the knobs tune the
+per-system solves, which windows replace where they apply.
 
     python -m paper_1807_07382_gb300.autotune --out tune.txt [--buckets 64,128,...]
     plan = Plan(ns, precision=..., tune_cache="tune.txt")
@@ -22,7 +24,7 @@ import math
 from typing import Iterable, Optional
 
 from . import PENT_F32_REFINE, PENT_F64, PENT_OPT_BLOCK_WARPS, PENT_OPT_PARTITION_ROWS, PENT_OPT_ROWS_PER_THREAD, \
-    PENT_OPT_THREADS_PER_SYSTEM, PENT_OPT_UNROLL, Plan
+    PENT_OPT_THREADS_PER_SYSTEM, PENT_OPT_UNROLL, PENT_OPT_WINDOW_ROWS, PENT_OPT_WINDOW_WARPS, Plan
 
 DEFAULT_BUCKETS = (64, 128, 256, 512, 1024, 2048, 4096, 8192, 16384)
 
@@ -96,13 +98,15 @@ def tune(buckets: Iterable[int] = DEFAULT_BUCKETS, rows: int = 1 << 26, steps: i
         sigma, f = _inputs(n, batch, device, seed + n)
         for kind in precisions:
             if kind == "f32":
-                cands = [((rpt, tps), {PENT_OPT_ROWS_PER_THREAD: rpt, PENT_OPT_THREADS_PER_SYSTEM: tps})
+                cands = [((rpt, tps), {PENT_OPT_ROWS_PER_THREAD: rpt, PENT_OPT_THREADS_PER_SYSTEM: tps,
+                                       PENT_OPT_WINDOW_WARPS: 0})
                          for rpt, tps in f32_candidates(n)]
                 prec = PENT_F32_REFINE
             else:
                 # partitioning off: the knobs tune the thread-per-system walk, which partitioned groups
                 # (long systems, or small batches) do not use
-                cands = [((u, bw), {PENT_OPT_UNROLL: u, PENT_OPT_BLOCK_WARPS: bw, PENT_OPT_PARTITION_ROWS: 0})
+                cands = [((u, bw), {PENT_OPT_UNROLL: u, PENT_OPT_BLOCK_WARPS: bw, PENT_OPT_PARTITION_ROWS: 0,
+                                    PENT_OPT_WINDOW_ROWS: 0})
                          for u, bw in f64_candidates(n)]
                 prec = PENT_F64
             best = None
