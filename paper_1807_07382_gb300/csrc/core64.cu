@@ -1210,8 +1210,16 @@ __global__ void k_win64_halo(DevPlan P, const int4* __restrict__ win, int64_t nw
 // pairs), the rows before them need none.  halo: the overlap rows of f, or nullptr (read f).
 // PERS: the persistent form, a resident grid whose warps take the windows in turn (else one
 // warp per window).
+// CTAs of 128 threads per SM the window walks' register allocation must allow (one-CTA-per-window
+// forms of up to 2 row pairs in flight; more pairs would spill): 5 (96 registers a thread, a few
+// spilled).  Uncapped (126 registers) the windows fill the SMs' register files and
+// the shorter groups' walks, launched beside them, wait: on GB300 the uneven batch's FP64 step
+// took 1.63-1.66 ms against 1.34-1.35 with the cap (6: 80 registers, more spills, 1.58 ms).
+#ifndef PENT_W64_MIN_BLOCKS
+#define PENT_W64_MIN_BLOCKS 5
+#endif
 template <int U2, bool PERS>
-__global__ void __launch_bounds__(128) k_solve64w(DevPlan P, F64Factors F, const int4* __restrict__ win, int64_t nwin,
+__global__ void __launch_bounds__(128, (PERS || U2 > 2) ? 1 : PENT_W64_MIN_BLOCKS) k_solve64w(DevPlan P, F64Factors F, const int4* __restrict__ win, int64_t nwin,
                                                   int omax, const double* f, double* x, double* __restrict__ gscr,
                                                   double2* __restrict__ side, const double2* __restrict__ halo) {
   const int64_t nwarps = PERS ? (int64_t)gridDim.x * blockDim.x / kWarp : nwin;
