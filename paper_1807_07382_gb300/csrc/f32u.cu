@@ -409,11 +409,11 @@ __device__ __forceinline__ int fexp(float h) { return (int)((__float_as_uint(h) 
 #define PENT_U_WARPS_PER_SM 40
 #endif
 
-// Warps per SM for the windows of long systems (FP64 in and out): 32 (64 registers a thread, no
-// spills; on GB300 the uneven batch with 4-warp windows takes 0.700 ms a step against 0.713 at 40
-// and 0.777 at 48).
+// Warps per SM for the windows of long systems (FP64 in and out): 36 (56 registers a thread; on
+// GB300 the uneven batch with 4-warp windows takes 0.686 ms a step against 0.695 at 32 warps, no
+// spills, and 0.707 at 40).
 #ifndef PENT_U_WIN_WARPS_PER_SM
-#define PENT_U_WIN_WARPS_PER_SM 32
+#define PENT_U_WIN_WARPS_PER_SM 36
 #endif
 
 // CTAs per SM the launch bound asks for: PENT_U_WARPS_PER_SM (windows: PENT_U_WIN_WARPS_PER_SM)
