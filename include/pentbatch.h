@@ -213,7 +213,7 @@ enum {
                                       resident, each taking windows in turn (bounded by the window count,
                                       no waits between CTAs); 0 (the default) one CTA (FP32) or warp (FP64)
                                       per window.  The same results either way. */
-  PENT_OPT_FP64_INTERIOR = 16      /* PENT_F64: 1 (the default) lets the walks of a hyperdiffusion
+  PENT_OPT_FP64_INTERIOR = 16,     /* PENT_F64: 1 (the default) lets the walks of a hyperdiffusion
                                       factorisation (pent_factor_hyperdiff, per-system matrices) take the
                                       records of the interior rows from registers: rows 2 .. n - 3 of
                                       I + sigma D4 share one band row and the factorisation's row step
@@ -222,6 +222,21 @@ enum {
                                       pent_factor_hyperdiff (not by pent_refactor_solve_hyperdiff, after
                                       which the walks read every record until the next factorisation);
                                       0 reads every record from memory.  Bitwise the same results. */
+  PENT_OPT_WINDOW_FORM = 17        /* PENT_F64, with PENT_OPT_WINDOW_ROWS: how the groups that take
+                                      windows are walked.  1 (the default): system windows, one thread
+                                      per window of one system, with that system's own overlap O (the
+                                      fewest multiple of 8 rows over which its interior row maps shrink
+                                      to 2^-56), listed in the order of the caller's rows so that a warp
+                                      reads and writes neighbouring rows; every window but a system's
+                                      last starts O rows before the first row not yet kept, the last
+                                      ends at the system's end, and each walks window_rows rows (fewer
+                                      for systems shorter than a window).  The forward and back walks
+                                      are two launches, and the factorisation copies the windowed
+                                      systems' records into a per-system layout (32 more workspace bytes
+                                      a row of those systems).  0: group windows, one warp per window of
+                                      a group (all 32 systems cut at the same rows, the group's largest
+                                      overlap).  Before pent_plan_bind (the workspace differs).  Both
+                                      forms keep the rows at least O from every cut. */
 };
 pent_status pent_plan_set_option(pent_plan* plan, int key, int64_t value);
 pent_status pent_plan_get_option(const pent_plan* plan, int key, int64_t* value);

@@ -17,7 +17,7 @@ from typing import Optional, Sequence
 
 from . import _lib
 from ._lib import (PENT_ENOCONV, PENT_ESINGULAR, PENT_F32_REFINE, PENT_F64, PENT_OK, PENT_OPT_BLOCK_WARPS,
-                   PENT_OPT_CLUSTER_WARPS, PENT_OPT_FP32_KERNEL, PENT_OPT_WINDOW_WARPS, PENT_OPT_WINDOWS, PENT_OPT_WINDOW_ROWS, PENT_OPT_PERSISTENT, PENT_OPT_FP64_INTERIOR,
+                   PENT_OPT_CLUSTER_WARPS, PENT_OPT_FP32_KERNEL, PENT_OPT_WINDOW_WARPS, PENT_OPT_WINDOWS, PENT_OPT_WINDOW_ROWS, PENT_OPT_PERSISTENT, PENT_OPT_FP64_INTERIOR, PENT_OPT_WINDOW_FORM,
                    PENT_OPT_PARTITION_ROWS, PENT_OPT_PERIODIC, PENT_OPT_REFINE_TOL_LOG2, PENT_OPT_RESIDUAL, PENT_OPT_ROWS_PER_THREAD,
                    PENT_OPT_THREADS_PER_SYSTEM,
                    PENT_OPT_UNROLL, PENT_RESIDUAL_F64,

@@ -39,6 +39,7 @@ PENT_OPT_WINDOWS = 13
 PENT_OPT_WINDOW_ROWS = 14
 PENT_OPT_PERSISTENT = 15
 PENT_OPT_FP64_INTERIOR = 16
+PENT_OPT_WINDOW_FORM = 17
 PENT_MAX_CACHED_GRAPHS = 16
 
 # every symbol the header declares, with (restype, argtypes)

@@ -1148,8 +1148,9 @@ __global__ void k_interior64(DevPlan P, F64Factors F, double2* __restrict__ icst
 constexpr double kWinTol64 = 1.3877787807814457e-17;  // 2^-56
 
 // Overlap rows per group (k_overlap64): the group's largest over its systems of at least 8 rows,
-// from the records of row n - 3 (interior), or 0x7fff if a system needs more than omax rows.
-__global__ void k_overlap64(DevPlan P, F64Factors F, int omax, int32_t* __restrict__ gover) {
+// from the records of row n - 3 (interior), or 0x7fff if a system needs more than omax rows; and,
+// if lover is not null, each system's own at its group lane (0 for systems under 8 rows).
+__global__ void k_overlap64(DevPlan P, F64Factors F, int omax, int32_t* __restrict__ gover, int32_t* __restrict__ lover) {
   const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kWarp;
   if (k >= P.ngroups) return;
   const int lane = threadIdx.x & (kWarp - 1);
@@ -1176,6 +1177,7 @@ __global__ void k_overlap64(DevPlan P, F64Factors F, int omax, int32_t* __restri
       }
     }
   }
+  if (lover) lover[k * kWarp + lane] = O;
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) O = max(O, __shfl_xor_sync(0xffffffffu, O, d));
   if (lane == 0) gover[k] = O;
@@ -1377,6 +1379,210 @@ __global__ void __launch_bounds__(128, (PERS || U2 > 2) ? 1 : PENT_W64_MIN_BLOCK
   }
 }
 
+
+// ---- windowed walks, one window per thread (system windows) ----
+//
+// The same windows as above, but each thread walks one window of one system: window (group lane
+// gl, first pair q0, kept pairs [k0, k1)) runs the system's forward substitution over pairs
+// q0 .. q0 + Rp - 1 from a zero state (exact at q0 = 0) and, in a second launch, the back
+// substitution from the window's last pair down to k0 from a zero state (exact where the window
+// ends the system), writing x of the kept pairs only.  The overlap is the system's own (not the
+// largest of its group), the windows are listed in the order of the caller's rows, so the 32
+// threads of a warp read and write neighbouring rows of one or two systems, and the records are a
+// per-system copy (sfwd / sbwd: pair q of the system at base + q, planes interleaved) made once
+// per factorisation.  The forward launch has read every f before the back launch writes any x,
+// so an in-place solve needs no copy of the overlap rows.
+//
+// Descriptor: int4 {gl, q0, k0, k1}; g of pair q (q >= k0) at gs[(w / 32) * Rp * 32 + (q - q0) * 32 + w % 32].
+__device__ __forceinline__ Interior interior_of_gl(const F64Factors& F, int64_t gl, int64_t n) {
+  Interior I;
+  if (F.ik) {
+    const int K = F.ik[gl];
+    if (K != INT_MAX) {
+      I.ia = F.icst[gl * 4 + 0];
+      I.be = F.icst[gl * 4 + 1];
+      I.ga = F.icst[gl * 4 + 2];
+      I.de = F.icst[gl * 4 + 3];
+      I.lo = K;
+      I.hi = (n - 4) / 2;
+    }
+  }
+  return I;
+}
+
+template <int U2>
+__global__ void __launch_bounds__(128) k_swin64_fwd(DevPlan P, F64Factors F, const int4* __restrict__ win, int64_t nwin,
+                                                    int Rp, const double2* __restrict__ sfwd,
+                                                    const int64_t* __restrict__ sbase, const double* f,
+                                                    double2* __restrict__ gs) {
+  const int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (w >= nwin) return;
+  const int4 d = win[w];
+  const int s = P.perm[d.x];
+  const int64_t n = P.n[s], fo = P.off[s];
+  const int64_t q0 = d.y, k0 = d.z, q1 = min(q0 + (int64_t)Rp, (n + 1) >> 1);
+  const double sg = F.sig[s];
+  const Interior I = interior_of_gl(F, d.x, n);
+  const double2* __restrict__ rec = sfwd + 2 * sbase[d.x];
+  double2* __restrict__ go = gs + (w >> 5) * (int64_t)Rp * kWarp + (w & (kWarp - 1));
+  // 16-byte accesses of f: a system starting at an even row reads pair (2q, 2q + 1) as one
+  // double2, one starting at an odd row the aligned (2q + 1, 2q + 2) with row 2q carried
+  const bool odd = (fo & 1) != 0;
+  const bool fvec = (((uintptr_t)f) & 15) == 0;
+  double fcarry = 0.0;
+  bool cvalid = false;
+  double2 ca[U2], cb[U2], cf[U2], na[U2], nb[U2], nf[U2];
+  auto load = [&](int64_t qb, double2* A, double2* B, double2* Fv) {
+#pragma unroll
+    for (int u = 0; u < U2; ++u) {
+      const int64_t q = qb + u;
+      if (q < q1) {
+        const int64_t r = 2 * q;
+        if (q >= I.lo && q <= I.hi) {
+          A[u] = I.ia;
+          B[u] = I.be;
+        } else {
+          A[u] = __ldg(rec + 2 * q);
+          B[u] = __ldg(rec + 2 * q + 1);
+        }
+        if (fvec && !odd && r + 1 < n) {
+          Fv[u] = *reinterpret_cast<const double2*>(f + fo + r);
+        } else if (fvec && odd && r + 2 < n) {
+          const double2 D = *reinterpret_cast<const double2*>(f + fo + r + 1);
+          Fv[u] = make_double2(cvalid ? fcarry : f[fo + r], D.x);
+          fcarry = D.y;
+          cvalid = true;
+        } else {
+          Fv[u].x = (r < n) ? f[fo + r] : 0.0;
+          Fv[u].y = (r + 1 < n) ? f[fo + r + 1] : 0.0;
+          cvalid = false;
+        }
+      }
+    }
+  };
+  double g1 = 0.0, g2 = 0.0;
+  load(q0, ca, cb, cf);
+  for (int64_t qb = q0; qb < q1; qb += U2) {
+    if (qb + U2 < q1) load(qb + U2, na, nb, nf);
+#pragma unroll
+    for (int u = 0; u < U2; ++u) {
+      const int64_t q = qb + u;
+      if (q < q1) {
+        const double ga = ca[u].x * fma(-cb[u].x, g1, fma(-sg, g2, cf[u].x));
+        const double gb = ca[u].y * fma(-cb[u].y, ga, fma(-sg, g1, cf[u].y));
+        if (q >= k0) go[(q - q0) * kWarp] = make_double2(ga, gb);
+        g2 = ga;
+        g1 = gb;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U2; ++u) {
+      ca[u] = na[u];
+      cb[u] = nb[u];
+      cf[u] = nf[u];
+    }
+  }
+}
+
+template <int U2>
+__global__ void __launch_bounds__(128) k_swin64_bwd(DevPlan P, F64Factors F, const int4* __restrict__ win, int64_t nwin,
+                                                    int Rp, const double2* __restrict__ sbwd,
+                                                    const int64_t* __restrict__ sbase, const double2* __restrict__ gs,
+                                                    double* x) {
+  const int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (w >= nwin) return;
+  const int4 d = win[w];
+  const int s = P.perm[d.x];
+  const int64_t n = P.n[s], fo = P.off[s];
+  const int64_t q0 = d.y, k0 = d.z, k1 = d.w, q1 = min(q0 + (int64_t)Rp, (n + 1) >> 1);
+  const Interior I = interior_of_gl(F, d.x, n);
+  const double2* __restrict__ rec = sbwd + 2 * sbase[d.x];
+  const double2* __restrict__ gi = gs + (w >> 5) * (int64_t)Rp * kWarp + (w & (kWarp - 1));
+  const bool odd = (fo & 1) != 0;
+  const bool xvec = (((uintptr_t)x) & 15) == 0;
+  double2 cg[U2], cd[U2], cG[U2], ng[U2], nd[U2], nG[U2];
+  auto load = [&](int64_t qb, double2* Ga, double2* De, double2* Gv) {
+#pragma unroll
+    for (int u = 0; u < U2; ++u) {
+      const int64_t q = qb - u;
+      if (q >= k0) {
+        if (q >= I.lo && q <= I.hi) {
+          Ga[u] = I.ga;
+          De[u] = I.de;
+        } else {
+          Ga[u] = __ldg(rec + 2 * q);
+          De[u] = __ldg(rec + 2 * q + 1);
+        }
+        Gv[u] = gi[(q - q0) * kWarp];
+      }
+    }
+  };
+  double x1 = 0.0, x2 = 0.0;
+  load(q1 - 1, cg, cd, cG);
+  for (int64_t qb = q1 - 1; qb >= k0; qb -= U2) {
+    if (qb - U2 >= k0) load(qb - U2, ng, nd, nG);
+#pragma unroll
+    for (int u = 0; u < U2; ++u) {
+      const int64_t q = qb - u;
+      if (q >= k0) {
+        const double xb = fma(-cg[u].y, x1, fma(-cd[u].y, x2, cG[u].y));
+        const double xa = fma(-cg[u].x, xb, fma(-cd[u].x, x1, cG[u].x));
+        if (q < k1) {
+          const int64_t r = 2 * q;
+          if (!odd && xvec && r + 1 < n) {
+            *reinterpret_cast<double2*>(x + fo + r) = make_double2(xa, xb);
+          } else if (!odd || !xvec) {
+            if (r < n) x[fo + r] = xa;
+            if (r + 1 < n) x[fo + r + 1] = xb;
+          } else {
+            // rows r + 1 (this pair) and r + 2 (x1, the pair above, if kept) as one aligned double2;
+            // row r goes out with the pair below, or alone at the first kept pair
+            if (q + 1 < k1 && r + 2 < n) {
+              *reinterpret_cast<double2*>(x + fo + r + 1) = make_double2(xb, x1);
+            } else if (r + 1 < n) {
+              x[fo + r + 1] = xb;
+            }
+            if (q == k0 && r < n) x[fo + r] = xa;
+          }
+        }
+        x2 = xb;
+        x1 = xa;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U2; ++u) {
+      cg[u] = ng[u];
+      cd[u] = nd[u];
+      cG[u] = nG[u];
+    }
+  }
+}
+
+// Per-system copy of the records of the systems walked in system windows: warp (blockIdx.x,
+// blockIdx.y) copies pairs [64 y, 64 y + 64) of windowed group wg[x], one lane per system
+// (sbase[gl] < 0: none); sfwd[2 (base + q) + p] = fwd plane p of pair q, the same for bwd.
+constexpr int kSrecPairs = 64;
+__global__ void __launch_bounds__(32) k_srec64(DevPlan P, F64Factors F, const int32_t* __restrict__ wg,
+                                               const int64_t* __restrict__ sbase, double2* __restrict__ sfwd,
+                                               double2* __restrict__ sbwd) {
+  const int64_t k = wg[blockIdx.x];
+  const int lane = threadIdx.x;
+  const Lane L = lane_setup<false>(P, k, lane);
+  const int64_t gl = k * kWarp + lane;
+  const int64_t b = L.s >= 0 ? sbase[gl] : -1;
+  if (b < 0) return;
+  const double2* __restrict__ fwd = reinterpret_cast<const double2*>(F.fwd);
+  const double2* __restrict__ bwd = reinterpret_cast<const double2*>(F.bwd);
+  const int64_t P0 = L.R0 >> 1, np = (L.n + 1) >> 1;
+  const int64_t qa = (int64_t)blockIdx.y * kSrecPairs, qe = min(qa + (int64_t)kSrecPairs, np);
+  for (int64_t q = qa; q < qe; ++q) {
+    sfwd[2 * (b + q)] = fwd[((P0 + q) * 2) * kWarp + lane];
+    sfwd[2 * (b + q) + 1] = fwd[((P0 + q) * 2 + 1) * kWarp + lane];
+    sbwd[2 * (b + q)] = bwd[((P0 + q) * 2) * kWarp + lane];
+    sbwd[2 * (b + q) + 1] = bwd[((P0 + q) * 2 + 1) * kWarp + lane];
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_factor64(const DevPlan& P, const double* a, const double* b, const double* c, const double* d,
@@ -1511,10 +1717,42 @@ cudaError_t launch_sigma_grad(const DevPlan& P, const double* mu, const double* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_overlap64(const DevPlan& P, F64Factors F, int omax, int32_t* gover, cudaStream_t st) {
+cudaError_t launch_overlap64(const DevPlan& P, F64Factors F, int omax, int32_t* gover, int32_t* lover, cudaStream_t st) {
   if (P.ngroups == 0 || P.shared || !F.sig) return cudaErrorInvalidValue;
-  k_overlap64<<<grid_for(P.ngroups * kWarp, 128), 128, 0, st>>>(P, F, omax, gover);
+  k_overlap64<<<grid_for(P.ngroups * kWarp, 128), 128, 0, st>>>(P, F, omax, gover, lover);
   return cudaGetLastError();
+}
+
+cudaError_t launch_srec64(const DevPlan& P, F64Factors F, const int32_t* wg, int64_t nwg, int64_t max_pairs,
+                          const int64_t* sbase, double2* sfwd, double2* sbwd, cudaStream_t st) {
+  if (nwg == 0) return cudaSuccess;
+  if (P.shared || !F.sig || max_pairs <= 0) return cudaErrorInvalidValue;
+  const int64_t ny = (max_pairs + kSrecPairs - 1) / kSrecPairs;
+  if (nwg > INT_MAX || ny > 65535) return cudaErrorInvalidValue;
+  k_srec64<<<dim3((unsigned)nwg, (unsigned)ny), kWarp, 0, st>>>(P, F, wg, sbase, sfwd, sbwd);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_swin64(const DevPlan& P, F64Factors F, const int4* win, int64_t nwin, int window_rows, int unroll,
+                          int block_warps, const double2* sfwd, const double2* sbwd, const int64_t* sbase,
+                          const double* f, double* x, double2* gs, cudaStream_t st) {
+  if (nwin == 0) return cudaSuccess;
+  if (P.shared || !F.sig || window_rows <= 0 || window_rows % 8 || block_warps < 1 || block_warps > 4)
+    return cudaErrorInvalidValue;
+  // one-warp CTAs by default: the windows' warps then spread over the SMs within one warp of each other
+  const int Rp = window_rows / 2, block = kWarp * block_warps;
+  const int grid = grid_for(nwin, block);
+  auto go = [&](auto fk, auto bk) {
+    fk<<<grid, block, 0, st>>>(P, F, win, nwin, Rp, sfwd, sbase, f, gs);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    bk<<<grid, block, 0, st>>>(P, F, win, nwin, Rp, sbwd, sbase, gs, x);
+    return cudaGetLastError();
+  };
+  if (unroll == 8) return go(k_swin64_fwd<4>, k_swin64_bwd<4>);
+  if (unroll == 4) return go(k_swin64_fwd<2>, k_swin64_bwd<2>);
+  if (unroll == 2) return go(k_swin64_fwd<1>, k_swin64_bwd<1>);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_solve64w(const DevPlan& P, F64Factors F, const int4* win, int64_t nwin, int omax, int unroll,

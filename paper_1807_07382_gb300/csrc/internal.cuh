@@ -132,7 +132,13 @@ cudaError_t launch_interior64(const DevPlan& P, F64Factors F, double2* icst, int
 // overlap rows a window needs (a multiple of 8; 0x7fff: more than omax).  win: per window (group,
 // first row, rows | overlap << 16); side: [nwin][omax / 2][32] double2 of g after the kept rows;
 // halo: [nwin][2][omax / 2][32] double2 of overlap rows, filled first when f == x.
-cudaError_t launch_overlap64(const DevPlan& P, F64Factors F, int omax, int32_t* gover, cudaStream_t st);
+cudaError_t launch_overlap64(const DevPlan& P, F64Factors F, int omax, int32_t* gover, int32_t* lover, cudaStream_t st);
+// system windows (one window per thread): the per-system record copy, then both walks
+cudaError_t launch_srec64(const DevPlan& P, F64Factors F, const int32_t* wg, int64_t nwg, int64_t max_pairs,
+                          const int64_t* sbase, double2* sfwd, double2* sbwd, cudaStream_t st);
+cudaError_t launch_swin64(const DevPlan& P, F64Factors F, const int4* win, int64_t nwin, int window_rows, int unroll,
+                          int block_warps, const double2* sfwd, const double2* sbwd, const int64_t* sbase,
+                          const double* f, double* x, double2* gs, cudaStream_t st);
 // persistent: a grid of as many CTAs as stay resident, whose warps take the windows in turn.
 cudaError_t launch_solve64w(const DevPlan& P, F64Factors F, const int4* win, int64_t nwin, int omax, int unroll,
                             int block_warps, const double* f, double* x, double* gscr, double* side, double* halo,

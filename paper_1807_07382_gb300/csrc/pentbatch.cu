@@ -81,6 +81,12 @@ struct pent_plan {
   bool persistent = false;        // PENT_OPT_PERSISTENT: window launches as resident grids
   bool f64_interior = true;       // PENT_OPT_FP64_INTERIOR: hyperdiffusion walks take interior records from registers
   bool interior_valid = false;    // the interior records are those of the current factorisation
+  // PENT_OPT_WINDOW_FORM 1: system windows (one thread per window of one system, the system's
+  // own overlap, records copied per system at factor time); 0: group windows (one warp each)
+  int win64_form = 1;
+  int64_t swin_cap = 0;           // system windows the workspace holds
+  int64_t srec_pairs = 0;         // row pairs of per-system records the workspace holds
+  int64_t srec_maxpairs = 0;      // row pairs of the longest system that can take system windows
   std::vector<F64Run> wruns;      // the runs of the other groups
   int64_t part_rows = -1;  // PENT_OPT_PARTITION_ROWS (-1: automatic)
   bool periodic = false;   // PENT_OPT_PERIODIC: cyclic systems (Navon's reduction)
@@ -129,7 +135,7 @@ struct pent_plan {
   Region r_info, r_perm, r_off, r_n, r_goff, r_glen, r_sigma, r_fwd, r_bwd, r_scr, r_fac32, r_sig32, r_foff, r_shape,
       r_sys32, r_adi, r_cmap, r_swU, r_swE, r_pck, r_pcc, r_pcbase, r_pcnum, r_pcmap, r_pU, r_pE, r_per, r_psinv,
       r_pg, r_rhs, r_psinv32, r_urec, r_kscale, r_uwin, r_win, r_whalo, r_wsys32, r_gover, r_win64, r_side64,
-      r_halo64, r_icst, r_ik;
+      r_halo64, r_icst, r_ik, r_lover, r_sbase, r_sfwd, r_sbwd, r_swin, r_sgs, r_swg;
   size_t ws_bytes = 0;
   // binding / state
   unsigned char* ws = nullptr;
@@ -444,6 +450,38 @@ int64_t window_layout(int64_t n, int R, int O, int32_t* out4, int64_t cap) {
   return k;
 }
 
+// System windows of a system of np row pairs, windows of Rp pairs with Op pairs of overlap
+// (0 < 4 Op <= Rp, or Op = 0 for systems of one window): three int32 per window {q0, k0, k1},
+// walking pairs [q0, min(q0 + Rp, np)) and keeping [k0, k1).  The first window starts at pair 0
+// and keeps [0, Rp - Op); each next one starts Op pairs before the first pair not yet kept and
+// keeps Rp - 2 Op; the last starts at np - Rp, so it walks Rp pairs too and ends at the system's
+// end, and keeps the rest (at least Op pairs from its start).  Returns the count.
+int64_t swin_layout(int64_t np, int Rp, int Op, int32_t* out3, int64_t cap) {
+  int64_t k = 0;
+  auto emit = [&](int64_t q0, int64_t k0, int64_t k1) {
+    if (out3 && k < cap) {
+      out3[3 * k] = (int32_t)q0;
+      out3[3 * k + 1] = (int32_t)k0;
+      out3[3 * k + 2] = (int32_t)k1;
+    }
+    ++k;
+  };
+  if (np <= 0) return 0;
+  if (np <= Rp) {
+    emit(0, 0, np);
+    return k;
+  }
+  if (Op <= 0 || 4 * Op > Rp) return 0;
+  emit(0, 0, Rp - Op);
+  int64_t a = Rp - Op;  // first pair not yet kept
+  while (np - a > Rp - Op) {
+    emit(a - Op, a, a + Rp - 2 * Op);
+    a += Rp - 2 * Op;
+  }
+  emit(np - Rp, a, np);
+  return k;
+}
+
 bool build_f32_shapes(pent_plan* p) {
   const int64_t nfac = p->shared ? 1 : p->batch;
   p->shape.assign(nfac, Shape{0, 0, 0});
@@ -532,11 +570,36 @@ void layout(pent_plan* p) {
       for (int64_t k = 0; k < p->ngroups; ++k)
         p->win64_cap += window_layout(p->glen[k], p->win64_rows, p->win64_omax, nullptr, 0);
     }
+    // system windows: room for every system of a group longer than one window
+    p->swin_cap = p->srec_pairs = p->srec_maxpairs = 0;
+    if (p->win64_cap > 0 && p->win64_form == 1) {
+      const int Rp = p->win64_rows / 2;
+      for (int64_t k = 0; k < p->ngroups; ++k) {
+        if (p->glen[k] <= p->win64_rows) continue;
+        for (int j = 0; j < kWarp; ++j) {
+          const int32_t s = p->perm[(size_t)(k * kWarp + j)];
+          if (s < 0) continue;
+          const int64_t np = (p->n[s] + 1) / 2;
+          p->srec_pairs += np;
+          p->srec_maxpairs = std::max(p->srec_maxpairs, np);
+          p->swin_cap += swin_layout(np, Rp, p->win64_omax / 2, nullptr, 0);
+        }
+      }
+      p->win64_cap = 0;  // the group windows' room is not needed
+    }
     const size_t wpairs = (size_t)p->win64_cap * (p->win64_omax / 2) * kWarp;  // double2 per window side
     // interior records per group lane (hyperdiffusion factorisations)
     take(p->r_icst, (size_t)(p->shared ? 0 : p->ngroups * kWarp) * 4 * sizeof(double2));
     take(p->r_ik, (size_t)(p->shared ? 0 : p->ngroups * kWarp) * sizeof(int32_t));
-    take(p->r_gover, (size_t)(p->win64_cap > 0 ? p->ngroups : 0) * sizeof(int32_t));
+    const bool any_win = p->win64_cap > 0 || p->swin_cap > 0;
+    take(p->r_gover, (size_t)(any_win ? p->ngroups : 0) * sizeof(int32_t));
+    take(p->r_lover, (size_t)(p->swin_cap > 0 ? p->ngroups * kWarp : 0) * sizeof(int32_t));
+    take(p->r_sbase, (size_t)(p->swin_cap > 0 ? p->ngroups * kWarp : 0) * sizeof(int64_t));
+    take(p->r_swg, (size_t)(p->swin_cap > 0 ? p->ngroups : 0) * sizeof(int32_t));
+    take(p->r_sfwd, (size_t)p->srec_pairs * 2 * sizeof(double2));
+    take(p->r_sbwd, (size_t)p->srec_pairs * 2 * sizeof(double2));
+    take(p->r_swin, (size_t)p->swin_cap * sizeof(int4));
+    take(p->r_sgs, (size_t)((p->swin_cap + kWarp - 1) / kWarp) * kWarp * (p->win64_rows / 2) * sizeof(double2));
     take(p->r_win64, (size_t)p->win64_cap * sizeof(int4));
     take(p->r_side64, wpairs * 2 * sizeof(double));
     take(p->r_halo64, wpairs * 4 * sizeof(double));
@@ -731,10 +794,11 @@ pent_status pent_plan_bind(pent_plan* p, void* ws, void* stream) {
   }
   // side streams (and fork/join events) so that several launches of one solve overlap
   p->drop_streams();
-  const size_t nlaunch = p->precision == PENT_F64 ? p->runs.size() + (p->win64_cap > 0 ? 1 : 0)
+  const bool win64 = p->win64_cap > 0 || p->swin_cap > 0;
+  const size_t nlaunch = p->precision == PENT_F64 ? p->runs.size() + (win64 ? 1 : 0)
                                                  : p->buckets.size() + (p->win_cap > 0 ? 1 : 0);
   // with windows the other launches share the side streams among themselves (fork_join's first_alone)
-  const size_t maxside = (p->win_cap > 0 || p->win64_cap > 0) ? 6 : 3;
+  const size_t maxside = (p->win_cap > 0 || win64) ? 6 : 3;
   const int nside = (int)std::min<size_t>(maxside, nlaunch > 1 ? nlaunch - 1 : 0);
   for (int k = 0; k < nside && e == cudaSuccess; ++k) {
     cudaStream_t ss;
@@ -869,6 +933,12 @@ pent_status pent_plan_set_option(pent_plan* p, int key, int64_t value) {
       p->win64_rows = (int)value;
       layout(p);
       return PENT_OK;
+    case PENT_OPT_WINDOW_FORM:
+      // changes the workspace size: only before binding
+      if (p->bound || p->precision != PENT_F64 || (value != 0 && value != 1)) return PENT_EINVAL;
+      p->win64_form = (int)value;
+      layout(p);
+      return PENT_OK;
     case PENT_OPT_WINDOW_WARPS:
       // changes the workspace size: only before binding
       if (p->bound || p->precision != PENT_F32_REFINE || p->periodic) return PENT_EINVAL;
@@ -911,6 +981,7 @@ pent_status pent_plan_get_option(const pent_plan* p, int key, int64_t* value) {
     case PENT_OPT_WINDOW_ROWS: *value = p->win64_rows; return PENT_OK;
     case PENT_OPT_PERSISTENT: *value = p->persistent ? 1 : 0; return PENT_OK;
     case PENT_OPT_FP64_INTERIOR: *value = p->f64_interior ? 1 : 0; return PENT_OK;
+    case PENT_OPT_WINDOW_FORM: *value = p->win64_form; return PENT_OK;
   }
   return PENT_EINVAL;
 }
@@ -1039,6 +1110,60 @@ static std::pair<int, int> win64_knobs(const pent_plan* p) {
 // room are walked in windows; the rest of each run is kept (a partitioned run keeps the chunks
 // of its remaining groups).  The overlaps are read back, which waits for the plan's stream; under
 // a stream capture no windows are built.
+//
+// System windows (PENT_OPT_WINDOW_FORM 1) of the windowed groups: every system of such a group is
+// laid out with its own overlap (lover, by group lane), the systems taken in the order of their
+// rows in the caller's layout (so are their windows and their records' copies), and the records
+// are copied into the per-system layout.  Sets nwin64.
+static cudaError_t build_system_windows(pent_plan* p, const std::vector<char>& windowed,
+                                        const std::vector<int32_t>& lover) {
+  const int Rp = p->win64_rows / 2;
+  std::vector<int64_t> sbase((size_t)p->ngroups * kWarp, -1);
+  std::vector<int32_t> wg, geo;
+  std::vector<std::pair<int64_t, int64_t>> sys;  // (first row in the caller's layout, group lane)
+  for (int64_t k = 0; k < p->ngroups; ++k) {
+    if (!windowed[k]) continue;
+    wg.push_back((int32_t)k);
+    for (int j = 0; j < kWarp; ++j) {
+      const int32_t s = p->perm[(size_t)(k * kWarp + j)];
+      if (s >= 0) sys.push_back({p->off[s], k * kWarp + j});
+    }
+  }
+  // systems, their windows and their records in the order of the caller's rows
+  std::stable_sort(sys.begin(), sys.end());
+  std::vector<int4> win;
+  int64_t acc = 0;
+  for (const auto& sg : sys) {
+    const int64_t gl = sg.second;
+    const int32_t s = p->perm[(size_t)gl];
+    const int64_t np = (p->n[s] + 1) / 2;
+    const int Op = lover[(size_t)gl] / 2;
+    const int64_t cnt = swin_layout(np, Rp, Op, nullptr, 0);
+    if (cnt <= 0) return cudaErrorInvalidValue;  // not reached: windowed groups have their overlaps in range
+    geo.resize((size_t)(3 * cnt));
+    swin_layout(np, Rp, Op, geo.data(), cnt);
+    for (int64_t i = 0; i < cnt; ++i) win.push_back(make_int4((int)gl, geo[3 * i], geo[3 * i + 1], geo[3 * i + 2]));
+    sbase[(size_t)gl] = acc;
+    acc += np;
+  }
+  if ((int64_t)win.size() > p->swin_cap || acc > p->srec_pairs) return cudaErrorInvalidValue;  // not reached
+  cudaError_t e = cudaSuccess;
+  if (!win.empty()) {
+    e = cudaMemcpy(p->at<int4>(p->r_swin), win.data(), win.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(p->at<int64_t>(p->r_sbase), sbase.data(), sbase.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(p->at<int32_t>(p->r_swg), wg.data(), wg.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    F64Factors F = p->f64();
+    F.sig = p->at<double>(p->r_sigma);
+    if (e == cudaSuccess)
+      e = launch_srec64(p->dev(), F, p->at<int32_t>(p->r_swg), (int64_t)wg.size(), p->srec_maxpairs,
+                        p->at<int64_t>(p->r_sbase), p->at<double2>(p->r_sfwd), p->at<double2>(p->r_sbwd), p->stream);
+  }
+  p->nwin64 = (int64_t)win.size();
+  return e;
+}
+
 static cudaError_t build_windows64(pent_plan* p) {
   const int64_t nprev = p->nwin64;
   p->nwin64 = 0;
@@ -1051,10 +1176,15 @@ static cudaError_t build_windows64(pent_plan* p) {
   }
   F64Factors F = p->f64();
   F.sig = p->at<double>(p->r_sigma);
-  e = launch_overlap64(p->dev(), F, p->win64_omax, p->at<int32_t>(p->r_gover), p->stream);
-  std::vector<int32_t> gover((size_t)p->ngroups);
+  const bool sysw = p->swin_cap > 0;
+  e = launch_overlap64(p->dev(), F, p->win64_omax, p->at<int32_t>(p->r_gover),
+                       sysw ? p->at<int32_t>(p->r_lover) : nullptr, p->stream);
+  std::vector<int32_t> gover((size_t)p->ngroups), lover(sysw ? (size_t)p->ngroups * kWarp : 0);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(gover.data(), p->at<int32_t>(p->r_gover), gover.size() * sizeof(int32_t),
+                        cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess && sysw)
+    e = cudaMemcpyAsync(lover.data(), p->at<int32_t>(p->r_lover), lover.size() * sizeof(int32_t),
                         cudaMemcpyDeviceToHost, p->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);  // also: no solve still reads the old windows
   if (e != cudaSuccess) return e;
@@ -1069,7 +1199,11 @@ static cudaError_t build_windows64(pent_plan* p) {
       if (p->glen[k] > R && (gover[k] <= 0 || gover[k] > p->win64_omax)) ok = false;
     for (int64_t k = r.g0; k < r.g1 && ok; ++k) windowed[k] = p->glen[k] > R;
   }
-  for (int64_t k = 0; k < p->ngroups; ++k) {
+  if (sysw) {
+    e = build_system_windows(p, windowed, lover);
+    if (e != cudaSuccess) return e;
+  }
+  for (int64_t k = 0; k < p->ngroups && !sysw; ++k) {
     const int O = gover[k];
     if (!windowed[k]) continue;
     const int64_t cnt = window_layout(p->glen[k], R, O, nullptr, 0);
@@ -1083,8 +1217,8 @@ static cudaError_t build_windows64(pent_plan* p) {
     }
     windowed[k] = 1;
   }
-  const int64_t nw = (int64_t)win.size() / 4;
-  if (nw > p->win64_cap) return cudaErrorInvalidValue;  // not reached: the room is sized for the largest overlap
+  const int64_t nw = sysw ? p->nwin64 : (int64_t)win.size() / 4;
+  if (!sysw && nw > p->win64_cap) return cudaErrorInvalidValue;  // not reached: the room is sized for the largest overlap
   p->wruns.clear();
   for (const auto& r : p->runs) {
     for (int64_t g = r.g0; g < r.g1;) {
@@ -1105,7 +1239,7 @@ static cudaError_t build_windows64(pent_plan* p) {
       g = h;
     }
   }
-  if (nw > 0) {
+  if (nw > 0 && !sysw) {
     e = cudaMemcpy(p->at<int4>(p->r_win64), win.data(), (size_t)nw * sizeof(int4), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
   }
@@ -1151,7 +1285,7 @@ static pent_status factor_common(pent_plan* p, const double* a, const double* b,
       p->interior_valid = err == cudaSuccess;
     }
     // windows of the long groups (hyperdiffusion records); a general band keeps the runs
-    if (err == cudaSuccess && p->win64_cap > 0) {
+    if (err == cudaSuccess && (p->win64_cap > 0 || p->swin_cap > 0)) {
       if (sigma && windows) {
         err = build_windows64(p);
       } else if (p->nwin64) {
@@ -1232,6 +1366,10 @@ static pent_status solve_launch(pent_plan* p, const double* f, double* x, int ma
     const size_t nw = p->nwin64 > 0 ? 1 : 0;
     const std::vector<pent_plan::F64Run>& runs = nw ? p->wruns : p->runs;
     err = fork_join(p, runs.size() + nw, [&](size_t i, cudaStream_t st) {
+      if (i < nw && p->swin_cap > 0)
+        return launch_swin64(P, F, p->at<int4>(p->r_swin), p->nwin64, p->win64_rows, win64_knobs(p).first,
+                             win64_knobs(p).second, p->at<double2>(p->r_sfwd), p->at<double2>(p->r_sbwd), p->at<int64_t>(p->r_sbase), f, x,
+                             p->at<double2>(p->r_sgs), st);
       if (i < nw)
         return launch_solve64w(P, F, p->at<int4>(p->r_win64), p->nwin64, p->win64_omax, win64_knobs(p).first,
                                win64_knobs(p).second, f, x, gscr, p->at<double>(p->r_side64),

@@ -329,3 +329,25 @@ def test_fp64_interior_option_host_checks(L):
     st, h = _create(L, batch=4, n_uniform=1024, prec=1)
     assert L.pent_plan_set_option(h, _lib.PENT_OPT_FP64_INTERIOR, 1) == _lib.PENT_EINVAL
     L.pent_plan_destroy(h)
+
+
+def test_window_form_option_host_checks(L):
+    """PENT_OPT_WINDOW_FORM: FP64 plans, before binding, 0 (group windows) or 1 (system windows,
+    the default); system windows reserve a per-system copy of the windowed systems' records
+    (64 bytes a row pair) in place of the group windows' side scratch and overlap rows."""
+    st, h = _create(L, batch=64, n=[5000] * 32 + [300] * 32)
+    assert st == 0
+    v = ctypes.c_int64(-1)
+    assert L.pent_plan_get_option(h, _lib.PENT_OPT_WINDOW_FORM, ctypes.byref(v)) == 0 and v.value == 1
+    ws1 = L.pent_plan_workspace_bytes(h)
+    assert L.pent_plan_set_option(h, _lib.PENT_OPT_WINDOW_FORM, 0) == 0
+    assert L.pent_plan_get_option(h, _lib.PENT_OPT_WINDOW_FORM, ctypes.byref(v)) == 0 and v.value == 0
+    ws0 = L.pent_plan_workspace_bytes(h)
+    group_room = len(pb.window_layout(5000, 1024, 128)) * 64 * 32 * 48  # side + halo of the group windows
+    assert ws1 - ws0 >= 32 * 2500 * 64 - group_room
+    for bad in (2, -1):
+        assert L.pent_plan_set_option(h, _lib.PENT_OPT_WINDOW_FORM, bad) == _lib.PENT_EINVAL
+    L.pent_plan_destroy(h)
+    st, h = _create(L, batch=8, n_uniform=5000, prec=1)
+    assert L.pent_plan_set_option(h, _lib.PENT_OPT_WINDOW_FORM, 0) == _lib.PENT_EINVAL
+    L.pent_plan_destroy(h)

@@ -10,9 +10,11 @@ FP32+refine solve: 1e-12 relative (per system, max |x - x_ref| / max |x_ref|) af
 refinement step for sigma in [1e-3, 10], and 1e-4 for the plain FP32 solve.  Systems whose
 decay is too slow for the window (the overlap above R / 8) keep the cluster path.
 
-FP64 per-system hyperdiffusion plans cut groups of 32 length-sorted systems (one warp, one
-system per lane) into windows of 1024 rows the same way, one warp each, with the group's
-largest overlap: against the oracle at 1e-12 and within 1e-14 of the whole-group walk."""
+FP64 per-system hyperdiffusion plans walk the groups of 32 length-sorted systems longer than
+one window (1024 rows) in windows too: as system windows (PENT_OPT_WINDOW_FORM 1, the default),
+one thread per window of one system with the system's own overlap, or as group windows (0), one
+warp per window of a group with the group's largest overlap; both against the oracle at 1e-12
+and within 1e-14 of the whole-group walk."""
 import numpy as np
 import pytest
 
@@ -260,13 +262,16 @@ def test_f64_slow_decay_and_general_bands_keep_their_walks():
     sig = np.concatenate([np.full(32, 1e4), np.full(32, 0.5), np.full(32, 2.0)])
     f = synth.uniform(76, 0, int(ns.sum()), -1, 1)
     runs = []
-    for wr in (1024, 0):
+    for wr, form in ((1024, 0), (1024, 1), (0, 1)):
         plan = pb.Plan(list(ns), precision=pb.PENT_F64,
-                       options={pb.PENT_OPT_PARTITION_ROWS: 5000, pb.PENT_OPT_WINDOW_ROWS: wr})
+                       options={pb.PENT_OPT_PARTITION_ROWS: 5000, pb.PENT_OPT_WINDOW_ROWS: wr,
+                                pb.PENT_OPT_WINDOW_FORM: form})
         plan.factor_hyperdiff(dev(sig))
         runs.append((plan.get_option(pb.PENT_OPT_WINDOWS), host(plan.solve(dev(f)))))
-    (nw, a), (nw0, b) = runs
-    assert nw0 == 0 and 2 <= nw <= len(pb.window_layout(1500, 1024, 128))
+    (nwg, ag), (nw, a), (nw0, b) = runs
+    assert nw0 == 0 and 2 <= nwg <= len(pb.window_layout(1500, 1024, 128))
+    assert nw == 32 * 2  # system windows: two of 512 row pairs for each 1,500-row system
+    assert np.array_equal(ag[:64 * 6000], b[:64 * 6000])
     assert np.array_equal(a[:64 * 6000], b[:64 * 6000])
     ref = oracle.hyperdiff_steps(ns[32:], sig[32:], f[32 * 6000:], 1)
     assert sys_rel_err(a[32 * 6000:], ref, ns[32:]) <= TOL
@@ -384,3 +389,45 @@ def test_f64_refactorisations_drop_stale_windows_and_interior_records():
     xs = dev(f)
     plan.solve_steps(xs, 2)
     assert sys_rel_err(host(xs), oracle.hyperdiff_steps(ns, sig2, f, 2), ns) <= 2 * TOL
+
+
+@pytest.mark.parametrize("case", ["uniform", "uneven", "odd", "steps", "short_lanes"])
+def test_f64_system_windows_against_group_windows_and_the_oracle(case):
+    """System windows (PENT_OPT_WINDOW_FORM 1): each system of a windowed group cut at its own
+    rows with its own overlap, the windows in the caller's row order.  Against the oracle at
+    1e-12 (steps x 1e-12 for graph steps), within 1e-14 of group windows and of the whole-group
+    walk; in place bitwise the out-of-place result.  Cases: equal lengths; log-uniform lengths
+    8 .. 16,384 (groups of both kinds); odd lengths (half the systems start at odd rows);
+    in-place steps in one graph; groups whose shortest systems fit one window (a window of
+    fewer rows than the others in the same warp)."""
+    if case == "uniform":
+        ns = np.full(40, 8192)
+    elif case == "uneven":
+        ns = np.floor(synth.log_uniform(94, 0, 300, 8.0, 16384.0)).astype(np.int64)
+    elif case == "odd":
+        ns = np.array([3001, 4097, 2049, 5001, 1025, 7777, 1023, 999] * 5)
+    elif case == "steps":
+        ns = np.floor(synth.log_uniform(95, 0, 120, 1000.0, 9000.0)).astype(np.int64)
+    else:
+        ns = np.array([1100] * 20 + [1000] * 12 + [700] * 10)
+    sig = synth.log_uniform(96, 0, len(ns), 1e-2, 10.0)
+    f = synth.uniform(97, 0, int(ns.sum()), -1, 1)
+    steps = 3 if case == "steps" else 1
+    ref = oracle.hyperdiff_steps(ns, sig, f, steps)
+    got = {}
+    for name, opts in (("system", {pb.PENT_OPT_WINDOW_FORM: 1}), ("group", {pb.PENT_OPT_WINDOW_FORM: 0}),
+                       ("whole", {pb.PENT_OPT_WINDOW_ROWS: 0})):
+        plan = pb.Plan(list(ns), precision=pb.PENT_F64, options=opts)
+        plan.factor_hyperdiff(dev(sig))
+        assert (plan.get_option(pb.PENT_OPT_WINDOWS) > 0) == (name != "whole")
+        x = dev(f)
+        if steps > 1:
+            plan.solve_steps(x, steps)
+        else:
+            plan.solve(x, x)
+        got[name] = host(x)
+        if name == "system" and steps == 1:
+            assert np.array_equal(host(plan.solve(dev(f))), got[name])
+    assert sys_rel_err(got["system"], ref, ns) <= steps * TOL
+    assert sys_rel_err(got["system"], got["group"], ns) <= 1e-14
+    assert sys_rel_err(got["system"], got["whole"], ns) <= 1e-14
