@@ -193,23 +193,23 @@ enum {
   PENT_OPT_WINDOWS = 13,           /* read only: windows of the current factorisation (0: none; FP32 plans
                                       the PENT_OPT_WINDOW_WARPS windows, FP64 those of PENT_OPT_WINDOW_ROWS) */
   PENT_OPT_WINDOW_ROWS = 14,       /* PENT_F64, per-system matrices factored by pent_factor_hyperdiff: a
-                                      group of 32 length-sorted systems (one warp walks one system per
-                                      lane) whose padded length exceeds this many rows (1024, the default;
-                                      a multiple of 64 in 256 .. 16384; 0 turns windows off) is walked as
-                                      windows of that many rows, one warp each, side by side in one launch:
-                                      a window enters each sweep with a zero state where it cuts the group
-                                      and writes x only for the rows at least O from a cut, O the fewest
-                                      multiple of 8 rows over which the interior row maps of every system
-                                      of the group shrink to 2^-56.  The groups of a launch setting (a run
-                                      of equal unroll, CTA width and partitioning) take windows only if
-                                      each of their long groups has an overlap within 1/8 of the window;
+                                      group of 32 length-sorted systems whose padded length exceeds this
+                                      many rows (1024, the default; a multiple of 64 in 256 .. 16384; 0
+                                      turns windows off) is walked in windows of that many rows, all in
+                                      one launch (PENT_OPT_WINDOW_FORM says how): a window enters each
+                                      sweep with a zero state where it cuts a system and writes x only
+                                      for the rows at least O from a cut, O the fewest multiple of 8 rows
+                                      over which the interior row maps shrink to 2^-56.  The groups of a
+                                      launch setting (a run of equal unroll, CTA width and partitioning)
+                                      take windows only if each of their long groups has an overlap
+                                      within 1/4 of the window (system windows; 1/8 for group windows);
                                       the others, and general bands (pent_factor_batch), keep their walks
                                       or partitioned solves.  The factorisation reads the overlaps back
                                       and so waits for the plan's stream (under a stream capture it lays
-                                      out no windows).  Before pent_plan_bind (the workspace reserves the
-                                      windows' overlap rows). */
-  PENT_OPT_PERSISTENT = 15,        /* not periodic: 1 launches the windows (PENT_OPT_WINDOW_WARPS,
-                                      PENT_OPT_WINDOW_ROWS) as a persistent grid, as many CTAs as stay
+                                      out no windows).  Before pent_plan_bind (the workspace reserves
+                                      the windows' room). */
+  PENT_OPT_PERSISTENT = 15,        /* not periodic: 1 launches the windows (PENT_OPT_WINDOW_WARPS, and
+                                      the group windows of PENT_OPT_WINDOW_ROWS) as a persistent grid, as many CTAs as stay
                                       resident, each taking windows in turn (bounded by the window count,
                                       no waits between CTAs); 0 (the default) one CTA (FP32) or warp (FP64)
                                       per window.  The same results either way. */
@@ -232,8 +232,9 @@ enum {
                                       ends at the system's end, and each walks window_rows rows (fewer
                                       for systems shorter than a window).  The forward and back walks
                                       are two launches, and the factorisation copies the windowed
-                                      systems' records into a per-system layout (32 more workspace bytes
-                                      a row of those systems).  0: group windows, one warp per window of
+                                      systems' records into a per-system layout (40 more workspace bytes
+                                      a row of those systems: 1/alpha, beta/alpha, sigma/alpha, gamma,
+                                      delta).  0: group windows, one warp per window of
                                       a group (all 32 systems cut at the same rows, the group's largest
                                       overlap).  Before pent_plan_bind (the workspace differs).  Both
                                       forms keep the rows at least O from every cut. */

@@ -1386,7 +1386,9 @@ __global__ void __launch_bounds__(128, (PERS || U2 > 2) ? 1 : PENT_W64_MIN_BLOCK
 // gl, first pair q0, kept pairs [k0, k1)) runs the system's forward substitution over pairs
 // q0 .. q0 + Rp - 1 from a zero state (exact at q0 = 0) and, in a second launch, the back
 // substitution from the window's last pair down to k0 from a zero state (exact where the window
-// ends the system), writing x of the kept pairs only.  The overlap is the system's own (not the
+// ends the system), writing x of the kept pairs only.  The forward step is written with one
+// dependent operation a row (the products with g_{i-2} and f_i do not wait for g_{i-1}), so a
+// window's serial chain is one FP64 operation a row in each sweep.  The overlap is the system's own (not the
 // largest of its group), the windows are listed in the order of the caller's rows, so the 32
 // threads of a warp read and write neighbouring rows of one or two systems, and the records are a
 // per-system copy (sfwd / sbwd: pair q of the system at base + q, planes interleaved) made once
@@ -1423,53 +1425,65 @@ __global__ void __launch_bounds__(128) k_swin64_fwd(DevPlan P, F64Factors F, con
   const int64_t q0 = d.y, k0 = d.z, q1 = min(q0 + (int64_t)Rp, (n + 1) >> 1);
   const double sg = F.sig[s];
   const Interior I = interior_of_gl(F, d.x, n);
-  const double2* __restrict__ rec = sfwd + 2 * sbase[d.x];
+  // the interior rows' 1/alpha, beta/alpha, sigma/alpha, formed as the record copy forms them
+  const double2 iia = I.ia, iib = make_double2(I.ia.x * I.be.x, I.ia.y * I.be.y),
+                iis = make_double2(I.ia.x * sg, I.ia.y * sg);
+  const double2* __restrict__ rec = sfwd + 3 * sbase[d.x];
   double2* __restrict__ go = gs + (w >> 5) * (int64_t)Rp * kWarp + (w & (kWarp - 1));
   // 16-byte accesses of f: a system starting at an even row reads pair (2q, 2q + 1) as one
-  // double2, one starting at an odd row the aligned (2q + 1, 2q + 2) with row 2q carried
+  // double2; one starting at an odd row reads the aligned double2s (2q - 1, 2q) and (2q + 1, 2q + 2)
+  // of each pair (U2 + 1 of them for U2 pairs: no value is carried from one batch to the next)
   const bool odd = (fo & 1) != 0;
   const bool fvec = (((uintptr_t)f) & 15) == 0;
-  double fcarry = 0.0;
-  bool cvalid = false;
-  double2 ca[U2], cb[U2], cf[U2], na[U2], nb[U2], nf[U2];
-  auto load = [&](int64_t qb, double2* A, double2* B, double2* Fv) {
+  auto ld_pair = [&](int64_t r) {  // rows r, r + 1 of the system (zero past its end)
+    double2 v = make_double2(0.0, 0.0);
+    if (fvec && r >= 0 && r + 1 < n) {
+      v = *reinterpret_cast<const double2*>(f + fo + r);
+    } else {
+      if (r >= 0 && r < n) v.x = f[fo + r];
+      if (r + 1 >= 0 && r + 1 < n) v.y = f[fo + r + 1];
+    }
+    return v;
+  };
+  double2 ca[U2], cb[U2], cc[U2], cf[U2], na[U2], nb[U2], nc[U2], nf[U2];
+  auto load = [&](int64_t qb, double2* A, double2* B, double2* C, double2* Fv) {
 #pragma unroll
     for (int u = 0; u < U2; ++u) {
       const int64_t q = qb + u;
       if (q < q1) {
-        const int64_t r = 2 * q;
         if (q >= I.lo && q <= I.hi) {
-          A[u] = I.ia;
-          B[u] = I.be;
+          A[u] = iia;
+          B[u] = iib;
+          C[u] = iis;
         } else {
-          A[u] = __ldg(rec + 2 * q);
-          B[u] = __ldg(rec + 2 * q + 1);
-        }
-        if (fvec && !odd && r + 1 < n) {
-          Fv[u] = *reinterpret_cast<const double2*>(f + fo + r);
-        } else if (fvec && odd && r + 2 < n) {
-          const double2 D = *reinterpret_cast<const double2*>(f + fo + r + 1);
-          Fv[u] = make_double2(cvalid ? fcarry : f[fo + r], D.x);
-          fcarry = D.y;
-          cvalid = true;
-        } else {
-          Fv[u].x = (r < n) ? f[fo + r] : 0.0;
-          Fv[u].y = (r + 1 < n) ? f[fo + r + 1] : 0.0;
-          cvalid = false;
+          A[u] = __ldg(rec + 3 * q);
+          B[u] = __ldg(rec + 3 * q + 1);
+          C[u] = __ldg(rec + 3 * q + 2);
         }
       }
     }
+    if (!odd) {
+#pragma unroll
+      for (int u = 0; u < U2; ++u)
+        if (qb + u < q1) Fv[u] = ld_pair(2 * (qb + u));
+    } else {
+      double2 D[U2 + 1];
+#pragma unroll
+      for (int u = 0; u <= U2; ++u) D[u] = (qb + u <= q1) ? ld_pair(2 * (qb + u) - 1) : make_double2(0.0, 0.0);
+#pragma unroll
+      for (int u = 0; u < U2; ++u) Fv[u] = make_double2(D[u].y, D[u + 1].x);
+    }
   };
   double g1 = 0.0, g2 = 0.0;
-  load(q0, ca, cb, cf);
+  load(q0, ca, cb, cc, cf);
   for (int64_t qb = q0; qb < q1; qb += U2) {
-    if (qb + U2 < q1) load(qb + U2, na, nb, nf);
+    if (qb + U2 < q1) load(qb + U2, na, nb, nc, nf);
 #pragma unroll
     for (int u = 0; u < U2; ++u) {
       const int64_t q = qb + u;
       if (q < q1) {
-        const double ga = ca[u].x * fma(-cb[u].x, g1, fma(-sg, g2, cf[u].x));
-        const double gb = ca[u].y * fma(-cb[u].y, ga, fma(-sg, g1, cf[u].y));
+        const double ga = fma(-cb[u].x, g1, fma(-cc[u].x, g2, ca[u].x * cf[u].x));
+        const double gb = fma(-cb[u].y, ga, fma(-cc[u].y, g1, ca[u].y * cf[u].y));
         if (q >= k0) go[(q - q0) * kWarp] = make_double2(ga, gb);
         g2 = ga;
         g1 = gb;
@@ -1479,6 +1493,7 @@ __global__ void __launch_bounds__(128) k_swin64_fwd(DevPlan P, F64Factors F, con
     for (int u = 0; u < U2; ++u) {
       ca[u] = na[u];
       cb[u] = nb[u];
+      cc[u] = nc[u];
       cf[u] = nf[u];
     }
   }
@@ -1560,7 +1575,10 @@ __global__ void __launch_bounds__(128) k_swin64_bwd(DevPlan P, F64Factors F, con
 
 // Per-system copy of the records of the systems walked in system windows: warp (blockIdx.x,
 // blockIdx.y) copies pairs [64 y, 64 y + 64) of windowed group wg[x], one lane per system
-// (sbase[gl] < 0: none); sfwd[2 (base + q) + p] = fwd plane p of pair q, the same for bwd.
+// (sbase[gl] < 0: none).  Forward, in the form whose row step has one dependent operation,
+// g_i = (1/alpha_i) f_i - (beta_i / alpha_i) g_{i-1} - (sigma / alpha_i) g_{i-2}:
+// sfwd[3 (base + q) + p] = 1/alpha, beta/alpha, sigma/alpha of pair q (p = 0, 1, 2, each the
+// product of the record 1/alpha with beta or sigma); back, sbwd[2 (base + q) + p] = gamma, delta.
 constexpr int kSrecPairs = 64;
 __global__ void __launch_bounds__(32) k_srec64(DevPlan P, F64Factors F, const int32_t* __restrict__ wg,
                                                const int64_t* __restrict__ sbase, double2* __restrict__ sfwd,
@@ -1575,9 +1593,12 @@ __global__ void __launch_bounds__(32) k_srec64(DevPlan P, F64Factors F, const in
   const double2* __restrict__ bwd = reinterpret_cast<const double2*>(F.bwd);
   const int64_t P0 = L.R0 >> 1, np = (L.n + 1) >> 1;
   const int64_t qa = (int64_t)blockIdx.y * kSrecPairs, qe = min(qa + (int64_t)kSrecPairs, np);
+  const double sg = F.sig[L.s];
   for (int64_t q = qa; q < qe; ++q) {
-    sfwd[2 * (b + q)] = fwd[((P0 + q) * 2) * kWarp + lane];
-    sfwd[2 * (b + q) + 1] = fwd[((P0 + q) * 2 + 1) * kWarp + lane];
+    const double2 ia = fwd[((P0 + q) * 2) * kWarp + lane], be = fwd[((P0 + q) * 2 + 1) * kWarp + lane];
+    sfwd[3 * (b + q)] = ia;
+    sfwd[3 * (b + q) + 1] = make_double2(ia.x * be.x, ia.y * be.y);
+    sfwd[3 * (b + q) + 2] = make_double2(ia.x * sg, ia.y * sg);
     sbwd[2 * (b + q)] = bwd[((P0 + q) * 2) * kWarp + lane];
     sbwd[2 * (b + q) + 1] = bwd[((P0 + q) * 2 + 1) * kWarp + lane];
   }

@@ -75,7 +75,7 @@ struct pent_plan {
   // windowed walks of groups of long hyperdiffusion systems (csrc/core64.cu): windows of
   // win64_rows rows, one warp each, built at factor time from each group's overlap
   int win64_rows = 1024;          // PENT_OPT_WINDOW_ROWS (0: off)
-  int win64_omax = 0;             // overlap rows reserved per window side (window rows / 8)
+  int win64_omax = 0;             // largest overlap a window takes (window rows / 8; / 4 for system windows)
   int64_t win64_cap = 0;          // windows the workspace holds
   int64_t nwin64 = 0;             // windows of the current factorisation (0: none)
   bool persistent = false;        // PENT_OPT_PERSISTENT: window launches as resident grids
@@ -573,6 +573,8 @@ void layout(pent_plan* p) {
     // system windows: room for every system of a group longer than one window
     p->swin_cap = p->srec_pairs = p->srec_maxpairs = 0;
     if (p->win64_cap > 0 && p->win64_form == 1) {
+      // a system window keeps its rows at least O from each cut: room for O up to a quarter of it
+      p->win64_omax = p->win64_rows / 4;
       const int Rp = p->win64_rows / 2;
       for (int64_t k = 0; k < p->ngroups; ++k) {
         if (p->glen[k] <= p->win64_rows) continue;
@@ -596,7 +598,7 @@ void layout(pent_plan* p) {
     take(p->r_lover, (size_t)(p->swin_cap > 0 ? p->ngroups * kWarp : 0) * sizeof(int32_t));
     take(p->r_sbase, (size_t)(p->swin_cap > 0 ? p->ngroups * kWarp : 0) * sizeof(int64_t));
     take(p->r_swg, (size_t)(p->swin_cap > 0 ? p->ngroups : 0) * sizeof(int32_t));
-    take(p->r_sfwd, (size_t)p->srec_pairs * 2 * sizeof(double2));
+    take(p->r_sfwd, (size_t)p->srec_pairs * 3 * sizeof(double2));
     take(p->r_sbwd, (size_t)p->srec_pairs * 2 * sizeof(double2));
     take(p->r_swin, (size_t)p->swin_cap * sizeof(int4));
     take(p->r_sgs, (size_t)((p->swin_cap + kWarp - 1) / kWarp) * kWarp * (p->win64_rows / 2) * sizeof(double2));

@@ -334,7 +334,7 @@ def test_fp64_interior_option_host_checks(L):
 def test_window_form_option_host_checks(L):
     """PENT_OPT_WINDOW_FORM: FP64 plans, before binding, 0 (group windows) or 1 (system windows,
     the default); system windows reserve a per-system copy of the windowed systems' records
-    (64 bytes a row pair) in place of the group windows' side scratch and overlap rows."""
+    (80 bytes a row pair) in place of the group windows' side scratch and overlap rows."""
     st, h = _create(L, batch=64, n=[5000] * 32 + [300] * 32)
     assert st == 0
     v = ctypes.c_int64(-1)
@@ -344,7 +344,7 @@ def test_window_form_option_host_checks(L):
     assert L.pent_plan_get_option(h, _lib.PENT_OPT_WINDOW_FORM, ctypes.byref(v)) == 0 and v.value == 0
     ws0 = L.pent_plan_workspace_bytes(h)
     group_room = len(pb.window_layout(5000, 1024, 128)) * 64 * 32 * 48  # side + halo of the group windows
-    assert ws1 - ws0 >= 32 * 2500 * 64 - group_room
+    assert ws1 - ws0 >= 32 * 2500 * 80 - group_room
     for bad in (2, -1):
         assert L.pent_plan_set_option(h, _lib.PENT_OPT_WINDOW_FORM, bad) == _lib.PENT_EINVAL
     L.pent_plan_destroy(h)
