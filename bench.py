@@ -528,7 +528,7 @@ def measure_uneven(pb, dev, stream, fp64, sms, steps=200):
     tune = os.path.join(ROOT, "paper_1807_07382_gb300", "tune_gb300.txt")
     peak, peak_kind = measured_peaks()
     out = {}
-    for prec, pname, alg, kern in ((pb.PENT_F64, "f64", 56, "k_solve64w (windows of 1024 rows) + k_solve64_pair"),
+    for prec, pname, alg, kern in ((pb.PENT_F64, "f64", 56, "k_swin64_fwd + k_swin64_bwd (system windows of 1024 rows) + k_solve64_pair"),
                                    (pb.PENT_F32_REFINE, "f32_refine", 36,
                                     "k_solve32u (windows of 1024 rows, single CTAs)")):
         plan = pb.Plan(list(w.n), precision=prec, stream=stream, device=dev, tune_cache=tune)
@@ -856,7 +856,8 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-PROFILE_CASES = ("fp32_steps", "fp64_solve", "fp32_windows", "fp64_windows", "uneven_fp32", "uneven_fp64",
+PROFILE_CASES = ("fp32_steps", "fp64_solve", "fp32_windows", "fp64_windows", "fp64_group_windows", "uneven_fp32",
+                 "uneven_fp64", "uneven_fp64_group_windows",
                  "adi_step")
 
 
@@ -866,7 +867,9 @@ def run_profile_case(name):
     (k_solve32u with float pairs in and out in the middle steps); fp64_solve: 32,768 x 1024 FP64,
     two solves (k_solve64_pair); fp32_windows: 2,000 x 8,192 FP32+refine, two out-of-place
     solves (k_solve32u windows); fp64_windows: 4,096 x 8,192 FP64, two in-place solves
-    (k_win64_halo, k_solve64w); uneven_fp32 / uneven_fp64: the uneven batch (20,000 systems),
+    (k_srec64 once, then k_swin64_fwd, k_swin64_bwd; fp64_group_windows: the same with group
+    windows, k_win64_halo, k_solve64w); uneven_fp32 / uneven_fp64 (/ uneven_fp64_group_windows): the
+    uneven batch (20,000 systems),
     factor and two 2-step graphs (the launch list of its steps); adi_step: the 2048^2 ADI workload,
     factor and one step (every kernel of the step once)."""
     import torch
@@ -890,7 +893,8 @@ def run_profile_case(name):
                                        seed_index=3, sigma_range=(1e-2, 10.0))
     else:
         w = synth.hyperdiff_parametric(batch=16384 if prec == pb.PENT_F32_REFINE else 32768, n=1024, steps=1)
-    plan = pb.Plan(list(w.n), precision=prec, stream=stream, device=dev, tune_cache=tune)
+    opts = {pb.PENT_OPT_WINDOW_FORM: 0} if name.endswith("group_windows") else {}
+    plan = pb.Plan(list(w.n), precision=prec, stream=stream, device=dev, tune_cache=tune, options=opts)
     plan.factor_hyperdiff(torch.from_numpy(w.sigma).to(dev))
     x = torch.from_numpy(w.field0).to(dev)
     if name == "fp32_steps":

@@ -1754,6 +1754,12 @@ cudaError_t launch_srec64(const DevPlan& P, F64Factors F, const int32_t* wg, int
   return cudaGetLastError();
 }
 
+// Row pairs the back walks of system windows load ahead when the forward walks load 2 (unroll 4;
+// 0: the same): 3, on GB300 the uneven FP64 step took 0.915 ms against 0.930 with 2 and 0.965
+// with 4 (the back walk waits on its loads of g and the records more than the forward one).
+#ifndef PENT_SWIN_BWD_U2
+#define PENT_SWIN_BWD_U2 3
+#endif
 cudaError_t launch_swin64(const DevPlan& P, F64Factors F, const int4* win, int64_t nwin, int window_rows, int unroll,
                           int block_warps, const double2* sfwd, const double2* sbwd, const int64_t* sbase,
                           const double* f, double* x, double2* gs, cudaStream_t st) {
@@ -1770,6 +1776,11 @@ cudaError_t launch_swin64(const DevPlan& P, F64Factors F, const int4* win, int64
     bk<<<grid, block, 0, st>>>(P, F, win, nwin, Rp, sbwd, sbase, gs, x);
     return cudaGetLastError();
   };
+#if PENT_SWIN_BWD_U2 == 4
+  if (unroll == 4) return go(k_swin64_fwd<2>, k_swin64_bwd<4>);
+#elif PENT_SWIN_BWD_U2 == 3
+  if (unroll == 4) return go(k_swin64_fwd<2>, k_swin64_bwd<3>);
+#endif
   if (unroll == 8) return go(k_swin64_fwd<4>, k_swin64_bwd<4>);
   if (unroll == 4) return go(k_swin64_fwd<2>, k_swin64_bwd<2>);
   if (unroll == 2) return go(k_swin64_fwd<1>, k_swin64_bwd<1>);
