@@ -1574,8 +1574,8 @@ __global__ void __launch_bounds__(128) k_swin64_bwd(DevPlan P, F64Factors F, con
 }
 
 // Per-system copy of the records of the systems walked in system windows: warp (blockIdx.x,
-// blockIdx.y) copies pairs [64 y, 64 y + 64) of windowed group wg[x], one lane per system
-// (sbase[gl] < 0: none).  Forward, in the form whose row step has one dependent operation,
+// blockIdx.y) copies pairs [64 y, 64 y + 64) of windowed group wg[x] (and every gridDim.y * 64
+// pairs after them), one lane per system (sbase[gl] < 0: none).  Forward, in the form whose row step has one dependent operation,
 // g_i = (1/alpha_i) f_i - (beta_i / alpha_i) g_{i-1} - (sigma / alpha_i) g_{i-2}:
 // sfwd[3 (base + q) + p] = 1/alpha, beta/alpha, sigma/alpha of pair q (p = 0, 1, 2, each the
 // product of the record 1/alpha with beta or sigma); back, sbwd[2 (base + q) + p] = gamma, delta.
@@ -1592,15 +1592,17 @@ __global__ void __launch_bounds__(32) k_srec64(DevPlan P, F64Factors F, const in
   const double2* __restrict__ fwd = reinterpret_cast<const double2*>(F.fwd);
   const double2* __restrict__ bwd = reinterpret_cast<const double2*>(F.bwd);
   const int64_t P0 = L.R0 >> 1, np = (L.n + 1) >> 1;
-  const int64_t qa = (int64_t)blockIdx.y * kSrecPairs, qe = min(qa + (int64_t)kSrecPairs, np);
   const double sg = F.sig[L.s];
-  for (int64_t q = qa; q < qe; ++q) {
-    const double2 ia = fwd[((P0 + q) * 2) * kWarp + lane], be = fwd[((P0 + q) * 2 + 1) * kWarp + lane];
-    sfwd[3 * (b + q)] = ia;
-    sfwd[3 * (b + q) + 1] = make_double2(ia.x * be.x, ia.y * be.y);
-    sfwd[3 * (b + q) + 2] = make_double2(ia.x * sg, ia.y * sg);
-    sbwd[2 * (b + q)] = bwd[((P0 + q) * 2) * kWarp + lane];
-    sbwd[2 * (b + q) + 1] = bwd[((P0 + q) * 2 + 1) * kWarp + lane];
+  for (int64_t qa = (int64_t)blockIdx.y * kSrecPairs; qa < np; qa += (int64_t)gridDim.y * kSrecPairs) {
+    const int64_t qe = min(qa + (int64_t)kSrecPairs, np);
+    for (int64_t q = qa; q < qe; ++q) {
+      const double2 ia = fwd[((P0 + q) * 2) * kWarp + lane], be = fwd[((P0 + q) * 2 + 1) * kWarp + lane];
+      sfwd[3 * (b + q)] = ia;
+      sfwd[3 * (b + q) + 1] = make_double2(ia.x * be.x, ia.y * be.y);
+      sfwd[3 * (b + q) + 2] = make_double2(ia.x * sg, ia.y * sg);
+      sbwd[2 * (b + q)] = bwd[((P0 + q) * 2) * kWarp + lane];
+      sbwd[2 * (b + q) + 1] = bwd[((P0 + q) * 2 + 1) * kWarp + lane];
+    }
   }
 }
 
@@ -1748,8 +1750,8 @@ cudaError_t launch_srec64(const DevPlan& P, F64Factors F, const int32_t* wg, int
                           const int64_t* sbase, double2* sfwd, double2* sbwd, cudaStream_t st) {
   if (nwg == 0) return cudaSuccess;
   if (P.shared || !F.sig || max_pairs <= 0) return cudaErrorInvalidValue;
-  const int64_t ny = (max_pairs + kSrecPairs - 1) / kSrecPairs;
-  if (nwg > INT_MAX || ny > 65535) return cudaErrorInvalidValue;
+  const int64_t ny = std::min<int64_t>((max_pairs + kSrecPairs - 1) / kSrecPairs, 65535);  // the CTAs loop beyond
+  if (nwg > INT_MAX) return cudaErrorInvalidValue;
   k_srec64<<<dim3((unsigned)nwg, (unsigned)ny), kWarp, 0, st>>>(P, F, wg, sbase, sfwd, sbwd);
   return cudaGetLastError();
 }

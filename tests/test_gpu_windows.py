@@ -391,7 +391,7 @@ def test_f64_refactorisations_drop_stale_windows_and_interior_records():
     assert sys_rel_err(host(xs), oracle.hyperdiff_steps(ns, sig2, f, 2), ns) <= 2 * TOL
 
 
-@pytest.mark.parametrize("case", ["uniform", "uneven", "odd", "steps", "short_lanes"])
+@pytest.mark.parametrize("case", ["uniform", "uneven", "odd", "steps", "short_lanes", "tiny_lanes"])
 def test_f64_system_windows_against_group_windows_and_the_oracle(case):
     """System windows (PENT_OPT_WINDOW_FORM 1): each system of a windowed group cut at its own
     rows with its own overlap, the windows in the caller's row order.  Against the oracle at
@@ -399,7 +399,8 @@ def test_f64_system_windows_against_group_windows_and_the_oracle(case):
     walk; in place bitwise the out-of-place result.  Cases: equal lengths; log-uniform lengths
     8 .. 16,384 (groups of both kinds); odd lengths (half the systems start at odd rows);
     in-place steps in one graph; groups whose shortest systems fit one window (a window of
-    fewer rows than the others in the same warp)."""
+    fewer rows than the others in the same warp); a group whose last lanes hold systems of 1, 2,
+    3 and 5 rows (one row pair or a few, no interior rows)."""
     if case == "uniform":
         ns = np.full(40, 8192)
     elif case == "uneven":
@@ -408,8 +409,10 @@ def test_f64_system_windows_against_group_windows_and_the_oracle(case):
         ns = np.array([3001, 4097, 2049, 5001, 1025, 7777, 1023, 999] * 5)
     elif case == "steps":
         ns = np.floor(synth.log_uniform(95, 0, 120, 1000.0, 9000.0)).astype(np.int64)
-    else:
+    elif case == "short_lanes":
         ns = np.array([1100] * 20 + [1000] * 12 + [700] * 10)
+    else:
+        ns = np.array([3000] * 28 + [1, 2, 3, 5])
     sig = synth.log_uniform(96, 0, len(ns), 1e-2, 10.0)
     f = synth.uniform(97, 0, int(ns.sum()), -1, 1)
     steps = 3 if case == "steps" else 1
