@@ -256,6 +256,21 @@ pent_status pent_plan_get_option(const pent_plan* plan, int key, int64_t* value)
 int64_t pent_window_layout(int64_t n, int window_rows, int overlap, int32_t* h_out4, int64_t cap);
 
 /*
+ * Host only: the FP64 system windows (PENT_OPT_WINDOW_FORM 1) of an n-row system, windows of
+ * `window_rows` rows with `overlap` rows of overlap (window_rows and overlap even, 0 < 4 overlap
+ * <= window_rows; overlap 0 is allowed when n <= window_rows), in row pairs as the walks take
+ * them.  A system of at most window_rows rows is one window; otherwise the first window covers
+ * rows [0, window_rows) and keeps [0, window_rows - overlap), each next one starts `overlap` rows
+ * before the first row not yet kept and keeps window_rows - 2 overlap rows, and the last covers
+ * the window_rows rows (rounded up to a whole row pair) that end the system and keeps the rest,
+ * so every window walks the same rows and the kept rows tile [0, n) once.  Writes, while `cap`
+ * lasts, three int32 per window into h_out3 (host memory, may be NULL): the first row walked,
+ * and the first and the end of the kept rows (absolute; the end clipped to n); returns the
+ * number of windows, 0 for n <= 0 or sizes that do not qualify.
+ */
+int64_t pent_system_window_layout(int64_t n, int window_rows, int overlap, int32_t* h_out3, int64_t cap);
+
+/*
  * The settings that solve system `system` (0 <= system < batch), as chosen by
  * options, the tune cache or the built-in rules: for PENT_F32_REFINE
  * *a = rows per thread and *b = threads per system; for PENT_F64 *a = unroll

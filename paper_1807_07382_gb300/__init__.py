@@ -24,7 +24,7 @@ from ._lib import (PENT_ENOCONV, PENT_ESINGULAR, PENT_F32_REFINE, PENT_F64, PENT
                    PENT_RESIDUAL_FF, PentError, check)
 
 __all__ = ["Plan", "PentError", "PENT_F64", "PENT_F32_REFINE", "PENT_RESIDUAL_FF", "PENT_RESIDUAL_F64",
-           "library_path", "load_library", "window_layout", "adi_plans_factor", "adi_step_2d", "adi_steps_2d", "ADI2D"]
+           "library_path", "load_library", "window_layout", "system_window_layout", "adi_plans_factor", "adi_step_2d", "adi_steps_2d", "ADI2D"]
 
 __version__ = "0.1.0"
 
@@ -276,6 +276,18 @@ def window_layout(n: int, window_rows: int, overlap: int):
     out = np.zeros((max(cnt, 0), 4), dtype=np.int32)
     if cnt > 0:
         L.pent_window_layout(int(n), int(window_rows), int(overlap), out.ctypes.data_as(ctypes.c_void_p), cnt)
+    return out
+
+
+def system_window_layout(n: int, window_rows: int, overlap: int):
+    """The FP64 system windows of an n-row system (pent_system_window_layout): an int32 array of
+    rows (first row walked, first kept, end kept), one window for n <= window_rows."""
+    import numpy as np
+    L = _lib.load()
+    cnt = int(L.pent_system_window_layout(int(n), int(window_rows), int(overlap), None, 0))
+    out = np.zeros((max(cnt, 0), 3), dtype=np.int32)
+    if cnt > 0:
+        L.pent_system_window_layout(int(n), int(window_rows), int(overlap), out.ctypes.data_as(ctypes.c_void_p), cnt)
     return out
 
 

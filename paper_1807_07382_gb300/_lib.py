@@ -75,6 +75,7 @@ SIGNATURES = {
     "pent_gbsv_batch_noalloc": (_int, [_i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "pent_probe_fp64_fma": (_int, [_i64, _i64, _vp, _vp, ctypes.POINTER(_dbl)]),
     "pent_window_layout": (_i64, [_i64, _int, _int, _vp, _i64]),
+    "pent_system_window_layout": (_i64, [_i64, _int, _int, _vp, _i64]),
     "pent_plan_destroy": (None, [_vp]),
     "pent_status_string": (ctypes.c_char_p, [_int]),
     "pent_version": (ctypes.c_char_p, []),

@@ -761,6 +761,18 @@ int64_t pent_window_layout(int64_t n, int window_rows, int overlap, int32_t* h_o
   return window_layout(n, window_rows, overlap, h_out4, cap < 0 ? 0 : cap);
 }
 
+int64_t pent_system_window_layout(int64_t n, int window_rows, int overlap, int32_t* h_out3, int64_t cap) {
+  if (n <= 0 || window_rows <= 0 || window_rows % 2 || overlap < 0 || overlap % 2) return 0;
+  const int64_t np = (n + 1) / 2;
+  const int64_t cnt = swin_layout(np, window_rows / 2, overlap / 2, h_out3, cap < 0 ? 0 : cap);
+  for (int64_t i = 0; h_out3 && i < std::min(cnt, cap); ++i) {
+    h_out3[3 * i] *= 2;
+    h_out3[3 * i + 1] *= 2;
+    h_out3[3 * i + 2] = (int32_t)std::min<int64_t>(2 * (int64_t)h_out3[3 * i + 2], n);
+  }
+  return cnt;
+}
+
 pent_status pent_plan_bind(pent_plan* p, void* ws, void* stream) {
   if (!p || !ws) return PENT_EINVAL;
   if (((uintptr_t)ws) % kAlign) return PENT_EINVAL;

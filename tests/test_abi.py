@@ -351,3 +351,28 @@ def test_window_form_option_host_checks(L):
     st, h = _create(L, batch=8, n_uniform=5000, prec=1)
     assert L.pent_plan_set_option(h, _lib.PENT_OPT_WINDOW_FORM, 0) == _lib.PENT_EINVAL
     L.pent_plan_destroy(h)
+
+
+@pytest.mark.parametrize("R", [256, 1024, 2048])
+def test_system_window_layout_tiles_every_length(L, R):
+    """pent_system_window_layout (FP64 system windows): the kept rows tile [0, n) once, every
+    window of a system walks the same min(R, n rounded up to a pair) rows starting at an even row,
+    and every kept row is at least O from each cut (a cut is a window edge inside the system)."""
+    for O in (8, 16, R // 8, R // 4):
+        for n in list(range(1, 3 * R + 3, 7)) + [R - 1, R, R + 1, R + 2, 2 * R - 2 * O, 2 * R - 2 * O + 1, 40001]:
+            w = pb.system_window_layout(n, R, O)
+            assert len(w) >= 1
+            walk = min(R, 2 * ((n + 1) // 2))
+            cur = 0
+            for r0, k0, k1 in w:
+                assert r0 % 2 == 0 and r0 <= k0 < k1 <= n and k0 == cur
+                assert r0 + walk <= 2 * ((n + 1) // 2)
+                assert r0 == 0 or k0 - r0 >= O
+                assert r0 + walk >= n or r0 + walk - k1 >= O
+                cur = k1
+            assert cur == n
+            if n <= R:
+                assert w.tolist() == [[0, 0, n]]
+    assert len(pb.system_window_layout(3000, R, R // 4 + 2)) == 0  # more overlap than a quarter window
+    assert len(pb.system_window_layout(3000, R, 7)) == 0             # odd overlap
+    assert len(pb.system_window_layout(0, R, 8)) == 0
