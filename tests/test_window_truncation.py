@@ -8,7 +8,8 @@ multiple of 8 rows at which both 8-row interior chunk maps (forward on (g_{i-2},
 (x_{i+1}, x_{i+2})) have every entry at most 2^-56.  The rows kept must equal the whole system's
 solution to FP64 rounding, for every sigma that windows are used for; the kernels compute O the
 same way (in FP64, from the interior factors), and their own tests hold the windowed GPU solves
-to the oracle."""
+to the oracle.  The last test pins the form of the forward step that the FP64 system windows
+take (the coefficients beta/alpha and sigma/alpha formed once) against the oracle's solve."""
 import numpy as np
 import pytest
 
@@ -101,3 +102,33 @@ def test_overlap_grows_with_sigma():
     assert Os[:4] == sorted(Os[:4])
     assert Os[0] <= 24 and 80 <= Os[3] <= 104
     assert Os[4] is None or Os[4] > 128
+
+
+@pytest.mark.parametrize("sigma", [1e-3, 0.1, 1.0, 10.0, 30.0])
+def test_forward_step_with_its_coefficients_formed_once(sigma):
+    """The FP64 system windows' forward step, g_i = (1/alpha_i) f_i - (beta_i/alpha_i) g_{i-1}
+    - (sigma/alpha_i) g_{i-2}, with beta_i/alpha_i and sigma/alpha_i formed once per row as
+    products with the stored 1/alpha_i, followed by the back substitution, agrees with the oracle's
+    solve (Sec. 2.4's division form) to FP64 rounding; and the hyperdiffusion band's epsilon_i
+    (= a_i) is exactly sigma on every row from 2 on, which every hyperdiffusion walk takes instead
+    of a stored epsilon."""
+    n = 3001
+    fac, bad = oracle.factor(oracle.band_hyperdiff(n, sigma))
+    assert bad == -1
+    al, be, ga, de, ep = fac
+    assert np.all(ep[2:] == sigma)
+    f = synth.uniform(502, 0, n, -1.0, 1.0)
+    ia = 1.0 / al
+    iab, ias = ia * be, ia * sigma
+    g = np.zeros(n)
+    g1 = g2 = 0.0
+    for i in range(n):
+        g[i] = ia[i] * f[i] - ias[i] * g2 - iab[i] * g1
+        g2, g1 = g1, g[i]
+    x = np.zeros(n)
+    x1 = x2 = 0.0
+    for i in range(n - 1, -1, -1):
+        x[i] = g[i] - ga[i] * x1 - de[i] * x2
+        x2, x1 = x1, x[i]
+    ref = oracle.solve(fac, f)
+    assert np.max(np.abs(x - ref)) <= 1e-14 * np.max(np.abs(ref))
